@@ -1,0 +1,282 @@
+/*
+ * revo.h -- C ABI of the B300 (sm_103a) neural loss-recovery library.
+ *
+ * The library recovers the lost pixels of decoded RGB (uint8) and depth
+ * (uint16 mm) video frames, the post-decode recovery step of ReVo's receiver
+ * (Section 3.4, "Neural Loss Recovery Module"): a ViViT encoder-decoder reads
+ * the k closest clean frames and the corrupted current frame and outputs a
+ * reconstructed frame (Section 3.4.1); RGB and depth use separate models of the
+ * same architecture (Section 3.4.2) and run on independent CUDA streams
+ * (Section 3.1, Challenge 2).  Intact and corrupted pixels are fed alike
+ * (Appendix B.1, point 3); tokens are tubelets of T frames x p x p pixels
+ * (Appendix B.3).  The per-pixel loss mask does not enter the network: it
+ * selects, per pixel, the decoded value (received) or the recovered value
+ * (lost), so received pixels pass through bit for bit.
+ *
+ * Conventions for every call:
+ *  - Nothing throws across this boundary; every call returns a revo_status.
+ *  - Pointers are plain host or device pointers as each argument states.
+ *  - Frames: RGB uint8 interleaved [H][W][3] with a row pitch in bytes; depth
+ *    uint16 millimetres [H][W] with a row pitch in bytes, 0 = no depth.
+ *  - Loss mask: 1 bit per pixel, 1 = lost, row-major, bit (x % 32) of 32-bit
+ *    word (x / 32), with a row pitch in words (at least ceil(W / 32)).
+ *  - H and W must be multiples of the patch size p.
+ *  - A revo_ctx is used by one host thread at a time.
+ */
+#ifndef REVO_H
+#define REVO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  REVO_OK = 0,
+  REVO_EAGAIN = 1,      /* not finished yet, or no capacity right now          */
+  REVO_EINVAL = -1,     /* bad argument: null pointer, bad size, bad shape      */
+  REVO_ENOMEM = -2,     /* device memory or the HBM budget cannot hold it       */
+  REVO_ETIMEDOUT = -3,  /* poll timed out, or a device-side wait gave up        */
+  REVO_ENOREF = -4,     /* the stream holds fewer than k clean reference frames */
+  REVO_ECUDA = -5,      /* a CUDA call failed (the message is in revo_last_error) */
+  REVO_ENOTSUP = -6     /* the device or the configuration is not supported     */
+} revo_status;
+
+typedef enum { REVO_FP32 = 0, REVO_BF16 = 1, REVO_FP8 = 2 } revo_precision;
+
+/* Request flags. */
+#define REVO_RGB 1u     /* the request carries an RGB plane                   */
+#define REVO_DEPTH 2u   /* the request carries a depth plane                  */
+#define REVO_CLEAN 4u   /* intact frame: push it into the stream's reference
+                           history and run nothing (Section 3.1.1 forwards intact
+                           frames directly; the paper reuses clean references
+                           across a GoP, Section 3.4.1)                         */
+
+/*
+ * Network shape and runtime limits.  revo_config_default() fills the ViT-B
+ * reading: k = 5 references, tubelet T = 2, patch p = 16, encoder 768 wide x 12
+ * blocks x 12 heads, decoder 384 wide x 4 blocks x 6 heads, MLP ratio 4.
+ * Requirements: (k + 1) % T == 0, k <= 7; head width (dim / heads) == 64;
+ * dims multiples of 64; p == 16.
+ *
+ * Weights are flat little-endian float32 arrays in this order (Linear weights
+ * [out][in]; the tubelet embedding is a Linear over a tubelet flattened as
+ * (t, c, y, x); the head's outputs are ordered (t, c, y, x) too):
+ *   patch_embed.w [D][T*C*p*p], patch_embed.b [D],
+ *   per encoder block: ln1.g [D], ln1.b [D], qkv.w [3D][D], qkv.b [3D],
+ *     proj.w [D][D], proj.b [D], ln2.g [D], ln2.b [D], fc1.w [rD][D],
+ *     fc1.b [rD], fc2.w [D][rD], fc2.b [D]   (qkv rows: q | k | v),
+ *   enc_norm.g [D], enc_norm.b [D], enc2dec.w [D'][D], enc2dec.b [D'],
+ *   per decoder block: the same at width D',
+ *   dec_norm.g [D'], dec_norm.b [D'], head.w [T*C*p*p][D'], head.b [T*C*p*p].
+ * The weights are copied at create; the caller keeps ownership of its arrays.
+ */
+typedef struct {
+  int k, tubelet, patch;
+  int enc_dim, enc_depth, enc_heads;
+  int dec_dim, dec_depth, dec_heads;
+  int mlp_ratio;
+  revo_precision precision;
+  int device;                    /* CUDA device ordinal                         */
+  size_t hbm_budget_bytes;       /* cap on the context's device memory; 0 = 40 GB */
+  int max_streams;               /* conference streams with a reference history */
+  int max_height, max_width;     /* largest frame any stream will submit        */
+  int max_batch;                 /* requests fused into one launch (>= 1)        */
+  int lanes;                     /* batches in flight at once (>= 1)             */
+  void* cuda_stream;             /* cudaStream_t for the work, NULL = own streams */
+  int use_graphs;                /* 1 = replay captured CUDA graphs per batch shape */
+  const float* rgb_weights;      /* host, flat float32, NULL = no RGB model      */
+  size_t rgb_weights_count;
+  const float* depth_weights;    /* host, flat float32, NULL = no depth model    */
+  size_t depth_weights_count;
+} revo_config;
+
+typedef struct revo_ctx revo_ctx;
+
+/* One image plane: RGB uint8 [H][W][3] or depth uint16 [H][W]. */
+typedef struct {
+  const void* data;
+  int height, width;
+  size_t pitch_bytes;
+} revo_plane;
+
+/*
+ * One frame of one conference stream (the problem statement of Section 3.4.1:
+ * frame, loss mask and reference frames in, recovered frame out).
+ *  - stream_id < max_streams; frame_index increases along the stream.  The
+ *    temporal distances the network embeds are frame_index minus the indices
+ *    of the stream's clean references.
+ *  - flags: REVO_RGB and/or REVO_DEPTH, plus REVO_CLEAN for an intact frame.
+ *  - inputs_on_device: 1 = data/mask pointers are device pointers and must stay
+ *    valid until the request completes; 0 = host pointers, copied during submit.
+ *  - outputs: rgb_out (uint8 [H][W][3], pitch rgb_out_pitch) and depth_out
+ *    (uint16 [H][W], pitch depth_out_pitch) receive the blended frame; the
+ *    optional *_values (float32 [H][W][3] in [0,1] units / float32 [H][W] in mm,
+ *    dense) receive the de-normalised network output at every pixel before the
+ *    blend.  outputs_on_device says whether these are device or host pointers;
+ *    they are borrowed until poll returns REVO_OK for the ticket.
+ */
+typedef struct {
+  uint32_t stream_id;
+  int64_t frame_index;
+  uint32_t flags;
+  int inputs_on_device;
+  revo_plane rgb;
+  const uint32_t* rgb_lost_mask;
+  size_t rgb_mask_pitch_words;
+  revo_plane depth;
+  const uint32_t* depth_lost_mask;
+  size_t depth_mask_pitch_words;
+  int outputs_on_device;
+  void* rgb_out;
+  size_t rgb_out_pitch;
+  void* depth_out;
+  size_t depth_out_pitch;
+  float* rgb_values;
+  float* depth_values;
+} revo_request;
+
+typedef struct {
+  revo_status status;
+  uint32_t stream_id;
+  int64_t frame_index;
+  double latency_ms;   /* host clock, submit -> completion observed            */
+  double device_ms;    /* CUDA-event time of the batch that carried the request */
+  int batch_size;      /* requests in that batch                                */
+} revo_result;
+
+/* Fills *cfg with the ViT-B reading above and precision BF16. */
+void revo_config_default(revo_config* cfg);
+
+/*
+ * Creates a context on cfg->device: uploads both models' weights (float32
+ * master copies and the precision's tensor-core copies), allocates the
+ * reference histories and the work arenas within hbm_budget_bytes.
+ * Errors: REVO_EINVAL (shape rules above, weight count mismatch, null out),
+ * REVO_ENOTSUP (the tensor-core path needs an sm_100-class device),
+ * REVO_ENOMEM (budget or device memory), REVO_ECUDA.  On error *out is NULL.
+ */
+revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out);
+
+/*
+ * Submits one request and returns a ticket.  REVO_CLEAN requests are queued on
+ * the device at once (the frame enters the stream's history).  Other requests
+ * join the pending batch; a batch is launched when max_batch requests are
+ * pending, when a lane is free and requests are waiting, or on poll/flush.
+ * Host inputs are copied before return.
+ * Errors: REVO_EINVAL (bad ids, flags, shapes, pointers), REVO_ENOREF (fewer
+ * than k clean frames in the stream's history for a requested modality),
+ * REVO_EAGAIN (pending queue full: poll and retry), REVO_ECUDA.
+ */
+revo_status revo_recover_submit(revo_ctx* ctx, const revo_request* req, uint64_t* ticket);
+
+/* Launches every pending request now (in batches of at most max_batch). */
+revo_status revo_recover_flush(revo_ctx* ctx);
+
+/*
+ * Waits up to timeout_us microseconds (0 = do not wait, < 0 = forever) for a
+ * ticket.  REVO_OK: finished, *out filled, outputs written, the ticket is
+ * retired.  REVO_EAGAIN: still running (timeout 0).  REVO_ETIMEDOUT: the wait
+ * ran out.  REVO_EINVAL: unknown ticket.  A device-side failure of the batch is
+ * reported in out->status.
+ */
+revo_status revo_recover_poll(revo_ctx* ctx, uint64_t ticket, int64_t timeout_us, revo_result* out);
+
+/* Drains the work in flight, then frees everything the context owns. */
+void revo_recover_destroy(revo_ctx* ctx);
+
+/* The last error message of the calling thread ("" if none). */
+const char* revo_last_error(void);
+
+/* ------------------------------------------------------------------------ *
+ * Step-level entry points.  Each runs one stage of the recovery forward on
+ * caller-owned device buffers, on the given stream (cudaStream_t, NULL = the
+ * default stream), asynchronously.  They exist so that each stage can be
+ * checked on its own; the context above chains the same kernels.  All return
+ * REVO_EINVAL for null pointers or sizes outside the stated limits and
+ * REVO_ECUDA if the launch fails.  Row-major everywhere.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Tubelet assembly (Appendix B.3) fused with input normalisation: for one
+ * request, writes the token matrix A [S*Hp*Wp][T*C*p*p] (token order slot,
+ * patch row, patch column; vector order t, c, y, x) from the k reference
+ * frames (host array `refs` of k device pointers, oldest first) and the
+ * decoded current frame, all in the plane format above with one pitch.  RGB
+ * (C = 3): (x/255 - mean_c)/std_c with the ImageNet statistics.  Depth (C = 1):
+ * (d - mu)/sigma with mu_sigma[2] a device float pair.  out_bf16 != 0 writes
+ * bf16, else float32.  k <= 7, p <= 16.
+ */
+revo_status revo_op_assemble(int channels, int k, int T, int p, int height, int width,
+                             const void* const* refs, const void* current, size_t pitch_bytes,
+                             const float* mu_sigma, void* out, int out_bf16, void* stream);
+
+/*
+ * Depth statistics of one uint16 frame: mean and biased standard deviation of
+ * the non-zero pixels, written as float32 to mu_sigma[0..1] (device).  No valid
+ * pixel gives (0, 1); the deviation is floored at 1 mm.  scratch is a device
+ * buffer of revo_depth_stats_scratch_bytes() bytes that only one call at a time
+ * may use.
+ */
+size_t revo_depth_stats_scratch_bytes(void);
+revo_status revo_op_depth_stats(const uint16_t* depth, int height, int width, size_t pitch_bytes,
+                                float* mu_sigma, void* scratch, void* stream);
+
+/*
+ * Y = epilogue(A W^T + b) with A [M][K], W [N][K] (Linear [out][in]), b [N]
+ * (b may be NULL).
+ *   precision REVO_FP32: A, W float32, SIMT FMA (K % 8 == 0).  REVO_BF16: A, W
+ *   bf16 on the tcgen05 tensor cores with float32 accumulation (K % 64 == 0,
+ *   N % 32 == 0); `tile_n` picks the 128- or 256-column tile (0 = automatic).
+ *   epilogue 0: out = acc + b (float32 out)
+ *   epilogue 1: out = acc + b (bf16 out; FP32 precision writes float32)
+ *   epilogue 2: out = gelu(acc + b) (bf16 out; FP32 precision writes float32)
+ *   epilogue 3: out += acc + b (float32 residual, in place)
+ */
+revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A, const void* W,
+                           const float* bias, void* out, int M, int N, int K, int tile_n, void* stream);
+
+/* Row-wise LayerNorm, eps 1e-6: x float32 [M][D] -> out (bf16 if out_bf16, else float32). */
+revo_status revo_op_layernorm(const float* x, const float* gamma, const float* beta, void* out,
+                              int M, int D, int out_bf16, void* stream);
+
+/*
+ * Multi-head softmax attention over segments of tokens (the exact scaled
+ * dot-product attention of Appendix B.1, point 4).  qkv is [M][3D] (q | k | v,
+ * head h owns columns h*64 .. h*64+63 of each part); seg_start[n_seg + 1] is a
+ * host array of segment boundaries in [0, M]; tokens attend only within their
+ * segment.  out [M][D].  REVO_FP32: float32 in and out.  REVO_BF16: qkv and out
+ * bf16, tcgen05 tensor cores, float32 softmax.  n_seg <= 64.
+ */
+revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D,
+                              int heads, const int* seg_start, int n_seg, void* stream);
+
+/*
+ * x[(s*Hp + r)*Wp + c][:] += the sinusoidal embedding of (taus[s], r, c), each
+ * part D/3 wide, half sines half cosines at frequencies 10000^(-2i/(D/3))
+ * (Section 3.4.1: the embedding encodes the temporal distance between the
+ * references and the target).  x float32 device; taus host, `slots` <= 8.
+ */
+revo_status revo_op_add_position(float* x, int slots, int grid_h, int grid_w, int D, const int* taus,
+                                 void* stream);
+
+/*
+ * De-normalise, quantise and blend one recovered frame.  head [Hp*Wp][C*p*p]
+ * float32 holds, per patch of the current frame, the pixel head's outputs for
+ * that frame ordered (c, y, x).  RGB: v = y*std_c + mean_c in [0,1] units, code
+ * = clamp(rint(255 v), 0, 255).  Depth: v = y*sigma + mu mm, code = clamp(rint(v),
+ * 0, 65535).  out = lost ? code : decoded, bit for bit for received pixels;
+ * values (optional, dense float32 [H][W][C]) gets v at every pixel.
+ */
+revo_status revo_op_blend(int channels, int p, int height, int width, const float* head,
+                          const void* decoded, size_t pitch_bytes, const uint32_t* mask,
+                          size_t mask_pitch_words, const float* mu_sigma, void* out,
+                          size_t out_pitch, float* values, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REVO_H */

@@ -1,0 +1,383 @@
+// Memory-bound stages of the recovery forward: input unpack + normalisation
+// fused with the tubelet gather, the sinusoidal (temporal distance, row,
+// column) embedding, LayerNorm, depth statistics, and the warp-level
+// de-normalise / quantise / masked-blend writeback.
+#include <math.h>
+
+#include "common.cuh"
+#include "revo_internal.h"
+
+namespace revo {
+
+namespace {
+
+__constant__ float kRgbMean[3] = {0.485f, 0.456f, 0.406f};
+__constant__ float kRgbStd[3] = {0.229f, 0.224f, 0.225f};
+
+// ------------------------------------------------------------- assemble --
+// One thread writes one run of p outputs: token n, frame t of its tubelet,
+// channel c, patch row y (vector order t, c, y, x; Appendix B.3).
+__global__ void assemble_kernel(const __grid_constant__ AssembleArgs a) {
+  const int p = a.p, C = a.C, T = a.T;
+  const int Hp = a.H / p, Wp = a.W / p;
+  const int S = a.F / T;
+  const long long runs = static_cast<long long>(S) * Hp * Wp * T * C * p;
+  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (idx >= runs) return;
+  long long rest = idx;
+  const int y = rest % p;
+  rest /= p;
+  const int c = rest % C;
+  rest /= C;
+  const int t = rest % T;
+  const long long n = rest / T;
+  const int s = static_cast<int>(n / (Hp * Wp));
+  const int rem = static_cast<int>(n % (Hp * Wp));
+  const int ty = rem / Wp, tx = rem % Wp;
+  const int f = s * T + t;
+  const int row = ty * p + y;
+  const int col0 = tx * p;
+  const uint8_t* src = static_cast<const uint8_t*>(a.frames[f]) + static_cast<size_t>(row) * a.pitch[f];
+  const int K = T * C * p * p;
+  const size_t o = static_cast<size_t>(n) * K + static_cast<size_t>((t * C + c) * p + y) * p;
+
+  float v[16];
+  if (C == 3) {
+    const float mean = kRgbMean[c], sd = kRgbStd[c];
+#pragma unroll
+    for (int x = 0; x < 16; ++x)
+      if (x < p) v[x] = (static_cast<float>(src[(col0 + x) * 3 + c]) / 255.0f - mean) / sd;
+  } else {
+    const float mu = a.mu_sigma[0], sg = a.mu_sigma[1];
+    const uint16_t* s16 = reinterpret_cast<const uint16_t*>(src);
+#pragma unroll
+    for (int x = 0; x < 16; ++x)
+      if (x < p) v[x] = (static_cast<float>(s16[col0 + x]) - mu) / sg;
+  }
+  if (a.out_bf16) {
+    __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(a.out) + o;
+    if (p == 16) {
+      uint4* d4 = reinterpret_cast<uint4*>(dst);
+      d4[0] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                         pack_bf16x2(v[6], v[7]));
+      d4[1] = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]), pack_bf16x2(v[12], v[13]),
+                         pack_bf16x2(v[14], v[15]));
+    } else {
+#pragma unroll
+      for (int x = 0; x < 16; ++x)
+        if (x < p) dst[x] = __float2bfloat16_rn(v[x]);
+    }
+  } else {
+    float* dst = static_cast<float*>(a.out) + o;
+    if (p == 16) {
+      float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else {
+#pragma unroll
+      for (int x = 0; x < 16; ++x)
+        if (x < p) dst[x] = v[x];
+    }
+  }
+}
+
+// ------------------------------------------------------------------- PE --
+struct PeArgs {
+  float omega[128];  // 10000^(-2i/part), i < part / 2
+  int taus[8];
+  int Hp, Wp, D, part;
+};
+
+__global__ void add_pe_kernel(float* __restrict__ x, long long total, const __grid_constant__ PeArgs a) {
+  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (idx >= total) return;
+  const int d = static_cast<int>(idx % a.D);
+  const long long n = idx / a.D;
+  const int s = static_cast<int>(n / (a.Hp * a.Wp));
+  const int rem = static_cast<int>(n % (a.Hp * a.Wp));
+  const int which = d / a.part;
+  const int j = d % a.part;
+  const int half = a.part / 2;
+  const float pos = which == 0 ? static_cast<float>(a.taus[s]) : which == 1 ? static_cast<float>(rem / a.Wp)
+                                                                            : static_cast<float>(rem % a.Wp);
+  const float arg = pos * a.omega[j % half];
+  x[idx] += (j < half) ? sinf(arg) : cosf(arg);
+}
+
+// ------------------------------------------------------------ LayerNorm --
+// One warp per row, two passes over registers, eps 1e-6, biased variance.
+constexpr int kLnMaxVec = 8;  // D <= 1024
+
+__global__ void layernorm_kernel(const float* __restrict__ x, const float* __restrict__ g,
+                                 const float* __restrict__ b, void* __restrict__ out, int M, int D, int out_bf16) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= M) return;
+  const float4* xr = reinterpret_cast<const float4*>(x + static_cast<size_t>(warp) * D);
+  const int nv = D / 4;
+  float4 v[kLnMaxVec];
+  float sum = 0.f;
+#pragma unroll
+  for (int i = 0; i < kLnMaxVec; ++i) {
+    const int c = lane + 32 * i;
+    if (c < nv) {
+      v[i] = __ldg(xr + c);
+      sum += (v[i].x + v[i].y) + (v[i].z + v[i].w);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  const float mean = sum / D;
+  float sq = 0.f;
+#pragma unroll
+  for (int i = 0; i < kLnMaxVec; ++i) {
+    const int c = lane + 32 * i;
+    if (c < nv) {
+      const float a0 = v[i].x - mean, a1 = v[i].y - mean, a2 = v[i].z - mean, a3 = v[i].w - mean;
+      sq += (a0 * a0 + a1 * a1) + (a2 * a2 + a3 * a3);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  const float rstd = 1.0f / sqrtf(sq / D + 1e-6f);
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+#pragma unroll
+  for (int i = 0; i < kLnMaxVec; ++i) {
+    const int c = lane + 32 * i;
+    if (c < nv) {
+      const float4 gg = __ldg(g4 + c), bb = __ldg(b4 + c);
+      const float y0 = (v[i].x - mean) * rstd * gg.x + bb.x;
+      const float y1 = (v[i].y - mean) * rstd * gg.y + bb.y;
+      const float y2 = (v[i].z - mean) * rstd * gg.z + bb.z;
+      const float y3 = (v[i].w - mean) * rstd * gg.w + bb.w;
+      if (out_bf16) {
+        uint2* o = reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out) + static_cast<size_t>(warp) * D) + c;
+        *o = make_uint2(pack_bf16x2(y0, y1), pack_bf16x2(y2, y3));
+      } else {
+        float4* o = reinterpret_cast<float4*>(static_cast<float*>(out) + static_cast<size_t>(warp) * D) + c;
+        *o = make_float4(y0, y1, y2, y3);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------- depth stats --
+// Two passes over the frame.  Pass 1: exact integer count and sum of the
+// non-zero pixels -> mean.  Pass 2: float sum of squared deviations -> biased
+// standard deviation.  Per-block partials go to scratch; the last block to
+// finish (atomic ticket) reduces them in a fixed order, so the result is
+// deterministic.
+constexpr int kStatsBlocks = 256;
+constexpr int kStatsThreads = 256;
+
+struct StatsScratch {
+  unsigned int ticket[4];
+  unsigned long long count[kStatsBlocks];
+  unsigned long long sum[kStatsBlocks];
+  float sq[kStatsBlocks];
+  float mean;
+  float pad[3];
+};
+
+template <typename T>
+REVO_DEVI T block_sum(T v, T* red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  T r = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) r += red[i];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kStatsThreads) depth_stats_pass1(const uint16_t* __restrict__ d, int H, int W,
+                                                                   size_t pitch, StatsScratch* sc) {
+  __shared__ unsigned long long red[kStatsThreads / 32];
+  __shared__ bool last;
+  unsigned long long cnt = 0, sum = 0;
+  const long long total = static_cast<long long>(H) * W;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int y = static_cast<int>(i / W), x = static_cast<int>(i % W);
+    const uint16_t v = *reinterpret_cast<const uint16_t*>(reinterpret_cast<const uint8_t*>(d) + y * pitch + 2 * x);
+    if (v) {
+      ++cnt;
+      sum += v;
+    }
+  }
+  cnt = block_sum(cnt, red);
+  sum = block_sum(sum, red);
+  if (threadIdx.x == 0) {
+    sc->count[blockIdx.x] = cnt;
+    sc->sum[blockIdx.x] = sum;
+    __threadfence();
+    last = atomicAdd(&sc->ticket[0], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    unsigned long long c = 0, s = 0;
+    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
+      c += *reinterpret_cast<volatile unsigned long long*>(&sc->count[b]);
+      s += *reinterpret_cast<volatile unsigned long long*>(&sc->sum[b]);
+    }
+    sc->mean = c ? static_cast<float>(s) / static_cast<float>(c) : 0.f;
+    sc->count[0] = c;  // total, read by pass 2
+    sc->ticket[0] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kStatsThreads) depth_stats_pass2(const uint16_t* __restrict__ d, int H, int W,
+                                                                   size_t pitch, StatsScratch* sc,
+                                                                   float* mu_sigma) {
+  __shared__ float red[kStatsThreads / 32];
+  __shared__ bool last;
+  const float mean = *reinterpret_cast<volatile float*>(&sc->mean);
+  float sq = 0.f;
+  const long long total = static_cast<long long>(H) * W;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int y = static_cast<int>(i / W), x = static_cast<int>(i % W);
+    const uint16_t v = *reinterpret_cast<const uint16_t*>(reinterpret_cast<const uint8_t*>(d) + y * pitch + 2 * x);
+    if (v) {
+      const float e = static_cast<float>(v) - mean;
+      sq += e * e;
+    }
+  }
+  sq = block_sum(sq, red);
+  if (threadIdx.x == 0) {
+    sc->sq[blockIdx.x] = sq;
+    __threadfence();
+    last = atomicAdd(&sc->ticket[1], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    float s = 0.f;
+    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) s += *reinterpret_cast<volatile float*>(&sc->sq[b]);
+    const unsigned long long c = *reinterpret_cast<volatile unsigned long long*>(&sc->count[0]);
+    float mu = 0.f, sigma = 1.f;
+    if (c) {
+      mu = mean;
+      sigma = fmaxf(sqrtf(s / static_cast<float>(c)), 1.0f);
+    }
+    mu_sigma[0] = mu;
+    mu_sigma[1] = sigma;
+    sc->ticket[1] = 0;
+  }
+}
+
+// ---------------------------------------------------------------- blend --
+// One warp per run of 32 pixels of one row; lane i owns pixel 32*w + i and bit
+// i of the row's mask word w.  Received pixels copy the decoded value; lost
+// pixels take the quantised recovery (round half to even, clamped).
+__global__ void blend_kernel(const __grid_constant__ BlendArgs a) {
+  const int words = (a.W + 31) / 32;
+  const long long gw = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= static_cast<long long>(a.H) * words) return;
+  const int y = static_cast<int>(gw / words);
+  const int w = static_cast<int>(gw % words);
+  const int x = w * 32 + lane;
+  const uint32_t word = __ldg(a.mask + static_cast<size_t>(y) * a.mask_pitch + w);
+  if (x >= a.W) return;
+  const bool lost = (word >> lane) & 1u;
+  const int p = a.p, C = a.C;
+  const int Wp = a.W / p;
+  const size_t n = static_cast<size_t>(y / p) * Wp + x / p;
+  const float* hrow = a.head + n * (C * p * p) + (y % p) * p + (x % p);
+  if (C == 3) {
+    const uint8_t* dec = static_cast<const uint8_t*>(a.decoded) + static_cast<size_t>(y) * a.pitch + 3 * x;
+    uint8_t* o = static_cast<uint8_t*>(a.out) + static_cast<size_t>(y) * a.out_pitch + 3 * x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float v = __ldg(hrow + c * p * p) * kRgbStd[c] + kRgbMean[c];
+      if (a.values) a.values[(static_cast<size_t>(y) * a.W + x) * 3 + c] = v;
+      const float q = fminf(fmaxf(rintf(v * 255.0f), 0.f), 255.f);
+      o[c] = lost ? static_cast<uint8_t>(q) : dec[c];
+    }
+  } else {
+    const uint16_t* dec = reinterpret_cast<const uint16_t*>(static_cast<const uint8_t*>(a.decoded) +
+                                                            static_cast<size_t>(y) * a.pitch) + x;
+    uint16_t* o = reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(a.out) + static_cast<size_t>(y) * a.out_pitch) + x;
+    const float v = __ldg(hrow) * a.mu_sigma[1] + a.mu_sigma[0];
+    if (a.values) a.values[static_cast<size_t>(y) * a.W + x] = v;
+    const float q = fminf(fmaxf(rintf(v), 0.f), 65535.f);
+    *o = lost ? static_cast<uint16_t>(q) : *dec;
+  }
+}
+
+__global__ void f32_to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {
+  const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (i < n) out[i] = __float2bfloat16_rn(in[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st) {
+  if (a.T <= 0 || a.F % a.T != 0 || a.p <= 0 || a.p > 16 || a.H % a.p || a.W % a.p || a.F > kMaxRefs + 1 ||
+      (a.C != 1 && a.C != 3))
+    return cudaErrorInvalidValue;
+  const long long runs = static_cast<long long>(a.F / a.T) * (a.H / a.p) * (a.W / a.p) * a.T * a.C * a.p;
+  if (runs == 0) return cudaSuccess;
+  assemble_kernel<<<static_cast<unsigned>((runs + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, int D, cudaStream_t st) {
+  PeArgs a{};
+  a.Hp = Hp;
+  a.Wp = Wp;
+  a.D = D;
+  a.part = D / 3;
+  if (D % 6 != 0 || a.part / 2 > 128 || slots > 8 || slots < 0) return cudaErrorInvalidValue;
+  for (int i = 0; i < a.part / 2; ++i) a.omega[i] = static_cast<float>(pow(10000.0, -2.0 * i / a.part));
+  for (int s = 0; s < slots; ++s) a.taus[s] = taus[s];
+  const long long total = static_cast<long long>(slots) * Hp * Wp * D;
+  if (total == 0) return cudaSuccess;
+  add_pe_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(x, total, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layernorm(const float* x, const float* g, const float* b, void* out, int M, int D, int out_bf16,
+                             cudaStream_t st) {
+  if (D % 4 != 0 || D > 4 * 32 * kLnMaxVec) return cudaErrorInvalidValue;
+  if (M <= 0) return cudaSuccess;
+  layernorm_kernel<<<(M + 7) / 8, 256, 0, st>>>(x, g, b, out, M, D, out_bf16);
+  return cudaGetLastError();
+}
+
+size_t depth_stats_scratch_bytes() { return sizeof(StatsScratch); }
+
+cudaError_t launch_depth_stats(const uint16_t* d, int H, int W, size_t pitch, float* mu_sigma, void* scratch,
+                               cudaStream_t st) {
+  StatsScratch* sc = static_cast<StatsScratch*>(scratch);
+  cudaError_t e = cudaMemsetAsync(sc->ticket, 0, sizeof(sc->ticket), st);
+  if (e != cudaSuccess) return e;
+  const long long total = static_cast<long long>(H) * W;
+  const long long want = (total + kStatsThreads * 8 - 1) / (kStatsThreads * 8);
+  const int blocks = static_cast<int>(want < 1 ? 1 : (want > kStatsBlocks ? kStatsBlocks : want));
+  depth_stats_pass1<<<blocks, kStatsThreads, 0, st>>>(d, H, W, pitch, sc);
+  depth_stats_pass2<<<blocks, kStatsThreads, 0, st>>>(d, H, W, pitch, sc, mu_sigma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st) {
+  if (a.p <= 0 || a.H % a.p || a.W % a.p || (a.C != 1 && a.C != 3)) return cudaErrorInvalidValue;
+  const long long warps = static_cast<long long>(a.H) * ((a.W + 31) / 32);
+  if (warps == 0) return cudaSuccess;
+  blend_kernel<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_bf16(const float* in, void* out, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  f32_to_bf16_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(in, static_cast<__nv_bfloat16*>(out), n);
+  return cudaGetLastError();
+}
+
+}  // namespace revo

@@ -1,0 +1,85 @@
+// Internal interfaces between the kernel files and the runtime.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace revo {
+
+// GEMM epilogues (Y = A W^T + b, then):
+enum Epilogue : int {
+  kEpiF32 = 0,       // store float32
+  kEpiBf16 = 1,      // store bf16
+  kEpiGeluBf16 = 2,  // store bf16(gelu(.))
+  kEpiResidF32 = 3,  // float32 out += .
+};
+
+constexpr int kMaxSegments = 64;
+constexpr int kMaxRefs = 7;  // k <= 7
+
+// Token segments (one per request) for attention: tokens attend within their
+// segment only.
+struct Segments {
+  int n;
+  int start[kMaxSegments + 1];
+};
+
+// ---- tensor maps
+bool encode_tmap_bf16_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t row_stride_elems,
+                         uint32_t box_rows, uint32_t box_cols);
+
+// ---- GEMMs
+cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, int bn, int epi, const float* bias, void* out,
+                           int ldo, int M, int N, int K, int* err, int num_sms, cudaStream_t st);
+cudaError_t launch_gemm_simt(int epi, const float* A, const float* W, const float* bias, void* out, int ldo, int M,
+                             int N, int K, cudaStream_t st);
+
+// ---- attention (qkv [M][3D] row-major; out [M][D])
+cudaError_t launch_attention_simt(const float* qkv, float* out, int M, int D, int heads, const Segments& seg,
+                                  cudaStream_t st);
+cudaError_t launch_attention_tc(const CUtensorMap& qkv_map, void* out, int M, int D, int heads, const Segments& seg,
+                                int* err, cudaStream_t st);
+bool encode_attention_tmap(CUtensorMap* map, const void* qkv, int M, int D);
+
+// ---- element-wise stages
+struct AssembleArgs {
+  const void* frames[kMaxRefs + 1];  // k refs oldest first, then the current frame
+  size_t pitch[kMaxRefs + 1];        // bytes
+  const float* mu_sigma;             // depth statistics (C == 1)
+  void* out;                         // [S*Hp*Wp][T*C*p*p]
+  int C, F, T, p, H, W;
+  int out_bf16;
+};
+cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st);
+
+// x[(s*Hp + r)*Wp + c][:] += sincos(tau_s) | sincos(r) | sincos(c), each D/3 wide.
+cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, int D, cudaStream_t st);
+
+cudaError_t launch_layernorm(const float* x, const float* g, const float* b, void* out, int M, int D, int out_bf16,
+                             cudaStream_t st);
+
+size_t depth_stats_scratch_bytes();
+cudaError_t launch_depth_stats(const uint16_t* d, int H, int W, size_t pitch, float* mu_sigma, void* scratch,
+                               cudaStream_t st);
+
+struct BlendArgs {
+  int C, p, H, W;
+  const float* head;  // [Hp*Wp][C*p*p]
+  const void* decoded;
+  size_t pitch;
+  const uint32_t* mask;
+  size_t mask_pitch;  // words
+  const float* mu_sigma;
+  void* out;
+  size_t out_pitch;
+  float* values;  // optional dense [H][W][C]
+};
+cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st);
+
+cudaError_t launch_f32_to_bf16(const float* in, void* out, size_t n, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace revo
