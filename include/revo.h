@@ -29,6 +29,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define REVO_API __attribute__((visibility("default")))
+#else
+#define REVO_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -148,7 +154,7 @@ typedef struct {
 } revo_result;
 
 /* Fills *cfg with the ViT-B reading above and precision BF16. */
-void revo_config_default(revo_config* cfg);
+REVO_API void revo_config_default(revo_config* cfg);
 
 /*
  * Creates a context on cfg->device: uploads both models' weights (float32
@@ -158,7 +164,7 @@ void revo_config_default(revo_config* cfg);
  * REVO_ENOTSUP (the tensor-core path needs an sm_100-class device),
  * REVO_ENOMEM (budget or device memory), REVO_ECUDA.  On error *out is NULL.
  */
-revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out);
+REVO_API revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out);
 
 /*
  * Submits one request and returns a ticket.  REVO_CLEAN requests are queued on
@@ -170,10 +176,10 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out);
  * than k clean frames in the stream's history for a requested modality),
  * REVO_EAGAIN (pending queue full: poll and retry), REVO_ECUDA.
  */
-revo_status revo_recover_submit(revo_ctx* ctx, const revo_request* req, uint64_t* ticket);
+REVO_API revo_status revo_recover_submit(revo_ctx* ctx, const revo_request* req, uint64_t* ticket);
 
 /* Launches every pending request now (in batches of at most max_batch). */
-revo_status revo_recover_flush(revo_ctx* ctx);
+REVO_API revo_status revo_recover_flush(revo_ctx* ctx);
 
 /*
  * Waits up to timeout_us microseconds (0 = do not wait, < 0 = forever) for a
@@ -182,13 +188,13 @@ revo_status revo_recover_flush(revo_ctx* ctx);
  * ran out.  REVO_EINVAL: unknown ticket.  A device-side failure of the batch is
  * reported in out->status.
  */
-revo_status revo_recover_poll(revo_ctx* ctx, uint64_t ticket, int64_t timeout_us, revo_result* out);
+REVO_API revo_status revo_recover_poll(revo_ctx* ctx, uint64_t ticket, int64_t timeout_us, revo_result* out);
 
 /* Drains the work in flight, then frees everything the context owns. */
-void revo_recover_destroy(revo_ctx* ctx);
+REVO_API void revo_recover_destroy(revo_ctx* ctx);
 
 /* The last error message of the calling thread ("" if none). */
-const char* revo_last_error(void);
+REVO_API const char* revo_last_error(void);
 
 /* ------------------------------------------------------------------------ *
  * Step-level entry points.  Each runs one stage of the recovery forward on
@@ -209,7 +215,7 @@ const char* revo_last_error(void);
  * (d - mu)/sigma with mu_sigma[2] a device float pair.  out_bf16 != 0 writes
  * bf16, else float32.  k <= 7, p <= 16.
  */
-revo_status revo_op_assemble(int channels, int k, int T, int p, int height, int width,
+REVO_API revo_status revo_op_assemble(int channels, int k, int T, int p, int height, int width,
                              const void* const* refs, const void* current, size_t pitch_bytes,
                              const float* mu_sigma, void* out, int out_bf16, void* stream);
 
@@ -220,8 +226,8 @@ revo_status revo_op_assemble(int channels, int k, int T, int p, int height, int 
  * buffer of revo_depth_stats_scratch_bytes() bytes that only one call at a time
  * may use.
  */
-size_t revo_depth_stats_scratch_bytes(void);
-revo_status revo_op_depth_stats(const uint16_t* depth, int height, int width, size_t pitch_bytes,
+REVO_API size_t revo_depth_stats_scratch_bytes(void);
+REVO_API revo_status revo_op_depth_stats(const uint16_t* depth, int height, int width, size_t pitch_bytes,
                                 float* mu_sigma, void* scratch, void* stream);
 
 /*
@@ -235,11 +241,11 @@ revo_status revo_op_depth_stats(const uint16_t* depth, int height, int width, si
  *   epilogue 2: out = gelu(acc + b) (bf16 out; FP32 precision writes float32)
  *   epilogue 3: out += acc + b (float32 residual, in place)
  */
-revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A, const void* W,
+REVO_API revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A, const void* W,
                            const float* bias, void* out, int M, int N, int K, int tile_n, void* stream);
 
 /* Row-wise LayerNorm, eps 1e-6: x float32 [M][D] -> out (bf16 if out_bf16, else float32). */
-revo_status revo_op_layernorm(const float* x, const float* gamma, const float* beta, void* out,
+REVO_API revo_status revo_op_layernorm(const float* x, const float* gamma, const float* beta, void* out,
                               int M, int D, int out_bf16, void* stream);
 
 /*
@@ -250,7 +256,7 @@ revo_status revo_op_layernorm(const float* x, const float* gamma, const float* b
  * segment.  out [M][D].  REVO_FP32: float32 in and out.  REVO_BF16: qkv and out
  * bf16, tcgen05 tensor cores, float32 softmax.  n_seg <= 64.
  */
-revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D,
+REVO_API revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D,
                               int heads, const int* seg_start, int n_seg, void* stream);
 
 /*
@@ -259,7 +265,7 @@ revo_status revo_op_attention(revo_precision precision, const void* qkv, void* o
  * (Section 3.4.1: the embedding encodes the temporal distance between the
  * references and the target).  x float32 device; taus host, `slots` <= 8.
  */
-revo_status revo_op_add_position(float* x, int slots, int grid_h, int grid_w, int D, const int* taus,
+REVO_API revo_status revo_op_add_position(float* x, int slots, int grid_h, int grid_w, int D, const int* taus,
                                  void* stream);
 
 /*
@@ -270,10 +276,18 @@ revo_status revo_op_add_position(float* x, int slots, int grid_h, int grid_w, in
  * 0, 65535).  out = lost ? code : decoded, bit for bit for received pixels;
  * values (optional, dense float32 [H][W][C]) gets v at every pixel.
  */
-revo_status revo_op_blend(int channels, int p, int height, int width, const float* head,
+REVO_API revo_status revo_op_blend(int channels, int p, int height, int width, const float* head,
                           const void* decoded, size_t pitch_bytes, const uint32_t* mask,
                           size_t mask_pitch_words, const float* mu_sigma, void* out,
                           size_t out_pitch, float* values, void* stream);
+
+/*
+ * Returns and clears the device error word of the step-level tensor-core
+ * kernels on the current device: 0 = no failure, otherwise the code of the
+ * first pipeline wait that gave up (the kernel then returned early and its
+ * output is incomplete).  -1 if the word cannot be read.  Synchronous.
+ */
+REVO_API int revo_op_take_device_error(void);
 
 #ifdef __cplusplus
 }

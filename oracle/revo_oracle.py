@@ -211,24 +211,30 @@ def forward(w: dict, cfg, frames: np.ndarray, taus) -> np.ndarray:
 
 # ---------------------------------------------------------------- step 6 ----
 
-def denormalise_rgb(y: np.ndarray) -> np.ndarray:
-    """[3, H, W] normalised -> [H, W, 3] in [0, 1] units (not clamped)."""
-    return (y.transpose(1, 2, 0) * RGB_STD + RGB_MEAN)
+# The de-normalise and quantise steps take a ``dtype``: float64 by default; a
+# check of codes produced in float32 passes np.float32 so that the rounding
+# decision is taken in the same precision (each product and sum rounded once,
+# no fused multiply-add).
+
+def denormalise_rgb(y: np.ndarray, dtype=np.float64) -> np.ndarray:
+    """[3, H, W] normalised -> [H, W, 3] in [0, 1] units (not clamped): y std_c + mean_c."""
+    y = np.asarray(y, dtype=dtype)
+    return y.transpose(1, 2, 0) * RGB_STD.astype(dtype) + RGB_MEAN.astype(dtype)
 
 
-def denormalise_depth(y: np.ndarray, mu: float, sigma: float) -> np.ndarray:
-    """[1, H, W] normalised -> [H, W] millimetres (not clamped)."""
-    return y[0] * sigma + mu
+def denormalise_depth(y: np.ndarray, mu: float, sigma: float, dtype=np.float64) -> np.ndarray:
+    """[1, H, W] normalised -> [H, W] millimetres (not clamped): y sigma + mu."""
+    return np.asarray(y, dtype=dtype)[0] * dtype(sigma) + dtype(mu)
 
 
-def quantise_rgb(v: np.ndarray) -> np.ndarray:
+def quantise_rgb(v: np.ndarray, dtype=np.float64) -> np.ndarray:
     """[0, 1] units -> uint8: round half to even of 255 v, clamped to [0, 255]."""
-    return np.clip(np.rint(v * 255.0), 0, 255).astype(np.uint8)
+    return np.clip(np.rint(np.asarray(v, dtype=dtype) * dtype(255.0)), 0, 255).astype(np.uint8)
 
 
-def quantise_depth(v: np.ndarray) -> np.ndarray:
+def quantise_depth(v: np.ndarray, dtype=np.float64) -> np.ndarray:
     """millimetres -> uint16: round half to even, clamped to [0, 65535]."""
-    return np.clip(np.rint(v), 0, 65535).astype(np.uint16)
+    return np.clip(np.rint(np.asarray(v, dtype=dtype)), 0, 65535).astype(np.uint16)
 
 
 def blend(decoded: np.ndarray, lost: np.ndarray, recovered_codes: np.ndarray) -> np.ndarray:

@@ -1,0 +1,287 @@
+"""Python binding of librevo (the C ABI declared in include/revo.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Importing this module does not load the library; the first call does, and
+raises if librevo.so has not been built (``python -m paper_2604_27441_b300.build``).
+Tensors may be passed as torch tensors, numpy arrays or raw integer pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librevo.so")
+
+REVO_OK, REVO_EAGAIN, REVO_EINVAL, REVO_ENOMEM, REVO_ETIMEDOUT, REVO_ENOREF, REVO_ECUDA, REVO_ENOTSUP = \
+    0, 1, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "REVO_OK", 1: "REVO_EAGAIN", -1: "REVO_EINVAL", -2: "REVO_ENOMEM", -3: "REVO_ETIMEDOUT",
+                -4: "REVO_ENOREF", -5: "REVO_ECUDA", -6: "REVO_ENOTSUP"}
+FP32, BF16, FP8 = 0, 1, 2
+RGB, DEPTH, CLEAN = 1, 2, 4
+EPI_F32, EPI_BF16, EPI_GELU_BF16, EPI_RESID_F32 = 0, 1, 2, 3
+
+
+class RevoError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("k", C.c_int), ("tubelet", C.c_int), ("patch", C.c_int),
+                ("enc_dim", C.c_int), ("enc_depth", C.c_int), ("enc_heads", C.c_int),
+                ("dec_dim", C.c_int), ("dec_depth", C.c_int), ("dec_heads", C.c_int),
+                ("mlp_ratio", C.c_int), ("precision", C.c_int), ("device", C.c_int),
+                ("hbm_budget_bytes", C.c_size_t), ("max_streams", C.c_int),
+                ("max_height", C.c_int), ("max_width", C.c_int), ("max_batch", C.c_int), ("lanes", C.c_int),
+                ("cuda_stream", C.c_void_p), ("use_graphs", C.c_int),
+                ("rgb_weights", C.c_void_p), ("rgb_weights_count", C.c_size_t),
+                ("depth_weights", C.c_void_p), ("depth_weights_count", C.c_size_t)]
+
+
+class Plane(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("height", C.c_int), ("width", C.c_int), ("pitch_bytes", C.c_size_t)]
+
+
+class Request(C.Structure):
+    _fields_ = [("stream_id", C.c_uint32), ("frame_index", C.c_int64), ("flags", C.c_uint32),
+                ("inputs_on_device", C.c_int),
+                ("rgb", Plane), ("rgb_lost_mask", C.c_void_p), ("rgb_mask_pitch_words", C.c_size_t),
+                ("depth", Plane), ("depth_lost_mask", C.c_void_p), ("depth_mask_pitch_words", C.c_size_t),
+                ("outputs_on_device", C.c_int),
+                ("rgb_out", C.c_void_p), ("rgb_out_pitch", C.c_size_t),
+                ("depth_out", C.c_void_p), ("depth_out_pitch", C.c_size_t),
+                ("rgb_values", C.c_void_p), ("depth_values", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("stream_id", C.c_uint32), ("frame_index", C.c_int64),
+                ("latency_ms", C.c_double), ("device_ms", C.c_double), ("batch_size", C.c_int)]
+
+
+_lib = None
+
+_SIGS = {
+    "revo_config_default": (None, [C.POINTER(Config)]),
+    "revo_recover_create": (C.c_int, [C.POINTER(Config), C.POINTER(C.c_void_p)]),
+    "revo_recover_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "revo_recover_flush": (C.c_int, [C.c_void_p]),
+    "revo_recover_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(Result)]),
+    "revo_recover_destroy": (None, [C.c_void_p]),
+    "revo_last_error": (C.c_char_p, []),
+    "revo_op_assemble": (C.c_int, [C.c_int] * 6 + [C.POINTER(C.c_void_p), C.c_void_p, C.c_size_t, C.c_void_p,
+                                                  C.c_void_p, C.c_int, C.c_void_p]),
+    "revo_depth_stats_scratch_bytes": (C.c_size_t, []),
+    "revo_op_depth_stats": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_size_t, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
+    "revo_op_linear": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                 C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "revo_op_layernorm": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "revo_op_attention": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                    C.POINTER(C.c_int), C.c_int, C.c_void_p]),
+    "revo_op_add_position": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                       C.c_void_p]),
+    "revo_op_blend": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
+                                C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
+                                C.c_void_p]),
+    "revo_op_take_device_error": (C.c_int, []),
+}
+
+
+def lib():
+    """The loaded library (loads it on first use; raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"librevo.so is not built ({LIB_PATH}); run python -m paper_2604_27441_b300.build")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return (lib().revo_last_error() or b"").decode()
+
+
+def _check(status: int, where: str) -> int:
+    if status not in (REVO_OK, REVO_EAGAIN):
+        raise RevoError(status, where, last_error())
+    return status
+
+
+def ptr(x) -> int | None:
+    """Raw address of a torch tensor / numpy array / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+# ------------------------------------------------------------ step-level ops
+
+def op_assemble(channels, k, T, p, height, width, refs, current, pitch_bytes, mu_sigma, out, out_bf16,
+                stream=None):
+    arr = (C.c_void_p * max(k, 1))(*[ptr(r) for r in refs])
+    return _check(lib().revo_op_assemble(channels, k, T, p, height, width, arr, ptr(current), pitch_bytes,
+                                         ptr(mu_sigma), ptr(out), int(out_bf16), _stream(stream)), "revo_op_assemble")
+
+
+def depth_stats_scratch_bytes() -> int:
+    return lib().revo_depth_stats_scratch_bytes()
+
+
+def op_depth_stats(depth, height, width, pitch_bytes, mu_sigma, scratch, stream=None):
+    return _check(lib().revo_op_depth_stats(ptr(depth), height, width, pitch_bytes, ptr(mu_sigma), ptr(scratch),
+                                            _stream(stream)), "revo_op_depth_stats")
+
+
+def op_linear(precision, epilogue, A, W, bias, out, M, N, K, tile_n=0, stream=None):
+    return _check(lib().revo_op_linear(precision, epilogue, ptr(A), ptr(W), ptr(bias), ptr(out), M, N, K, tile_n,
+                                       _stream(stream)), "revo_op_linear")
+
+
+def op_layernorm(x, gamma, beta, out, M, D, out_bf16, stream=None):
+    return _check(lib().revo_op_layernorm(ptr(x), ptr(gamma), ptr(beta), ptr(out), M, D, int(out_bf16),
+                                          _stream(stream)), "revo_op_layernorm")
+
+
+def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None):
+    n = len(seg_start) - 1
+    arr = (C.c_int * len(seg_start))(*[int(v) for v in seg_start])
+    return _check(lib().revo_op_attention(precision, ptr(qkv), ptr(out), M, D, heads, arr, n, _stream(stream)),
+                  "revo_op_attention")
+
+
+def op_add_position(x, slots, grid_h, grid_w, D, taus, stream=None):
+    arr = (C.c_int * max(len(taus), 1))(*[int(t) for t in taus])
+    return _check(lib().revo_op_add_position(ptr(x), slots, grid_h, grid_w, D, arr, _stream(stream)),
+                  "revo_op_add_position")
+
+
+def op_blend(channels, p, height, width, head, decoded, pitch_bytes, mask, mask_pitch_words, mu_sigma, out,
+             out_pitch, values=None, stream=None):
+    return _check(lib().revo_op_blend(channels, p, height, width, ptr(head), ptr(decoded), pitch_bytes, ptr(mask),
+                                      mask_pitch_words, ptr(mu_sigma), ptr(out), out_pitch, ptr(values),
+                                      _stream(stream)), "revo_op_blend")
+
+
+def take_device_error() -> int:
+    return lib().revo_op_take_device_error()
+
+
+# ------------------------------------------------------------------ context
+
+def config(**kw) -> Config:
+    cfg = Config()
+    lib().revo_config_default(C.byref(cfg))
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Context:
+    """A recovery context: revo_recover_create / submit / flush / poll / destroy."""
+
+    def __init__(self, cfg: Config, rgb_weights=None, depth_weights=None, stream=None):
+        self._keep = (rgb_weights, depth_weights)
+        if rgb_weights is not None:
+            cfg.rgb_weights = ptr(rgb_weights)
+            cfg.rgb_weights_count = int(rgb_weights.size)
+        if depth_weights is not None:
+            cfg.depth_weights = ptr(depth_weights)
+            cfg.depth_weights_count = int(depth_weights.size)
+        if stream is not None:
+            cfg.cuda_stream = _stream(stream)
+        h = C.c_void_p()
+        _check(lib().revo_recover_create(C.byref(cfg), C.byref(h)), "revo_recover_create")
+        self.cfg = cfg
+        self.handle = h
+
+    def submit(self, req: Request) -> int:
+        t = C.c_uint64()
+        st = lib().revo_recover_submit(self.handle, C.byref(req), C.byref(t))
+        if st != REVO_OK:
+            raise RevoError(st, "revo_recover_submit", last_error())
+        return t.value
+
+    def flush(self):
+        _check(lib().revo_recover_flush(self.handle), "revo_recover_flush")
+
+    def poll(self, ticket: int, timeout_us: int = -1):
+        """Returns a Result, or None if the request is still running (timeout 0)."""
+        r = Result()
+        st = lib().revo_recover_poll(self.handle, ticket, timeout_us, C.byref(r))
+        if st == REVO_EAGAIN:
+            return None
+        if st != REVO_OK:
+            raise RevoError(st, "revo_recover_poll", last_error())
+        return r
+
+    def close(self):
+        if self.handle:
+            lib().revo_recover_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plane(data, height, width, pitch_bytes) -> Plane:
+    return Plane(ptr(data), height, width, pitch_bytes)
+
+
+def request(stream_id, frame_index, flags, *, on_device, rgb=None, rgb_mask=None, depth=None, depth_mask=None,
+            rgb_out=None, depth_out=None, rgb_values=None, depth_values=None, outputs_on_device=None) -> Request:
+    """A Request from per-modality (data, H, W) tuples; pitches and mask pitches are dense."""
+    r = Request()
+    r.stream_id = stream_id
+    r.frame_index = frame_index
+    r.flags = flags
+    r.inputs_on_device = int(on_device)
+    r.outputs_on_device = int(on_device if outputs_on_device is None else outputs_on_device)
+    if rgb is not None:
+        d, H, W = rgb
+        r.rgb = Plane(ptr(d), H, W, W * 3)
+        r.rgb_lost_mask = ptr(rgb_mask)
+        r.rgb_mask_pitch_words = (W + 31) // 32
+        r.rgb_out = ptr(rgb_out)
+        r.rgb_out_pitch = W * 3
+        r.rgb_values = ptr(rgb_values)
+    if depth is not None:
+        d, H, W = depth
+        r.depth = Plane(ptr(d), H, W, W * 2)
+        r.depth_lost_mask = ptr(depth_mask)
+        r.depth_mask_pitch_words = (W + 31) // 32
+        r.depth_out = ptr(depth_out)
+        r.depth_out_pitch = W * 2
+        r.depth_values = ptr(depth_values)
+    return r

@@ -274,7 +274,9 @@ __global__ void __launch_bounds__(kStatsThreads) depth_stats_pass2(const uint16_
 // ---------------------------------------------------------------- blend --
 // One warp per run of 32 pixels of one row; lane i owns pixel 32*w + i and bit
 // i of the row's mask word w.  Received pixels copy the decoded value; lost
-// pixels take the quantised recovery (round half to even, clamped).
+// pixels take the quantised recovery (round half to even, clamped).  The
+// de-normalisation is done as separate float32 multiply and add (no fused
+// multiply-add), so a float32 restatement reproduces every code exactly.
 __global__ void blend_kernel(const __grid_constant__ BlendArgs a) {
   const int words = (a.W + 31) / 32;
   const long long gw = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
@@ -295,16 +297,16 @@ __global__ void blend_kernel(const __grid_constant__ BlendArgs a) {
     uint8_t* o = static_cast<uint8_t*>(a.out) + static_cast<size_t>(y) * a.out_pitch + 3 * x;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float v = __ldg(hrow + c * p * p) * kRgbStd[c] + kRgbMean[c];
+      const float v = __fadd_rn(__fmul_rn(__ldg(hrow + c * p * p), kRgbStd[c]), kRgbMean[c]);
       if (a.values) a.values[(static_cast<size_t>(y) * a.W + x) * 3 + c] = v;
-      const float q = fminf(fmaxf(rintf(v * 255.0f), 0.f), 255.f);
+      const float q = fminf(fmaxf(rintf(__fmul_rn(v, 255.0f)), 0.f), 255.f);
       o[c] = lost ? static_cast<uint8_t>(q) : dec[c];
     }
   } else {
     const uint16_t* dec = reinterpret_cast<const uint16_t*>(static_cast<const uint8_t*>(a.decoded) +
                                                             static_cast<size_t>(y) * a.pitch) + x;
     uint16_t* o = reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(a.out) + static_cast<size_t>(y) * a.out_pitch) + x;
-    const float v = __ldg(hrow) * a.mu_sigma[1] + a.mu_sigma[0];
+    const float v = __fadd_rn(__fmul_rn(__ldg(hrow), a.mu_sigma[1]), a.mu_sigma[0]);
     if (a.values) a.values[static_cast<size_t>(y) * a.W + x] = v;
     const float q = fminf(fmaxf(rintf(v), 0.f), 65535.f);
     *o = lost ? static_cast<uint16_t>(q) : *dec;

@@ -1,0 +1,377 @@
+// The recovery network on the device (Section 3.4.1, Appendix B.1, B.3):
+// tubelet embedding + (temporal distance, row, column) embedding, pre-LN
+// encoder blocks, final LN, encoder->decoder Linear + decoder embedding, pre-LN
+// decoder blocks, final LN and the pixel head for the target frame, then the
+// masked blend.  A batch of same-modality requests runs as one forward whose
+// Linear layers see every request's tokens stacked along the rows; attention
+// keeps each request's tokens to themselves (one segment per request).
+#include <string.h>
+
+#include "model.h"
+
+namespace revo {
+
+namespace {
+
+size_t block_params(int d, int r) {
+  return 2ull * d + (3ull * d * d + 3ull * d) + (1ull * d * d + d) + 2ull * d + (1ull * r * d * d + 1ull * r * d) +
+         (1ull * r * d * d + d);
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int pick_bn(int M, int N, int sms) {
+  if (N < 256) return 128;
+  auto cost = [&](int bn) {
+    const long long tiles = static_cast<long long>((M + 127) / 128) * ((N + bn - 1) / bn);
+    return ((tiles + sms - 1) / sms) * bn;
+  };
+  return cost(256) < cost(128) ? 256 : 128;
+}
+
+bool make_weight_maps(LinearW& w) {
+  if (!w.w16) return true;
+  if (!encode_tmap_bf16_2d(&w.map128, w.w16, w.out, w.in, w.in, 128, 64)) return false;
+  if (w.out >= 256 && !encode_tmap_bf16_2d(&w.map256, w.w16, w.out, w.in, w.in, 256, 64)) return false;
+  return true;
+}
+
+}  // namespace
+
+size_t param_count(const NetShape& s) {
+  const size_t D = s.D, Dd = s.Dd, K = s.token_dim();
+  return D * K + D + s.L * block_params(s.D, s.r) + 2 * D + Dd * D + Dd + s.Ld * block_params(s.Dd, s.r) + 2 * Dd +
+         K * Dd + K;
+}
+
+std::string check_shape(const NetShape& s) {
+  if (s.C != 1 && s.C != 3) return "channels must be 1 or 3";
+  if (s.k < 1 || s.k > kMaxRefs) return "k must be in 1..7";
+  if (s.T < 1 || (s.k + 1) % s.T) return "(k + 1) must be a multiple of the tubelet size";
+  if (s.slots() > 8) return "at most 8 tubelet slots";
+  if (s.p != 16) return "patch size must be 16";
+  if (s.D % 64 || s.Dd % 64 || s.D <= 0 || s.Dd <= 0) return "widths must be positive multiples of 64";
+  if (s.D % 6 || s.Dd % 6) return "widths must split into three even embedding parts";
+  if (s.D > 1024 || s.Dd > 1024) return "widths above 1024 are not supported";
+  if (s.H * 64 != s.D || s.Hd * 64 != s.Dd) return "head width must be 64";
+  if (s.r < 1 || s.L < 0 || s.Ld < 1) return "bad depth or MLP ratio";
+  return "";
+}
+
+size_t net_bytes(const NetShape& s, int precision) {
+  const size_t n = param_count(s);
+  return align_up(n * 4, 256) + (precision != REVO_FP32 ? align_up(n * 2, 256) : 0);
+}
+
+Net* net_create(const NetShape& s, int precision, const float* host_weights, std::string* err) {
+  Net* net = new Net();
+  net->s = s;
+  net->precision = precision;
+  const size_t n = param_count(s);
+  const bool tc = precision != REVO_FP32;
+  if (cudaMalloc(&net->blob, n * 4) != cudaSuccess ||
+      cudaMemcpy(net->blob, host_weights, n * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    *err = "weight upload failed";
+    net_destroy(net);
+    return nullptr;
+  }
+  if (tc) {
+    if (cudaMalloc(&net->blob16, n * 2) != cudaSuccess || launch_f32_to_bf16(net->blob, net->blob16, n, 0) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+      *err = "bf16 weight copy failed";
+      net_destroy(net);
+      return nullptr;
+    }
+  }
+  size_t off = 0;
+  auto take = [&](size_t count) {
+    const size_t o = off;
+    off += count;
+    return o;
+  };
+  auto lin = [&](int out, int in) {
+    LinearW w;
+    w.out = out;
+    w.in = in;
+    const size_t ow = take(static_cast<size_t>(out) * in);
+    const size_t ob = take(out);
+    w.w32 = net->blob + ow;
+    w.b = net->blob + ob;
+    if (tc) w.w16 = net->blob16 + ow;
+    return w;
+  };
+  auto block = [&](int d) {
+    BlockW b;
+    b.ln1g = net->blob + take(d);
+    b.ln1b = net->blob + take(d);
+    b.qkv = lin(3 * d, d);
+    b.proj = lin(d, d);
+    b.ln2g = net->blob + take(d);
+    b.ln2b = net->blob + take(d);
+    b.fc1 = lin(s.r * d, d);
+    b.fc2 = lin(d, s.r * d);
+    return b;
+  };
+  net->patch = lin(s.D, s.token_dim());
+  for (int i = 0; i < s.L; ++i) net->enc.push_back(block(s.D));
+  net->enc_norm_g = net->blob + take(s.D);
+  net->enc_norm_b = net->blob + take(s.D);
+  net->enc2dec = lin(s.Dd, s.D);
+  for (int i = 0; i < s.Ld; ++i) net->dec.push_back(block(s.Dd));
+  net->dec_norm_g = net->blob + take(s.Dd);
+  net->dec_norm_b = net->blob + take(s.Dd);
+  {
+    // Keep only the head rows of the tubelet's last frame (the target frame).
+    const int K = s.token_dim(), Cpp = s.head_dim_out();
+    const size_t ow = take(static_cast<size_t>(K) * s.Dd);
+    const size_t ob = take(K);
+    const size_t row0 = static_cast<size_t>(s.T - 1) * Cpp;
+    LinearW w;
+    w.out = Cpp;
+    w.in = s.Dd;
+    w.w32 = net->blob + ow + row0 * s.Dd;
+    w.b = net->blob + ob + row0;
+    if (tc) w.w16 = net->blob16 + ow + row0 * s.Dd;
+    net->head = w;
+  }
+  if (off != n) {
+    *err = "internal parameter layout mismatch";
+    net_destroy(net);
+    return nullptr;
+  }
+  if (tc) {
+    bool ok = make_weight_maps(net->patch) && make_weight_maps(net->enc2dec) && make_weight_maps(net->head);
+    for (auto& b : net->enc)
+      ok = ok && make_weight_maps(b.qkv) && make_weight_maps(b.proj) && make_weight_maps(b.fc1) &&
+           make_weight_maps(b.fc2);
+    for (auto& b : net->dec)
+      ok = ok && make_weight_maps(b.qkv) && make_weight_maps(b.proj) && make_weight_maps(b.fc1) &&
+           make_weight_maps(b.fc2);
+    if (!ok) {
+      *err = "weight tensor map encoding failed";
+      net_destroy(net);
+      return nullptr;
+    }
+  }
+  return net;
+}
+
+void net_destroy(Net* n) {
+  if (!n) return;
+  if (n->blob) cudaFree(n->blob);
+  if (n->blob16) cudaFree(n->blob16);
+  delete n;
+}
+
+namespace {
+struct WsLayout {
+  size_t tok, x, h, qkv, att, mlp, head, err, total;
+};
+WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp) {
+  const size_t e = precision != REVO_FP32 ? 2 : 4;
+  const size_t D = s.D > s.Dd ? s.D : s.Dd;
+  WsLayout l{};
+  size_t o = 0;
+  auto put = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  l.tok = put(static_cast<size_t>(cap) * s.token_dim() * e);
+  l.x = put(static_cast<size_t>(cap) * D * 4);
+  l.h = put(static_cast<size_t>(cap) * D * e);
+  l.qkv = put(static_cast<size_t>(cap) * 3 * D * e);
+  l.att = put(static_cast<size_t>(cap) * D * e);
+  l.mlp = put(static_cast<size_t>(cap) * s.r * D * e);
+  l.head = put(static_cast<size_t>(capp) * s.head_dim_out() * 4);
+  l.err = put(256);
+  l.total = o;
+  return l;
+}
+}  // namespace
+
+size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches) {
+  return ws_layout(s, precision, cap_tokens, cap_patches).total;
+}
+
+Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, int cap_patches, std::string* err) {
+  const WsLayout l = ws_layout(s, precision, cap_tokens, cap_patches);
+  uint8_t* base = nullptr;
+  if (cudaMalloc(&base, l.total) != cudaSuccess) {
+    *err = "workspace allocation failed";
+    return nullptr;
+  }
+  // Zero once so that rows never written by a request stay finite.
+  if (cudaMemset(base, 0, l.total) != cudaSuccess) {
+    cudaFree(base);
+    *err = "workspace clear failed";
+    return nullptr;
+  }
+  Workspace* w = new Workspace();
+  w->cap_tokens = cap_tokens;
+  w->cap_patches = cap_patches;
+  w->tok = base + l.tok;
+  w->x = reinterpret_cast<float*>(base + l.x);
+  w->h = base + l.h;
+  w->qkv = base + l.qkv;
+  w->att = base + l.att;
+  w->mlp = base + l.mlp;
+  w->head = reinterpret_cast<float*>(base + l.head);
+  w->err = reinterpret_cast<int*>(base + l.err);
+  w->bytes = l.total;
+  return w;
+}
+
+void workspace_destroy(Workspace* w) {
+  if (!w) return;
+  if (w->tok) cudaFree(w->tok);  // the arena's base
+  delete w;
+}
+
+namespace {
+
+struct Fwd {
+  Net* net;
+  Workspace* ws;
+  cudaStream_t st;
+  int sms;
+  bool tc;
+  size_t e;  // activation element size
+
+  cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M) {
+    if (!tc) return launch_gemm_simt(epi, static_cast<const float*>(A), w.w32, w.b, out, ldo, M, w.out, w.in, st);
+    const int bn = pick_bn(M, w.out, sms);
+    return launch_gemm_tc(*amap, bn == 256 ? w.map256 : w.map128, bn, epi, w.b, out, ldo, M, w.out, w.in, ws->err,
+                          sms, st);
+  }
+
+  cudaError_t block(const BlockW& b, int d, int heads, int M, const Segments& seg, const CUtensorMap* m_h,
+                    const CUtensorMap* m_att, const CUtensorMap* m_mlp, const CUtensorMap* m_qkv) {
+    cudaError_t e;
+    if ((e = launch_layernorm(ws->x, b.ln1g, b.ln1b, ws->h, M, d, tc, st)) != cudaSuccess) return e;
+    if ((e = linear(m_h, ws->h, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, M)) != cudaSuccess) return e;
+    if (tc)
+      e = launch_attention_tc(*m_qkv, ws->att, M, d, heads, seg, ws->err, st);
+    else
+      e = launch_attention_simt(static_cast<const float*>(ws->qkv), static_cast<float*>(ws->att), M, d, heads, seg,
+                                st);
+    if (e != cudaSuccess) return e;
+    if ((e = linear(m_att, ws->att, b.proj, kEpiResidF32, ws->x, d, M)) != cudaSuccess) return e;
+    if ((e = launch_layernorm(ws->x, b.ln2g, b.ln2b, ws->h, M, d, tc, st)) != cudaSuccess) return e;
+    if ((e = linear(m_h, ws->h, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, M)) != cudaSuccess) return e;
+    return linear(m_mlp, ws->mlp, b.fc2, kEpiResidF32, ws->x, d, M);
+  }
+};
+
+bool encode_maps(const NetShape& s, Workspace* ws, int M) {
+  if (ws->maps_rows == M) return true;
+  const uint64_t rows = M > 0 ? M : 1;
+  bool ok = encode_tmap_bf16_2d(&ws->m_tok, ws->tok, rows, s.token_dim(), s.token_dim(), 128, 64) &&
+            encode_tmap_bf16_2d(&ws->m_h_enc, ws->h, rows, s.D, s.D, 128, 64) &&
+            encode_tmap_bf16_2d(&ws->m_att_enc, ws->att, rows, s.D, s.D, 128, 64) &&
+            encode_tmap_bf16_2d(&ws->m_mlp_enc, ws->mlp, rows, s.r * s.D, s.r * s.D, 128, 64) &&
+            encode_tmap_bf16_2d(&ws->m_h_dec, ws->h, rows, s.Dd, s.Dd, 128, 64) &&
+            encode_tmap_bf16_2d(&ws->m_att_dec, ws->att, rows, s.Dd, s.Dd, 128, 64) &&
+            encode_tmap_bf16_2d(&ws->m_mlp_dec, ws->mlp, rows, s.r * s.Dd, s.r * s.Dd, 128, 64) &&
+            encode_attention_tmap(&ws->m_qkv_enc, ws->qkv, static_cast<int>(rows), s.D) &&
+            encode_attention_tmap(&ws->m_qkv_dec, ws->qkv, static_cast<int>(rows), s.Dd);
+  ws->maps_rows = ok ? M : -1;
+  return ok;
+}
+
+}  // namespace
+
+cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms) {
+  const NetShape& s = net->s;
+  if (n <= 0) return cudaSuccess;
+  if (n > kMaxSegments) return cudaErrorInvalidValue;
+  Fwd f{net, ws, st, num_sms, net->precision != REVO_FP32, net->precision != REVO_FP32 ? 2u : 4u};
+  Segments seg{};
+  seg.n = n;
+  seg.start[0] = 0;
+  int patches = 0;
+  for (int i = 0; i < n; ++i) {
+    if (jobs[i].H % s.p || jobs[i].W % s.p || jobs[i].H <= 0 || jobs[i].W <= 0) return cudaErrorInvalidValue;
+    seg.start[i + 1] = seg.start[i] + request_tokens(s, jobs[i].H, jobs[i].W);
+    patches += request_patches(s, jobs[i].H, jobs[i].W);
+  }
+  const int M = seg.start[n];
+  if (M > ws->cap_tokens || patches > ws->cap_patches) return cudaErrorInvalidValue;
+  if (f.tc && !encode_maps(s, ws, M)) return cudaErrorInvalidValue;
+  cudaError_t e;
+  uint8_t* tok = static_cast<uint8_t*>(ws->tok);
+
+  // Tubelet assembly + normalisation, tubelet embedding, embeddings.
+  for (int i = 0; i < n; ++i) {
+    AssembleArgs a{};
+    for (int fidx = 0; fidx <= s.k; ++fidx) {
+      a.frames[fidx] = jobs[i].frames[fidx];
+      a.pitch[fidx] = jobs[i].pitch[fidx];
+    }
+    a.mu_sigma = jobs[i].mu_sigma;
+    a.out = tok + static_cast<size_t>(seg.start[i]) * s.token_dim() * f.e;
+    a.C = s.C;
+    a.F = s.frames();
+    a.T = s.T;
+    a.p = s.p;
+    a.H = jobs[i].H;
+    a.W = jobs[i].W;
+    a.out_bf16 = f.tc;
+    if ((e = launch_assemble(a, st)) != cudaSuccess) return e;
+  }
+  if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32, ws->x, s.D, M)) != cudaSuccess) return e;
+  for (int i = 0; i < n; ++i)
+    if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.D, jobs[i].H / s.p, jobs[i].W / s.p,
+                           s.slots(), jobs[i].taus, s.D, st)) != cudaSuccess)
+      return e;
+
+  for (const BlockW& b : net->enc)
+    if ((e = f.block(b, s.D, s.H, M, seg, &ws->m_h_enc, &ws->m_att_enc, &ws->m_mlp_enc, &ws->m_qkv_enc)) !=
+        cudaSuccess)
+      return e;
+  if ((e = launch_layernorm(ws->x, net->enc_norm_g, net->enc_norm_b, ws->h, M, s.D, f.tc, st)) != cudaSuccess) return e;
+  if ((e = f.linear(&ws->m_h_enc, ws->h, net->enc2dec, kEpiF32, ws->x, s.Dd, M)) != cudaSuccess) return e;
+  for (int i = 0; i < n; ++i)
+    if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.Dd, jobs[i].H / s.p, jobs[i].W / s.p,
+                           s.slots(), jobs[i].taus, s.Dd, st)) != cudaSuccess)
+      return e;
+  for (const BlockW& b : net->dec)
+    if ((e = f.block(b, s.Dd, s.Hd, M, seg, &ws->m_h_dec, &ws->m_att_dec, &ws->m_mlp_dec, &ws->m_qkv_dec)) !=
+        cudaSuccess)
+      return e;
+
+  // Final LN and pixel head on the last slot's tokens of each request, then the blend.
+  int hoff = 0;
+  uint8_t* h = static_cast<uint8_t*>(ws->h);
+  for (int i = 0; i < n; ++i) {
+    const int P = request_patches(s, jobs[i].H, jobs[i].W);
+    const size_t row0 = static_cast<size_t>(seg.start[i]) + static_cast<size_t>(s.slots() - 1) * P;
+    void* hrows = h + row0 * s.Dd * f.e;
+    if ((e = launch_layernorm(ws->x + row0 * s.Dd, net->dec_norm_g, net->dec_norm_b, hrows, P, s.Dd, f.tc, st)) !=
+        cudaSuccess)
+      return e;
+    float* head = ws->head + static_cast<size_t>(hoff) * s.head_dim_out();
+    CUtensorMap m_rows;
+    if (f.tc && !encode_tmap_bf16_2d(&m_rows, hrows, P, s.Dd, s.Dd, 128, 64)) return cudaErrorInvalidValue;
+    if ((e = f.linear(&m_rows, hrows, net->head, kEpiF32, head, s.head_dim_out(), P)) != cudaSuccess) return e;
+    BlendArgs bl{};
+    bl.C = s.C;
+    bl.p = s.p;
+    bl.H = jobs[i].H;
+    bl.W = jobs[i].W;
+    bl.head = head;
+    bl.decoded = jobs[i].frames[s.k];
+    bl.pitch = jobs[i].pitch[s.k];
+    bl.mask = jobs[i].mask;
+    bl.mask_pitch = jobs[i].mask_pitch;
+    bl.mu_sigma = jobs[i].mu_sigma;
+    bl.out = jobs[i].out;
+    bl.out_pitch = jobs[i].out_pitch;
+    bl.values = jobs[i].values;
+    if ((e = launch_blend(bl, st)) != cudaSuccess) return e;
+    hoff += P;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace revo

@@ -1,0 +1,101 @@
+// The recovery network on the device: weights, work arena, and the forward of
+// a ragged batch of same-modality requests whose tokens are concatenated
+// along the row dimension of every activation matrix.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "revo_internal.h"
+
+namespace revo {
+
+struct NetShape {
+  int C, k, T, p;
+  int D, L, H;     // encoder width, blocks, heads
+  int Dd, Ld, Hd;  // decoder width, blocks, heads
+  int r;           // MLP ratio
+  int frames() const { return k + 1; }
+  int slots() const { return (k + 1) / T; }
+  int token_dim() const { return T * C * p * p; }
+  int head_dim_out() const { return C * p * p; }  // head rows kept: the last frame of a tubelet
+};
+
+size_t param_count(const NetShape& s);
+// Empty string if the shape is supported by the kernels, else the reason.
+std::string check_shape(const NetShape& s);
+
+struct LinearW {
+  const float* w32 = nullptr;
+  const float* b = nullptr;
+  const __nv_bfloat16* w16 = nullptr;
+  int out = 0, in = 0;
+  CUtensorMap map128{}, map256{};
+};
+
+struct BlockW {
+  const float *ln1g, *ln1b, *ln2g, *ln2b;
+  LinearW qkv, proj, fc1, fc2;
+};
+
+struct Net {
+  NetShape s{};
+  int precision = 0;
+  float* blob = nullptr;            // float32 master copy of every parameter
+  __nv_bfloat16* blob16 = nullptr;  // bf16 copy (tensor-core path)
+  LinearW patch, enc2dec, head;     // head: the rows that produce the target frame
+  std::vector<BlockW> enc, dec;
+  const float *enc_norm_g, *enc_norm_b, *dec_norm_g, *dec_norm_b;
+};
+
+// One request of one modality inside a batch (all pointers are device pointers).
+struct PlaneJob {
+  int H, W;
+  const void* frames[kMaxRefs + 1];  // k refs (oldest first) then the decoded current frame
+  size_t pitch[kMaxRefs + 1];
+  const uint32_t* mask;
+  size_t mask_pitch;  // words
+  const float* mu_sigma;  // depth statistics (C == 1)
+  int taus[8];            // temporal distance per slot
+  void* out;              // blended frame
+  size_t out_pitch;
+  float* values;          // optional dense float32 output
+};
+
+struct Workspace {
+  int cap_tokens = 0, cap_patches = 0;
+  void* tok = nullptr;   // [cap][T*C*p*p]
+  float* x = nullptr;    // [cap][D]   residual stream
+  void* h = nullptr;     // [cap][D]   LayerNorm output
+  void* qkv = nullptr;   // [cap][3D]
+  void* att = nullptr;   // [cap][D]
+  void* mlp = nullptr;   // [cap][rD]
+  float* head = nullptr; // [cap_patches][C*p*p]
+  int* err = nullptr;    // device error word of the tensor-core kernels
+  size_t bytes = 0;
+  // Tensor maps of the A operands, valid for `maps_rows` rows.
+  int maps_rows = -1;
+  CUtensorMap m_tok{}, m_h_enc{}, m_att_enc{}, m_mlp_enc{}, m_h_dec{}, m_att_dec{}, m_mlp_dec{};
+  CUtensorMap m_qkv_enc{}, m_qkv_dec{};
+};
+
+Net* net_create(const NetShape& s, int precision, const float* host_weights, std::string* err);
+void net_destroy(Net* n);
+size_t net_bytes(const NetShape& s, int precision);
+
+size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches);
+Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, int cap_patches, std::string* err);
+void workspace_destroy(Workspace* w);
+
+// Tokens of one request of height H and width W.
+inline int request_tokens(const NetShape& s, int H, int W) { return s.slots() * (H / s.p) * (W / s.p); }
+inline int request_patches(const NetShape& s, int H, int W) { return (H / s.p) * (W / s.p); }
+
+// Enqueues the whole forward (assemble ... blend) of `n` jobs on `st`.
+cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms);
+
+}  // namespace revo

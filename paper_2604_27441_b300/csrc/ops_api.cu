@@ -1,0 +1,228 @@
+// Step-level entry points of the C ABI: each runs one stage of the recovery
+// forward on caller-owned device buffers.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+#include "revo.h"
+#include "revo_internal.h"
+
+namespace revo {
+
+namespace {
+thread_local std::string g_last_error;
+std::mutex g_err_mu;
+int* g_err_word[64] = {nullptr};
+}  // namespace
+
+void set_last_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+revo_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return REVO_OK;
+  set_last_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorInvalidValue ? REVO_EINVAL : REVO_ECUDA;
+}
+
+// The device error word the step-level tensor-core kernels report timeouts in
+// (one per device, allocated on first use).
+int* op_error_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_word[dev]) {
+    int* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+    g_err_word[dev] = p;
+  }
+  return g_err_word[dev];
+}
+
+}  // namespace revo
+
+using namespace revo;
+
+extern "C" {
+
+const char* revo_last_error(void) { return g_last_error.c_str(); }
+
+int revo_op_take_device_error(void) {
+  int* w = op_error_word();
+  if (!w) return -1;
+  int v = 0;
+  if (cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  if (v) cudaMemset(w, 0, sizeof(int));
+  return v;
+}
+
+revo_status revo_op_assemble(int channels, int k, int T, int p, int height, int width, const void* const* refs,
+                             const void* current, size_t pitch_bytes, const float* mu_sigma, void* out, int out_bf16,
+                             void* stream) {
+  if (!current || !out || (k > 0 && !refs) || k < 0 || k > kMaxRefs || (channels == 1 && !mu_sigma)) {
+    set_last_error("revo_op_assemble: null pointer or k out of range");
+    return REVO_EINVAL;
+  }
+  AssembleArgs a{};
+  for (int i = 0; i < k; ++i) {
+    if (!refs[i]) {
+      set_last_error("revo_op_assemble: null reference frame");
+      return REVO_EINVAL;
+    }
+    a.frames[i] = refs[i];
+    a.pitch[i] = pitch_bytes;
+  }
+  a.frames[k] = current;
+  a.pitch[k] = pitch_bytes;
+  a.mu_sigma = mu_sigma;
+  a.out = out;
+  a.C = channels;
+  a.F = k + 1;
+  a.T = T;
+  a.p = p;
+  a.H = height;
+  a.W = width;
+  a.out_bf16 = out_bf16;
+  return cuda_status(launch_assemble(a, static_cast<cudaStream_t>(stream)), "revo_op_assemble");
+}
+
+size_t revo_depth_stats_scratch_bytes(void) { return depth_stats_scratch_bytes(); }
+
+revo_status revo_op_depth_stats(const uint16_t* depth, int height, int width, size_t pitch_bytes, float* mu_sigma,
+                                void* scratch, void* stream) {
+  if (!depth || !mu_sigma || !scratch || height < 0 || width < 0 || pitch_bytes < 2ull * width) {
+    set_last_error("revo_op_depth_stats: bad argument");
+    return REVO_EINVAL;
+  }
+  return cuda_status(
+      launch_depth_stats(depth, height, width, pitch_bytes, mu_sigma, scratch, static_cast<cudaStream_t>(stream)),
+      "revo_op_depth_stats");
+}
+
+revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A, const void* W, const float* bias,
+                           void* out, int M, int N, int K, int tile_n, void* stream) {
+  if (!A || !W || !out || M < 0 || N <= 0 || K <= 0 || epilogue < 0 || epilogue > 3) {
+    set_last_error("revo_op_linear: bad argument");
+    return REVO_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (precision == REVO_FP32) {
+    if (K % 8) {
+      set_last_error("revo_op_linear: FP32 path needs K %% 8 == 0");
+      return REVO_EINVAL;
+    }
+    return cuda_status(launch_gemm_simt(epilogue, static_cast<const float*>(A), static_cast<const float*>(W), bias,
+                                        out, N, M, N, K, st),
+                       "revo_op_linear");
+  }
+  if (precision != REVO_BF16) {
+    set_last_error("revo_op_linear: precision not supported by this entry point");
+    return REVO_ENOTSUP;
+  }
+  if (K % 64 || N % 32) {
+    set_last_error("revo_op_linear: BF16 path needs K %% 64 == 0 and N %% 32 == 0");
+    return REVO_EINVAL;
+  }
+  const int bn = tile_n == 256 ? 256 : 128;
+  CUtensorMap ma, mb;
+  if (!encode_tmap_bf16_2d(&ma, A, M > 0 ? M : 1, K, K, 128, 64) || !encode_tmap_bf16_2d(&mb, W, N, K, K, bn, 64)) {
+    set_last_error("revo_op_linear: tensor map encoding failed (alignment?)");
+    return REVO_EINVAL;
+  }
+  int* err = op_error_word();
+  if (!err) {
+    set_last_error("revo_op_linear: no device error word");
+    return REVO_ECUDA;
+  }
+  return cuda_status(launch_gemm_tc(ma, mb, bn, epilogue, bias, out, N, M, N, K, err, device_sm_count(), st),
+                     "revo_op_linear");
+}
+
+revo_status revo_op_layernorm(const float* x, const float* gamma, const float* beta, void* out, int M, int D,
+                              int out_bf16, void* stream) {
+  if (!x || !gamma || !beta || !out || M < 0 || D <= 0) {
+    set_last_error("revo_op_layernorm: bad argument");
+    return REVO_EINVAL;
+  }
+  return cuda_status(launch_layernorm(x, gamma, beta, out, M, D, out_bf16, static_cast<cudaStream_t>(stream)),
+                     "revo_op_layernorm");
+}
+
+revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D, int heads,
+                              const int* seg_start, int n_seg, void* stream) {
+  if (!qkv || !out || !seg_start || n_seg <= 0 || n_seg > kMaxSegments || heads <= 0 || D != 64 * heads) {
+    set_last_error("revo_op_attention: bad argument (head width must be 64, n_seg <= 64)");
+    return REVO_EINVAL;
+  }
+  Segments seg{};
+  seg.n = n_seg;
+  for (int i = 0; i <= n_seg; ++i) {
+    seg.start[i] = seg_start[i];
+    if (seg.start[i] < 0 || seg.start[i] > M || (i && seg.start[i] < seg.start[i - 1])) {
+      set_last_error("revo_op_attention: segment bounds not increasing within [0, M]");
+      return REVO_EINVAL;
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (precision == REVO_FP32)
+    return cuda_status(
+        launch_attention_simt(static_cast<const float*>(qkv), static_cast<float*>(out), M, D, heads, seg, st),
+        "revo_op_attention");
+  if (precision != REVO_BF16) {
+    set_last_error("revo_op_attention: precision not supported");
+    return REVO_ENOTSUP;
+  }
+  CUtensorMap m;
+  if (!encode_attention_tmap(&m, qkv, M > 0 ? M : 1, D)) {
+    set_last_error("revo_op_attention: tensor map encoding failed");
+    return REVO_EINVAL;
+  }
+  int* err = op_error_word();
+  if (!err) return REVO_ECUDA;
+  return cuda_status(launch_attention_tc(m, out, M, D, heads, seg, err, st), "revo_op_attention");
+}
+
+revo_status revo_op_add_position(float* x, int slots, int grid_h, int grid_w, int D, const int* taus, void* stream) {
+  if (!x || !taus || slots < 0 || slots > 8 || grid_h < 0 || grid_w < 0 || D % 6) {
+    set_last_error("revo_op_add_position: bad argument");
+    return REVO_EINVAL;
+  }
+  return cuda_status(launch_add_pe(x, grid_h, grid_w, slots, taus, D, static_cast<cudaStream_t>(stream)),
+                     "revo_op_add_position");
+}
+
+revo_status revo_op_blend(int channels, int p, int height, int width, const float* head, const void* decoded,
+                          size_t pitch_bytes, const uint32_t* mask, size_t mask_pitch_words, const float* mu_sigma,
+                          void* out, size_t out_pitch, float* values, void* stream) {
+  if (!head || !decoded || !mask || !out || (channels == 1 && !mu_sigma) ||
+      mask_pitch_words < static_cast<size_t>((width + 31) / 32)) {
+    set_last_error("revo_op_blend: bad argument");
+    return REVO_EINVAL;
+  }
+  BlendArgs a{};
+  a.C = channels;
+  a.p = p;
+  a.H = height;
+  a.W = width;
+  a.head = head;
+  a.decoded = decoded;
+  a.pitch = pitch_bytes;
+  a.mask = mask;
+  a.mask_pitch = mask_pitch_words;
+  a.mu_sigma = mu_sigma;
+  a.out = out;
+  a.out_pitch = out_pitch;
+  a.values = values;
+  return cuda_status(launch_blend(a, static_cast<cudaStream_t>(stream)), "revo_op_blend");
+}
+
+}  // extern "C"

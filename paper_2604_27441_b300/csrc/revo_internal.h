@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "revo.h"
+
 namespace revo {
 
 // GEMM epilogues (Y = A W^T + b, then):
@@ -81,5 +83,9 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st);
 cudaError_t launch_f32_to_bf16(const float* in, void* out, size_t n, cudaStream_t st);
 
 int device_sm_count();
+
+// ---- errors
+void set_last_error(const char* fmt, ...);
+revo_status cuda_status(cudaError_t e, const char* what);
 
 }  // namespace revo

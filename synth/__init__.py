@@ -142,6 +142,11 @@ def flatten(w: "OrderedDict[str, np.ndarray]") -> np.ndarray:
     return np.concatenate([np.ascontiguousarray(a, dtype=np.float32).ravel() for a in w.values()])
 
 
+def normal(seed: int, shape, scale: float = 1.0, dtype=np.float32) -> np.ndarray:
+    """Seeded i.i.d. N(0, scale^2) array, for step-level checks."""
+    return (np.random.default_rng(seed).normal(0.0, scale, size=shape)).astype(dtype)
+
+
 # --------------------------------------------------------------------------
 # Frames
 # --------------------------------------------------------------------------

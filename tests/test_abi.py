@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads, exports every symbol include/revo.h
+declares, and validates arguments on the host (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2604_27441_b300 as R
+from paper_2604_27441_b300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(R.LIB_PATH):
+        B.build()
+    return R.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "revo.h")).read()
+    return sorted(set(re.findall(r"^REVO_API\s+[\w\s\*]*?\b(revo_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_four_recovery_calls():
+    syms = declared_symbols()
+    for name in ("revo_recover_create", "revo_recover_submit", "revo_recover_poll", "revo_recover_destroy"):
+        assert name in syms
+    assert len(syms) >= 16
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_config_default_is_the_vit_b_reading(lib):
+    cfg = R.config()
+    assert (cfg.k, cfg.tubelet, cfg.patch) == (5, 2, 16)
+    assert (cfg.enc_dim, cfg.enc_depth, cfg.enc_heads) == (768, 12, 12)
+    assert (cfg.dec_dim, cfg.dec_depth, cfg.dec_heads, cfg.mlp_ratio) == (384, 4, 6, 4)
+    assert cfg.precision == R.BF16 and cfg.max_batch == 1 and cfg.lanes == 1
+
+
+def test_struct_layouts_match_the_header(lib, tmp_path):
+    """The binding's ctypes structs have the C compiler's sizes and offsets."""
+    src = tmp_path / "layout.c"
+    fields = {"revo_config": R.Config, "revo_plane": R.Plane, "revo_request": R.Request, "revo_result": R.Result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "revo.h"', "int main(void) {"]
+    for cname, py in fields.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                                check=True).stdout.split("\n") if line)
+    for cname, py in fields.items():
+        assert int(out[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(out[f"{cname}.{f}"]) == getattr(py, f).offset, f"{cname}.{f}"
+
+
+def test_null_arguments_are_rejected_before_any_device_work(lib):
+    assert lib.revo_op_linear(R.FP32, 0, None, None, None, None, 4, 4, 8, 0, None) == R.REVO_EINVAL
+    assert lib.revo_op_layernorm(None, None, None, None, 4, 8, 0, None) == R.REVO_EINVAL
+    seg = (C.c_int * 2)(0, 4)
+    assert lib.revo_op_attention(R.FP32, None, None, 4, 64, 1, seg, 1, None) == R.REVO_EINVAL
+    assert lib.revo_op_attention(R.FP32, 1, 1, 4, 96, 1, seg, 1, None) == R.REVO_EINVAL  # head width 96
+    assert lib.revo_op_depth_stats(None, 4, 4, 8, None, None, None) == R.REVO_EINVAL
+    assert "bad argument" in R.last_error() or R.last_error()
+    h = C.c_void_p()
+    assert lib.revo_recover_create(None, C.byref(h)) == R.REVO_EINVAL
+    assert lib.revo_recover_submit(None, None, None) == R.REVO_EINVAL
+    assert lib.revo_recover_poll(None, 1, 0, None) == R.REVO_EINVAL
+    lib.revo_recover_destroy(None)
+
+
+def test_bad_config_is_rejected(lib):
+    cfg = R.config(max_batch=0)
+    h = C.c_void_p()
+    assert lib.revo_recover_create(C.byref(cfg), C.byref(h)) == R.REVO_EINVAL
+    assert h.value is None
+    cfg = R.config()  # no weights
+    assert lib.revo_recover_create(C.byref(cfg), C.byref(h)) == R.REVO_EINVAL
+
+
+def test_depth_stats_scratch_is_small(lib):
+    n = R.depth_stats_scratch_bytes()
+    assert 0 < n < 64 * 1024

@@ -1,0 +1,236 @@
+"""Step-level parity of the CUDA kernels (through the C ABI) against the FP64
+oracle, element by element, at sizes that span several tiles and a ragged
+tail.  bf16 paths are compared with the oracle evaluated on the same
+bf16-rounded operands, so the tolerance only has to cover accumulation order
+and output rounding."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import revo_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+R = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global R
+    import paper_2604_27441_b300 as mod
+    mod.lib()
+    R = mod
+    yield
+    assert R.take_device_error() == 0
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+
+
+def f64(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+# ------------------------------------------------------------------ linear
+
+SHAPES = [(300, 256, 192, 128), (1000, 768, 768, 256), (517, 384, 128, 256), (5120, 1152, 1536, 128),
+          (3600, 2304, 768, 0), (1, 64, 64, 128), (129, 3072, 768, 256)]
+
+
+@pytest.mark.parametrize("M,N,K,bn", SHAPES)
+@pytest.mark.parametrize("epi", [0, 1, 2, 3])
+def test_linear_bf16_tcgen05(M, N, K, bn, epi):
+    seed = M * 7 + N + K
+    A = bf16(synth.normal(seed, (M, K)))
+    W = bf16(synth.normal(seed + 1, (N, K), 1.0 / np.sqrt(K)))
+    b = synth.normal(seed + 2, (N,), 0.1)
+    ref = O.linear(f64(A), f64(W), b.astype(np.float64))
+    if epi == 2:
+        ref = O.gelu(ref)
+    out_dtype = torch.float32 if epi in (0, 3) else torch.bfloat16
+    base = synth.normal(seed + 3, (M, N)) if epi == 3 else np.zeros((M, N), np.float32)
+    out = torch.from_numpy(base).to(out_dtype).cuda()
+    R.op_linear(R.BF16, epi, A.cuda(), W.cuda(), dev(b), out, M, N, K, bn)
+    torch.cuda.synchronize()
+    got = f64(out)
+    if epi == 3:
+        ref = ref + base
+    if out_dtype == torch.float32:
+        np.testing.assert_allclose(got, ref, rtol=1e-4, atol=2e-4)
+    else:
+        np.testing.assert_allclose(got, ref, rtol=8e-3, atol=8e-3)
+
+
+@pytest.mark.parametrize("M,N,K", [(300, 256, 192), (1000, 768, 768), (77, 96, 24)])
+@pytest.mark.parametrize("epi", [0, 2, 3])
+def test_linear_fp32_simt(M, N, K, epi):
+    seed = M + N * 3 + K
+    A = synth.normal(seed, (M, K))
+    W = synth.normal(seed + 1, (N, K), 1.0 / np.sqrt(K))
+    b = synth.normal(seed + 2, (N,), 0.1)
+    ref = O.linear(A.astype(np.float64), W.astype(np.float64), b.astype(np.float64))
+    if epi == 2:
+        ref = O.gelu(ref)
+    base = synth.normal(seed + 3, (M, N)) if epi == 3 else np.zeros((M, N), np.float32)
+    out = dev(base)
+    R.op_linear(R.FP32, epi, dev(A), dev(W), dev(b), out, M, N, K)
+    torch.cuda.synchronize()
+    if epi == 3:
+        ref = ref + base
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5, atol=2e-5)
+
+
+# --------------------------------------------------------------- layernorm
+
+@pytest.mark.parametrize("M,D", [(333, 768), (1000, 384), (1, 192)])
+@pytest.mark.parametrize("out_bf16", [0, 1])
+def test_layernorm(M, D, out_bf16):
+    x = synth.normal(M + D, (M, D), 3.0) + 0.5
+    g = 1 + synth.normal(M + D + 1, (D,), 0.1)
+    b = synth.normal(M + D + 2, (D,), 0.1)
+    out = torch.zeros((M, D), dtype=torch.bfloat16 if out_bf16 else torch.float32, device="cuda")
+    R.op_layernorm(dev(x), dev(g), dev(b), out, M, D, out_bf16)
+    torch.cuda.synchronize()
+    ref = O.layer_norm(x.astype(np.float64), g.astype(np.float64), b.astype(np.float64))
+    if out_bf16:
+        np.testing.assert_allclose(f64(out), ref, rtol=8e-3, atol=8e-3)
+    else:
+        np.testing.assert_allclose(f64(out), ref, rtol=0, atol=5e-5)
+
+
+# --------------------------------------------------------------- attention
+
+def _oracle_segments(qkv, heads, seg):
+    out = np.zeros((qkv.shape[0], qkv.shape[1] // 3))
+    for a, b in zip(seg[:-1], seg[1:]):
+        if b > a:
+            out[a:b] = O.attention(qkv[a:b], heads)
+    return out
+
+
+ATT_CASES = [((0, 300, 1000), 2), ((0, 5, 5, 133, 900), 3), ((0, 3600), 12), ((0, 128, 256), 1),
+             ((0, 900, 1800, 2700), 6)]
+
+
+@pytest.mark.parametrize("seg,heads", ATT_CASES)
+def test_attention_bf16_tcgen05(seg, heads):
+    M, D = seg[-1], 64 * heads
+    qkv = bf16(synth.normal(M + heads, (M, 3 * D)))
+    out = torch.zeros((M, D), dtype=torch.bfloat16, device="cuda")
+    R.op_attention(R.BF16, qkv.cuda(), out, M, D, heads, seg)
+    torch.cuda.synchronize()
+    ref = _oracle_segments(f64(qkv), heads, seg)
+    np.testing.assert_allclose(f64(out), ref, rtol=2e-2, atol=1.5e-2)
+
+
+@pytest.mark.parametrize("seg,heads", ATT_CASES[:2] + [((0, 700), 4)])
+def test_attention_fp32_simt(seg, heads):
+    M, D = seg[-1], 64 * heads
+    qkv = synth.normal(M * 3 + heads, (M, 3 * D))
+    out = torch.zeros((M, D), dtype=torch.float32, device="cuda")
+    R.op_attention(R.FP32, dev(qkv), out, M, D, heads, seg)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.cpu().numpy(), _oracle_segments(qkv.astype(np.float64), heads, seg),
+                               rtol=0, atol=2e-5)
+
+
+# --------------------------------------------------- assemble / statistics
+
+@pytest.mark.parametrize("modality,k", [("rgb", 5), ("depth", 5), ("rgb", 1), ("depth", 3)])
+@pytest.mark.parametrize("out_bf16", [0, 1])
+def test_assemble(modality, k, out_bf16):
+    H, W, T, p = 48, 80, 2, 16
+    pl = synth.make_tiny_plane(k * 11 + len(modality), modality, H, W, k)
+    C = 3 if modality == "rgb" else 1
+    if modality == "rgb":
+        frames = np.stack([O.normalise_rgb(f) for f in pl.refs] + [O.normalise_rgb(pl.decoded)])
+        mu_sigma = None
+        pitch = W * 3
+    else:
+        mu, sg = O.depth_stats(pl.refs[-1])
+        frames = np.stack([O.normalise_depth(f, mu, sg) for f in pl.refs] + [O.normalise_depth(pl.decoded, mu, sg)])
+        mu_sigma = dev(np.array([mu, sg], np.float32))
+        pitch = W * 2
+    ref = O.tubelets(frames, T, p)
+    refs_d = [dev(f) for f in pl.refs]
+    out = torch.zeros(ref.shape, dtype=torch.bfloat16 if out_bf16 else torch.float32, device="cuda")
+    R.op_assemble(C, k, T, p, H, W, refs_d, dev(pl.decoded), pitch, mu_sigma, out, out_bf16)
+    torch.cuda.synchronize()
+    if out_bf16:
+        np.testing.assert_allclose(f64(out), ref, rtol=8e-3, atol=1e-6)
+    else:
+        np.testing.assert_allclose(f64(out), ref, rtol=2e-6, atol=2e-6)
+
+
+@pytest.mark.parametrize("case", ["synthetic", "zeros", "constant", "two_values"])
+def test_depth_stats(case):
+    if case == "synthetic":
+        _, dep = synth.make_request(3003, "1280x720+640x576")
+        d = dep.refs[-1]
+    elif case == "zeros":
+        d = np.zeros((480, 640), np.uint16)
+    elif case == "constant":
+        d = np.full((240, 320), 1234, np.uint16)
+        d[::7, ::5] = 0
+    else:
+        d = np.zeros((16, 64), np.uint16)
+        d[:, ::2] = 1000
+        d[:, 1::4] = 3000
+    H, W = d.shape
+    ms = torch.zeros(2, dtype=torch.float32, device="cuda")
+    scratch = torch.zeros(R.depth_stats_scratch_bytes(), dtype=torch.uint8, device="cuda")
+    for _ in range(2):   # the scratch is reused: the second call must give the same answer
+        R.op_depth_stats(dev(d), H, W, W * 2, ms, scratch)
+        torch.cuda.synchronize()
+        mu, sg = O.depth_stats(d)
+        got = ms.cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(got, [mu, sg], rtol=2e-6, atol=0)
+
+
+@pytest.mark.parametrize("D,hp,wp,taus", [(768, 15, 20, (5, 3, 1)), (384, 45, 80, (7, 5, 3)), (192, 2, 3, (1,))])
+def test_position_embedding(D, hp, wp, taus):
+    S = len(taus)
+    x = torch.zeros((S * hp * wp, D), dtype=torch.float32, device="cuda")
+    R.op_add_position(x, S, hp, wp, D, list(taus))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(x.cpu().numpy(), O.position_embedding(list(taus), hp, wp, D), rtol=0, atol=2e-5)
+
+
+# -------------------------------------------------------------------- blend
+
+@pytest.mark.parametrize("modality,H,W", [("rgb", 48, 80), ("depth", 64, 48), ("rgb", 240, 320)])
+def test_blend_codes_bit_exact(modality, H, W):
+    """Received pixels are copied bit for bit; lost pixels carry the float32
+    de-normalise + round-half-even + clamp code exactly."""
+    C, p = (3, 16) if modality == "rgb" else (1, 16)
+    pl = synth.make_tiny_plane(H + W, modality, H, W, 1)
+    Hp, Wp = H // p, W // p
+    head = synth.normal(H * W, (Hp * Wp, C * p * p), 1.5 if modality == "rgb" else 0.8)
+    y = O.untubelet_frame(head.astype(np.float64), C, 1, p, Hp, Wp, 0).astype(np.float32)  # [C, H, W]
+    if modality == "rgb":
+        vals = O.denormalise_rgb(y, np.float32)
+        codes = O.quantise_rgb(vals, np.float32)
+        ms = None
+        pitch = W * 3
+    else:
+        mu, sg = 2500.0, 700.0
+        vals = O.denormalise_depth(y, mu, sg, np.float32)
+        codes = O.quantise_depth(vals, np.float32)
+        ms = dev(np.array([mu, sg], np.float32))
+        pitch = W * 2
+    expect = O.blend(pl.decoded, O.unpack_mask(pl.mask, W), codes)
+    out = torch.zeros(pl.decoded.shape, dtype=torch.uint8 if modality == "rgb" else torch.int16, device="cuda")
+    values = torch.zeros(vals.shape, dtype=torch.float32, device="cuda")
+    R.op_blend(C, p, H, W, dev(head), dev(pl.decoded), pitch, dev(pl.mask), pl.mask.shape[1], ms, out, pitch,
+               values)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint8 if modality == "rgb" else np.uint16)
+    np.testing.assert_array_equal(got, expect)
+    np.testing.assert_array_equal(got[~pl.lost], pl.decoded[~pl.lost])
+    np.testing.assert_array_equal(values.cpu().numpy(), vals)

@@ -1,0 +1,286 @@
+"""End-to-end parity of revo_recover_create/submit/poll/destroy with the FP64
+oracle on seeded synthetic RGB-D frames.
+
+Tolerances on the de-normalised float outputs (every pixel of the network
+output, before the blend):
+  FP32 path: max |error| <= 1e-4 on [0, 1] RGB and <= 1 mm on depth;
+  BF16 path: PSNR >= 45 dB on [0, 1] RGB and on depth / 65535, max depth
+             error <= 8 mm.
+Blended codes: received pixels bit-exact; lost pixels within one code of the
+oracle's and equal wherever the oracle's value is farther than the tolerance
+from a rounding boundary.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import revo_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+R = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global R
+    import paper_2604_27441_b300 as mod
+    mod.lib()
+    R = mod
+
+
+SMALL = dict(k=5, tubelet=2, patch=16, enc_dim=192, enc_depth=2, enc_heads=3, dec_dim=192, dec_depth=1,
+             dec_heads=3, mlp_ratio=4)
+VITB = dict(k=5, tubelet=2, patch=16, enc_dim=768, enc_depth=12, enc_heads=12, dec_dim=384, dec_depth=4,
+            dec_heads=6, mlp_ratio=4)
+
+
+def model_cfg(shape, C):
+    return synth.ModelConfig(channels=C, k=shape["k"], tubelet=shape["tubelet"], patch=shape["patch"],
+                             enc_dim=shape["enc_dim"], enc_depth=shape["enc_depth"], enc_heads=shape["enc_heads"],
+                             dec_dim=shape["dec_dim"], dec_depth=shape["dec_depth"], dec_heads=shape["dec_heads"],
+                             mlp_ratio=shape["mlp_ratio"])
+
+
+_WEIGHTS = {}
+
+
+def weights(shape, C):
+    key = (tuple(sorted(shape.items())), C)
+    if key not in _WEIGHTS:
+        _WEIGHTS[key] = synth.weights(model_cfg(shape, C), seed=0 if C == 3 else 1)
+    return _WEIGHTS[key]
+
+
+def make_ctx(shape, precision, max_hw, max_batch=1, lanes=1, max_streams=4):
+    w_rgb = synth.flatten(weights(shape, 3))
+    w_dep = synth.flatten(weights(shape, 1))
+    cfg = R.config(**shape, precision=precision, max_height=max_hw[0], max_width=max_hw[1], max_batch=max_batch,
+                   lanes=lanes, max_streams=max_streams)
+    return R.Context(cfg, w_rgb, w_dep)
+
+
+def push_refs(ctx, sid, rgb, dep, on_device=True):
+    keep = []
+    for j in range(rgb.refs.shape[0]):
+        fr, fd = rgb.refs[j], dep.refs[j]
+        if on_device:
+            fr, fd = torch.from_numpy(fr).cuda(), torch.from_numpy(fd.view(np.int16)).cuda()
+        keep += [fr, fd]
+        req = R.request(sid, int(rgb.ref_index[j]), R.RGB | R.DEPTH | R.CLEAN, on_device=on_device,
+                        rgb=(fr, rgb.height, rgb.width), depth=(fd, dep.height, dep.width))
+        ctx.poll(ctx.submit(req))
+    return keep
+
+
+class Outputs:
+    def __init__(self, rgb, dep, on_device=True):
+        self.on_device = on_device
+        if on_device:
+            self.rgb_in = torch.from_numpy(rgb.decoded).cuda()
+            self.dep_in = torch.from_numpy(dep.decoded.view(np.int16)).cuda()
+            self.rgb_mask = torch.from_numpy(rgb.mask.view(np.int32)).cuda()
+            self.dep_mask = torch.from_numpy(dep.mask.view(np.int32)).cuda()
+            self.rgb_out = torch.zeros(rgb.decoded.shape, dtype=torch.uint8, device="cuda")
+            self.dep_out = torch.zeros(dep.decoded.shape, dtype=torch.int16, device="cuda")
+            self.rgb_val = torch.zeros(rgb.decoded.shape, dtype=torch.float32, device="cuda")
+            self.dep_val = torch.zeros(dep.decoded.shape, dtype=torch.float32, device="cuda")
+        else:
+            self.rgb_in, self.dep_in = rgb.decoded, dep.decoded
+            self.rgb_mask, self.dep_mask = rgb.mask, dep.mask
+            self.rgb_out = np.zeros(rgb.decoded.shape, np.uint8)
+            self.dep_out = np.zeros(dep.decoded.shape, np.uint16)
+            self.rgb_val = np.zeros(rgb.decoded.shape, np.float32)
+            self.dep_val = np.zeros(dep.decoded.shape, np.float32)
+
+    def request(self, sid, rgb, dep):
+        return R.request(sid, rgb.index, R.RGB | R.DEPTH, on_device=self.on_device,
+                         rgb=(self.rgb_in, rgb.height, rgb.width), rgb_mask=self.rgb_mask,
+                         depth=(self.dep_in, dep.height, dep.width), depth_mask=self.dep_mask,
+                         rgb_out=self.rgb_out, depth_out=self.dep_out, rgb_values=self.rgb_val,
+                         depth_values=self.dep_val)
+
+    def numpy(self):
+        def cv(t):
+            return t.cpu().numpy() if isinstance(t, torch.Tensor) else t
+        return (cv(self.rgb_out), cv(self.dep_out).view(np.uint16), cv(self.rgb_val), cv(self.dep_val))
+
+
+def run(ctx, sid, rgb, dep, on_device=True):
+    keep = push_refs(ctx, sid, rgb, dep, on_device)
+    o = Outputs(rgb, dep, on_device)
+    res = ctx.poll(ctx.submit(o.request(sid, rgb, dep)))
+    assert res.status == R.REVO_OK
+    del keep
+    return o.numpy()
+
+
+_ORACLE = {}
+
+
+def oracle(shape, rgb, dep, key):
+    if key not in _ORACLE:
+        out = []
+        for mod, pl, C in (("rgb", rgb, 3), ("depth", dep, 1)):
+            out.append(O.recover(mod, weights(shape, C), model_cfg(shape, C), pl.refs, pl.ref_index, pl.decoded,
+                                 pl.mask, pl.index))
+        _ORACLE[key] = out
+    return _ORACLE[key]
+
+
+def psnr(err, peak):
+    mse = float(np.mean(np.square(err)))
+    return np.inf if mse == 0 else 10 * np.log10(peak * peak / mse)
+
+
+def check(precision, got, ref, rgb, dep, report=None):
+    g_rgb, g_dep, v_rgb, v_dep = got
+    (c_rgb, o_rgb), (c_dep, o_dep) = ref
+    e_rgb = v_rgb.astype(np.float64) - o_rgb
+    e_dep = v_dep.astype(np.float64) - o_dep
+    stats = dict(rgb_max=float(np.abs(e_rgb).max()), dep_max_mm=float(np.abs(e_dep).max()),
+                 rgb_psnr=psnr(e_rgb, 1.0), dep_psnr=psnr(e_dep / 65535.0, 1.0),
+                 rgb_psnr_lost=psnr(e_rgb[rgb.lost], 1.0) if rgb.lost.any() else np.inf)
+    if report is not None:
+        report.update(stats)
+    if precision == R.FP32:
+        tol_rgb, tol_dep = 1e-4, 1.0
+        assert stats["rgb_max"] <= tol_rgb, stats
+        assert stats["dep_max_mm"] <= tol_dep, stats
+    else:
+        tol_rgb, tol_dep = None, 8.0
+        assert stats["rgb_psnr"] >= 45.0, stats
+        assert stats["dep_psnr"] >= 45.0, stats
+        assert stats["dep_max_mm"] <= tol_dep, stats
+    # Blended codes.
+    for g, c, o, pl, scale, tol in ((g_rgb, c_rgb, o_rgb, rgb, 255.0, e_rgb), (g_dep, c_dep, o_dep, dep, 1.0, e_dep)):
+        np.testing.assert_array_equal(g[~pl.lost], pl.decoded[~pl.lost])
+        lost = pl.lost
+        d = np.abs(g.astype(np.int64) - c.astype(np.int64))
+        assert d[lost].max(initial=0) <= 1
+        # away from a rounding boundary (by more than the observed error) the codes agree exactly
+        frac = np.abs((o * scale) - np.floor(o * scale) - 0.5)
+        margin = np.abs(tol) * scale + 1e-6
+        safe = lost & (frac > margin)
+        if o.ndim == 3:
+            safe = lost[..., None] & (frac > margin)
+            np.testing.assert_array_equal(g[safe], c[safe])
+        else:
+            np.testing.assert_array_equal(g[safe], c[safe])
+    return stats
+
+
+# ------------------------------------------------------------------ tests
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_small_network_parity(precision):
+    rgb, dep = synth.make_request(11, "320x240")
+    rgb = synth.make_tiny_plane(21, "rgb", 64, 96, 5)
+    dep = synth.make_tiny_plane(22, "depth", 64, 96, 5)
+    with make_ctx(SMALL, precision, (64, 96)) as ctx:
+        got = run(ctx, 0, rgb, dep)
+    check(precision, got, oracle(SMALL, rgb, dep, "small"), rgb, dep)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vitb_320x240_parity(precision):
+    rgb, dep = synth.make_request(1001, "320x240")
+    with make_ctx(VITB, precision, (240, 320)) as ctx:
+        got = run(ctx, 0, rgb, dep)
+    check(precision, got, oracle(VITB, rgb, dep, "320"), rgb, dep)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_vitb_640x480_parity(precision):
+    rgb, dep = synth.make_request(2001, "640x480", loss_rate=0.2)
+    with make_ctx(VITB, precision, (480, 640)) as ctx:
+        got = run(ctx, 0, rgb, dep)
+    check(precision, got, oracle(VITB, rgb, dep, "640"), rgb, dep)
+
+
+def test_host_buffers_match_device_buffers():
+    rgb, dep = synth.make_request(1002, "320x240")
+    with make_ctx(VITB, R.BF16, (240, 320)) as ctx:
+        a = run(ctx, 0, rgb, dep, on_device=True)
+        b = run(ctx, 1, rgb, dep, on_device=False)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_batch_result_equals_alone():
+    """Requests fused into one launch give exactly what each gives alone."""
+    reqs = [synth.make_request(1003, "320x240"), synth.make_request(2003, "640x480", loss_rate=0.1),
+            synth.make_request(1004, "320x240")]
+    alone = []
+    with make_ctx(VITB, R.BF16, (480, 640), max_streams=4) as ctx:
+        for sid, (rgb, dep) in enumerate(reqs):
+            alone.append(run(ctx, sid, rgb, dep))
+    with make_ctx(VITB, R.BF16, (480, 640), max_batch=3, max_streams=4) as ctx:
+        keep = [push_refs(ctx, sid, rgb, dep) for sid, (rgb, dep) in enumerate(reqs)]
+        outs = [Outputs(rgb, dep) for rgb, dep in reqs]
+        # hold the lane busy so all three are admitted into one batch
+        tickets = [ctx.submit(o.request(sid, *reqs[sid])) for sid, o in enumerate(outs)]
+        ctx.flush()
+        sizes = [ctx.poll(t).batch_size for t in tickets]
+        del keep
+    assert max(sizes) >= 2
+    for a, o in zip(alone, outs):
+        for x, y in zip(a, o.numpy()):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_two_lanes_interleaved_streams():
+    reqs = [synth.make_request(1010 + i, "320x240") for i in range(4)]
+    alone = []
+    with make_ctx(VITB, R.BF16, (240, 320)) as ctx:
+        for sid, (rgb, dep) in enumerate(reqs):
+            alone.append(run(ctx, sid, rgb, dep))
+    with make_ctx(VITB, R.BF16, (240, 320), max_batch=2, lanes=2) as ctx:
+        keep = [push_refs(ctx, sid, rgb, dep) for sid, (rgb, dep) in enumerate(reqs)]
+        outs = [Outputs(rgb, dep) for rgb, dep in reqs]
+        tickets = [ctx.submit(o.request(sid, *reqs[sid])) for sid, o in enumerate(outs)]
+        for t in tickets[::-1]:
+            assert ctx.poll(t).status == R.REVO_OK
+        del keep
+    for a, o in zip(alone, outs):
+        for x, y in zip(a, o.numpy()):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_temporal_distance_reaches_the_network():
+    """Same references at a larger distance to the target (Section 3.4.1) give
+    another output, matching the oracle's."""
+    rgb, dep = synth.make_request(1005, "320x240", index=100, delta=3)
+    with make_ctx(SMALL, R.FP32, (240, 320)) as ctx:
+        got = run(ctx, 0, rgb, dep)
+    check(R.FP32, got, oracle(SMALL, rgb, dep, "delta3"), rgb, dep)
+    rgb1, dep1 = synth.make_request(1005, "320x240", index=100, delta=1)
+    assert not np.array_equal(rgb1.ref_index, rgb.ref_index)
+
+
+def test_error_statuses():
+    rgb, dep = synth.make_request(1006, "320x240")
+    with make_ctx(SMALL, R.BF16, (240, 320)) as ctx:
+        o = Outputs(rgb, dep)
+        with pytest.raises(R.RevoError) as ei:
+            ctx.submit(o.request(0, rgb, dep))
+        assert ei.value.status == R.REVO_ENOREF
+        with pytest.raises(R.RevoError) as ei:
+            ctx.poll(12345, 0)
+        assert ei.value.status == R.REVO_EINVAL
+        keep = push_refs(ctx, 0, rgb, dep)
+        small = synth.make_tiny_plane(3, "rgb", 64, 96, 5)
+        req = R.request(0, 200, R.RGB, on_device=True, rgb=(o.rgb_in, 64, 96), rgb_mask=o.rgb_mask,
+                        rgb_out=o.rgb_out)
+        with pytest.raises(R.RevoError) as ei:
+            ctx.submit(req)   # frame size differs from the stream's references
+        assert ei.value.status == R.REVO_EINVAL
+        req = R.request(9, 200, R.RGB, on_device=True, rgb=(o.rgb_in, 240, 320), rgb_mask=o.rgb_mask,
+                        rgb_out=o.rgb_out)
+        with pytest.raises(R.RevoError) as ei:
+            ctx.submit(req)   # stream id beyond max_streams
+        assert ei.value.status == R.REVO_EINVAL
+        t = ctx.submit(o.request(0, rgb, dep))
+        assert ctx.poll(t).status == R.REVO_OK
+        del keep, small
