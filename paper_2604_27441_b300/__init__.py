@@ -121,8 +121,12 @@ def ptr(x) -> int | None:
     if isinstance(x, int):
         return x
     if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous (the C ABI takes row-major buffers)")
         return x.data_ptr()
     if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous (the C ABI takes row-major buffers)")
         return x.ctypes.data
     raise TypeError(f"cannot take the address of {type(x)}")
 

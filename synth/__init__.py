@@ -157,7 +157,7 @@ def _shift(img: np.ndarray, dx: int, dy: int) -> np.ndarray:
     H, W = img.shape[:2]
     ys = np.clip(np.arange(H) - dy, 0, H - 1)
     xs = np.clip(np.arange(W) - dx, 0, W - 1)
-    return img[ys][:, xs]
+    return np.ascontiguousarray(img[ys][:, xs])
 
 
 def rgb_frame(rng: np.random.Generator, H: int, W: int) -> np.ndarray:
@@ -300,7 +300,7 @@ def _history(rng: np.random.Generator, cur: np.ndarray, k: int) -> np.ndarray:
         dx += int(rng.integers(-3, 4))
         dy += int(rng.integers(-3, 4))
         refs.append(_shift(cur, dx, dy))
-    return np.stack(refs[::-1])
+    return np.ascontiguousarray(np.stack(refs[::-1]))
 
 
 def make_plane(rng: np.random.Generator, modality: str, H: int, W: int, k: int,
@@ -318,8 +318,14 @@ def make_plane(rng: np.random.Generator, modality: str, H: int, W: int, k: int,
     decoded = cur.copy()
     decoded[lost] = 0
     ref_index = np.arange(index - delta - k + 1, index - delta + 1, dtype=np.int64)
-    return Plane(refs=refs, ref_index=ref_index, clean=cur, decoded=decoded, lost=lost,
-                 mask=pack_mask(lost), index=index)
+    return _plane(refs, ref_index, cur, decoded, lost, index)
+
+
+def _plane(refs, ref_index, cur, decoded, lost, index) -> Plane:
+    # Every array C-contiguous: the C ABI takes raw row-major pointers.
+    c = np.ascontiguousarray
+    return Plane(refs=c(refs), ref_index=c(ref_index), clean=c(cur), decoded=c(decoded), lost=c(lost),
+                 mask=c(pack_mask(lost)), index=index)
 
 
 # Workloads shaped like the paper's (face-cropped RGB-D conference frames).
@@ -370,5 +376,4 @@ def make_tiny_plane(seed: int, modality: str, H: int, W: int, k: int, lost_rows=
     decoded = cur.copy()
     decoded[lost] = 0
     ref_index = np.arange(index - delta - k + 1, index - delta + 1, dtype=np.int64)
-    return Plane(refs=refs, ref_index=ref_index, clean=cur, decoded=decoded, lost=lost,
-                 mask=pack_mask(lost), index=index)
+    return _plane(refs, ref_index, cur, decoded, lost, index)

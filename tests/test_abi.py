@@ -93,3 +93,19 @@ def test_bad_config_is_rejected(lib):
 def test_depth_stats_scratch_is_small(lib):
     n = R.depth_stats_scratch_bytes()
     assert 0 < n < 64 * 1024
+
+
+def test_binding_refuses_non_contiguous_buffers():
+    import numpy as np
+    a = np.zeros((4, 6, 3), np.uint8)
+    assert R.ptr(a) == a.ctypes.data
+    with pytest.raises(ValueError):
+        R.ptr(a.transpose(1, 0, 2))
+
+
+def test_synthetic_frames_are_row_major():
+    import synth
+    rgb, dep = synth.make_request(1, "320x240")
+    for pl in (rgb, dep, synth.make_tiny_plane(5, "rgb", 48, 80, 5)):
+        for name in ("refs", "decoded", "mask", "clean", "lost"):
+            assert getattr(pl, name).flags["C_CONTIGUOUS"], name
