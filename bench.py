@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the ReVo neural loss-recovery hot path on B300.
+
+One step = recovery of one corrupted RGB-D frame (640x480 RGB uint8 +
+640x480 depth uint16, batch 1): tubelet assembly + normalisation, the ViT-B
+encoder-decoder forward of both modality models (run concurrently on two CUDA
+streams), the pixel head and the masked blend, through the library's C ABI
+(revo_recover_submit + revo_recover_poll).  Four conference streams, one per
+Gilbert-Elliott slice-loss rate (5/10/20/40 %), each with five clean
+references resident on the device, take turns.  Random-init weights and
+seeded synthetic frames.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "recovered RGB-D frames/s + p99 latency, BF16/FP8 vs FP32, at ≥45 dB vs FP64 oracle"
+UNIT = "frames/s"
+WORKLOAD = "640x480"
+H, W = 480, 640
+LOSS_RATES = (0.05, 0.10, 0.20, 0.40)
+VITB = dict(k=5, tubelet=2, patch=16, enc_dim=768, enc_depth=12, enc_heads=12, dec_dim=384, dec_depth=4,
+            dec_heads=6, mlp_ratio=4)
+FRAME_BUDGET_MS = 33.0
+
+
+def flops_per_model(C: int, h: int, w: int) -> dict:
+    """Algorithmic FLOPs of one forward (2 per multiply-add), exact savings applied:
+    the pixel head runs on the target frame's rows of the last slot only."""
+    k, T, p, D, L, Dd, Ld, r = 5, 2, 16, 768, 12, 384, 4, 4
+    P = (h // p) * (w // p)
+    N = (k + 1) // T * P
+    Kt = T * C * p * p
+    lin = 2 * N * Kt * D
+    lin += L * 2 * N * (3 * D * D + D * D + 2 * r * D * D)
+    lin += 2 * N * D * Dd
+    lin += Ld * 2 * N * (3 * Dd * Dd + Dd * Dd + 2 * r * Dd * Dd)
+    lin += 2 * P * Dd * (C * p * p)
+    attn_enc = 4 * N * N * D
+    attn_dec = 4 * N * N * Dd
+    return dict(N=N, linear=lin, attn_enc_per_block=attn_enc, attn=L * attn_enc + Ld * attn_dec,
+                total=lin + L * attn_enc + Ld * attn_dec)
+
+
+def peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# --------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle arm --
+
+def oracle_rgb_sample(seed: int = 2002):
+    """Times the FP64 oracle recovering the RGB plane of one 640x480 frame (the
+    bounded sample); returns (seconds, the oracle's values, the plane)."""
+    import synth
+    from oracle import revo_oracle as O
+    rgb, _ = synth.make_request(seed, WORKLOAD, loss_rate=0.2)
+    w = synth.weights(synth.RGB, seed=0)
+    t0 = time.perf_counter()
+    codes, values = O.recover("rgb", w, synth.RGB, rgb.refs, rgb.ref_index, rgb.decoded, rgb.mask, rgb.index)
+    return time.perf_counter() - t0, values, rgb
+
+
+def cpu_baseline(seconds_rgb: float) -> dict:
+    f_rgb = flops_per_model(3, H, W)["total"]
+    f_dep = flops_per_model(1, H, W)["total"]
+    per_frame = seconds_rgb * (f_rgb + f_dep) / f_rgb
+    return {"value": 1.0 / per_frame, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 oracle recovering the RGB plane of one {WORKLOAD} frame "
+                      f"({seconds_rgb:.1f} s), scaled to an RGB-D frame by the FLOP ratio "
+                      f"{(f_rgb + f_dep) / f_rgb:.3f}"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import revo_oracle as O
+    import synth
+    # Each step: one oracle encoder block of the RGB model at the workload's
+    # full token count (a bounded sample); a frame costs `blocks_per_frame`
+    # such blocks by FLOP count.
+    fr = flops_per_model(3, H, W)
+    fd = flops_per_model(1, H, W)
+    N, D = fr["N"], 768
+    block_flops = 2 * N * (3 * D * D + D * D + 8 * D * D) + fr["attn_enc_per_block"]
+    blocks_per_frame = (fr["total"] + fd["total"]) / block_flops
+    cfg = synth.RGB
+    w = {n: a.astype(np.float64) for n, a in synth.weights(cfg, seed=0).items() if n.startswith("enc.0.")}
+    x = synth.normal(7, (N, D)).astype(np.float64)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.block(x, w, "enc.0.", cfg.enc_heads)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    per_frame = statistics.mean(times) * blocks_per_frame
+    value = 1.0 / per_frame
+    sample = (f"per step one FP64 oracle encoder block at N={N} tokens; an RGB-D frame = "
+              f"{blocks_per_frame:.2f} such blocks by FLOP count")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " RGB + " + WORKLOAD + " depth, batch 1", "model": "ViT-B enc-dec",
+                   "global_batch": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# -------------------------------------------------------------- our arm --
+
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    import paper_2604_27441_b300 as R
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    precision = R.BF16 if args.precision == "bf16" else R.FP32
+    stream = torch.cuda.Stream()
+    w_rgb = synth.flatten(synth.weights(synth.RGB, seed=0))
+    w_dep = synth.flatten(synth.weights(synth.DEPTH, seed=1))
+    cfg = R.config(**VITB, precision=precision, device=local, max_height=H, max_width=W, max_streams=8,
+                   max_batch=1, lanes=1)
+    ctx = R.Context(cfg, w_rgb, w_dep, stream=stream)
+
+    # Four conference streams (one per loss rate), references pushed once.
+    reqs = [synth.make_request(2000 + 100 * rank + i, WORKLOAD, loss_rate=r) for i, r in enumerate(LOSS_RATES)]
+    keep = []
+    dev_req, host_req, dev_bufs = [], [], []
+    for sid, (rgb, dep) in enumerate(reqs):
+        for j in range(rgb.refs.shape[0]):
+            fr = torch.from_numpy(rgb.refs[j]).cuda()
+            fd = torch.from_numpy(dep.refs[j].view(np.int16)).cuda()
+            keep += [fr, fd]
+            ctx.poll(ctx.submit(R.request(sid, int(rgb.ref_index[j]), R.RGB | R.DEPTH | R.CLEAN, on_device=True,
+                                          rgb=(fr, H, W), depth=(fd, H, W))))
+        d = dict(ri=torch.from_numpy(rgb.decoded).cuda(), di=torch.from_numpy(dep.decoded.view(np.int16)).cuda(),
+                 rm=torch.from_numpy(rgb.mask.view(np.int32)).cuda(), dm=torch.from_numpy(dep.mask.view(np.int32)).cuda(),
+                 ro=torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda"),
+                 do=torch.zeros((H, W), dtype=torch.int16, device="cuda"),
+                 rv=torch.zeros((H, W, 3), dtype=torch.float32, device="cuda"))
+        keep.append(d)
+        dev_bufs.append(d)
+        dev_req.append(R.request(sid, rgb.index, R.RGB | R.DEPTH, on_device=True, rgb=(d["ri"], H, W),
+                                 rgb_mask=d["rm"], depth=(d["di"], H, W), depth_mask=d["dm"], rgb_out=d["ro"],
+                                 depth_out=d["do"], rgb_values=d["rv"] if sid == 2 else None))
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        h = dict(ri=pin(rgb.decoded), di=pin(dep.decoded.view(np.int16)), rm=pin(rgb.mask.view(np.int32)),
+                 dm=pin(dep.mask.view(np.int32)), ro=torch.zeros((H, W, 3), dtype=torch.uint8).pin_memory(),
+                 do=torch.zeros((H, W), dtype=torch.int16).pin_memory())
+        keep.append(h)
+        host_req.append(R.request(sid, rgb.index, R.RGB | R.DEPTH, on_device=False, rgb=(h["ri"], H, W),
+                                  rgb_mask=h["rm"], depth=(h["di"], H, W), depth_mask=h["dm"], rgb_out=h["ro"],
+                                  depth_out=h["do"]))
+    h2d = H * W * 3 + H * W * 2 + 2 * H * ((W + 31) // 32) * 4
+    d2h = H * W * 3 + H * W * 2
+
+    def step(req_list, i):
+        t0 = time.perf_counter()
+        res = ctx.poll(ctx.submit(req_list[i % len(req_list)]))
+        if res.status != R.REVO_OK:
+            raise RuntimeError(f"recovery failed: {R.STATUS_NAMES.get(res.status)} {R.last_error()}")
+        return (time.perf_counter() - t0) * 1e3, res
+
+    for i in range(args.warmup):
+        step(dev_req, i)
+    torch.cuda.synchronize()
+    barrier()
+
+    # Timed region: device-resident inputs and outputs.
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat, launches = [], 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        start.record(stream)
+        for i in range(args.steps):
+            ms, res = step(dev_req, i)
+            lat.append(ms)
+            launches += res.kernel_launches
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    dev_s = start.elapsed_time(end) / 1e3
+    dev_s_max = max_over_ranks(dev_s)
+    value = world * args.steps / dev_s_max
+    clocks = clk.summary()
+
+    # End to end: host (pinned) buffers, copies inside the timed region, host clock.
+    for i in range(2):
+        step(host_req, i)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(host_req, i)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # Dominant kernel, timed alone on the same stream with CUDA events: the
+    # tcgen05 flash attention of one encoder block at N = 3600 tokens.
+    fl = flops_per_model(3, H, W)
+    N, D = fl["N"], 768
+    roof = None
+    if precision == R.BF16:
+        qkv = (torch.randn((N, 3 * D), device="cuda") * 1.0).to(torch.bfloat16)
+        out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 50
+            e0.record(stream)
+            for _ in range(reps):
+                R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        per_launch = e0.elapsed_time(e1) / 1e3 / reps
+        pk = peaks()
+        peak = pk.get("bf16_tflops")
+        achieved = fl["attn_enc_per_block"] / per_launch / 1e12
+        roof = {"kernel": "attn_tc_kernel (tcgen05 flash attention, N=3600, 12 heads x 64)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)" if peak else None,
+                "flops_per_launch": fl["attn_enc_per_block"], "us_per_launch": per_launch * 1e6}
+        assert R.take_device_error() == 0
+
+    # Quality of the timed configuration against the FP64 oracle (RGB plane of the
+    # 20 %-loss stream) + the CPU baseline from the same oracle run.
+    quality, cpu = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        secs, o_vals, pl = oracle_rgb_sample()
+        cpu = cpu_baseline(secs)
+        # stream 2 carries the 20 %-loss frame the oracle recovered (same seed)
+        err = dev_bufs[2]["rv"].cpu().numpy().astype(np.float64) - o_vals
+        mse = float(np.mean(err * err))
+        quality = {"rgb_psnr_db_vs_fp64": 10 * np.log10(1.0 / mse) if mse > 0 else float("inf"),
+                   "rgb_max_abs_err": float(np.abs(err).max()), "gate_db": 45.0}
+
+    if rank == 0:
+        lat_s = sorted(lat)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if precision == R.BF16 else "f32",
+            "data": "synthetic (seeded RGB-D frames, Gilbert-Elliott slice loss, random-init ViT-B weights)",
+            "config": {"workload": f"{WORKLOAD} RGB uint8 + {WORKLOAD} depth uint16, batch 1, "
+                                   "loss 5/10/20/40% (4 streams in turn)",
+                       "model": "ViT-B enc-dec (768x12 / 384x4), k=5, T=2, p=16", "global_batch": world,
+                       "seq_len": fl["N"], "parallelism": f"replicas x{world}",
+                       "l2": "working set > L2: bf16 weights of both models (0.37 GB) stream every step"},
+            "latency_ms": {"p50": float(np.percentile(lat_s, 50)), "p99": float(np.percentile(lat_s, 99)),
+                           "budget": FRAME_BUDGET_MS},
+            "flops_per_step": flops_per_model(3, H, W)["total"] + flops_per_model(1, H, W)["total"],
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "cpu_baseline": cpu, "quality": quality,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

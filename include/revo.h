@@ -151,6 +151,7 @@ typedef struct {
   double latency_ms;   /* host clock, submit -> completion observed            */
   double device_ms;    /* CUDA-event time of the batch that carried the request */
   int batch_size;      /* requests in that batch                                */
+  int kernel_launches; /* CUDA kernels the batch launched (both modalities)     */
 } revo_result;
 
 /* Fills *cfg with the ViT-B reading above and precision BF16. */

@@ -57,7 +57,8 @@ class Request(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("stream_id", C.c_uint32), ("frame_index", C.c_int64),
-                ("latency_ms", C.c_double), ("device_ms", C.c_double), ("batch_size", C.c_int)]
+                ("latency_ms", C.c_double), ("device_ms", C.c_double), ("batch_size", C.c_int),
+                ("kernel_launches", C.c_int)]
 
 
 _lib = None

@@ -281,8 +281,10 @@ bool encode_maps(const NetShape& s, Workspace* ws, int M) {
 
 }  // namespace
 
-cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms) {
+cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
+                        int* launches) {
   const NetShape& s = net->s;
+  if (launches) *launches = 0;
   if (n <= 0) return cudaSuccess;
   if (n > kMaxSegments) return cudaErrorInvalidValue;
   Fwd f{net, ws, st, num_sms, net->precision != REVO_FP32, net->precision != REVO_FP32 ? 2u : 4u};
@@ -371,6 +373,9 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
     if ((e = launch_blend(bl, st)) != cudaSuccess) return e;
     hoff += P;
   }
+  // One kernel per step: per request assemble, 2 embeddings, final LN, head, blend;
+  // tubelet embedding, encoder LN, encoder->decoder; 7 per transformer block.
+  if (launches) *launches = 3 + 7 * (s.L + s.Ld) + 6 * n;
   return cudaSuccess;
 }
 

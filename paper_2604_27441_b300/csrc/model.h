@@ -95,7 +95,9 @@ void workspace_destroy(Workspace* w);
 inline int request_tokens(const NetShape& s, int H, int W) { return s.slots() * (H / s.p) * (W / s.p); }
 inline int request_patches(const NetShape& s, int H, int W) { return (H / s.p) * (W / s.p); }
 
-// Enqueues the whole forward (assemble ... blend) of `n` jobs on `st`.
-cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms);
+// Enqueues the whole forward (assemble ... blend) of `n` jobs on `st`; *launches
+// receives the number of kernels enqueued.
+cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
+                        int* launches);
 
 }  // namespace revo

@@ -71,6 +71,7 @@ struct Batch {
   bool done = false;
   revo_status status = REVO_OK;
   double device_ms = 0;
+  int launches = 0;
 };
 
 struct TicketInfo {
@@ -220,7 +221,9 @@ revo_status launch_batch(revo_ctx* c, int count) {
     if (jobs[m].empty()) continue;
     cudaStream_t s = L.st[m];
     cudaMemsetAsync(L.ws[m]->err, 0, sizeof(int), s);
-    e = net_forward(c->net[m], L.ws[m], jobs[m].data(), static_cast<int>(jobs[m].size()), s, c->sms);
+    int nl = 0;
+    e = net_forward(c->net[m], L.ws[m], jobs[m].data(), static_cast<int>(jobs[m].size()), s, c->sms, &nl);
+    b.launches += nl;
     if (e != cudaSuccess) st = cuda_status(e, "forward launch");
     cudaMemcpyAsync(b.err_host + m, L.ws[m]->err, sizeof(int), cudaMemcpyDeviceToHost, s);
   }
@@ -659,6 +662,7 @@ revo_status revo_recover_poll(revo_ctx* c, uint64_t ticket, int64_t timeout_us, 
     out->latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - it->second.t_submit).count();
     out->device_ms = b.device_ms;
     out->batch_size = b.size;
+    out->kernel_launches = b.launches;
   }
   const uint64_t bid = it->second.batch;
   auto& tv = b.tickets;
