@@ -232,6 +232,29 @@ REVO_API revo_status revo_op_depth_stats(const uint16_t* depth, int height, int 
                                 float* mu_sigma, void* scratch, void* stream);
 
 /*
+ * The same depth statistics for callers that cannot allocate device memory:
+ * for example a receiver loop that must not call cudaMalloc while frames are in
+ * flight (it can synchronise the device and stall other streams past the frame
+ * deadline), or a host application whose device memory is all reserved up
+ * front by its own pool.  The paper has no counterpart; this is a library
+ * convenience.  It allocates nothing: the scratch is a fixed 8 KB array inside
+ * the library, held by every GPU that loads the library until the process
+ * exits.  The caller still passes the frame and the output pair.
+ *  - Frames up to 2^24 pixels (height * width); larger frames return
+ *    REVO_EINVAL with a message.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any CUDA
+ *    stream capture.
+ *  - Every call shares the one array.  Calls whose work overlaps on the GPU
+ *    (other streams, other host threads) race on it and give wrong results;
+ *    order them on one stream or serialise them.  Each call clears the
+ *    counters it needs at the start, so leftovers of an earlier call do not
+ *    matter.
+ */
+REVO_API revo_status revo_op_depth_stats_noalloc(const uint16_t* depth, int height, int width,
+                                                 size_t pitch_bytes, float* mu_sigma, void* stream);
+
+/*
  * Y = epilogue(A W^T + b) with A [M][K], W [N][K] (Linear [out][in]), b [N]
  * (b may be NULL).
  *   precision REVO_FP32: A, W float32, SIMT FMA (K % 8 == 0).  REVO_BF16: A, W

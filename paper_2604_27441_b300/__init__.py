@@ -87,6 +87,7 @@ _SIGS = {
                                 C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
                                 C.c_void_p]),
     "revo_op_take_device_error": (C.c_int, []),
+    "revo_op_depth_stats_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_size_t, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -156,6 +157,12 @@ def depth_stats_scratch_bytes() -> int:
 def op_depth_stats(depth, height, width, pitch_bytes, mu_sigma, scratch, stream=None):
     return _check(lib().revo_op_depth_stats(ptr(depth), height, width, pitch_bytes, ptr(mu_sigma), ptr(scratch),
                                             _stream(stream)), "revo_op_depth_stats")
+
+
+def op_depth_stats_noalloc(depth, height, width, pitch_bytes, mu_sigma, stream=None):
+    """Depth statistics with the library's built-in scratch (no device allocation)."""
+    return _check(lib().revo_op_depth_stats_noalloc(ptr(depth), height, width, pitch_bytes, ptr(mu_sigma),
+                                                    _stream(stream)), "revo_op_depth_stats_noalloc")
 
 
 def op_linear(precision, epilogue, A, W, bias, out, M, N, K, tile_n=0, stream=None):
