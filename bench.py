@@ -360,8 +360,45 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def run_profile_kernel(args) -> None:
+    """Launches one kernel of the step at the bench's shape (for ncu captures):
+    W warm-up + K timed launches on one stream, CUDA-event timed."""
+    import torch
+
+    import paper_2604_27441_b300 as R
+    fl = flops_per_model(3, H, W)
+    N, D = fl["N"], 768
+    stream = torch.cuda.Stream()
+    if args.profile_kernel == "attention":
+        qkv = torch.randn((N, 3 * D), device="cuda").to(torch.bfloat16)
+        out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
+        launch = lambda: R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream)  # noqa: E731
+        flops = fl["attn_enc_per_block"]
+    else:  # fc1 of an encoder block: [N, 768] x [3072, 768]^T + GELU
+        a = torch.randn((N, D), device="cuda").to(torch.bfloat16)
+        w = (torch.randn((4 * D, D), device="cuda") / 28).to(torch.bfloat16)
+        b = torch.zeros(4 * D, device="cuda")
+        out = torch.empty((N, 4 * D), dtype=torch.bfloat16, device="cuda")
+        launch = lambda: R.op_linear(R.BF16, 2, a, w, b, out, N, 4 * D, D, 0, stream=stream)  # noqa: E731
+        flops = 2 * N * D * 4 * D
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        launch()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / args.steps
+    print(json.dumps({"kernel": args.profile_kernel, "us_per_launch": us, "tflops": flops / us / 1e6,
+                      "device_error": R.take_device_error()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-kernel", choices=["attention", "fc1"], default=None,
+                    help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
@@ -371,7 +408,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.profile_kernel:
+        run_profile_kernel(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
