@@ -259,7 +259,8 @@ REVO_API revo_status revo_op_depth_stats_noalloc(const uint16_t* depth, int heig
  * (b may be NULL).
  *   precision REVO_FP32: A, W float32, SIMT FMA (K % 8 == 0).  REVO_BF16: A, W
  *   bf16 on the tcgen05 tensor cores with float32 accumulation (K % 64 == 0,
- *   N % 32 == 0); `tile_n` picks the 128- or 256-column tile (0 = automatic).
+ *   N % 32 == 0, N % 64 == 0 for the bf16 epilogues 1 and 2); `tile_n` picks
+ *   the 128- or 256-column tile (other values: 128).
  *   epilogue 0: out = acc + b (float32 out)
  *   epilogue 1: out = acc + b (bf16 out; FP32 precision writes float32)
  *   epilogue 2: out = gelu(acc + b) (bf16 out; FP32 precision writes float32)

@@ -7,13 +7,17 @@
 // and BN x 64 tiles with the 128-byte swizzle straight into the operand layout
 // tcgen05.mma reads.  The accumulator (128 lanes x BN f32 columns) lives in
 // TMEM, double-buffered so the epilogue of one tile overlaps the main loop of
-// the next.  The epilogue fuses the bias, the exact GELU, the residual add and
-// the bf16 downcast.
+// the next.  The epilogue adds the bias, applies the exact GELU and the bf16
+// downcast in registers, stages 32-row chunks in 128-byte-swizzled shared
+// memory and hands them to TMA: a bulk store, or for the residual layers a
+// bulk f32 add-reduction into the residual stream (one rounding per element,
+// exactly as x += y).
 //
-// Warp roles (192 threads, one CTA per SM, persistent over output tiles):
+// Warp roles (320 threads, one CTA per SM, persistent over output tiles):
 //   warp 0      TMA producer (one thread)
 //   warp 1      TMEM allocator + MMA issuer (one thread)
-//   warps 2..5  epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 = tile rows
+//   warps 2..9  epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (tile rows);
+//               warps 2..5 take the left half of the tile's columns, 6..9 the right.
 #include "common.cuh"
 #include "revo_internal.h"
 
@@ -23,6 +27,9 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;  // 64 bf16 = one 128-byte swizzle atom per row
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kOutChunkBytes = 32 * 128;  // 32 rows x 128 B staging per epilogue warp
 
 template <int BN>
 struct TcGemmCfg {
@@ -31,67 +38,101 @@ struct TcGemmCfg {
   static constexpr int kBBytes = BN * kBK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kTmemCols = 2 * BN;
-  static constexpr int kSmemBytes = 1024 /*align slack*/ + kStages * kStageBytes + 256 /*barriers*/;
+  static constexpr int kSmemBytes =
+      1024 /*align slack*/ + kStages * kStageBytes + kEpiWarps * kOutChunkBytes + 256 /*barriers*/;
 };
 
+// Writes this thread's 128-byte row (eight 16-byte pieces) into a 32 x 128 B
+// chunk with the 128-byte swizzle TMA expects: piece k of row i sits at k ^ (i % 8).
+REVO_DEVI void stage_row(uint8_t* chunk, int row, const uint4 (&pieces)[8]) {
+  uint8_t* base = chunk + row * 128;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) *reinterpret_cast<uint4*>(base + ((k ^ (row & 7)) << 4)) = pieces[k];
+}
+
+REVO_DEVI void add_bias(float (&v)[32], const float* __restrict__ bias, int col) {
+  if (bias == nullptr) return;
+  const float4* b4 = reinterpret_cast<const float4*>(bias + col);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 b = __ldg(b4 + i);
+    v[4 * i] += b.x;
+    v[4 * i + 1] += b.y;
+    v[4 * i + 2] += b.z;
+    v[4 * i + 3] += b.w;
+  }
+}
+
+// One epilogue chunk: 32 rows (this warp's lanes) x 128 bytes of output
+// (32 f32 columns or 64 bf16 columns) starting at tile column `c0`.
 template <int EPI>
-REVO_DEVI void store_chunk(const uint32_t (&r)[32], const float* __restrict__ bias, void* out, int ldo, int row,
-                           int col0) {
-  float v[32];
+REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, int n0, int c0, uint8_t* chunk,
+                              const CUtensorMap* map, int row0, int lane) {
+  uint4 pieces[8];
+  if (EPI == kEpiF32 || EPI == kEpiResidF32) {
+    uint32_t r[32];
+    tmem_ld32(taddr + c0, r);
+    tmem_wait_ld();
+    float v[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-  if (bias != nullptr) {
-    const float4* b4 = reinterpret_cast<const float4*>(bias + col0);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    add_bias(v, bias, n0 + c0);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float4 b = __ldg(b4 + i);
-      v[4 * i] += b.x;
-      v[4 * i + 1] += b.y;
-      v[4 * i + 2] += b.z;
-      v[4 * i + 3] += b.w;
-    }
-  }
-  if (EPI == kEpiGeluBf16) {
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = gelu_exact(v[i]);
-  }
-  if (EPI == kEpiF32) {
-    float4* o = reinterpret_cast<float4*>(static_cast<float*>(out) + static_cast<size_t>(row) * ldo + col0);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-  } else if (EPI == kEpiResidF32) {
-    float4* o = reinterpret_cast<float4*>(static_cast<float*>(out) + static_cast<size_t>(row) * ldo + col0);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float4 x = o[i];
-      x.x += v[4 * i];
-      x.y += v[4 * i + 1];
-      x.z += v[4 * i + 2];
-      x.w += v[4 * i + 3];
-      o[i] = x;
-    }
+    for (int k = 0; k < 8; ++k)
+      pieces[k] = make_uint4(__float_as_uint(v[4 * k]), __float_as_uint(v[4 * k + 1]), __float_as_uint(v[4 * k + 2]),
+                             __float_as_uint(v[4 * k + 3]));
   } else {
-    uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + static_cast<size_t>(row) * ldo + col0);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      o[i] = make_uint4(pack_bf16x2(v[8 * i], v[8 * i + 1]), pack_bf16x2(v[8 * i + 2], v[8 * i + 3]),
-                        pack_bf16x2(v[8 * i + 4], v[8 * i + 5]), pack_bf16x2(v[8 * i + 6], v[8 * i + 7]));
+    for (int half = 0; half < 2; ++half) {
+      uint32_t r[32];
+      tmem_ld32(taddr + c0 + 32 * half, r);
+      tmem_wait_ld();
+      float v[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+      add_bias(v, bias, n0 + c0 + 32 * half);
+      if (EPI == kEpiGeluBf16) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = gelu_exact(v[i]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        pieces[4 * half + k] =
+            make_uint4(pack_bf16x2(v[8 * k], v[8 * k + 1]), pack_bf16x2(v[8 * k + 2], v[8 * k + 3]),
+                       pack_bf16x2(v[8 * k + 4], v[8 * k + 5]), pack_bf16x2(v[8 * k + 6], v[8 * k + 7]));
+    }
+  }
+  // The staging chunk is free once the previous bulk copy has read it.
+  if (lane == 0) bulk_wait_read0();
+  __syncwarp();
+  stage_row(chunk, lane, pieces);
+  fence_proxy_async_smem();
+  __syncwarp();
+  if (lane == 0) {
+    if (EPI == kEpiResidF32)
+      tma_reduce_add_2d(map, chunk, n0 + c0, row0);
+    else
+      tma_store_2d(map, chunk, n0 + c0, row0);
+    bulk_commit();
   }
 }
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const float* __restrict__ bias, void* out, int ldo, int M, int N, int K, int* err) {
+                   const __grid_constant__ CUtensorMap tmC, const float* __restrict__ bias, int M, int N, int K,
+                   int* err) {
   using Cfg = TcGemmCfg<BN>;
   constexpr int S = Cfg::kStages;
   constexpr uint32_t kIdesc = idesc_bf16(kBM, BN);
+  constexpr int kChunkCols = (EPI == kEpiF32 || EPI == kEpiResidF32) ? 32 : 64;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + S * Cfg::kABytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + S * Cfg::kBBytes);
+  uint8_t* sOut = sB + S * Cfg::kBBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sOut + kEpiWarps * kOutChunkBytes);
   uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
@@ -107,13 +148,14 @@ __global__ void __launch_bounds__(192, 1)
   if (threadIdx.x == 0) {
     tma_prefetch_desc(&tmA);
     tma_prefetch_desc(&tmB);
+    tma_prefetch_desc(&tmC);
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 4);
+      mbar_init(&tempty[a], kEpiWarps);
     }
     fence_mbarrier_init();
   }
@@ -183,7 +225,10 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
+    const int e = warp - 2;
     const int q = warp & 3;
+    const int half = e >> 2;
+    uint8_t* chunk = sOut + e * kOutChunkBytes;
     int t_local = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++t_local) {
       const int acc = t_local & 1;
@@ -192,19 +237,17 @@ __global__ void __launch_bounds__(192, 1)
       tc_fence_after();
       const int m0 = (tile % m_tiles) * kBM;
       const int n0 = (tile / m_tiles) * BN;
-      const int row = m0 + q * 32 + lane;
+      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BN;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BN + c * 32, r);
-        tmem_wait_ld();
-        const int col0 = n0 + c * 32;
-        if (row < M && col0 < N) store_chunk<EPI>(r, bias, out, ldo, row, col0);
+      for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += kChunkCols) {
+        if (n0 + c0 >= N) break;
+        epilogue_chunk<EPI>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
     }
+    if (lane == 0) bulk_wait_all();
   }
 
   __syncthreads();
@@ -214,8 +257,12 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+}  // namespace
+
+namespace {
+
 template <int BN, int EPI>
-cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const float* bias, void* out, int ldo, int M,
+cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const float* bias, int M,
                           int N, int K, int* err, int num_sms, cudaStream_t st) {
   using Cfg = TcGemmCfg<BN>;
   auto kern = gemm_tc_kernel<BN, EPI>;
@@ -223,29 +270,30 @@ cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const floa
   if (e != cudaSuccess) return e;
   const int tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
   const int grid = tiles < num_sms ? tiles : num_sms;
-  kern<<<grid, 192, Cfg::kSmemBytes, st>>>(a, b, bias, out, ldo, M, N, K, err);
+  kern<<<grid, kThreads, Cfg::kSmemBytes, st>>>(a, b, c, bias, M, N, K, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, int bn, int epi, const float* bias, void* out,
-                           int ldo, int M, int N, int K, int* err, int num_sms, cudaStream_t st) {
+cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
+                           const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (K % kBK != 0 || N % 32 != 0) return cudaErrorInvalidValue;
+  const bool bf16_out = epi == kEpiBf16 || epi == kEpiGeluBf16;
+  if (K % kBK != 0 || N % (bf16_out ? 64 : 32) != 0) return cudaErrorInvalidValue;
   if (bn == 256) {
     switch (epi) {
-      case kEpiF32: return launch_bn_epi<256, kEpiF32>(a, b, bias, out, ldo, M, N, K, err, num_sms, st);
-      case kEpiBf16: return launch_bn_epi<256, kEpiBf16>(a, b, bias, out, ldo, M, N, K, err, num_sms, st);
-      case kEpiGeluBf16: return launch_bn_epi<256, kEpiGeluBf16>(a, b, bias, out, ldo, M, N, K, err, num_sms, st);
-      case kEpiResidF32: return launch_bn_epi<256, kEpiResidF32>(a, b, bias, out, ldo, M, N, K, err, num_sms, st);
+      case kEpiF32: return launch_bn_epi<256, kEpiF32>(a, b, c, bias, M, N, K, err, num_sms, st);
+      case kEpiBf16: return launch_bn_epi<256, kEpiBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
+      case kEpiGeluBf16: return launch_bn_epi<256, kEpiGeluBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
+      case kEpiResidF32: return launch_bn_epi<256, kEpiResidF32>(a, b, c, bias, M, N, K, err, num_sms, st);
     }
   } else {
     switch (epi) {
-      case kEpiF32: return launch_bn_epi<128, kEpiF32>(a, b, bias, out, ldo, M, N, K, err, num_sms, st);
-      case kEpiBf16: return launch_bn_epi<128, kEpiBf16>(a, b, bias, out, ldo, M, N, K, err, num_sms, st);
-      case kEpiGeluBf16: return launch_bn_epi<128, kEpiGeluBf16>(a, b, bias, out, ldo, M, N, K, err, num_sms, st);
-      case kEpiResidF32: return launch_bn_epi<128, kEpiResidF32>(a, b, bias, out, ldo, M, N, K, err, num_sms, st);
+      case kEpiF32: return launch_bn_epi<128, kEpiF32>(a, b, c, bias, M, N, K, err, num_sms, st);
+      case kEpiBf16: return launch_bn_epi<128, kEpiBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
+      case kEpiGeluBf16: return launch_bn_epi<128, kEpiGeluBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
+      case kEpiResidF32: return launch_bn_epi<128, kEpiResidF32>(a, b, c, bias, M, N, K, err, num_sms, st);
     }
   }
   return cudaErrorInvalidValue;

@@ -238,28 +238,35 @@ struct Fwd {
   bool tc;
   size_t e;  // activation element size
 
-  cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M) {
+  // `amap` / `cmap`: the A operand and output tensor maps (tensor-core path).
+  cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M,
+                     const CUtensorMap* cmap) {
     if (!tc) return launch_gemm_simt(epi, static_cast<const float*>(A), w.w32, w.b, out, ldo, M, w.out, w.in, st);
     const int bn = pick_bn(M, w.out, sms);
-    return launch_gemm_tc(*amap, bn == 256 ? w.map256 : w.map128, bn, epi, w.b, out, ldo, M, w.out, w.in, ws->err,
-                          sms, st);
+    return launch_gemm_tc(*amap, bn == 256 ? w.map256 : w.map128, *cmap, bn, epi, w.b, M, w.out, w.in, ws->err, sms,
+                          st);
   }
 
-  cudaError_t block(const BlockW& b, int d, int heads, int M, const Segments& seg, const CUtensorMap* m_h,
-                    const CUtensorMap* m_att, const CUtensorMap* m_mlp, const CUtensorMap* m_qkv) {
+  struct Maps {
+    const CUtensorMap *h, *att, *mlp, *qkv;  // operands / attention input
+    const CUtensorMap *o_x, *o_qkv, *o_mlp;  // epilogue outputs
+  };
+
+  cudaError_t block(const BlockW& b, int d, int heads, int M, const Segments& seg, const Maps& mp) {
     cudaError_t e;
     if ((e = launch_layernorm(ws->x, b.ln1g, b.ln1b, ws->h, M, d, tc, st)) != cudaSuccess) return e;
-    if ((e = linear(m_h, ws->h, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, M)) != cudaSuccess) return e;
+    if ((e = linear(mp.h, ws->h, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, M, mp.o_qkv)) != cudaSuccess)
+      return e;
     if (tc)
-      e = launch_attention_tc(*m_qkv, ws->att, M, d, heads, seg, ws->err, st);
+      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st);
     else
       e = launch_attention_simt(static_cast<const float*>(ws->qkv), static_cast<float*>(ws->att), M, d, heads, seg,
                                 st);
     if (e != cudaSuccess) return e;
-    if ((e = linear(m_att, ws->att, b.proj, kEpiResidF32, ws->x, d, M)) != cudaSuccess) return e;
+    if ((e = linear(mp.att, ws->att, b.proj, kEpiResidF32, ws->x, d, M, mp.o_x)) != cudaSuccess) return e;
     if ((e = launch_layernorm(ws->x, b.ln2g, b.ln2b, ws->h, M, d, tc, st)) != cudaSuccess) return e;
-    if ((e = linear(m_h, ws->h, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, M)) != cudaSuccess) return e;
-    return linear(m_mlp, ws->mlp, b.fc2, kEpiResidF32, ws->x, d, M);
+    if ((e = linear(mp.h, ws->h, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, M, mp.o_mlp)) != cudaSuccess) return e;
+    return linear(mp.mlp, ws->mlp, b.fc2, kEpiResidF32, ws->x, d, M, mp.o_x);
   }
 };
 
@@ -274,7 +281,13 @@ bool encode_maps(const NetShape& s, Workspace* ws, int M) {
             encode_tmap_bf16_2d(&ws->m_att_dec, ws->att, rows, s.Dd, s.Dd, 128, 64) &&
             encode_tmap_bf16_2d(&ws->m_mlp_dec, ws->mlp, rows, s.r * s.Dd, s.r * s.Dd, 128, 64) &&
             encode_attention_tmap(&ws->m_qkv_enc, ws->qkv, static_cast<int>(rows), s.D) &&
-            encode_attention_tmap(&ws->m_qkv_dec, ws->qkv, static_cast<int>(rows), s.Dd);
+            encode_attention_tmap(&ws->m_qkv_dec, ws->qkv, static_cast<int>(rows), s.Dd) &&
+            encode_tmap_out_2d(&ws->o_x_enc, ws->x, true, rows, s.D, s.D) &&
+            encode_tmap_out_2d(&ws->o_x_dec, ws->x, true, rows, s.Dd, s.Dd) &&
+            encode_tmap_out_2d(&ws->o_qkv_enc, ws->qkv, false, rows, 3 * s.D, 3 * s.D) &&
+            encode_tmap_out_2d(&ws->o_qkv_dec, ws->qkv, false, rows, 3 * s.Dd, 3 * s.Dd) &&
+            encode_tmap_out_2d(&ws->o_mlp_enc, ws->mlp, false, rows, s.r * s.D, s.r * s.D) &&
+            encode_tmap_out_2d(&ws->o_mlp_dec, ws->mlp, false, rows, s.r * s.Dd, s.r * s.Dd);
   ws->maps_rows = ok ? M : -1;
   return ok;
 }
@@ -321,26 +334,27 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
     a.out_bf16 = f.tc;
     if ((e = launch_assemble(a, st)) != cudaSuccess) return e;
   }
-  if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32, ws->x, s.D, M)) != cudaSuccess) return e;
+  if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32, ws->x, s.D, M, &ws->o_x_enc)) != cudaSuccess) return e;
   for (int i = 0; i < n; ++i)
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.D, jobs[i].H / s.p, jobs[i].W / s.p,
                            s.slots(), jobs[i].taus, s.D, st)) != cudaSuccess)
       return e;
 
+  const Fwd::Maps enc_maps{&ws->m_h_enc, &ws->m_att_enc, &ws->m_mlp_enc, &ws->m_qkv_enc,
+                           &ws->o_x_enc, &ws->o_qkv_enc, &ws->o_mlp_enc};
+  const Fwd::Maps dec_maps{&ws->m_h_dec, &ws->m_att_dec, &ws->m_mlp_dec, &ws->m_qkv_dec,
+                           &ws->o_x_dec, &ws->o_qkv_dec, &ws->o_mlp_dec};
   for (const BlockW& b : net->enc)
-    if ((e = f.block(b, s.D, s.H, M, seg, &ws->m_h_enc, &ws->m_att_enc, &ws->m_mlp_enc, &ws->m_qkv_enc)) !=
-        cudaSuccess)
-      return e;
+    if ((e = f.block(b, s.D, s.H, M, seg, enc_maps)) != cudaSuccess) return e;
   if ((e = launch_layernorm(ws->x, net->enc_norm_g, net->enc_norm_b, ws->h, M, s.D, f.tc, st)) != cudaSuccess) return e;
-  if ((e = f.linear(&ws->m_h_enc, ws->h, net->enc2dec, kEpiF32, ws->x, s.Dd, M)) != cudaSuccess) return e;
+  if ((e = f.linear(&ws->m_h_enc, ws->h, net->enc2dec, kEpiF32, ws->x, s.Dd, M, &ws->o_x_dec)) != cudaSuccess)
+    return e;
   for (int i = 0; i < n; ++i)
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.Dd, jobs[i].H / s.p, jobs[i].W / s.p,
                            s.slots(), jobs[i].taus, s.Dd, st)) != cudaSuccess)
       return e;
   for (const BlockW& b : net->dec)
-    if ((e = f.block(b, s.Dd, s.Hd, M, seg, &ws->m_h_dec, &ws->m_att_dec, &ws->m_mlp_dec, &ws->m_qkv_dec)) !=
-        cudaSuccess)
-      return e;
+    if ((e = f.block(b, s.Dd, s.Hd, M, seg, dec_maps)) != cudaSuccess) return e;
 
   // Final LN and pixel head on the last slot's tokens of each request, then the blend.
   int hoff = 0;
@@ -353,9 +367,12 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
         cudaSuccess)
       return e;
     float* head = ws->head + static_cast<size_t>(hoff) * s.head_dim_out();
-    CUtensorMap m_rows;
-    if (f.tc && !encode_tmap_bf16_2d(&m_rows, hrows, P, s.Dd, s.Dd, 128, 64)) return cudaErrorInvalidValue;
-    if ((e = f.linear(&m_rows, hrows, net->head, kEpiF32, head, s.head_dim_out(), P)) != cudaSuccess) return e;
+    CUtensorMap m_rows, o_head;
+    if (f.tc && (!encode_tmap_bf16_2d(&m_rows, hrows, P, s.Dd, s.Dd, 128, 64) ||
+                 !encode_tmap_out_2d(&o_head, head, true, P, s.head_dim_out(), s.head_dim_out())))
+      return cudaErrorInvalidValue;
+    if ((e = f.linear(&m_rows, hrows, net->head, kEpiF32, head, s.head_dim_out(), P, &o_head)) != cudaSuccess)
+      return e;
     BlendArgs bl{};
     bl.C = s.C;
     bl.p = s.p;

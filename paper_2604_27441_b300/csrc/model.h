@@ -81,6 +81,8 @@ struct Workspace {
   int maps_rows = -1;
   CUtensorMap m_tok{}, m_h_enc{}, m_att_enc{}, m_mlp_enc{}, m_h_dec{}, m_att_dec{}, m_mlp_dec{};
   CUtensorMap m_qkv_enc{}, m_qkv_dec{};
+  // Output maps of the GEMM epilogues.
+  CUtensorMap o_x_enc{}, o_x_dec{}, o_qkv_enc{}, o_qkv_dec{}, o_mlp_enc{}, o_mlp_dec{};
 };
 
 Net* net_create(const NetShape& s, int precision, const float* host_weights, std::string* err);

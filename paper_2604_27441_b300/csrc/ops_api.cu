@@ -128,13 +128,16 @@ revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A
     set_last_error("revo_op_linear: precision not supported by this entry point");
     return REVO_ENOTSUP;
   }
-  if (K % 64 || N % 32) {
-    set_last_error("revo_op_linear: BF16 path needs K %% 64 == 0 and N %% 32 == 0");
+  const bool f32_out = epilogue == 0 || epilogue == 3;
+  if (K % 64 || N % (f32_out ? 32 : 64)) {
+    set_last_error("revo_op_linear: BF16 path needs K %% 64 == 0 and N %% 32 == 0 (N %% 64 == 0 for bf16 outputs)");
     return REVO_EINVAL;
   }
   const int bn = tile_n == 256 ? 256 : 128;
-  CUtensorMap ma, mb;
-  if (!encode_tmap_bf16_2d(&ma, A, M > 0 ? M : 1, K, K, 128, 64) || !encode_tmap_bf16_2d(&mb, W, N, K, K, bn, 64)) {
+  CUtensorMap ma, mb, mc;
+  const uint64_t rows = M > 0 ? M : 1;
+  if (!encode_tmap_bf16_2d(&ma, A, rows, K, K, 128, 64) || !encode_tmap_bf16_2d(&mb, W, N, K, K, bn, 64) ||
+      !encode_tmap_out_2d(&mc, out, f32_out, rows, N, N)) {
     set_last_error("revo_op_linear: tensor map encoding failed (alignment?)");
     return REVO_EINVAL;
   }
@@ -143,7 +146,7 @@ revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A
     set_last_error("revo_op_linear: no device error word");
     return REVO_ECUDA;
   }
-  return cuda_status(launch_gemm_tc(ma, mb, bn, epilogue, bias, out, N, M, N, K, err, device_sm_count(), st),
+  return cuda_status(launch_gemm_tc(ma, mb, mc, bn, epilogue, bias, M, N, K, err, device_sm_count(), st),
                      "revo_op_linear");
 }
 

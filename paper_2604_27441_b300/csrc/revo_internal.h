@@ -32,9 +32,14 @@ struct Segments {
 bool encode_tmap_bf16_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t row_stride_elems,
                          uint32_t box_rows, uint32_t box_cols);
 
+bool encode_tmap_out_2d(CUtensorMap* map, const void* base, bool f32, uint64_t rows, uint64_t cols,
+                        uint64_t row_stride_elems);
+
 // ---- GEMMs
-cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, int bn, int epi, const float* bias, void* out,
-                           int ldo, int M, int N, int K, int* err, int num_sms, cudaStream_t st);
+// `c` is the output map (encode_tmap_out_2d): float32 for kEpiF32 and
+// kEpiResidF32 (the residual epilogue adds into it), bf16 otherwise.
+cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
+                           const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st);
 cudaError_t launch_gemm_simt(int epi, const float* A, const float* W, const float* bias, void* out, int ldo, int M,
                              int N, int K, cudaStream_t st);
 

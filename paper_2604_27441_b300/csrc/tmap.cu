@@ -39,6 +39,26 @@ bool encode_tmap_bf16_2d(CUtensorMap* map, const void* base, uint64_t rows, uint
   return r == CUDA_SUCCESS;
 }
 
+// Output map of a GEMM epilogue: rows x cols of float32 (32-column box) or
+// bf16 (64-column box), 32-row box, 128-byte swizzle (one 128-byte row per
+// box row).
+bool encode_tmap_out_2d(CUtensorMap* map, const void* base, bool f32, uint64_t rows, uint64_t cols,
+                        uint64_t row_stride_elems) {
+  std::call_once(g_once, resolve);
+  if (!g_encode) return false;
+  const uint64_t esz = f32 ? 4 : 2;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_stride_elems * esz) % 16) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {row_stride_elems * esz};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int device_sm_count() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
