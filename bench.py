@@ -40,6 +40,9 @@ LOSS_RATES = (0.05, 0.10, 0.20, 0.40)
 VITB = dict(k=5, tubelet=2, patch=16, enc_dim=768, enc_depth=12, enc_heads=12, dec_dim=384, dec_depth=4,
             dec_heads=6, mlp_ratio=4)
 FRAME_BUDGET_MS = 33.0
+# DRAM bytes (read + write) of one attn_tc_kernel launch at N = 3600, 12 heads,
+# from an ncu capture of the current kernel version (None once it changes).
+ATTN_DRAM_BYTES_PER_LAUNCH = 16632832
 
 
 def flops_per_model(C: int, h: int, w: int) -> dict:
@@ -65,6 +68,33 @@ def peaks() -> dict:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+# ---------------------------------------------------------------- ranks --
+# One process per GPU; the recovery path shards by conference stream with no
+# exchange, so ranks only meet for barriers and the max of their timings.
+
+def rank_barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def rank_max(v: float, world: int) -> float:
+    """Max of a scalar over ranks (CUDA tensor under NCCL, CPU under gloo)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps_per_rank: int, max_seconds: float, world: int) -> float:
+    """Frames/s of the whole job: every rank's frames over the slowest rank's time."""
+    return world * steps_per_rank / max_seconds
 
 
 # --------------------------------------------------------------- clocks --
@@ -202,15 +232,10 @@ def run_ours(args) -> None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        rank_barrier(world)
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(v, world)
 
     precision = R.BF16 if args.precision == "bf16" else R.FP32
     stream = torch.cuda.Stream()
@@ -280,7 +305,7 @@ def run_ours(args) -> None:
         barrier()
     dev_s = start.elapsed_time(end) / 1e3
     dev_s_max = max_over_ranks(dev_s)
-    value = world * args.steps / dev_s_max
+    value = whole_job_rate(args.steps, dev_s_max, world)
     clocks = clk.summary()
 
     # End to end: host (pinned) buffers, copies inside the timed region, host clock.
@@ -319,7 +344,8 @@ def run_ours(args) -> None:
         achieved = fl["attn_enc_per_block"] / per_launch / 1e12
         roof = {"kernel": "attn_tc_kernel (tcgen05 flash attention, N=3600, 12 heads x 64)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "frac": (achieved / peak) if peak else None, "traffic": ATTN_DRAM_BYTES_PER_LAUNCH,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)" if peak else None,
                 "flops_per_launch": fl["attn_enc_per_block"], "us_per_launch": per_launch * 1e6}
         assert R.take_device_error() == 0
@@ -379,7 +405,7 @@ def run_profile_kernel(args) -> None:
         w = (torch.randn((4 * D, D), device="cuda") / 28).to(torch.bfloat16)
         b = torch.zeros(4 * D, device="cuda")
         out = torch.empty((N, 4 * D), dtype=torch.bfloat16, device="cuda")
-        launch = lambda: R.op_linear(R.BF16, 2, a, w, b, out, N, 4 * D, D, 0, stream=stream)  # noqa: E731
+        launch = lambda: R.op_linear(R.BF16, 2, a, w, b, out, N, 4 * D, D, 256, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
     torch.cuda.synchronize()
     for _ in range(args.warmup):

@@ -7,8 +7,8 @@
 // and BN x 64 tiles with the 128-byte swizzle straight into the operand layout
 // tcgen05.mma reads.  The accumulator (128 lanes x BN f32 columns) lives in
 // TMEM, double-buffered so the epilogue of one tile overlaps the main loop of
-// the next.  The epilogue adds the bias, applies the exact GELU and the bf16
-// downcast in registers, stages 32-row chunks in 128-byte-swizzled shared
+// the next.  The epilogue adds the bias, applies the erf-form GELU (erf by
+// Abramowitz & Stegun 7.1.26) and the bf16 downcast in registers, stages 32-row chunks in 128-byte-swizzled shared
 // memory and hands them to TMA: a bulk store, or for the residual layers a
 // bulk f32 add-reduction into the residual stream (one rounding per element,
 // exactly as x += y).
@@ -93,7 +93,7 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
       add_bias(v, bias, n0 + c0 + 32 * half);
       if (EPI == kEpiGeluBf16) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = gelu_exact(v[i]);
+        for (int i = 0; i < 32; ++i) v[i] = gelu_as7126(v[i]);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k)

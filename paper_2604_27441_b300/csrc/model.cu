@@ -20,14 +20,10 @@ size_t block_params(int d, int r) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-int pick_bn(int M, int N, int sms) {
-  if (N < 256) return 128;
-  auto cost = [&](int bn) {
-    const long long tiles = static_cast<long long>((M + 127) / 128) * ((N + bn - 1) / bn);
-    return ((tiles + sms - 1) / sms) * bn;
-  };
-  return cost(256) < cost(128) ? 256 : 128;
-}
+// 128 x 256 tiles halve the A-operand traffic per FLOP and measured faster than
+// 128 x 128 at every Linear shape of the network (also with fewer tiles than
+// SMs), so they are used whenever N allows.
+int pick_bn(int /*M*/, int N, int /*sms*/) { return N >= 256 ? 256 : 128; }
 
 bool make_weight_maps(LinearW& w) {
   if (!w.w16) return true;
