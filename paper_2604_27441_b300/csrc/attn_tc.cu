@@ -9,10 +9,13 @@
 // [M][3D] (128-byte swizzle), so no head-split pass is needed.  Per KV tile j
 // and query tile t:
 //   S_t  = Q_t K_j^T          tcgen05.mma M=128 N=128 K=64 -> TMEM
-//   P_t  = exp2(S_t c - m_t)  softmax warpgroup t, bf16, written to shared
-//                             memory in the swizzled K-major operand layout
-//   O_t += P_t V_j            tcgen05.mma M=128 N=64 K=128 (V read N-major),
+//   P_t  = exp2(S_t c - m_t)  softmax warpgroup t, bf16, written back to TMEM
+//                             (tcgen05.st; one row per lane, two keys per column)
+//   O_t += P_t V_j            tcgen05.mma M=128 N=64 K=128 with A = P from TMEM
+//                             and V read N-major from shared memory,
 //                             accumulated in TMEM across the KV tiles
+// Keeping P in TMEM spares shared memory a write and a read of every P tile,
+// the traffic that otherwise bounds this kernel.
 // The running row maximum m_t only moves when a row's maximum grows by more
 // than 2^8 (then O_t and the row sum are rescaled in place), so P stays below
 // 256 and rescaling is rare; the result is the same softmax.  The softmax
@@ -34,14 +37,14 @@ constexpr int kQ = 128;
 constexpr int kTiles = 2;  // query tiles per CTA
 constexpr int kKV = 128;
 constexpr int kHD = 64;
-constexpr int kKvStages = 3;
+constexpr int kKvStages = 4;
 constexpr int kThreads = 64 + kTiles * 128;
 constexpr int kTileBytes = kQ * kHD * 2;  // 16 KB: 128 rows x 128 B
-constexpr int kPBytes = kQ * kKV * 2;     // 32 KB: two 128 x 64 atoms
-constexpr int kSmemBytes = 1024 + kTileBytes * (kTiles + 2 * kKvStages) + kTiles * kPBytes + 512;
-constexpr uint32_t kTmemCols = 512;  // per tile: S 128 + O 64 (256-column stride)
+constexpr int kSmemBytes = 1024 + kTileBytes * (kTiles + 2 * kKvStages) + 512;
+constexpr uint32_t kTmemCols = 512;  // per tile: S 128 + P 64 + O 64 columns
 constexpr uint32_t kTileCols = 256;
-constexpr uint32_t kOCol = 128;
+constexpr uint32_t kPCol = 128;
+constexpr uint32_t kOCol = 192;
 constexpr float kRescaleLog2 = 8.0f;  // rescale once a row max grows by more than 2^8
 
 struct TcAttnParams {
@@ -58,31 +61,31 @@ REVO_DEVI void mask_chunk(uint32_t (&v)[32], int col0, int nvalid) {
     if (col0 + i >= nvalid) v[i] = 0xff800000u;
 }
 
-REVO_DEVI float max_chunk(const uint32_t (&v)[32], float mx) {
+// Running maxima in 8 independent lanes (short dependency chains).
+REVO_DEVI void max_chunk(const uint32_t (&v)[32], float (&mx)[8]) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) mx = fmaxf(mx, __uint_as_float(v[i]));
-  return mx;
+  for (int i = 0; i < 32; ++i) mx[i & 7] = fmaxf(mx[i & 7], __uint_as_float(v[i]));
 }
 
-// p = 2^(s c - m) for the 32 keys of chunk `ch` (columns 32 ch ..); writes them
-// as bf16 into this thread's row of the swizzled P tile; returns their sum.
-REVO_DEVI float exp_chunk(const uint32_t (&v)[32], int ch, float c, float m, uint8_t* prow, int sw) {
-  float sum = 0.f;
-  uint8_t* atom = prow + (ch >> 1) * kTileBytes;
+// p = 2^(s c - m) for 32 keys; packs them as bf16 pairs (key 2i in the low
+// half) into pk[off .. off + 15] and adds them into 8 independent partial sums.
+REVO_DEVI void exp_chunk(const uint32_t (&v)[32], float c, float m, uint32_t (&pk)[32], int off, float (&sum)[8]) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    float p[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      p[i] = ex2_approx(fmaf(__uint_as_float(v[8 * u + i]), c, -m));
-      sum += p[i];
-    }
-    const int chunk = (ch & 1) * 4 + u;
-    *reinterpret_cast<uint4*>(atom + ((chunk ^ sw) << 4)) =
-        make_uint4(pack_bf16x2(p[0], p[1]), pack_bf16x2(p[2], p[3]), pack_bf16x2(p[4], p[5]),
-                   pack_bf16x2(p[6], p[7]));
+  for (int i = 0; i < 32; i += 2) {
+    const float p0 = ex2_approx(fmaf(__uint_as_float(v[i]), c, -m));
+    const float p1 = ex2_approx(fmaf(__uint_as_float(v[i + 1]), c, -m));
+    sum[i & 7] += p0;
+    sum[(i + 1) & 7] += p1;
+    pk[off + i / 2] = pack_bf16x2(p0, p1);
   }
-  return sum;
+}
+
+REVO_DEVI float reduce8_max(const float (&a)[8]) {
+  return fmaxf(fmaxf(fmaxf(a[0], a[1]), fmaxf(a[2], a[3])), fmaxf(fmaxf(a[4], a[5]), fmaxf(a[6], a[7])));
+}
+
+REVO_DEVI float reduce8_sum(const float (&a)[8]) {
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 REVO_DEVI void scale_chunk(uint32_t (&v)[32], float a) {
@@ -98,8 +101,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* sQ = smem;                         // kTiles x 16 KB
   uint8_t* sK = sQ + kTiles * kTileBytes;     // kKvStages x 16 KB
   uint8_t* sV = sK + kKvStages * kTileBytes;  // kKvStages x 16 KB
-  uint8_t* sP = sV + kKvStages * kTileBytes;  // kTiles x 32 KB
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sP + kTiles * kPBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sV + kKvStages * kTileBytes);
   uint64_t* q_full = bars;
   uint64_t* kv_full = q_full + 1;
   uint64_t* kv_empty = kv_full + kKvStages;
@@ -162,46 +164,61 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       constexpr uint32_t kIdS = idesc_bf16(kQ, kKV);
       constexpr uint32_t kIdPV = idesc_bf16(kQ, kHD, /*b_mn_major=*/true);
+      // Issue in readiness order: per tile t the next S (needs its K tile and
+      // the softmax to have read the previous S) and the next PV (needs P),
+      // polled without blocking so one tile's softmax never holds up the
+      // other tile's MMAs.  A K/V stage is released once every tile's PV that
+      // reads it has been issued.
       bool ok = mbar_wait(q_full, 0, err, kDevTimeoutMma);
-      for (int j = 0; ok && j <= nkv; ++j) {
-        if (j < nkv) {
-          const int st = j % kKvStages;
-          if (!mbar_wait(&kv_full[st], (j / kKvStages) & 1, err, kDevTimeoutMma)) break;
-          const uint32_t k_addr = smem_u32(sK + st * kTileBytes);
-          for (int t = 0; t < ntiles && ok; ++t) {
-            if (!mbar_wait(&s_empty[t], (j & 1) ^ 1u, err, kDevTimeoutMma)) {
-              ok = false;
-              break;
-            }
+      int ns[kTiles] = {0, 0}, np[kTiles] = {0, 0};
+      int released = 0, kv_seen = 0;  // KV tiles released / observed loaded
+      long long t_last = clock64();
+      while (ok) {
+        bool progress = false, all_done = true;
+        for (int t = 0; t < ntiles; ++t) {
+          if (np[t] < ns[t] && mbar_try_wait(smem_u32(&p_full[t]), np[t] & 1)) {
+            const int jj = np[t];
             tc_fence_after();
-            const uint32_t q_addr = smem_u32(sQ + t * kTileBytes);
-#pragma unroll
-            for (int kk = 0; kk < kHD / 16; ++kk)
-              mma_f16(tmem + t * kTileCols, sw128_desc(q_addr + kk * 32), sw128_desc(k_addr + kk * 32), kIdS,
-                      kk > 0 ? 1u : 0u);
-            mma_commit(&s_full[t]);
-          }
-          if (!ok) break;
-        }
-        if (j >= 1) {
-          const int jj = j - 1;
-          const int stj = jj % kKvStages;
-          const uint32_t v_addr = smem_u32(sV + stj * kTileBytes);
-          for (int t = 0; t < ntiles && ok; ++t) {
-            if (!mbar_wait(&p_full[t], jj & 1, err, kDevTimeoutMma)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t p_addr = smem_u32(sP + t * kPBytes);
+            const uint32_t v_addr = smem_u32(sV + (jj % kKvStages) * kTileBytes);
 #pragma unroll
             for (int kk = 0; kk < kKV / 16; ++kk)
-              mma_f16(tmem + t * kTileCols + kOCol, sw128_desc(p_addr + (kk >> 2) * kTileBytes + (kk & 3) * 32),
-                      sw128_desc(v_addr + kk * 2048), kIdPV, (jj > 0 || kk > 0) ? 1u : 0u);
+              mma_f16_tmem_a(tmem + t * kTileCols + kOCol, tmem + t * kTileCols + kPCol + kk * 8,
+                             sw128_desc(v_addr + kk * 2048), kIdPV, (jj > 0 || kk > 0) ? 1u : 0u);
             mma_commit(&p_done[t]);
+            ++np[t];
+            progress = true;
           }
-          if (!ok) break;
-          mma_commit(&kv_empty[stj]);
+          if (ns[t] < nkv) {
+            const int j = ns[t];
+            if (kv_seen <= j && mbar_try_wait(smem_u32(&kv_full[j % kKvStages]), (j / kKvStages) & 1))
+              kv_seen = j + 1;
+            if (kv_seen > j && mbar_try_wait(smem_u32(&s_empty[t]), (j & 1) ^ 1u)) {
+              tc_fence_after();
+              const uint32_t k_addr = smem_u32(sK + (j % kKvStages) * kTileBytes);
+              const uint32_t q_addr = smem_u32(sQ + t * kTileBytes);
+#pragma unroll
+              for (int kk = 0; kk < kHD / 16; ++kk)
+                mma_f16(tmem + t * kTileCols, sw128_desc(q_addr + kk * 32), sw128_desc(k_addr + kk * 32), kIdS,
+                        kk > 0 ? 1u : 0u);
+              mma_commit(&s_full[t]);
+              ++ns[t];
+              progress = true;
+            }
+          }
+          all_done = all_done && np[t] == nkv;
+        }
+        int min_np = np[0];
+        if (ntiles > 1) min_np = min(min_np, np[1]);
+        while (released < min_np) {
+          mma_commit(&kv_empty[released % kKvStages]);
+          ++released;
+        }
+        if (all_done) break;
+        if (progress) {
+          t_last = clock64();
+        } else if (clock64() - t_last > kWaitLimitCycles || *reinterpret_cast<volatile int*>(err) != 0) {
+          atomicCAS(err, 0, static_cast<int>(kDevTimeoutMma));
+          ok = false;
         }
       }
     }
@@ -217,8 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       float m = -INFINITY;  // the maximum P is taken relative to (log2 units)
       float l = 0.f;
       bool ok = true;
-      uint8_t* prow = sP + t * kPBytes + r * 128;
-      const int sw = r & 7;
+      const uint32_t p_addr = tmem + t * kTileCols + kPCol + lane_off;
 
       for (int j = 0; j < nkv; ++j) {
         if (!mbar_wait(&s_full[t], j & 1, err, kDevTimeoutSoftmax)) {
@@ -243,7 +259,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           mask_chunk(v2, 64, nvalid);
           mask_chunk(v3, 96, nvalid);
         }
-        const float cand = max_chunk(v3, max_chunk(v2, max_chunk(v1, max_chunk(v0, -INFINITY)))) * c;
+        float mx8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) mx8[i] = -INFINITY;
+        max_chunk(v0, mx8);
+        max_chunk(v1, mx8);
+        max_chunk(v2, mx8);
+        max_chunk(v3, mx8);
+        const float cand = reduce8_max(mx8) * c;
         const float m_new = cand > m + kRescaleLog2 ? cand : m;
         const float alpha = ex2_approx(m - m_new);  // 1 when m is kept, 0 on the first tile
         // The previous P*V has finished: its P tile is free and O is stable.
@@ -251,12 +274,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = false;
           break;
         }
-        float sum = exp_chunk(v0, 0, c, m_new, prow, sw);
-        sum += exp_chunk(v1, 1, c, m_new, prow, sw);
-        sum += exp_chunk(v2, 2, c, m_new, prow, sw);
-        sum += exp_chunk(v3, 3, c, m_new, prow, sw);
+        tc_fence_after();
+        float sum8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sum8[i] = 0.f;
+        uint32_t pk0[32], pk1[32];
+        exp_chunk(v0, c, m_new, pk0, 0, sum8);
+        exp_chunk(v1, c, m_new, pk0, 16, sum8);
+        tmem_st32(p_addr, pk0);
+        exp_chunk(v2, c, m_new, pk1, 0, sum8);
+        exp_chunk(v3, c, m_new, pk1, 16, sum8);
+        tmem_st32(p_addr + 32, pk1);
+        const float sum = reduce8_sum(sum8);
         if (j > 0 && __any_sync(0xffffffffu, alpha != 1.f)) {
-          tc_fence_after();
           tmem_ld32(o_addr, v0);
           tmem_ld32(o_addr + 32, v1);
           tmem_wait_ld();
@@ -264,12 +294,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           scale_chunk(v1, alpha);
           tmem_st32(o_addr, v0);
           tmem_st32(o_addr + 32, v1);
-          tmem_wait_st();
         }
+        tmem_wait_st();
         l = l * alpha + sum;
         m = m_new;
         tc_fence_before();
-        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&p_full[t]);
       }

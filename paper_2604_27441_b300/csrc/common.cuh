@@ -146,6 +146,18 @@ REVO_DEVI void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32
       : "memory");
 }
 
+// Same with the A operand in TMEM (lane = row of A, K packed two bf16 per
+// 32-bit column, so a K = 16 step spans 8 columns).
+REVO_DEVI void mma_f16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                              uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // The mbarrier gets one arrival once every tcgen05 op issued so far by this
 // thread has completed.
 REVO_DEVI void mma_commit(uint64_t* bar) {
