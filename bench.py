@@ -42,7 +42,7 @@ VITB = dict(k=5, tubelet=2, patch=16, enc_dim=768, enc_depth=12, enc_heads=12, d
 FRAME_BUDGET_MS = 33.0
 # DRAM bytes (read + write) of one attn_tc_kernel launch at N = 3600, 12 heads,
 # from an ncu capture of the current kernel version (None once it changes).
-ATTN_DRAM_BYTES_PER_LAUNCH = 16632832
+ATTN_DRAM_BYTES_PER_LAUNCH = None
 
 
 def flops_per_model(C: int, h: int, w: int) -> dict:
@@ -242,7 +242,7 @@ def run_ours(args) -> None:
     w_rgb = synth.flatten(synth.weights(synth.RGB, seed=0))
     w_dep = synth.flatten(synth.weights(synth.DEPTH, seed=1))
     cfg = R.config(**VITB, precision=precision, device=local, max_height=H, max_width=W, max_streams=8,
-                   max_batch=1, lanes=1)
+                   max_batch=1, lanes=1, use_graphs=0 if args.no_graphs else 1)
     ctx = R.Context(cfg, w_rgb, w_dep, stream=stream)
 
     # Four conference streams (one per loss rate), references pushed once.
@@ -373,6 +373,7 @@ def run_ours(args) -> None:
                                    "loss 5/10/20/40% (4 streams in turn)",
                        "model": "ViT-B enc-dec (768x12 / 384x4), k=5, T=2, p=16", "global_batch": world,
                        "seq_len": fl["N"], "parallelism": f"replicas x{world}",
+                       "launch": "kernels" if args.no_graphs else "CUDA graph replay per request-size pattern",
                        "l2": "working set > L2: bf16 weights of both models (0.37 GB) stream every step"},
             "latency_ms": {"p50": float(np.percentile(lat_s, 50)), "p99": float(np.percentile(lat_s, 99)),
                            "budget": FRAME_BUDGET_MS},
@@ -426,11 +427,12 @@ def main():
     ap.add_argument("--profile-kernel", choices=["attention", "fc1"], default=None,
                     help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16", "fp32"], default="bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true", help="plain kernel launches instead of graph replay")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

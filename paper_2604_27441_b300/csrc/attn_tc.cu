@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       while (ok) {
         bool progress = false, all_done = true;
         for (int t = 0; t < ntiles; ++t) {
-          if (np[t] < ns[t] && mbar_try_wait(smem_u32(&p_full[t]), np[t] & 1)) {
+          if (np[t] < ns[t] && mbar_test(smem_u32(&p_full[t]), np[t] & 1)) {
             const int jj = np[t];
             tc_fence_after();
             const uint32_t v_addr = smem_u32(sV + (jj % kKvStages) * kTileBytes);
@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (ns[t] < nkv) {
             const int j = ns[t];
-            if (kv_seen <= j && mbar_try_wait(smem_u32(&kv_full[j % kKvStages]), (j / kKvStages) & 1))
+            if (kv_seen <= j && mbar_test(smem_u32(&kv_full[j % kKvStages]), (j / kKvStages) & 1))
               kv_seen = j + 1;
-            if (kv_seen > j && mbar_try_wait(smem_u32(&s_empty[t]), (j & 1) ^ 1u)) {
+            if (kv_seen > j && mbar_test(smem_u32(&s_empty[t]), (j & 1) ^ 1u)) {
               tc_fence_after();
               const uint32_t k_addr = smem_u32(sK + (j % kKvStages) * kTileBytes);
               const uint32_t q_addr = smem_u32(sQ + t * kTileBytes);
@@ -269,23 +269,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float cand = reduce8_max(mx8) * c;
         const float m_new = cand > m + kRescaleLog2 ? cand : m;
         const float alpha = ex2_approx(m - m_new);  // 1 when m is kept, 0 on the first tile
-        // The previous P*V has finished: its P tile is free and O is stable.
-        if (j > 0 && !mbar_wait(&p_done[t], (j - 1) & 1, err, kDevTimeoutSoftmax)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
+        // The exponentials only need S; they overlap the previous P*V.
         float sum8[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) sum8[i] = 0.f;
         uint32_t pk0[32], pk1[32];
         exp_chunk(v0, c, m_new, pk0, 0, sum8);
         exp_chunk(v1, c, m_new, pk0, 16, sum8);
-        tmem_st32(p_addr, pk0);
         exp_chunk(v2, c, m_new, pk1, 0, sum8);
         exp_chunk(v3, c, m_new, pk1, 16, sum8);
-        tmem_st32(p_addr + 32, pk1);
         const float sum = reduce8_sum(sum8);
+        // The previous P*V has finished: its P columns are free and O is stable.
+        if (j > 0 && !mbar_wait(&p_done[t], (j - 1) & 1, err, kDevTimeoutSoftmax)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        tmem_st32(p_addr, pk0);
+        tmem_st32(p_addr + 32, pk1);
         if (j > 0 && __any_sync(0xffffffffu, alpha != 1.f)) {
           tmem_ld32(o_addr, v0);
           tmem_ld32(o_addr + 32, v1);
@@ -361,7 +362,8 @@ cudaError_t launch_attention_tc(const CUtensorMap& qkv_map, void* out, int M, in
   P.start[seg.n] = seg.start[seg.n];
   P.item_prefix[seg.n] = items;
   if (items == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(attn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  static thread_local unsigned long long attr_done = 0;
+  cudaError_t e = ensure_smem_attr(attn_tc_kernel, kSmemBytes, attr_done);
   if (e != cudaSuccess) return e;
   attn_tc_kernel<<<dim3(items, heads), kThreads, kSmemBytes, st>>>(qkv_map, static_cast<__nv_bfloat16*>(out), P, err);
   return cudaGetLastError();

@@ -64,6 +64,19 @@ REVO_DEVI bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking probe of a phase (never suspends the thread): for polling loops.
+REVO_DEVI bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for the phase of the given parity to complete.  Returns false (after
 // recording `code` in *err) if the wait ran out or another role already failed.
 REVO_DEVI bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {

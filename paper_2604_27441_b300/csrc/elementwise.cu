@@ -17,7 +17,7 @@ __constant__ float kRgbStd[3] = {0.229f, 0.224f, 0.225f};
 // ------------------------------------------------------------- assemble --
 // One thread writes one run of p outputs: token n, frame t of its tubelet,
 // channel c, patch row y (vector order t, c, y, x; Appendix B.3).
-__global__ void assemble_kernel(const __grid_constant__ AssembleArgs a) {
+REVO_DEVI void assemble_body(const AssembleArgs& a) {
   const int p = a.p, C = a.C, T = a.T;
   const int Hp = a.H / p, Wp = a.W / p;
   const int S = a.F / T;
@@ -81,10 +81,16 @@ __global__ void assemble_kernel(const __grid_constant__ AssembleArgs a) {
   }
 }
 
+// Arguments by value (step-level calls) or from a device table (the runtime's
+// captured graphs read per-request arguments written just before each replay).
+__global__ void assemble_kernel(const __grid_constant__ AssembleArgs a) { assemble_body(a); }
+__global__ void assemble_kernel_dev(const AssembleArgs* __restrict__ a) { assemble_body(*a); }
+
 // ------------------------------------------------------------------- PE --
 struct PeArgs {
   float omega[128];  // 10000^(-2i/part), i < part / 2
   int taus[8];
+  const int* taus_dev;  // if set, the temporal distances are read from here
   int Hp, Wp, D, part;
 };
 
@@ -98,7 +104,8 @@ __global__ void add_pe_kernel(float* __restrict__ x, long long total, const __gr
   const int which = d / a.part;
   const int j = d % a.part;
   const int half = a.part / 2;
-  const float pos = which == 0 ? static_cast<float>(a.taus[s]) : which == 1 ? static_cast<float>(rem / a.Wp)
+  const int tau = a.taus_dev ? __ldg(a.taus_dev + s) : a.taus[s];
+  const float pos = which == 0 ? static_cast<float>(tau) : which == 1 ? static_cast<float>(rem / a.Wp)
                                                                             : static_cast<float>(rem % a.Wp);
   const float arg = pos * a.omega[j % half];
   x[idx] += (j < half) ? sinf(arg) : cosf(arg);
@@ -277,7 +284,7 @@ __global__ void __launch_bounds__(kStatsThreads) depth_stats_pass2(const uint16_
 // pixels take the quantised recovery (round half to even, clamped).  The
 // de-normalisation is done as separate float32 multiply and add (no fused
 // multiply-add), so a float32 restatement reproduces every code exactly.
-__global__ void blend_kernel(const __grid_constant__ BlendArgs a) {
+REVO_DEVI void blend_body(const BlendArgs& a) {
   const int words = (a.W + 31) / 32;
   const long long gw = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -313,6 +320,9 @@ __global__ void blend_kernel(const __grid_constant__ BlendArgs a) {
   }
 }
 
+__global__ void blend_kernel(const __grid_constant__ BlendArgs a) { blend_body(a); }
+__global__ void blend_kernel_dev(const BlendArgs* __restrict__ a) { blend_body(*a); }
+
 __global__ void f32_to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {
   const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
   if (i < n) out[i] = __float2bfloat16_rn(in[i]);
@@ -320,25 +330,32 @@ __global__ void f32_to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16* 
 
 }  // namespace
 
-cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st) {
+cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st, const AssembleArgs* dev) {
   if (a.T <= 0 || a.F % a.T != 0 || a.p <= 0 || a.p > 16 || a.H % a.p || a.W % a.p || a.F > kMaxRefs + 1 ||
       (a.C != 1 && a.C != 3))
     return cudaErrorInvalidValue;
   const long long runs = static_cast<long long>(a.F / a.T) * (a.H / a.p) * (a.W / a.p) * a.T * a.C * a.p;
   if (runs == 0) return cudaSuccess;
-  assemble_kernel<<<static_cast<unsigned>((runs + 255) / 256), 256, 0, st>>>(a);
+  const unsigned grid = static_cast<unsigned>((runs + 255) / 256);
+  if (dev)
+    assemble_kernel_dev<<<grid, 256, 0, st>>>(dev);
+  else
+    assemble_kernel<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, int D, cudaStream_t st) {
+cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, int D, cudaStream_t st,
+                          const int* taus_dev) {
   PeArgs a{};
+  a.taus_dev = taus_dev;
   a.Hp = Hp;
   a.Wp = Wp;
   a.D = D;
   a.part = D / 3;
   if (D % 6 != 0 || a.part / 2 > 128 || slots > 8 || slots < 0) return cudaErrorInvalidValue;
   for (int i = 0; i < a.part / 2; ++i) a.omega[i] = static_cast<float>(pow(10000.0, -2.0 * i / a.part));
-  for (int s = 0; s < slots; ++s) a.taus[s] = taus[s];
+  if (!taus_dev)
+    for (int s = 0; s < slots; ++s) a.taus[s] = taus[s];
   const long long total = static_cast<long long>(slots) * Hp * Wp * D;
   if (total == 0) return cudaSuccess;
   add_pe_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(x, total, a);
@@ -368,11 +385,15 @@ cudaError_t launch_depth_stats(const uint16_t* d, int H, int W, size_t pitch, fl
   return cudaGetLastError();
 }
 
-cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st) {
+cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st, const BlendArgs* dev) {
   if (a.p <= 0 || a.H % a.p || a.W % a.p || (a.C != 1 && a.C != 3)) return cudaErrorInvalidValue;
   const long long warps = static_cast<long long>(a.H) * ((a.W + 31) / 32);
   if (warps == 0) return cudaSuccess;
-  blend_kernel<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, st>>>(a);
+  const unsigned grid = static_cast<unsigned>((warps * 32 + 255) / 256);
+  if (dev)
+    blend_kernel_dev<<<grid, 256, 0, st>>>(dev);
+  else
+    blend_kernel<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -290,50 +290,96 @@ bool encode_maps(const NetShape& s, Workspace* ws, int M) {
 
 }  // namespace
 
-cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
-                        int* launches) {
+namespace {
+
+// Token segments (one per request) and the patch total; false if a size is invalid.
+bool batch_segments(const NetShape& s, const PlaneJob* jobs, int n, Segments* seg, int* patches) {
+  seg->n = n;
+  seg->start[0] = 0;
+  *patches = 0;
+  for (int i = 0; i < n; ++i) {
+    if (jobs[i].H % s.p || jobs[i].W % s.p || jobs[i].H <= 0 || jobs[i].W <= 0) return false;
+    seg->start[i + 1] = seg->start[i] + request_tokens(s, jobs[i].H, jobs[i].W);
+    *patches += request_patches(s, jobs[i].H, jobs[i].W);
+  }
+  return true;
+}
+
+}  // namespace
+
+cudaError_t prepare_job_args(const Net* net, const Workspace* ws, const PlaneJob* jobs, int n, JobArgs* args) {
   const NetShape& s = net->s;
-  if (launches) *launches = 0;
   if (n <= 0) return cudaSuccess;
   if (n > kMaxSegments) return cudaErrorInvalidValue;
-  Fwd f{net, ws, st, num_sms, net->precision != REVO_FP32, net->precision != REVO_FP32 ? 2u : 4u};
   Segments seg{};
-  seg.n = n;
-  seg.start[0] = 0;
   int patches = 0;
-  for (int i = 0; i < n; ++i) {
-    if (jobs[i].H % s.p || jobs[i].W % s.p || jobs[i].H <= 0 || jobs[i].W <= 0) return cudaErrorInvalidValue;
-    seg.start[i + 1] = seg.start[i] + request_tokens(s, jobs[i].H, jobs[i].W);
-    patches += request_patches(s, jobs[i].H, jobs[i].W);
-  }
-  const int M = seg.start[n];
-  if (M > ws->cap_tokens || patches > ws->cap_patches) return cudaErrorInvalidValue;
-  if (f.tc && !encode_maps(s, ws, M)) return cudaErrorInvalidValue;
-  cudaError_t e;
+  if (!batch_segments(s, jobs, n, &seg, &patches)) return cudaErrorInvalidValue;
+  const bool tc = net->precision != REVO_FP32;
+  const size_t e = tc ? 2 : 4;
   uint8_t* tok = static_cast<uint8_t*>(ws->tok);
-
-  // Tubelet assembly + normalisation, tubelet embedding, embeddings.
+  int hoff = 0;
   for (int i = 0; i < n; ++i) {
-    AssembleArgs a{};
+    JobArgs& j = args[i];
+    j = JobArgs{};
+    AssembleArgs& a = j.assemble;
     for (int fidx = 0; fidx <= s.k; ++fidx) {
       a.frames[fidx] = jobs[i].frames[fidx];
       a.pitch[fidx] = jobs[i].pitch[fidx];
     }
     a.mu_sigma = jobs[i].mu_sigma;
-    a.out = tok + static_cast<size_t>(seg.start[i]) * s.token_dim() * f.e;
+    a.out = tok + static_cast<size_t>(seg.start[i]) * s.token_dim() * e;
     a.C = s.C;
     a.F = s.frames();
     a.T = s.T;
     a.p = s.p;
     a.H = jobs[i].H;
     a.W = jobs[i].W;
-    a.out_bf16 = f.tc;
-    if ((e = launch_assemble(a, st)) != cudaSuccess) return e;
+    a.out_bf16 = tc;
+    BlendArgs& bl = j.blend;
+    bl.C = s.C;
+    bl.p = s.p;
+    bl.H = jobs[i].H;
+    bl.W = jobs[i].W;
+    bl.head = ws->head + static_cast<size_t>(hoff) * s.head_dim_out();
+    bl.decoded = jobs[i].frames[s.k];
+    bl.pitch = jobs[i].pitch[s.k];
+    bl.mask = jobs[i].mask;
+    bl.mask_pitch = jobs[i].mask_pitch;
+    bl.mu_sigma = jobs[i].mu_sigma;
+    bl.out = jobs[i].out;
+    bl.out_pitch = jobs[i].out_pitch;
+    bl.values = jobs[i].values;
+    for (int t = 0; t < 8; ++t) j.taus[t] = jobs[i].taus[t];
+    hoff += request_patches(s, jobs[i].H, jobs[i].W);
   }
+  return cudaSuccess;
+}
+
+cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
+                        int* launches, const JobArgs* dev_args) {
+  const NetShape& s = net->s;
+  if (launches) *launches = 0;
+  if (n <= 0) return cudaSuccess;
+  if (n > kMaxSegments) return cudaErrorInvalidValue;
+  Fwd f{net, ws, st, num_sms, net->precision != REVO_FP32, net->precision != REVO_FP32 ? 2u : 4u};
+  Segments seg{};
+  int patches = 0;
+  if (!batch_segments(s, jobs, n, &seg, &patches)) return cudaErrorInvalidValue;
+  const int M = seg.start[n];
+  if (M > ws->cap_tokens || patches > ws->cap_patches) return cudaErrorInvalidValue;
+  if (f.tc && !encode_maps(s, ws, M)) return cudaErrorInvalidValue;
+  std::vector<JobArgs> args(n);
+  cudaError_t e = prepare_job_args(net, ws, jobs, n, args.data());
+  if (e != cudaSuccess) return e;
+
+  // Tubelet assembly + normalisation, tubelet embedding, embeddings.
+  for (int i = 0; i < n; ++i)
+    if ((e = launch_assemble(args[i].assemble, st, dev_args ? &dev_args[i].assemble : nullptr)) != cudaSuccess)
+      return e;
   if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32, ws->x, s.D, M, &ws->o_x_enc)) != cudaSuccess) return e;
   for (int i = 0; i < n; ++i)
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.D, jobs[i].H / s.p, jobs[i].W / s.p,
-                           s.slots(), jobs[i].taus, s.D, st)) != cudaSuccess)
+                           s.slots(), args[i].taus, s.D, st, dev_args ? dev_args[i].taus : nullptr)) != cudaSuccess)
       return e;
 
   const Fwd::Maps enc_maps{&ws->m_h_enc, &ws->m_att_enc, &ws->m_mlp_enc, &ws->m_qkv_enc,
@@ -347,13 +393,12 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
     return e;
   for (int i = 0; i < n; ++i)
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.Dd, jobs[i].H / s.p, jobs[i].W / s.p,
-                           s.slots(), jobs[i].taus, s.Dd, st)) != cudaSuccess)
+                           s.slots(), args[i].taus, s.Dd, st, dev_args ? dev_args[i].taus : nullptr)) != cudaSuccess)
       return e;
   for (const BlockW& b : net->dec)
     if ((e = f.block(b, s.Dd, s.Hd, M, seg, dec_maps)) != cudaSuccess) return e;
 
   // Final LN and pixel head on the last slot's tokens of each request, then the blend.
-  int hoff = 0;
   uint8_t* h = static_cast<uint8_t*>(ws->h);
   for (int i = 0; i < n; ++i) {
     const int P = request_patches(s, jobs[i].H, jobs[i].W);
@@ -362,29 +407,14 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
     if ((e = launch_layernorm(ws->x + row0 * s.Dd, net->dec_norm_g, net->dec_norm_b, hrows, P, s.Dd, f.tc, st)) !=
         cudaSuccess)
       return e;
-    float* head = ws->head + static_cast<size_t>(hoff) * s.head_dim_out();
+    float* head = const_cast<float*>(args[i].blend.head);
     CUtensorMap m_rows, o_head;
     if (f.tc && (!encode_tmap_bf16_2d(&m_rows, hrows, P, s.Dd, s.Dd, 128, 64) ||
                  !encode_tmap_out_2d(&o_head, head, true, P, s.head_dim_out(), s.head_dim_out())))
       return cudaErrorInvalidValue;
     if ((e = f.linear(&m_rows, hrows, net->head, kEpiF32, head, s.head_dim_out(), P, &o_head)) != cudaSuccess)
       return e;
-    BlendArgs bl{};
-    bl.C = s.C;
-    bl.p = s.p;
-    bl.H = jobs[i].H;
-    bl.W = jobs[i].W;
-    bl.head = head;
-    bl.decoded = jobs[i].frames[s.k];
-    bl.pitch = jobs[i].pitch[s.k];
-    bl.mask = jobs[i].mask;
-    bl.mask_pitch = jobs[i].mask_pitch;
-    bl.mu_sigma = jobs[i].mu_sigma;
-    bl.out = jobs[i].out;
-    bl.out_pitch = jobs[i].out_pitch;
-    bl.values = jobs[i].values;
-    if ((e = launch_blend(bl, st)) != cudaSuccess) return e;
-    hoff += P;
+    if ((e = launch_blend(args[i].blend, st, dev_args ? &dev_args[i].blend : nullptr)) != cudaSuccess) return e;
   }
   // One kernel per step: per request assemble, 2 embeddings, final LN, head, blend;
   // tubelet embedding, encoder LN, encoder->decoder; 7 per transformer block.

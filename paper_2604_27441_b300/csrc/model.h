@@ -97,9 +97,25 @@ void workspace_destroy(Workspace* w);
 inline int request_tokens(const NetShape& s, int H, int W) { return s.slots() * (H / s.p) * (W / s.p); }
 inline int request_patches(const NetShape& s, int H, int W) { return (H / s.p) * (W / s.p); }
 
+// The per-request kernel arguments of a batch: everything that changes from one
+// batch to the next when the request sizes do not (frame, mask, output and
+// statistics pointers; temporal distances).  A batch whose sizes match an
+// earlier one can replay that batch's captured graph after writing these.
+struct JobArgs {
+  AssembleArgs assemble;
+  BlendArgs blend;
+  int taus[8];
+};
+
+// Fills args[0..n) for `jobs` (host only; the token offsets follow from the sizes).
+cudaError_t prepare_job_args(const Net* net, const Workspace* ws, const PlaneJob* jobs, int n, JobArgs* args);
+
 // Enqueues the whole forward (assemble ... blend) of `n` jobs on `st`; *launches
-// receives the number of kernels enqueued.
+// receives the number of kernels enqueued.  With `dev_args` (a device copy of
+// prepare_job_args' output, written before the kernels run) the per-request
+// kernels read their arguments from it instead of taking them by value, so the
+// enqueued work depends on the request sizes only and can be captured once.
 cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
-                        int* launches);
+                        int* launches, const JobArgs* dev_args = nullptr);
 
 }  // namespace revo

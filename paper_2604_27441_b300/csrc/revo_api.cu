@@ -81,12 +81,30 @@ struct TicketInfo {
   Clock::time_point t_submit;
 };
 
+constexpr int kArgRing = 4;     // pinned host copies of a batch's per-request arguments
+constexpr int kMaxGraphs = 64;  // captured forwards kept per lane and modality
+
+struct GraphEntry {
+  int seen = 0;
+  bool failed = false;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+};
+
 struct Lane {
   cudaStream_t st[2] = {nullptr, nullptr};
   bool own_main = true;
   Workspace* ws[2] = {nullptr, nullptr};
   cudaEvent_t fork = nullptr, join = nullptr, last_end = nullptr;
   bool used = false;
+  // Graph replay: per modality, the device table the per-request kernels read,
+  // a ring of pinned host tables it is uploaded from (an event per entry marks
+  // the upload done), and the captured forwards keyed by the request sizes.
+  JobArgs* dev_args[2] = {nullptr, nullptr};
+  JobArgs* host_args[2][kArgRing] = {};
+  cudaEvent_t args_ev[2][kArgRing] = {};
+  int args_next[2] = {0, 0};
+  std::map<std::vector<int>, GraphEntry> graphs[2];
 };
 
 }  // namespace
@@ -176,6 +194,65 @@ bool lane_idle(revo_ctx* c, int l) {
   return !L.used || cudaEventQuery(L.last_end) == cudaSuccess;
 }
 
+// Enqueues the forward of `jobs` (modality m) on lane L.  Without graphs: plain
+// launches.  With graphs: the per-request arguments are uploaded to the lane's
+// device table (one copy from pinned memory), then the graph captured for these
+// request sizes is replayed.  A size pattern runs eagerly (reading the same
+// table) the first time it is seen, so every kernel's one-time set-up happens
+// outside a capture, and is captured the second time.
+cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob>& jobs, int* launches) {
+  Net* net = c->net[m];
+  Workspace* ws = L.ws[m];
+  cudaStream_t s = L.st[m];
+  const int n = static_cast<int>(jobs.size());
+  if (!c->cfg.use_graphs || !L.dev_args[m]) return net_forward(net, ws, jobs.data(), n, s, c->sms, launches);
+
+  const int r = L.args_next[m];
+  L.args_next[m] = (r + 1) % kArgRing;
+  cudaError_t e = cudaEventSynchronize(L.args_ev[m][r]);  // that copy's last upload has been read
+  if (e != cudaSuccess) return e;
+  if ((e = prepare_job_args(net, ws, jobs.data(), n, L.host_args[m][r])) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(L.dev_args[m], L.host_args[m][r], n * sizeof(JobArgs), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaEventRecord(L.args_ev[m][r], s)) != cudaSuccess) return e;
+
+  std::vector<int> key;
+  for (const PlaneJob& j : jobs) {
+    key.push_back(j.H);
+    key.push_back(j.W);
+  }
+  auto it = L.graphs[m].find(key);
+  if (it == L.graphs[m].end()) {
+    if (static_cast<int>(L.graphs[m].size()) >= kMaxGraphs)
+      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m]);
+    it = L.graphs[m].emplace(key, GraphEntry{}).first;
+  }
+  GraphEntry& g = it->second;
+  if (!g.exec) {
+    if (g.failed || g.seen++ == 0) return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m]);
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    int nl = 0;
+    const cudaError_t ef = net_forward(net, ws, jobs.data(), n, s, c->sms, &nl, L.dev_args[m]);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    cudaError_t ei = cudaErrorUnknown;
+    if (ef == cudaSuccess && ec == cudaSuccess && graph) ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ef != cudaSuccess) return ef;  // an argument error, not a capture problem
+    if (ei != cudaSuccess) {
+      // The capture did not take: run this size pattern with plain launches from now on.
+      (void)cudaGetLastError();
+      g.exec = nullptr;
+      g.failed = true;
+      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m]);
+    }
+    g.launches = nl;
+  }
+  if (launches) *launches = g.launches;
+  return cudaGraphLaunch(g.exec, s);
+}
+
 revo_status launch_batch(revo_ctx* c, int count) {
   if (count <= 0 || c->pending.empty()) return REVO_OK;
   if (count > static_cast<int>(c->pending.size())) count = static_cast<int>(c->pending.size());
@@ -222,7 +299,7 @@ revo_status launch_batch(revo_ctx* c, int count) {
     cudaStream_t s = L.st[m];
     cudaMemsetAsync(L.ws[m]->err, 0, sizeof(int), s);
     int nl = 0;
-    e = net_forward(c->net[m], L.ws[m], jobs[m].data(), static_cast<int>(jobs[m].size()), s, c->sms, &nl);
+    e = lane_forward(c, L, m, jobs[m], &nl);
     b.launches += nl;
     if (e != cudaSuccess) st = cuda_status(e, "forward launch");
     cudaMemcpyAsync(b.err_host + m, L.ws[m]->err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -380,6 +457,12 @@ void revo_recover_destroy(revo_ctx* c) {
     for (int m = 0; m < 2; ++m) {
       if (L.st[m]) cudaStreamSynchronize(L.st[m]);
       workspace_destroy(L.ws[m]);
+      for (auto& kv : L.graphs[m])
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      for (int r = 0; r < kArgRing; ++r) {
+        if (L.host_args[m][r]) cudaFreeHost(L.host_args[m][r]);
+        if (L.args_ev[m][r]) cudaEventDestroy(L.args_ev[m][r]);
+      }
     }
     if (L.st[0] && L.own_main) cudaStreamDestroy(L.st[0]);
     if (L.st[1]) cudaStreamDestroy(L.st[1]);
@@ -464,6 +547,14 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
       L.ws[m] = workspace_create(c->shape[m], cfg->precision, cap_tok[m], cap_p[m], &err);
       if (!L.ws[m]) return fail(REVO_ENOMEM, "workspace: %s", err.c_str());
       c->bytes += L.ws[m]->bytes;
+      if (!cfg->use_graphs) continue;
+      const size_t tb = static_cast<size_t>(cfg->max_batch) * sizeof(JobArgs);
+      if (ctx_alloc(c.get(), reinterpret_cast<void**>(&L.dev_args[m]), tb) != cudaSuccess)
+        return fail(REVO_ENOMEM, "argument table allocation failed%s");
+      for (int r = 0; r < kArgRing; ++r)
+        if ((e = cudaMallocHost(reinterpret_cast<void**>(&L.host_args[m][r]), tb)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&L.args_ev[m][r], cudaEventDisableTiming)) != cudaSuccess)
+          return cuda_status(e, "argument table setup");
     }
   }
   if ((e = cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking)) != cudaSuccess ||

@@ -59,10 +59,14 @@ struct AssembleArgs {
   int C, F, T, p, H, W;
   int out_bf16;
 };
-cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st);
+// `dev` (optional): a device copy of `a` that the kernel reads instead of its
+// by-value arguments (the launch shape still comes from `a`).
+cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st, const AssembleArgs* dev = nullptr);
 
 // x[(s*Hp + r)*Wp + c][:] += sincos(tau_s) | sincos(r) | sincos(c), each D/3 wide.
-cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, int D, cudaStream_t st);
+// `taus_dev` (optional): device copy of the temporal distances, read instead of `taus`.
+cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, int D, cudaStream_t st,
+                          const int* taus_dev = nullptr);
 
 cudaError_t launch_layernorm(const float* x, const float* g, const float* b, void* out, int M, int D, int out_bf16,
                              cudaStream_t st);
@@ -83,11 +87,25 @@ struct BlendArgs {
   size_t out_pitch;
   float* values;  // optional dense [H][W][C]
 };
-cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st, const BlendArgs* dev = nullptr);
 
 cudaError_t launch_f32_to_bf16(const float* in, void* out, size_t n, cudaStream_t st);
 
 int device_sm_count();
+
+// Raises a kernel's dynamic shared-memory limit once per device (the attribute
+// call costs microseconds; launches happen hundreds of times per frame).
+// `done` is the caller's per-kernel mask of devices already set (bit = ordinal).
+template <typename Kernel>
+cudaError_t ensure_smem_attr(Kernel k, int bytes, unsigned long long& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && (done >> dev) & 1ull) return cudaSuccess;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  return e;
+}
 
 // ---- errors
 void set_last_error(const char* fmt, ...);

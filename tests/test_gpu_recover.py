@@ -53,11 +53,11 @@ def weights(shape, C):
     return _WEIGHTS[key]
 
 
-def make_ctx(shape, precision, max_hw, max_batch=1, lanes=1, max_streams=4):
+def make_ctx(shape, precision, max_hw, max_batch=1, lanes=1, max_streams=4, use_graphs=0):
     w_rgb = synth.flatten(weights(shape, 3))
     w_dep = synth.flatten(weights(shape, 1))
     cfg = R.config(**shape, precision=precision, max_height=max_hw[0], max_width=max_hw[1], max_batch=max_batch,
-                   lanes=lanes, max_streams=max_streams)
+                   lanes=lanes, max_streams=max_streams, use_graphs=use_graphs)
     return R.Context(cfg, w_rgb, w_dep)
 
 
@@ -228,6 +228,35 @@ def test_batch_result_equals_alone():
     for a, o in zip(alone, outs):
         for x, y in zip(a, o.numpy()):
             np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_equals_plain_launches(precision):
+    """With graph replay on, a size pattern runs eagerly, is then captured, then
+    replayed; every run reads its own requests' frames, masks and temporal
+    distances (new content each time, same sizes) and gives exactly what plain
+    launches give."""
+    shape = SMALL if precision == 0 else VITB
+    rounds = [[synth.make_request(3000 + 10 * it + j, wl, index=40 + it, delta=1 + (it + j) % 3)
+               for j, wl in enumerate(("320x240", "640x480", "320x240"))] for it in range(4)]
+    got = {}
+    for graphs in (0, 1):
+        with make_ctx(shape, precision, (480, 640), max_batch=3, max_streams=3, use_graphs=graphs) as ctx:
+            for it, reqs in enumerate(rounds):
+                keep = [push_refs(ctx, sid, rgb, dep) for sid, (rgb, dep) in enumerate(reqs)]
+                outs = [Outputs(rgb, dep) for rgb, dep in reqs]
+                tickets = [ctx.submit(o.request(sid, *reqs[sid])) for sid, o in enumerate(outs)]
+                ctx.flush()
+                for t in tickets:
+                    assert ctx.poll(t).status == R.REVO_OK
+                del keep
+                got[graphs, it] = [o.numpy() for o in outs]
+    for it in range(len(rounds)):
+        for a, b in zip(got[0, it], got[1, it]):
+            for x, y in zip(a, b):
+                np.testing.assert_array_equal(x, y)
+    # the content differs from round to round, so a stale argument table would show
+    assert not np.array_equal(got[1, 2][0][0], got[1, 3][0][0])
 
 
 def test_two_lanes_interleaved_streams():
