@@ -59,6 +59,11 @@ typedef enum { REVO_FP32 = 0, REVO_BF16 = 1, REVO_FP8 = 2 } revo_precision;
                            history and run nothing (Section 3.1.1 forwards intact
                            frames directly; the paper reuses clean references
                            across a GoP, Section 3.4.1)                         */
+#define REVO_HOLD 8u    /* admit the request to the pending batch without
+                           launching: the batch starts on the submit that fills
+                           max_batch, on a submit without this flag, or on
+                           flush / poll (no counterpart in the paper: a serving
+                           control)                                             */
 
 /*
  * Network shape and runtime limits.  revo_config_default() fills the ViT-B
@@ -93,6 +98,8 @@ typedef struct {
   int lanes;                     /* batches in flight at once (>= 1)             */
   void* cuda_stream;             /* cudaStream_t for the work, NULL = own streams */
   int use_graphs;                /* 1 = replay captured CUDA graphs per batch shape */
+  int autotune;                  /* 1 = time the GEMM tile widths per shape on first
+                                    use and keep the fastest (tensor-core path)  */
   const float* rgb_weights;      /* host, flat float32, NULL = no RGB model      */
   size_t rgb_weights_count;
   const float* depth_weights;    /* host, flat float32, NULL = no depth model    */
@@ -190,6 +197,21 @@ REVO_API revo_status revo_recover_flush(revo_ctx* ctx);
  * reported in out->status.
  */
 REVO_API revo_status revo_recover_poll(revo_ctx* ctx, uint64_t ticket, int64_t timeout_us, revo_result* out);
+
+/* Counters of a context (for serving dashboards and tests). */
+typedef struct {
+  size_t device_bytes;      /* device memory the context holds                     */
+  uint64_t batches;         /* forward batches launched                            */
+  uint64_t graph_replays;   /* of those modality forwards, replays of a captured graph */
+  int graphs_captured;      /* captured forwards held (all lanes, both modalities) */
+  int tuned_shapes;         /* GEMM shapes the autotuner has timed                 */
+  int tuned_wide;           /* of those, shapes where the 256-wide tile won        */
+  int pending;              /* submitted requests not yet in a batch               */
+  int in_flight;            /* batches launched and not yet retired                */
+} revo_stats;
+
+/* Fills *out.  Errors: REVO_EINVAL (null argument). */
+REVO_API revo_status revo_recover_stats(revo_ctx* ctx, revo_stats* out);
 
 /* Drains the work in flight, then frees everything the context owns. */
 REVO_API void revo_recover_destroy(revo_ctx* ctx);

@@ -18,7 +18,7 @@ REVO_OK, REVO_EAGAIN, REVO_EINVAL, REVO_ENOMEM, REVO_ETIMEDOUT, REVO_ENOREF, REV
 STATUS_NAMES = {0: "REVO_OK", 1: "REVO_EAGAIN", -1: "REVO_EINVAL", -2: "REVO_ENOMEM", -3: "REVO_ETIMEDOUT",
                 -4: "REVO_ENOREF", -5: "REVO_ECUDA", -6: "REVO_ENOTSUP"}
 FP32, BF16, FP8 = 0, 1, 2
-RGB, DEPTH, CLEAN = 1, 2, 4
+RGB, DEPTH, CLEAN, HOLD = 1, 2, 4, 8
 EPI_F32, EPI_BF16, EPI_GELU_BF16, EPI_RESID_F32 = 0, 1, 2, 3
 
 
@@ -35,7 +35,7 @@ class Config(C.Structure):
                 ("mlp_ratio", C.c_int), ("precision", C.c_int), ("device", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("max_streams", C.c_int),
                 ("max_height", C.c_int), ("max_width", C.c_int), ("max_batch", C.c_int), ("lanes", C.c_int),
-                ("cuda_stream", C.c_void_p), ("use_graphs", C.c_int),
+                ("cuda_stream", C.c_void_p), ("use_graphs", C.c_int), ("autotune", C.c_int),
                 ("rgb_weights", C.c_void_p), ("rgb_weights_count", C.c_size_t),
                 ("depth_weights", C.c_void_p), ("depth_weights_count", C.c_size_t)]
 
@@ -55,6 +55,12 @@ class Request(C.Structure):
                 ("rgb_values", C.c_void_p), ("depth_values", C.c_void_p)]
 
 
+class Stats(C.Structure):
+    _fields_ = [("device_bytes", C.c_size_t), ("batches", C.c_uint64), ("graph_replays", C.c_uint64),
+                ("graphs_captured", C.c_int), ("tuned_shapes", C.c_int), ("tuned_wide", C.c_int),
+                ("pending", C.c_int), ("in_flight", C.c_int)]
+
+
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("stream_id", C.c_uint32), ("frame_index", C.c_int64),
                 ("latency_ms", C.c_double), ("device_ms", C.c_double), ("batch_size", C.c_int),
@@ -70,6 +76,7 @@ _SIGS = {
     "revo_recover_flush": (C.c_int, [C.c_void_p]),
     "revo_recover_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(Result)]),
     "revo_recover_destroy": (None, [C.c_void_p]),
+    "revo_recover_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "revo_last_error": (C.c_char_p, []),
     "revo_op_assemble": (C.c_int, [C.c_int] * 6 + [C.POINTER(C.c_void_p), C.c_void_p, C.c_size_t, C.c_void_p,
                                                   C.c_void_p, C.c_int, C.c_void_p]),
@@ -248,6 +255,12 @@ class Context:
         if st != REVO_OK:
             raise RevoError(st, "revo_recover_poll", last_error())
         return r
+
+    def stats(self) -> dict:
+        """The context's counters (device bytes, batches, graph replays, tuned shapes, queue)."""
+        st = Stats()
+        _check(lib().revo_recover_stats(self.handle, C.byref(st)), "revo_recover_stats")
+        return {f: getattr(st, f) for f, _ in Stats._fields_}
 
     def close(self):
         if self.handle:

@@ -185,7 +185,7 @@ cudaError_t launch_attention_simt(const float* qkv, float* out, int M, int D, in
   P.tile_prefix[seg.n] = tiles;
   if (tiles == 0) return cudaSuccess;
   const int smem = kSmemFloats * static_cast<int>(sizeof(float));
-  static thread_local unsigned long long attr_done = 0;
+  static std::atomic<unsigned long long> attr_done{0};
   cudaError_t e = ensure_smem_attr(attn_simt_kernel, smem, attr_done);
   if (e != cudaSuccess) return e;
   attn_simt_kernel<<<dim3(tiles, heads), 256, smem, st>>>(qkv, out, D, P);

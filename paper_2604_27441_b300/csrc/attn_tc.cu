@@ -362,7 +362,7 @@ cudaError_t launch_attention_tc(const CUtensorMap& qkv_map, void* out, int M, in
   P.start[seg.n] = seg.start[seg.n];
   P.item_prefix[seg.n] = items;
   if (items == 0) return cudaSuccess;
-  static thread_local unsigned long long attr_done = 0;
+  static std::atomic<unsigned long long> attr_done{0};
   cudaError_t e = ensure_smem_attr(attn_tc_kernel, kSmemBytes, attr_done);
   if (e != cudaSuccess) return e;
   attn_tc_kernel<<<dim3(items, heads), kThreads, kSmemBytes, st>>>(qkv_map, static_cast<__nv_bfloat16*>(out), P, err);

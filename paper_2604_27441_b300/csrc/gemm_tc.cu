@@ -266,7 +266,7 @@ cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const CUte
                           int N, int K, int* err, int num_sms, cudaStream_t st) {
   using Cfg = TcGemmCfg<BN>;
   auto kern = gemm_tc_kernel<BN, EPI>;
-  static thread_local unsigned long long attr_done = 0;  // one per template instance
+  static std::atomic<unsigned long long> attr_done{0};  // one per template instance
   cudaError_t e = ensure_smem_attr(kern, Cfg::kSmemBytes, attr_done);
   if (e != cudaSuccess) return e;
   const int tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);

@@ -238,10 +238,76 @@ struct Fwd {
   cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M,
                      const CUtensorMap* cmap) {
     if (!tc) return launch_gemm_simt(epi, static_cast<const float*>(A), w.w32, w.b, out, ldo, M, w.out, w.in, st);
-    const int bn = pick_bn(M, w.out, sms);
+    int bn = pick_bn(M, w.out, sms);
+    if (net->autotune && M > 0) {
+      cudaError_t e = tuned_width(amap, w, epi, M, cmap, &bn);
+      if (e != cudaSuccess) return e;
+    }
     return launch_gemm_tc(*amap, bn == 256 ? w.map256 : w.map128, *cmap, bn, epi, w.b, M, w.out, w.in, ws->err, sms,
                           st);
   }
+
+  // The autotuner's choice for this shape, timing the candidates if it has none
+  // yet and the stream is not being captured.  The timed launches write the
+  // GEMM's own destination (the real launch overwrites it next), except for the
+  // residual epilogue, whose destination accumulates: those write into the
+  // qkv buffer, which holds nothing live between attention and the next block.
+  cudaError_t tuned_width(const CUtensorMap* amap, const LinearW& w, int epi, int M, const CUtensorMap* cmap,
+                          int* bn) {
+    // Row counts share a choice within buckets (128 rows up to 8192, then 2048),
+    // so a serving mix of batch sizes is not re-timed for every new total.
+    const int step = M <= 8192 ? 128 : 2048;
+    const uint64_t mb = static_cast<uint64_t>((M + step - 1) / step) * step;
+    const uint64_t key = (mb << 36) | (static_cast<uint64_t>(w.out) << 22) | (static_cast<uint64_t>(w.in) << 4) |
+                         static_cast<uint64_t>(epi);
+    auto it = net->tuned_bn.find(key);
+    if (it != net->tuned_bn.end()) {
+      *bn = it->second;
+      return cudaSuccess;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t rc = cudaStreamIsCapturing(st, &cap);
+    if (rc != cudaSuccess || cap != cudaStreamCaptureStatusNone) return rc;
+    CUtensorMap scratch;
+    const CUtensorMap* dst = cmap;
+    if (epi == kEpiResidF32) {
+      if (!encode_tmap_out_2d(&scratch, ws->qkv, true, M, w.out, w.out)) return cudaErrorInvalidValue;
+      dst = &scratch;
+    }
+    cudaEvent_t ev[2];
+    if ((rc = cudaEventCreate(&ev[0])) != cudaSuccess) return rc;
+    if ((rc = cudaEventCreate(&ev[1])) != cudaSuccess) {
+      cudaEventDestroy(ev[0]);
+      return rc;
+    }
+    float best = 0.f;
+    int best_bn = *bn;
+    for (int cand : {128, 256}) {
+      const CUtensorMap& wm = cand == 256 ? w.map256 : w.map128;
+      for (int rep = 0; rep < 4 && rc == cudaSuccess; ++rep) {
+        if (rep == 1) rc = cudaEventRecord(ev[0], st);
+        if (rc == cudaSuccess) rc = launch_gemm_tc(*amap, wm, *dst, cand, epi, w.b, M, w.out, w.in, ws->err, sms, st);
+      }
+      if (rc == cudaSuccess) rc = cudaEventRecord(ev[1], st);
+      if (rc == cudaSuccess) rc = cudaEventSynchronize(ev[1]);
+      float ms = 0.f;
+      if (rc == cudaSuccess) rc = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (rc != cudaSuccess) break;
+      if (best == 0.f || ms < best) {
+        best = ms;
+        best_bn = cand;
+      }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc != cudaSuccess) return rc;
+    net->tuned_bn[key] = best_bn;
+    ++(best_bn == 256 ? net->tuned_shapes_256 : net->tuned_shapes_128);
+    *bn = best_bn;
+    return cudaSuccess;
+  }
+
+
 
   struct Maps {
     const CUtensorMap *h, *att, *mlp, *qkv;  // operands / attention input

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -50,6 +51,13 @@ struct Net {
   LinearW patch, enc2dec, head;     // head: the rows that produce the target frame
   std::vector<BlockW> enc, dec;
   const float *enc_norm_g, *enc_norm_b, *dec_norm_g, *dec_norm_b;
+  // GEMM tile-width autotuner (tensor-core path): the first time a GEMM shape
+  // (M, N, K, epilogue) runs outside a graph capture, each candidate width is
+  // timed on the stream and the fastest is kept for every later launch and
+  // capture of that shape.  Off: a fixed rule (256 when N >= 256).
+  bool autotune = false;
+  std::map<uint64_t, int> tuned_bn;
+  int tuned_shapes_256 = 0, tuned_shapes_128 = 0;
 };
 
 // One request of one modality inside a batch (all pointers are device pointers).

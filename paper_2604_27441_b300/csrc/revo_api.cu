@@ -15,6 +15,7 @@
 // waits for every lane's last batch.
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <deque>
 #include <map>
@@ -130,6 +131,7 @@ struct revo_ctx {
   std::map<uint64_t, revo::TicketInfo> tickets;
   std::map<uint64_t, revo::Batch> batches;
   uint64_t next_ticket = 1, next_batch = 1;
+  uint64_t n_batches = 0, graph_replays = 0;
   size_t bytes = 0;
   std::vector<void*> allocs;
 };
@@ -250,6 +252,7 @@ cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob
     g.launches = nl;
   }
   if (launches) *launches = g.launches;
+  ++c->graph_replays;
   return cudaGraphLaunch(g.exec, s);
 }
 
@@ -287,6 +290,12 @@ revo_status launch_batch(revo_ctx* c, int count) {
   for (const Pending& p : taken)
     for (int m = 0; m < 2; ++m)
       if (p.has[m]) jobs[m].push_back(p.job[m]);
+  // Jobs in size order: the same mix of sizes maps to one captured graph
+  // whatever the arrival order (each job carries its own output pointers).
+  for (int m = 0; m < 2; ++m)
+    std::stable_sort(jobs[m].begin(), jobs[m].end(), [](const PlaneJob& a, const PlaneJob& b) {
+      return a.H != b.H ? a.H < b.H : a.W < b.W;
+    });
 
   cudaStream_t main = L.st[0];
   cudaEventRecord(b.ev_start, main);
@@ -333,6 +342,7 @@ revo_status launch_batch(revo_ctx* c, int count) {
     if (it != c->tickets.end()) it->second.batch = b.id;
   }
   b.size = count;
+  ++c->n_batches;
   if (st != REVO_OK) b.status = st;
   c->batches.emplace(b.id, b);
   return st;
@@ -526,6 +536,7 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
     if (!w[m]) continue;
     c->net[m] = net_create(c->shape[m], cfg->precision, w[m], &err);
     if (!c->net[m]) return fail(REVO_ENOMEM, "network upload: %s", err.c_str());
+    c->net[m]->autotune = cfg->autotune != 0 && cfg->precision != REVO_FP32;
     c->bytes += net_bytes(c->shape[m], cfg->precision);
   }
   cudaError_t e;
@@ -721,7 +732,26 @@ revo_status revo_recover_submit(revo_ctx* c, const revo_request* r, uint64_t* ti
   c->tickets[t] = ti;
   c->pending.push_back(p);
   *ticket = t;
-  dispatch(c, false);
+  if (!(r->flags & REVO_HOLD) || static_cast<int>(c->pending.size()) >= c->cfg.max_batch) dispatch(c, false);
+  return REVO_OK;
+}
+
+revo_status revo_recover_stats(revo_ctx* c, revo_stats* out) {
+  if (!c || !out) return fail(REVO_EINVAL, "null argument%s");
+  memset(out, 0, sizeof(*out));
+  out->device_bytes = c->bytes;
+  out->batches = c->n_batches;
+  out->graph_replays = c->graph_replays;
+  for (int l = 0; l < c->n_lanes; ++l)
+    for (int m = 0; m < 2; ++m)
+      for (const auto& kv : c->lanes[l].graphs[m]) out->graphs_captured += kv.second.exec != nullptr;
+  for (int m = 0; m < 2; ++m)
+    if (c->net[m]) {
+      out->tuned_shapes += static_cast<int>(c->net[m]->tuned_bn.size());
+      out->tuned_wide += c->net[m]->tuned_shapes_256;
+    }
+  out->pending = static_cast<int>(c->pending.size());
+  for (const auto& kv : c->batches) out->in_flight += kv.second.lane >= 0 && !kv.second.done;
   return REVO_OK;
 }
 

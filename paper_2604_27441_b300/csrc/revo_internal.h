@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "revo.h"
 
 namespace revo {
@@ -97,13 +99,13 @@ int device_sm_count();
 // call costs microseconds; launches happen hundreds of times per frame).
 // `done` is the caller's per-kernel mask of devices already set (bit = ordinal).
 template <typename Kernel>
-cudaError_t ensure_smem_attr(Kernel k, int bytes, unsigned long long& done) {
+cudaError_t ensure_smem_attr(Kernel k, int bytes, std::atomic<unsigned long long>& done) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 64 && (done >> dev) & 1ull) return cudaSuccess;
+  if (dev < 64 && (done.load(std::memory_order_acquire) >> dev) & 1ull) return cudaSuccess;
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  if (e == cudaSuccess && dev < 64) done.fetch_or(1ull << dev, std::memory_order_release);
   return e;
 }
 

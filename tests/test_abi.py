@@ -47,7 +47,8 @@ def test_config_default_is_the_vit_b_reading(lib):
 def test_struct_layouts_match_the_header(lib, tmp_path):
     """The binding's ctypes structs have the C compiler's sizes and offsets."""
     src = tmp_path / "layout.c"
-    fields = {"revo_config": R.Config, "revo_plane": R.Plane, "revo_request": R.Request, "revo_result": R.Result}
+    fields = {"revo_config": R.Config, "revo_plane": R.Plane, "revo_request": R.Request, "revo_result": R.Result,
+              "revo_stats": R.Stats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "revo.h"', "int main(void) {"]
     for cname, py in fields.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
@@ -78,6 +79,7 @@ def test_null_arguments_are_rejected_before_any_device_work(lib):
     assert lib.revo_recover_create(None, C.byref(h)) == R.REVO_EINVAL
     assert lib.revo_recover_submit(None, None, None) == R.REVO_EINVAL
     assert lib.revo_recover_poll(None, 1, 0, None) == R.REVO_EINVAL
+    assert lib.revo_recover_stats(None, None) == R.REVO_EINVAL
     lib.revo_recover_destroy(None)
 
 

@@ -63,3 +63,25 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.rank_max(1.5, 1) == 1.5
     assert bench.whole_job_rate(10, 2.0, 1) == 5.0
+
+
+def test_serving_arrival_schedule():
+    """30 frames/s per stream, jitter within +-5 ms, frames numbered in order."""
+    import numpy as np
+    import bench
+    ev = bench.arrival_schedule(4, 2.0, np.random.default_rng(1))
+    assert [t for t, _, _ in ev] == sorted(t for t, _, _ in ev)
+    for sid in range(4):
+        mine = [(t, n) for t, s, n in ev if s == sid]
+        assert [n for _, n in mine] == list(range(len(mine)))
+        assert 58 <= len(mine) <= 61
+        for t, n in mine:
+            assert abs(t - (mine[0][0] + n * 1000 / 30)) <= 10 + 1e-9
+
+
+def test_mixed16_proportions():
+    import bench
+    assert len(bench.MIX16) == 16
+    assert bench.MIX16.count("320x240") == 6 and bench.MIX16.count("640x480") == 6
+    assert bench.MIX16.count("1280x720+640x576") == 4
+    assert sorted(set(bench.MIX16[:3])) == sorted(set(bench.MIX16))

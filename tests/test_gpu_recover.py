@@ -53,11 +53,11 @@ def weights(shape, C):
     return _WEIGHTS[key]
 
 
-def make_ctx(shape, precision, max_hw, max_batch=1, lanes=1, max_streams=4, use_graphs=0):
+def make_ctx(shape, precision, max_hw, max_batch=1, lanes=1, max_streams=4, use_graphs=0, autotune=0):
     w_rgb = synth.flatten(weights(shape, 3))
     w_dep = synth.flatten(weights(shape, 1))
     cfg = R.config(**shape, precision=precision, max_height=max_hw[0], max_width=max_hw[1], max_batch=max_batch,
-                   lanes=lanes, max_streams=max_streams, use_graphs=use_graphs)
+                   lanes=lanes, max_streams=max_streams, use_graphs=use_graphs, autotune=autotune)
     return R.Context(cfg, w_rgb, w_dep)
 
 
@@ -257,6 +257,44 @@ def test_graph_replay_equals_plain_launches(precision):
                 np.testing.assert_array_equal(x, y)
     # the content differs from round to round, so a stale argument table would show
     assert not np.array_equal(got[1, 2][0][0], got[1, 3][0][0])
+
+
+def test_hold_batches_mixed_sizes_with_autotuned_tiles():
+    """REVO_HOLD admits requests without launching; the batch starts when it is
+    full.  Tile widths chosen by the autotuner leave every output unchanged (a
+    tile width changes which CTA computes an element, not its arithmetic)."""
+    reqs = [synth.make_request(3100 + i, wl, loss_rate=0.2)
+            for i, wl in enumerate(("640x480", "320x240", "1280x720+640x576", "320x240"))]
+    got = {}
+    for tune in (0, 1):
+        with make_ctx(VITB, R.BF16, (720, 1280), max_batch=4, max_streams=4, use_graphs=1, autotune=tune) as ctx:
+            keep = [push_refs(ctx, sid, rgb, dep) for sid, (rgb, dep) in enumerate(reqs)]
+            for rep in range(3):
+                outs = [Outputs(rgb, dep) for rgb, dep in reqs]
+                tickets = []
+                for sid, o in enumerate(outs):
+                    r = o.request(sid, *reqs[sid])
+                    r.flags |= R.HOLD
+                    tickets.append(ctx.submit(r))
+                    if sid < len(outs) - 1:
+                        assert ctx.stats()["pending"] == sid + 1
+                res = [ctx.poll(t) for t in tickets]
+                assert all(x.status == R.REVO_OK and x.batch_size == 4 for x in res)
+                got[tune, rep] = [o.numpy() for o in outs]
+            st = ctx.stats()
+            del keep
+        assert st["batches"] == 3 and st["pending"] == 0 and st["in_flight"] == 0
+        assert st["graphs_captured"] == 2 and st["graph_replays"] == 4  # 2 modalities x (capture, replay)
+        assert (st["tuned_shapes"] > 0) == bool(tune)
+    for rep in range(3):
+        for a, b in zip(got[0, rep], got[1, rep]):
+            for x, y in zip(a, b):
+                np.testing.assert_array_equal(x, y)
+    # the mixed batch equals the 640x480 request alone
+    with make_ctx(VITB, R.BF16, (480, 640)) as ctx:
+        alone = run(ctx, 0, *reqs[0])
+    for x, y in zip(alone, got[1, 2][0]):
+        np.testing.assert_array_equal(x, y)
 
 
 def test_two_lanes_interleaved_streams():
