@@ -40,6 +40,8 @@ LOSS_RATES = (0.05, 0.10, 0.20, 0.40)
 VITB = dict(k=5, tubelet=2, patch=16, enc_dim=768, enc_depth=12, enc_heads=12, dec_dim=384, dec_depth=4,
             dec_heads=6, mlp_ratio=4)
 FRAME_BUDGET_MS = 33.0
+PRECISIONS = {"bf16": lambda R: R.BF16, "fp32": lambda R: R.FP32, "fp8": lambda R: R.FP8}
+DTYPE_NAMES = {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3 (qkv, fc1; per-token x per-channel scales) + bf16"}
 # DRAM bytes (read + write) of one attn_tc_kernel launch at N = 3600, 12 heads,
 # from an ncu capture of the current kernel version (None once it changes).
 ATTN_DRAM_BYTES_PER_LAUNCH = None
@@ -240,7 +242,7 @@ def run_ours(args) -> None:
     def max_over_ranks(v: float) -> float:
         return rank_max(v, world)
 
-    precision = R.BF16 if args.precision == "bf16" else R.FP32
+    precision = PRECISIONS[args.precision](R)
     stream = torch.cuda.Stream()
     w_rgb = synth.flatten(synth.weights(synth.RGB, seed=0))
     w_dep = synth.flatten(synth.weights(synth.DEPTH, seed=1))
@@ -328,7 +330,7 @@ def run_ours(args) -> None:
     fl = flops_per_model(3, H, W)
     N, D = fl["N"], 768
     roof = None
-    if precision == R.BF16:
+    if precision != R.FP32:
         qkv = (torch.randn((N, 3 * D), device="cuda") * 1.0).to(torch.bfloat16)
         out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
         with torch.cuda.stream(stream):
@@ -365,12 +367,54 @@ def run_ours(args) -> None:
         quality = {"rgb_psnr_db_vs_fp64": 10 * np.log10(1.0 / mse) if mse > 0 else float("inf"),
                    "rgb_max_abs_err": float(np.abs(err).max()), "gate_db": 45.0}
 
+    # The other precisions on the same four streams and the same device buffers
+    # (each in a context of its own), device-timed, with the same quality check:
+    # the FP32 batch-1 path is the one the reduced-precision paths must beat.
+    compare = {}
+    if world == 1 and not args.no_compare:
+        for name in sorted(PRECISIONS):
+            if name == args.precision:
+                continue
+            c2 = R.Context(R.config(**VITB, precision=PRECISIONS[name](R), device=local, max_height=H, max_width=W,
+                                    max_streams=8, max_batch=1, lanes=1, use_graphs=0 if args.no_graphs else 1),
+                           w_rgb, w_dep, stream=stream)
+            for sid, (rgb, dep) in enumerate(reqs):
+                for j in range(rgb.refs.shape[0]):
+                    fr = torch.from_numpy(rgb.refs[j]).cuda()
+                    fd = torch.from_numpy(dep.refs[j].view(np.int16)).cuda()
+                    keep += [fr, fd]
+                    c2.poll(c2.submit(R.request(sid, int(rgb.ref_index[j]), R.RGB | R.DEPTH | R.CLEAN,
+                                                on_device=True, rgb=(fr, H, W), depth=(fd, H, W))))
+            n2 = 6 if name == "fp32" else 40
+            for i in range(4):
+                c2.poll(c2.submit(dev_req[i % 4]))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(n2):
+                r2 = c2.poll(c2.submit(dev_req[i % 4]))
+                assert r2.status == R.REVO_OK, R.last_error()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            entry = {"frames_per_s": n2 / sec, "ms_per_step": sec * 1e3 / n2, "steps": n2, "batch": 1}
+            c2.poll(c2.submit(dev_req[2]))
+            if quality is not None:
+                err = dev_bufs[2]["rv"].cpu().numpy().astype(np.float64) - o_vals
+                mse = float(np.mean(err * err))
+                entry["rgb_psnr_db_vs_fp64"] = 10 * np.log10(1.0 / mse) if mse > 0 else float("inf")
+                entry["rgb_max_abs_err"] = float(np.abs(err).max())
+            compare[name] = entry
+            c2.close()
+        if "fp32" in compare:
+            compare["speedup_vs_fp32_batch1"] = value / compare["fp32"]["frames_per_s"]
+
     if rank == 0:
         lat_s = sorted(lat)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if precision == R.BF16 else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[args.precision],
             "data": "synthetic (seeded RGB-D frames, Gilbert-Elliott slice loss, random-init ViT-B weights)",
             "config": {"workload": f"{WORKLOAD} RGB uint8 + {WORKLOAD} depth uint16, batch 1, "
                                    "loss 5/10/20/40% (4 streams in turn)",
@@ -382,7 +426,7 @@ def run_ours(args) -> None:
                            "budget": FRAME_BUDGET_MS},
             "flops_per_step": flops_per_model(3, H, W)["total"] + flops_per_model(1, H, W)["total"],
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-            "cpu_baseline": cpu, "quality": quality,
+            "cpu_baseline": cpu, "quality": quality, "precisions": compare,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -479,7 +523,7 @@ def run_mixed(args) -> None:
 
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    precision = R.BF16 if args.precision == "bf16" else R.FP32
+    precision = PRECISIONS[args.precision](R)
     cfg = R.config(**VITB, precision=precision, max_height=720, max_width=1280, max_streams=16, max_batch=16,
                    lanes=1, use_graphs=0 if args.no_graphs else 1, autotune=1)
     ctx = R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
@@ -526,7 +570,7 @@ def run_mixed(args) -> None:
     line = {"metric": METRIC, "value": out["batched"]["frames_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": out["batched"]["steps"], "warmup": args.warmup, "ms_per_step": out["batched"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if precision == R.BF16 else "f32", "data": "synthetic",
+            "dtype": DTYPE_NAMES[args.precision], "data": "synthetic",
             "config": {"workload": "mixed16: 6 x 320x240 + 6 x 640x480 + 4 x (1280x720 RGB + 640x576 depth), "
                                    "one batch of 16 per step", "flops_per_step": flops,
                        "launch": "kernels" if args.no_graphs else "CUDA graph replay, autotuned GEMM tiles"},
@@ -581,7 +625,7 @@ def run_serving(args) -> None:
     import synth
     torch.cuda.set_device(0)
     rng = np.random.default_rng(5000 + args.streams)
-    precision = R.BF16 if args.precision == "bf16" else R.FP32
+    precision = PRECISIONS[args.precision](R)
     cfg = R.config(**VITB, precision=precision, max_height=720, max_width=1280, max_streams=args.streams,
                    max_batch=args.max_batch, lanes=args.lanes, use_graphs=0 if args.no_graphs else 1, autotune=1,
                    hbm_budget_bytes=40 << 30)
@@ -649,7 +693,7 @@ def run_serving(args) -> None:
     offered = sum(1 for t, _, n in events if t >= args.serve_warmup * 1e3 and n % 30 != 29)
     line = {"metric": METRIC, "value": done_frames / (wall / 1e3), "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if precision == R.BF16 else "f32", "data": "synthetic",
+            "dtype": DTYPE_NAMES[args.precision], "data": "synthetic",
             "config": {"workload": f"serving: {args.streams} streams at 30 fps, resolutions {sorted(set(wls))}",
                        "seconds": args.seconds, "warmup_s": args.serve_warmup, "max_batch": args.max_batch,
                        "lanes": args.lanes, "hbm_budget_gb": 40, "inputs": "pinned host buffers"},
@@ -679,6 +723,15 @@ def run_profile_kernel(args) -> None:
         out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
         launch = lambda: R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream)  # noqa: E731
         flops = fl["attn_enc_per_block"]
+    elif args.profile_kernel == "fc1_fp8":  # the same fc1 with E4M3 operands
+        a = torch.randint(0, 120, (N, D), dtype=torch.uint8, device="cuda")
+        w = torch.randint(0, 120, (4 * D, D), dtype=torch.uint8, device="cuda")
+        sa = torch.full((N,), 0.01, device="cuda")
+        sw = torch.full((4 * D,), 0.01, device="cuda")
+        b = torch.zeros(4 * D, device="cuda")
+        out = torch.empty((N, 4 * D), dtype=torch.bfloat16, device="cuda")
+        launch = lambda: R.op_linear_fp8(2, a, sa, w, sw, b, out, N, 4 * D, D, 256, stream=stream)  # noqa: E731
+        flops = 2 * N * D * 4 * D
     else:  # fc1 of an encoder block: [N, 768] x [3072, 768]^T + GELU
         a = torch.randn((N, D), device="cuda").to(torch.bfloat16)
         w = (torch.randn((4 * D, D), device="cuda") / 28).to(torch.bfloat16)
@@ -702,15 +755,16 @@ def run_profile_kernel(args) -> None:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-kernel", choices=["attention", "fc1"], default=None,
+    ap.add_argument("--profile-kernel", choices=["attention", "fc1", "fc1_fp8"], default=None,
                     help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="plain kernel launches instead of graph replay")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
     ap.add_argument("--workload", choices=["640x480", "mixed16", "serving"], default="640x480",
                     help="640x480: the headline batch-1 step; mixed16: one batch of 16 mixed-size streams; "
                          "serving: real-time arrivals from --streams streams")

@@ -100,6 +100,10 @@ typedef struct {
   int use_graphs;                /* 1 = replay captured CUDA graphs per batch shape */
   int autotune;                  /* 1 = time the GEMM tile widths per shape on first
                                     use and keep the fastest (tensor-core path)  */
+  int fp8_layers;                /* REVO_FP8: which LayerNorm-fed layers run in E4M3
+                                    (bit 0 encoder qkv, 1 encoder fc1, 2 decoder
+                                    qkv, 3 decoder fc1; the rest stay bf16);
+                                    0 = the default set: encoder fc1 only       */
   const float* rgb_weights;      /* host, flat float32, NULL = no RGB model      */
   size_t rgb_weights_count;
   const float* depth_weights;    /* host, flat float32, NULL = no depth model    */
@@ -294,6 +298,34 @@ REVO_API revo_status revo_op_linear(revo_precision precision, int epilogue, cons
 /* Row-wise LayerNorm, eps 1e-6: x float32 [M][D] -> out (bf16 if out_bf16, else float32). */
 REVO_API revo_status revo_op_layernorm(const float* x, const float* gamma, const float* beta, void* out,
                               int M, int D, int out_bf16, void* stream);
+
+/*
+ * FP8 building blocks (no counterpart in the paper, which runs its model in
+ * full precision; this is the reduced-precision path of the linear layers).
+ * Codes are OCP FP8 E4M3 (bias 7, largest finite 448, no infinities).
+ *
+ * revo_op_quantize_rows_e4m3: per-row scale[r] = max_k |x[r][k]| / 448 (1 for
+ * an all-zero row) and codes q[r][k] = E4M3(x[r][k] * (448 / max)), rounded to
+ * nearest even and saturated to +-448; the product is taken in float32.  x is
+ * float32 [rows][cols], cols % 4 == 0; q is [rows][cols] bytes; all device.
+ * The weights use it with one row per output channel.
+ *
+ * revo_op_layernorm_e4m3: revo_op_layernorm (float32 result), then the same
+ * per-row quantisation: out [M][D] codes, row_scale [M].
+ *
+ * revo_op_linear_fp8: out = epilogue(a_scale[m] * w_scale[n] * sum_k A[m][k] W[n][k]
+ * + bias[n]) with A [M][K] and W [N][K] E4M3 codes (decoded exactly), the sum
+ * accumulated in float32 on the tensor cores.  epilogue 1 (bf16 out) or 2
+ * (GELU, bf16 out); out bf16 [M][N].  K % 128 == 0, N % 64 == 0; tile_n 128
+ * or 256.  Errors: REVO_EINVAL, REVO_ECUDA.
+ */
+REVO_API revo_status revo_op_quantize_rows_e4m3(const float* x, int rows, int cols, uint8_t* q, float* scale,
+                                                void* stream);
+REVO_API revo_status revo_op_layernorm_e4m3(const float* x, const float* gamma, const float* beta, uint8_t* out,
+                                            float* row_scale, int M, int D, void* stream);
+REVO_API revo_status revo_op_linear_fp8(int epilogue, const uint8_t* A, const float* a_scale, const uint8_t* W,
+                                        const float* w_scale, const float* bias, void* out, int M, int N, int K,
+                                        int tile_n, void* stream);
 
 /*
  * Multi-head softmax attention over segments of tokens (the exact scaled

@@ -36,6 +36,7 @@ class Config(C.Structure):
                 ("hbm_budget_bytes", C.c_size_t), ("max_streams", C.c_int),
                 ("max_height", C.c_int), ("max_width", C.c_int), ("max_batch", C.c_int), ("lanes", C.c_int),
                 ("cuda_stream", C.c_void_p), ("use_graphs", C.c_int), ("autotune", C.c_int),
+                ("fp8_layers", C.c_int),
                 ("rgb_weights", C.c_void_p), ("rgb_weights_count", C.c_size_t),
                 ("depth_weights", C.c_void_p), ("depth_weights_count", C.c_size_t)]
 
@@ -94,6 +95,9 @@ _SIGS = {
                                 C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
                                 C.c_void_p]),
     "revo_op_take_device_error": (C.c_int, []),
+    "revo_op_quantize_rows_e4m3": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "revo_op_layernorm_e4m3": (C.c_int, [C.c_void_p] * 5 + [C.c_int, C.c_int, C.c_void_p]),
+    "revo_op_linear_fp8": (C.c_int, [C.c_int] + [C.c_void_p] * 6 + [C.c_int] * 4 + [C.c_void_p]),
     "revo_op_depth_stats_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_size_t, C.c_void_p, C.c_void_p]),
 }
 
@@ -180,6 +184,21 @@ def op_linear(precision, epilogue, A, W, bias, out, M, N, K, tile_n=0, stream=No
 def op_layernorm(x, gamma, beta, out, M, D, out_bf16, stream=None):
     return _check(lib().revo_op_layernorm(ptr(x), ptr(gamma), ptr(beta), ptr(out), M, D, int(out_bf16),
                                           _stream(stream)), "revo_op_layernorm")
+
+
+def op_quantize_rows_e4m3(x, rows, cols, q, scale, stream=None):
+    return _check(lib().revo_op_quantize_rows_e4m3(ptr(x), rows, cols, ptr(q), ptr(scale), _stream(stream)),
+                  "revo_op_quantize_rows_e4m3")
+
+
+def op_layernorm_e4m3(x, gamma, beta, out, row_scale, M, D, stream=None):
+    return _check(lib().revo_op_layernorm_e4m3(ptr(x), ptr(gamma), ptr(beta), ptr(out), ptr(row_scale), M, D,
+                                               _stream(stream)), "revo_op_layernorm_e4m3")
+
+
+def op_linear_fp8(epilogue, A, a_scale, W, w_scale, bias, out, M, N, K, tile_n=0, stream=None):
+    return _check(lib().revo_op_linear_fp8(epilogue, ptr(A), ptr(a_scale), ptr(W), ptr(w_scale), ptr(bias), ptr(out),
+                                           M, N, K, tile_n, _stream(stream)), "revo_op_linear_fp8")
 
 
 def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None):

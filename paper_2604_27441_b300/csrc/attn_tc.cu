@@ -61,21 +61,51 @@ REVO_DEVI void mask_chunk(uint32_t (&v)[32], int col0, int nvalid) {
     if (col0 + i >= nvalid) v[i] = 0xff800000u;
 }
 
-// Running maxima in 8 independent lanes (short dependency chains).
-REVO_DEVI void max_chunk(const uint32_t (&v)[32], float (&mx)[8]) {
-#pragma unroll
-  for (int i = 0; i < 32; ++i) mx[i & 7] = fmaxf(mx[i & 7], __uint_as_float(v[i]));
+// Three-input maximum (one instruction for two new values).
+REVO_DEVI float max3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
 }
 
-// p = 2^(s c - m) for 32 keys; packs them as bf16 pairs (key 2i in the low
-// half) into pk[off .. off + 15] and adds them into 8 independent partial sums.
-REVO_DEVI void exp_chunk(const uint32_t (&v)[32], float c, float m, uint32_t (&pk)[32], int off, float (&sum)[8]) {
+// Packed pair arithmetic on the f32x2 path: d = a * b + c and d = a + b.
+REVO_DEVI uint64_t pk2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+REVO_DEVI void unpk2(uint64_t v, float& lo, float& hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+REVO_DEVI uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+REVO_DEVI uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Running maxima in 8 independent lanes (short dependency chains), two new
+// values per instruction.
+REVO_DEVI void max_chunk(const uint32_t (&v)[32], float (&mx)[8]) {
+#pragma unroll
+  for (int i = 0; i < 32; i += 2)
+    mx[(i >> 1) & 7] = max3(mx[(i >> 1) & 7], __uint_as_float(v[i]), __uint_as_float(v[i + 1]));
+}
+
+// p = 2^(s c - m) for 32 keys (scale and shift as packed pairs); packs them as
+// bf16 pairs (key 2i in the low half) into pk[off .. off + 15] and adds them
+// into 4 packed pairs of partial sums.
+REVO_DEVI void exp_chunk(const uint32_t (&v)[32], uint64_t c2, uint64_t negm2, uint32_t (&pk)[32], int off,
+                         uint64_t (&sum2)[4]) {
 #pragma unroll
   for (int i = 0; i < 32; i += 2) {
-    const float p0 = ex2_approx(fmaf(__uint_as_float(v[i]), c, -m));
-    const float p1 = ex2_approx(fmaf(__uint_as_float(v[i + 1]), c, -m));
-    sum[i & 7] += p0;
-    sum[(i + 1) & 7] += p1;
+    float a0, a1;
+    unpk2(fma2(pk2(__uint_as_float(v[i]), __uint_as_float(v[i + 1])), c2, negm2), a0, a1);
+    const float p0 = ex2_approx(a0);
+    const float p1 = ex2_approx(a1);
+    sum2[(i >> 1) & 3] = add2(sum2[(i >> 1) & 3], pk2(p0, p1));
     pk[off + i / 2] = pack_bf16x2(p0, p1);
   }
 }
@@ -173,6 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int ns[kTiles] = {0, 0}, np[kTiles] = {0, 0};
       int released = 0, kv_seen = 0;  // KV tiles released / observed loaded
       long long t_last = clock64();
+      uint32_t idle = 0;
       while (ok) {
         bool progress = false, all_done = true;
         for (int t = 0; t < ntiles; ++t) {
@@ -214,11 +245,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++released;
         }
         if (all_done) break;
+        // The failure checks (a global load and the clock) only run every 256
+        // idle polls: on the polling path they would delay every issue.
         if (progress) {
-          t_last = clock64();
-        } else if (clock64() - t_last > kWaitLimitCycles || *reinterpret_cast<volatile int*>(err) != 0) {
-          atomicCAS(err, 0, static_cast<int>(kDevTimeoutMma));
-          ok = false;
+          idle = 0;
+        } else if ((++idle & 255u) == 0) {
+          if (idle == 256u) t_last = clock64();
+          if (clock64() - t_last > kWaitLimitCycles || *reinterpret_cast<volatile int*>(err) != 0) {
+            atomicCAS(err, 0, static_cast<int>(kDevTimeoutMma));
+            ok = false;
+          }
         }
       }
     }
@@ -237,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t p_addr = tmem + t * kTileCols + kPCol + lane_off;
 
       for (int j = 0; j < nkv; ++j) {
-        if (!mbar_wait(&s_full[t], j & 1, err, kDevTimeoutSoftmax)) {
+        if (!mbar_wait_warp(&s_full[t], j & 1, err, kDevTimeoutSoftmax, lane)) {
           ok = false;
           break;
         }
@@ -270,17 +306,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float m_new = cand > m + kRescaleLog2 ? cand : m;
         const float alpha = ex2_approx(m - m_new);  // 1 when m is kept, 0 on the first tile
         // The exponentials only need S; they overlap the previous P*V.
+        uint64_t sum2[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sum2[i] = 0ull;  // +0.0f pairs
+        const uint64_t c2 = pk2(c, c), negm2 = pk2(-m_new, -m_new);
+        uint32_t pk0[32], pk1[32];
+        exp_chunk(v0, c2, negm2, pk0, 0, sum2);
+        exp_chunk(v1, c2, negm2, pk0, 16, sum2);
+        exp_chunk(v2, c2, negm2, pk1, 0, sum2);
+        exp_chunk(v3, c2, negm2, pk1, 16, sum2);
         float sum8[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) sum8[i] = 0.f;
-        uint32_t pk0[32], pk1[32];
-        exp_chunk(v0, c, m_new, pk0, 0, sum8);
-        exp_chunk(v1, c, m_new, pk0, 16, sum8);
-        exp_chunk(v2, c, m_new, pk1, 0, sum8);
-        exp_chunk(v3, c, m_new, pk1, 16, sum8);
+        for (int i = 0; i < 4; ++i) unpk2(sum2[i], sum8[2 * i], sum8[2 * i + 1]);
         const float sum = reduce8_sum(sum8);
         // The previous P*V has finished: its P columns are free and O is stable.
-        if (j > 0 && !mbar_wait(&p_done[t], (j - 1) & 1, err, kDevTimeoutSoftmax)) {
+        if (j > 0 && !mbar_wait_warp(&p_done[t], (j - 1) & 1, err, kDevTimeoutSoftmax, lane)) {
           ok = false;
           break;
         }
@@ -303,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&p_full[t]);
       }
-      if (ok && nkv > 0 && mbar_wait(&p_done[t], (nkv - 1) & 1, err, kDevTimeoutSoftmax)) {
+      if (ok && nkv > 0 && mbar_wait_warp(&p_done[t], (nkv - 1) & 1, err, kDevTimeoutSoftmax, lane)) {
         tc_fence_after();
         uint32_t o0[32], o1[32];
         tmem_ld32(o_addr, o0);

@@ -95,6 +95,17 @@ REVO_DEVI bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
   }
 }
 
+// Warp-wide wait with one polling lane: lane 0 waits, the warp then
+// synchronises on it (the other lanes' memory view is ordered by __syncwarp).
+// 32 lanes polling one barrier slow every other waiter on the SM.
+REVO_DEVI bool mbar_wait_warp(uint64_t* bar, uint32_t parity, int* err, int code, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = mbar_wait(bar, parity, err, code) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
 // ------------------------------------------------------------------ TMA --
 
 REVO_DEVI void tma_load_2d(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -171,6 +182,17 @@ REVO_DEVI void mma_f16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
       : "memory");
 }
 
+// kind::f8f6f4 with both operands 8-bit floats from shared memory (K = 32 per
+// instruction, 32 bytes of a 128-byte swizzled row).
+REVO_DEVI void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // The mbarrier gets one arrival once every tcgen05 op issued so far by this
 // thread has completed.
 REVO_DEVI void mma_commit(uint64_t* bar) {
@@ -183,6 +205,12 @@ REVO_DEVI void mma_commit(uint64_t* bar) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major = false) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn_major ? 1u : 0u) << 16) |
          (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::f8f6f4: D f32, A and B E4M3 (format code 0),
+// M x N, both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 // Shared-memory matrix descriptor for a 128-byte-swizzled tile whose rows are

@@ -2,6 +2,7 @@
 // fused with the tubelet gather, the sinusoidal (temporal distance, row,
 // column) embedding, LayerNorm, depth statistics, and the warp-level
 // de-normalise / quantise / masked-blend writeback.
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -115,8 +116,31 @@ __global__ void add_pe_kernel(float* __restrict__ x, long long total, const __gr
 // One warp per row, two passes over registers, eps 1e-6, biased variance.
 constexpr int kLnMaxVec = 8;  // D <= 1024
 
+// Four floats -> four E4M3 codes (round to nearest even, saturating to +-448),
+// the first value in the lowest byte.
+REVO_DEVI uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return lo | (hi << 16);
+}
+
+// Per-row E4M3 scale rule: s = amax / 448, inverse 448 / amax; an all-zero row
+// keeps s = 1.
+REVO_DEVI void e4m3_row_scale(float amax, float* s, float* inv) {
+  if (amax > 0.f) {
+    *s = amax / 448.0f;
+    *inv = 448.0f / amax;
+  } else {
+    *s = 1.0f;
+    *inv = 1.0f;
+  }
+}
+
+// OUT: 0 float32, 1 bf16, 2 E4M3 codes + a per-row scale.
+template <int OUT>
 __global__ void layernorm_kernel(const float* __restrict__ x, const float* __restrict__ g,
-                                 const float* __restrict__ b, void* __restrict__ out, int M, int D, int out_bf16) {
+                                 const float* __restrict__ b, void* __restrict__ out, float* __restrict__ row_scale,
+                                 int M, int D) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= M) return;
@@ -149,6 +173,7 @@ __global__ void layernorm_kernel(const float* __restrict__ x, const float* __res
   const float rstd = 1.0f / sqrtf(sq / D + 1e-6f);
   const float4* g4 = reinterpret_cast<const float4*>(g);
   const float4* b4 = reinterpret_cast<const float4*>(b);
+  float amax = 0.f;
 #pragma unroll
   for (int i = 0; i < kLnMaxVec; ++i) {
     const int c = lane + 32 * i;
@@ -158,7 +183,10 @@ __global__ void layernorm_kernel(const float* __restrict__ x, const float* __res
       const float y1 = (v[i].y - mean) * rstd * gg.y + bb.y;
       const float y2 = (v[i].z - mean) * rstd * gg.z + bb.z;
       const float y3 = (v[i].w - mean) * rstd * gg.w + bb.w;
-      if (out_bf16) {
+      if (OUT == 2) {
+        v[i] = make_float4(y0, y1, y2, y3);
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(y0), fabsf(y1)), fmaxf(fabsf(y2), fabsf(y3))));
+      } else if (OUT == 1) {
         uint2* o = reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out) + static_cast<size_t>(warp) * D) + c;
         *o = make_uint2(pack_bf16x2(y0, y1), pack_bf16x2(y2, y3));
       } else {
@@ -167,6 +195,44 @@ __global__ void layernorm_kernel(const float* __restrict__ x, const float* __res
       }
     }
   }
+  if (OUT == 2) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    float sc, inv;
+    e4m3_row_scale(amax, &sc, &inv);
+    uint32_t* orow = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(out) + static_cast<size_t>(warp) * D);
+#pragma unroll
+    for (int i = 0; i < kLnMaxVec; ++i) {
+      const int c = lane + 32 * i;
+      if (c < nv) orow[c] = pack_e4m3x4(v[i].x * inv, v[i].y * inv, v[i].z * inv, v[i].w * inv);
+    }
+    if (lane == 0) row_scale[warp] = sc;
+  }
+}
+
+// One warp per row: amax pass, then the codes.
+__global__ void quantize_rows_e4m3_kernel(const float* __restrict__ x, int rows, int cols, uint8_t* __restrict__ q,
+                                          float* __restrict__ scale) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const float4* xr = reinterpret_cast<const float4*>(x + static_cast<size_t>(row) * cols);
+  const int nv = cols / 4;
+  float amax = 0.f;
+  for (int c = lane; c < nv; c += 32) {
+    const float4 a = __ldg(xr + c);
+    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  float sc, inv;
+  e4m3_row_scale(amax, &sc, &inv);
+  uint32_t* qr = reinterpret_cast<uint32_t*>(q + static_cast<size_t>(row) * cols);
+  for (int c = lane; c < nv; c += 32) {
+    const float4 a = __ldg(xr + c);
+    qr[c] = pack_e4m3x4(a.x * inv, a.y * inv, a.z * inv, a.w * inv);
+  }
+  if (lane == 0) scale[row] = sc;
 }
 
 // ---------------------------------------------------------- depth stats --
@@ -366,7 +432,25 @@ cudaError_t launch_layernorm(const float* x, const float* g, const float* b, voi
                              cudaStream_t st) {
   if (D % 4 != 0 || D > 4 * 32 * kLnMaxVec) return cudaErrorInvalidValue;
   if (M <= 0) return cudaSuccess;
-  layernorm_kernel<<<(M + 7) / 8, 256, 0, st>>>(x, g, b, out, M, D, out_bf16);
+  if (out_bf16)
+    layernorm_kernel<1><<<(M + 7) / 8, 256, 0, st>>>(x, g, b, out, nullptr, M, D);
+  else
+    layernorm_kernel<0><<<(M + 7) / 8, 256, 0, st>>>(x, g, b, out, nullptr, M, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layernorm_e4m3(const float* x, const float* g, const float* b, uint8_t* out, float* row_scale,
+                                  int M, int D, cudaStream_t st) {
+  if (D % 4 != 0 || D > 4 * 32 * kLnMaxVec || !row_scale) return cudaErrorInvalidValue;
+  if (M <= 0) return cudaSuccess;
+  layernorm_kernel<2><<<(M + 7) / 8, 256, 0, st>>>(x, g, b, out, row_scale, M, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_rows_e4m3(const float* x, int rows, int cols, uint8_t* q, float* scale, cudaStream_t st) {
+  if (cols % 4 != 0 || cols <= 0 || rows < 0) return cudaErrorInvalidValue;
+  if (rows == 0) return cudaSuccess;
+  quantize_rows_e4m3_kernel<<<(rows + 7) / 8, 256, 0, st>>>(x, rows, cols, q, scale);
   return cudaGetLastError();
 }
 

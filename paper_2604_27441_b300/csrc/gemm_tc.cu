@@ -13,6 +13,11 @@
 // bulk f32 add-reduction into the residual stream (one rounding per element,
 // exactly as x += y).
 //
+// The FP8 variant takes E4M3 operands (tcgen05 kind::f8f6f4, 128 elements =
+// one 128-byte swizzle atom per stage row, so the pipeline is byte-for-byte the
+// same) and multiplies each accumulator by its row's activation scale and its
+// column's weight scale before the bias.
+//
 // Warp roles (320 threads, one CTA per SM, persistent over output tiles):
 //   warp 0      TMA producer (one thread)
 //   warp 1      TMEM allocator + MMA issuer (one thread)
@@ -27,6 +32,7 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;  // 64 bf16 = one 128-byte swizzle atom per row
+constexpr int kBK8 = 128;  // 128 E4M3 = the same 128 bytes
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kOutChunkBytes = 32 * 128;  // 32 rows x 128 B staging per epilogue warp
@@ -50,6 +56,19 @@ REVO_DEVI void stage_row(uint8_t* chunk, int row, const uint4 (&pieces)[8]) {
   for (int k = 0; k < 8; ++k) *reinterpret_cast<uint4*>(base + ((k ^ (row & 7)) << 4)) = pieces[k];
 }
 
+// v[i] *= rs * cs[col + i] (FP8 dequantisation: token scale x channel scale).
+REVO_DEVI void apply_scales(float (&v)[32], float rs, const float* __restrict__ cs, int col) {
+  const float4* c4 = reinterpret_cast<const float4*>(cs + col);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 c = __ldg(c4 + i);
+    v[4 * i] *= rs * c.x;
+    v[4 * i + 1] *= rs * c.y;
+    v[4 * i + 2] *= rs * c.z;
+    v[4 * i + 3] *= rs * c.w;
+  }
+}
+
 REVO_DEVI void add_bias(float (&v)[32], const float* __restrict__ bias, int col) {
   if (bias == nullptr) return;
   const float4* b4 = reinterpret_cast<const float4*>(bias + col);
@@ -65,9 +84,9 @@ REVO_DEVI void add_bias(float (&v)[32], const float* __restrict__ bias, int col)
 
 // One epilogue chunk: 32 rows (this warp's lanes) x 128 bytes of output
 // (32 f32 columns or 64 bf16 columns) starting at tile column `c0`.
-template <int EPI>
+template <int EPI, bool F8>
 REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, int n0, int c0, uint8_t* chunk,
-                              const CUtensorMap* map, int row0, int lane) {
+                              const CUtensorMap* map, int row0, int lane, float rs, const float* __restrict__ cs) {
   uint4 pieces[8];
   if (EPI == kEpiF32 || EPI == kEpiResidF32) {
     uint32_t r[32];
@@ -76,6 +95,7 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
     float v[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    if (F8) apply_scales(v, rs, cs, n0 + c0);
     add_bias(v, bias, n0 + c0);
 #pragma unroll
     for (int k = 0; k < 8; ++k)
@@ -90,6 +110,7 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
       float v[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+      if (F8) apply_scales(v, rs, cs, n0 + c0 + 32 * half);
       add_bias(v, bias, n0 + c0 + 32 * half);
       if (EPI == kEpiGeluBf16) {
 #pragma unroll
@@ -117,14 +138,16 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
   }
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmC, const float* __restrict__ bias, int M, int N, int K,
+                   const __grid_constant__ CUtensorMap tmC, const float* __restrict__ bias,
+                   const float* __restrict__ row_scale, const float* __restrict__ col_scale, int M, int N, int K,
                    int* err) {
   using Cfg = TcGemmCfg<BN>;
   constexpr int S = Cfg::kStages;
-  constexpr uint32_t kIdesc = idesc_bf16(kBM, BN);
+  constexpr uint32_t kIdesc = F8 ? idesc_e4m3(kBM, BN) : idesc_bf16(kBM, BN);
+  constexpr int kKe = F8 ? kBK8 : kBK;  // K elements per stage
   constexpr int kChunkCols = (EPI == kEpiF32 || EPI == kEpiResidF32) ? 32 : 64;
 
   extern __shared__ uint8_t smem_raw[];
@@ -143,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int m_tiles = (M + kBM - 1) / kBM;
   const int n_tiles = (N + BN - 1) / BN;
   const int num_tiles = m_tiles * n_tiles;
-  const int num_kb = K / kBK;
+  const int num_kb = K / kKe;
 
   if (threadIdx.x == 0) {
     tma_prefetch_desc(&tmA);
@@ -182,8 +205,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
-          tma_load_2d(sA + stage * Cfg::kABytes, &tmA, kb * kBK, m0, &full[stage]);
-          tma_load_2d(sB + stage * Cfg::kBBytes, &tmB, kb * kBK, n0, &full[stage]);
+          tma_load_2d(sA + stage * Cfg::kABytes, &tmA, kb * kKe, m0, &full[stage]);
+          tma_load_2d(sB + stage * Cfg::kBBytes, &tmB, kb * kKe, n0, &full[stage]);
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -212,9 +235,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a_addr = smem_u32(sA + stage * Cfg::kABytes);
           const uint32_t b_addr = smem_u32(sB + stage * Cfg::kBBytes);
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk)
-            mma_f16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
-                    (kb | kk) != 0 ? 1u : 0u);
+          for (int kk = 0; kk < 4; ++kk) {  // 4 x 32 bytes of K per stage
+            if (F8)
+              mma_f8(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
+                     (kb | kk) != 0 ? 1u : 0u);
+            else
+              mma_f16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
+                      (kb | kk) != 0 ? 1u : 0u);
+          }
           mma_commit(&empty[stage]);
           if (++stage == S) {
             stage = 0;
@@ -238,10 +266,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int m0 = (tile % m_tiles) * kBM;
       const int n0 = (tile / m_tiles) * BN;
       const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BN;
+      const int my_row = m0 + q * 32 + lane;
+      const float rs = (F8 && my_row < M) ? __ldg(row_scale + my_row) : 0.f;
 #pragma unroll 1
       for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += kChunkCols) {
         if (n0 + c0 >= N) break;
-        epilogue_chunk<EPI>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane);
+        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale);
       }
       tc_fence_before();
       __syncwarp();
@@ -261,17 +291,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 namespace {
 
-template <int BN, int EPI>
+template <int BN, int EPI, bool F8 = false>
 cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const float* bias, int M,
-                          int N, int K, int* err, int num_sms, cudaStream_t st) {
+                          int N, int K, int* err, int num_sms, cudaStream_t st, const float* row_scale = nullptr,
+                          const float* col_scale = nullptr) {
   using Cfg = TcGemmCfg<BN>;
-  auto kern = gemm_tc_kernel<BN, EPI>;
+  auto kern = gemm_tc_kernel<BN, EPI, F8>;
   static std::atomic<unsigned long long> attr_done{0};  // one per template instance
   cudaError_t e = ensure_smem_attr(kern, Cfg::kSmemBytes, attr_done);
   if (e != cudaSuccess) return e;
   const int tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
   const int grid = tiles < num_sms ? tiles : num_sms;
-  kern<<<grid, kThreads, Cfg::kSmemBytes, st>>>(a, b, c, bias, M, N, K, err);
+  kern<<<grid, kThreads, Cfg::kSmemBytes, st>>>(a, b, c, bias, row_scale, col_scale, M, N, K, err);
   return cudaGetLastError();
 }
 
@@ -295,6 +326,29 @@ cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUt
       case kEpiBf16: return launch_bn_epi<128, kEpiBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
       case kEpiGeluBf16: return launch_bn_epi<128, kEpiGeluBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
       case kEpiResidF32: return launch_bn_epi<128, kEpiResidF32>(a, b, c, bias, M, N, K, err, num_sms, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemm_tc_fp8(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
+                               const float* bias, const float* row_scale, const float* col_scale, int M, int N, int K,
+                               int* err, int num_sms, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K % kBK8 != 0 || N % 64 != 0 || !row_scale || !col_scale) return cudaErrorInvalidValue;
+  if (bn == 256) {
+    switch (epi) {
+      case kEpiBf16: return launch_bn_epi<256, kEpiBf16, true>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale,
+                                                                col_scale);
+      case kEpiGeluBf16: return launch_bn_epi<256, kEpiGeluBf16, true>(a, b, c, bias, M, N, K, err, num_sms, st,
+                                                                        row_scale, col_scale);
+    }
+  } else {
+    switch (epi) {
+      case kEpiBf16: return launch_bn_epi<128, kEpiBf16, true>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale,
+                                                                col_scale);
+      case kEpiGeluBf16: return launch_bn_epi<128, kEpiGeluBf16, true>(a, b, c, bias, M, N, K, err, num_sms, st,
+                                                                        row_scale, col_scale);
     }
   }
   return cudaErrorInvalidValue;

@@ -29,8 +29,16 @@ bool make_weight_maps(LinearW& w) {
   if (!w.w16) return true;
   if (!encode_tmap_bf16_2d(&w.map128, w.w16, w.out, w.in, w.in, 128, 64)) return false;
   if (w.out >= 256 && !encode_tmap_bf16_2d(&w.map256, w.w16, w.out, w.in, w.in, 256, 64)) return false;
+  if (w.w8) {
+    if (!encode_tmap_u8_2d(&w.map8_128, w.w8, w.out, w.in, w.in, 128)) return false;
+    if (w.out >= 256 && !encode_tmap_u8_2d(&w.map8_256, w.w8, w.out, w.in, w.in, 256)) return false;
+  }
   return true;
 }
+
+// E4M3 weight elements (and scales) of the FP8 layers: qkv and fc1 of every block.
+size_t fp8_block_elems(int d, int r) { return 3ull * d * d + 1ull * r * d * d; }
+size_t fp8_block_rows(int d, int r) { return 3ull * d + 1ull * r * d; }
 
 }  // namespace
 
@@ -56,7 +64,12 @@ std::string check_shape(const NetShape& s) {
 
 size_t net_bytes(const NetShape& s, int precision) {
   const size_t n = param_count(s);
-  return align_up(n * 4, 256) + (precision != REVO_FP32 ? align_up(n * 2, 256) : 0);
+  size_t b = align_up(n * 4, 256) + (precision != REVO_FP32 ? align_up(n * 2, 256) : 0);
+  if (precision == REVO_FP8) {
+    b += align_up(s.L * fp8_block_elems(s.D, s.r) + s.Ld * fp8_block_elems(s.Dd, s.r), 256);
+    b += align_up(4 * (s.L * fp8_block_rows(s.D, s.r) + s.Ld * fp8_block_rows(s.Dd, s.r)), 256);
+  }
+  return b;
 }
 
 Net* net_create(const NetShape& s, int precision, const float* host_weights, std::string* err) {
@@ -135,6 +148,39 @@ Net* net_create(const NetShape& s, int precision, const float* host_weights, std
     net_destroy(net);
     return nullptr;
   }
+  if (precision == REVO_FP8) {
+    // Per-output-channel E4M3 copies of the LayerNorm-fed layers.
+    const size_t elems = s.L * fp8_block_elems(s.D, s.r) + s.Ld * fp8_block_elems(s.Dd, s.r);
+    const size_t rows = s.L * fp8_block_rows(s.D, s.r) + s.Ld * fp8_block_rows(s.Dd, s.r);
+    if (cudaMalloc(&net->blob8, elems) != cudaSuccess || cudaMalloc(&net->blob8_scale, rows * 4) != cudaSuccess) {
+      *err = "fp8 weight allocation failed";
+      net_destroy(net);
+      return nullptr;
+    }
+    size_t eo = 0, ro = 0;
+    bool ok = true;
+    auto quant = [&](LinearW& w) {
+      w.w8 = net->blob8 + eo;
+      w.w8_scale = net->blob8_scale + ro;
+      ok = ok && launch_quantize_rows_e4m3(w.w32, w.out, w.in, net->blob8 + eo, net->blob8_scale + ro, 0) ==
+                     cudaSuccess;
+      eo += static_cast<size_t>(w.out) * w.in;
+      ro += w.out;
+    };
+    for (auto& b : net->enc) {
+      quant(b.qkv);
+      quant(b.fc1);
+    }
+    for (auto& b : net->dec) {
+      quant(b.qkv);
+      quant(b.fc1);
+    }
+    if (!ok || eo != elems || ro != rows || cudaDeviceSynchronize() != cudaSuccess) {
+      *err = "fp8 weight quantisation failed";
+      net_destroy(net);
+      return nullptr;
+    }
+  }
   if (tc) {
     bool ok = make_weight_maps(net->patch) && make_weight_maps(net->enc2dec) && make_weight_maps(net->head);
     for (auto& b : net->enc)
@@ -156,12 +202,14 @@ void net_destroy(Net* n) {
   if (!n) return;
   if (n->blob) cudaFree(n->blob);
   if (n->blob16) cudaFree(n->blob16);
+  if (n->blob8) cudaFree(n->blob8);
+  if (n->blob8_scale) cudaFree(n->blob8_scale);
   delete n;
 }
 
 namespace {
 struct WsLayout {
-  size_t tok, x, h, qkv, att, mlp, head, err, total;
+  size_t tok, x, h, qkv, att, mlp, head, err, h8, h8s, total;
 };
 WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp) {
   const size_t e = precision != REVO_FP32 ? 2 : 4;
@@ -181,6 +229,10 @@ WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp) {
   l.mlp = put(static_cast<size_t>(cap) * s.r * D * e);
   l.head = put(static_cast<size_t>(capp) * s.head_dim_out() * 4);
   l.err = put(256);
+  if (precision == REVO_FP8) {
+    l.h8 = put(static_cast<size_t>(cap) * D);
+    l.h8s = put(static_cast<size_t>(cap) * 4);
+  }
   l.total = o;
   return l;
 }
@@ -214,6 +266,10 @@ Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, in
   w->mlp = base + l.mlp;
   w->head = reinterpret_cast<float*>(base + l.head);
   w->err = reinterpret_cast<int*>(base + l.err);
+  if (precision == REVO_FP8) {
+    w->h8 = base + l.h8;
+    w->h8_scale = reinterpret_cast<float*>(base + l.h8s);
+  }
   w->bytes = l.total;
   return w;
 }
@@ -240,10 +296,29 @@ struct Fwd {
     if (!tc) return launch_gemm_simt(epi, static_cast<const float*>(A), w.w32, w.b, out, ldo, M, w.out, w.in, st);
     int bn = pick_bn(M, w.out, sms);
     if (net->autotune && M > 0) {
-      cudaError_t e = tuned_width(amap, w, epi, M, cmap, &bn);
+      cudaError_t e = tuned_width(amap, w, epi, M, cmap, false, &bn);
       if (e != cudaSuccess) return e;
     }
-    return launch_gemm_tc(*amap, bn == 256 ? w.map256 : w.map128, *cmap, bn, epi, w.b, M, w.out, w.in, ws->err, sms,
+    return launch(amap, w, epi, M, false, bn, cmap);
+  }
+
+  // FP8 Linear: A = the E4M3 LayerNorm output with its per-token scales.
+  cudaError_t linear8(const CUtensorMap* amap, const LinearW& w, int epi, int M, const CUtensorMap* cmap) {
+    int bn = pick_bn(M, w.out, sms);
+    if (net->autotune && M > 0) {
+      cudaError_t e = tuned_width(amap, w, epi, M, cmap, true, &bn);
+      if (e != cudaSuccess) return e;
+    }
+    return launch(amap, w, epi, M, true, bn, cmap);
+  }
+
+  // One launch of width bn writing through `dst`.
+  cudaError_t launch(const CUtensorMap* amap, const LinearW& w, int epi, int M, bool f8, int bn,
+                     const CUtensorMap* dst) {
+    if (f8)
+      return launch_gemm_tc_fp8(*amap, bn == 256 ? w.map8_256 : w.map8_128, *dst, bn, epi, w.b, ws->h8_scale,
+                                w.w8_scale, M, w.out, w.in, ws->err, sms, st);
+    return launch_gemm_tc(*amap, bn == 256 ? w.map256 : w.map128, *dst, bn, epi, w.b, M, w.out, w.in, ws->err, sms,
                           st);
   }
 
@@ -252,14 +327,14 @@ struct Fwd {
   // GEMM's own destination (the real launch overwrites it next), except for the
   // residual epilogue, whose destination accumulates: those write into the
   // qkv buffer, which holds nothing live between attention and the next block.
-  cudaError_t tuned_width(const CUtensorMap* amap, const LinearW& w, int epi, int M, const CUtensorMap* cmap,
+  cudaError_t tuned_width(const CUtensorMap* amap, const LinearW& w, int epi, int M, const CUtensorMap* cmap, bool f8,
                           int* bn) {
     // Row counts share a choice within buckets (128 rows up to 8192, then 2048),
     // so a serving mix of batch sizes is not re-timed for every new total.
     const int step = M <= 8192 ? 128 : 2048;
     const uint64_t mb = static_cast<uint64_t>((M + step - 1) / step) * step;
     const uint64_t key = (mb << 36) | (static_cast<uint64_t>(w.out) << 22) | (static_cast<uint64_t>(w.in) << 4) |
-                         static_cast<uint64_t>(epi);
+                         (static_cast<uint64_t>(f8) << 3) | static_cast<uint64_t>(epi);
     auto it = net->tuned_bn.find(key);
     if (it != net->tuned_bn.end()) {
       *bn = it->second;
@@ -283,10 +358,10 @@ struct Fwd {
     float best = 0.f;
     int best_bn = *bn;
     for (int cand : {128, 256}) {
-      const CUtensorMap& wm = cand == 256 ? w.map256 : w.map128;
+      if (cand == 256 && w.out < 256) continue;
       for (int rep = 0; rep < 4 && rc == cudaSuccess; ++rep) {
         if (rep == 1) rc = cudaEventRecord(ev[0], st);
-        if (rc == cudaSuccess) rc = launch_gemm_tc(*amap, wm, *dst, cand, epi, w.b, M, w.out, w.in, ws->err, sms, st);
+        if (rc == cudaSuccess) rc = launch(amap, w, epi, M, f8, cand, dst);
       }
       if (rc == cudaSuccess) rc = cudaEventRecord(ev[1], st);
       if (rc == cudaSuccess) rc = cudaEventSynchronize(ev[1]);
@@ -312,12 +387,27 @@ struct Fwd {
   struct Maps {
     const CUtensorMap *h, *att, *mlp, *qkv;  // operands / attention input
     const CUtensorMap *o_x, *o_qkv, *o_mlp;  // epilogue outputs
+    const CUtensorMap* h8;                   // E4M3 LayerNorm output (FP8 precision)
   };
 
-  cudaError_t block(const BlockW& b, int d, int heads, int M, const Segments& seg, const Maps& mp) {
+  // LayerNorm then a LayerNorm-fed Linear (qkv, fc1): in E4M3 with per-token
+  // and per-channel scales at FP8 precision, else from the bf16 / f32 LN output.
+  cudaError_t ln_linear(const float* g, const float* bb, int d, int M, const LinearW& w, int epi, void* out, int ldo,
+                        const Maps& mp, const CUtensorMap* cmap, int fp8_bit) {
     cudaError_t e;
-    if ((e = launch_layernorm(ws->x, b.ln1g, b.ln1b, ws->h, M, d, tc, st)) != cudaSuccess) return e;
-    if ((e = linear(mp.h, ws->h, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, M, mp.o_qkv)) != cudaSuccess)
+    if (net->precision == REVO_FP8 && (net->fp8_mask >> fp8_bit) & 1) {
+      if ((e = launch_layernorm_e4m3(ws->x, g, bb, ws->h8, ws->h8_scale, M, d, st)) != cudaSuccess) return e;
+      return linear8(mp.h8, w, epi, M, cmap);
+    }
+    if ((e = launch_layernorm(ws->x, g, bb, ws->h, M, d, tc, st)) != cudaSuccess) return e;
+    return linear(mp.h, ws->h, w, epi, out, ldo, M, cmap);
+  }
+
+  cudaError_t block(const BlockW& b, int d, int heads, int M, const Segments& seg, const Maps& mp, bool dec) {
+    cudaError_t e;
+    const int bit = dec ? 2 : 0;
+    if ((e = ln_linear(b.ln1g, b.ln1b, d, M, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, mp, mp.o_qkv, bit)) !=
+        cudaSuccess)
       return e;
     if (tc)
       e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st);
@@ -326,8 +416,9 @@ struct Fwd {
                                 st);
     if (e != cudaSuccess) return e;
     if ((e = linear(mp.att, ws->att, b.proj, kEpiResidF32, ws->x, d, M, mp.o_x)) != cudaSuccess) return e;
-    if ((e = launch_layernorm(ws->x, b.ln2g, b.ln2b, ws->h, M, d, tc, st)) != cudaSuccess) return e;
-    if ((e = linear(mp.h, ws->h, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, M, mp.o_mlp)) != cudaSuccess) return e;
+    if ((e = ln_linear(b.ln2g, b.ln2b, d, M, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, mp, mp.o_mlp, bit + 1)) !=
+        cudaSuccess)
+      return e;
     return linear(mp.mlp, ws->mlp, b.fc2, kEpiResidF32, ws->x, d, M, mp.o_x);
   }
 };
@@ -350,6 +441,9 @@ bool encode_maps(const NetShape& s, Workspace* ws, int M) {
             encode_tmap_out_2d(&ws->o_qkv_dec, ws->qkv, false, rows, 3 * s.Dd, 3 * s.Dd) &&
             encode_tmap_out_2d(&ws->o_mlp_enc, ws->mlp, false, rows, s.r * s.D, s.r * s.D) &&
             encode_tmap_out_2d(&ws->o_mlp_dec, ws->mlp, false, rows, s.r * s.Dd, s.r * s.Dd);
+  if (ok && ws->h8)
+    ok = encode_tmap_u8_2d(&ws->m_h8_enc, ws->h8, rows, s.D, s.D, 128) &&
+         encode_tmap_u8_2d(&ws->m_h8_dec, ws->h8, rows, s.Dd, s.Dd, 128);
   ws->maps_rows = ok ? M : -1;
   return ok;
 }
@@ -449,11 +543,11 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
       return e;
 
   const Fwd::Maps enc_maps{&ws->m_h_enc, &ws->m_att_enc, &ws->m_mlp_enc, &ws->m_qkv_enc,
-                           &ws->o_x_enc, &ws->o_qkv_enc, &ws->o_mlp_enc};
+                           &ws->o_x_enc, &ws->o_qkv_enc, &ws->o_mlp_enc, &ws->m_h8_enc};
   const Fwd::Maps dec_maps{&ws->m_h_dec, &ws->m_att_dec, &ws->m_mlp_dec, &ws->m_qkv_dec,
-                           &ws->o_x_dec, &ws->o_qkv_dec, &ws->o_mlp_dec};
+                           &ws->o_x_dec, &ws->o_qkv_dec, &ws->o_mlp_dec, &ws->m_h8_dec};
   for (const BlockW& b : net->enc)
-    if ((e = f.block(b, s.D, s.H, M, seg, enc_maps)) != cudaSuccess) return e;
+    if ((e = f.block(b, s.D, s.H, M, seg, enc_maps, false)) != cudaSuccess) return e;
   if ((e = launch_layernorm(ws->x, net->enc_norm_g, net->enc_norm_b, ws->h, M, s.D, f.tc, st)) != cudaSuccess) return e;
   if ((e = f.linear(&ws->m_h_enc, ws->h, net->enc2dec, kEpiF32, ws->x, s.Dd, M, &ws->o_x_dec)) != cudaSuccess)
     return e;
@@ -462,7 +556,7 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
                            s.slots(), args[i].taus, s.Dd, st, dev_args ? dev_args[i].taus : nullptr)) != cudaSuccess)
       return e;
   for (const BlockW& b : net->dec)
-    if ((e = f.block(b, s.Dd, s.Hd, M, seg, dec_maps)) != cudaSuccess) return e;
+    if ((e = f.block(b, s.Dd, s.Hd, M, seg, dec_maps, true)) != cudaSuccess) return e;
 
   // Final LN and pixel head on the last slot's tokens of each request, then the blend.
   uint8_t* h = static_cast<uint8_t*>(ws->h);

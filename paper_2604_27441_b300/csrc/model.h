@@ -36,6 +36,11 @@ struct LinearW {
   const __nv_bfloat16* w16 = nullptr;
   int out = 0, in = 0;
   CUtensorMap map128{}, map256{};
+  // FP8 precision, the LayerNorm-fed layers (qkv, fc1): E4M3 codes with one
+  // scale per output channel, and their maps.
+  const uint8_t* w8 = nullptr;
+  const float* w8_scale = nullptr;
+  CUtensorMap map8_128{}, map8_256{};
 };
 
 struct BlockW {
@@ -48,6 +53,8 @@ struct Net {
   int precision = 0;
   float* blob = nullptr;            // float32 master copy of every parameter
   __nv_bfloat16* blob16 = nullptr;  // bf16 copy (tensor-core path)
+  uint8_t* blob8 = nullptr;         // E4M3 copies of the qkv and fc1 weights (FP8 precision)
+  float* blob8_scale = nullptr;     // their per-output-channel scales
   LinearW patch, enc2dec, head;     // head: the rows that produce the target frame
   std::vector<BlockW> enc, dec;
   const float *enc_norm_g, *enc_norm_b, *dec_norm_g, *dec_norm_b;
@@ -56,6 +63,9 @@ struct Net {
   // timed on the stream and the fastest is kept for every later launch and
   // capture of that shape.  Off: a fixed rule (256 when N >= 256).
   bool autotune = false;
+  // FP8 precision: E4M3 layers (bit 0 encoder qkv, 1 encoder fc1, 2 decoder
+  // qkv, 3 decoder fc1).
+  int fp8_mask = 0;
   std::map<uint64_t, int> tuned_bn;
   int tuned_shapes_256 = 0, tuned_shapes_128 = 0;
 };
@@ -83,12 +93,15 @@ struct Workspace {
   void* att = nullptr;   // [cap][D]
   void* mlp = nullptr;   // [cap][rD]
   float* head = nullptr; // [cap_patches][C*p*p]
+  uint8_t* h8 = nullptr;  // [cap][max width] E4M3 LayerNorm output (FP8 precision)
+  float* h8_scale = nullptr;  // [cap] its per-token scales
   int* err = nullptr;    // device error word of the tensor-core kernels
   size_t bytes = 0;
   // Tensor maps of the A operands, valid for `maps_rows` rows.
   int maps_rows = -1;
   CUtensorMap m_tok{}, m_h_enc{}, m_att_enc{}, m_mlp_enc{}, m_h_dec{}, m_att_dec{}, m_mlp_dec{};
   CUtensorMap m_qkv_enc{}, m_qkv_dec{};
+  CUtensorMap m_h8_enc{}, m_h8_dec{};
   // Output maps of the GEMM epilogues.
   CUtensorMap o_x_enc{}, o_x_dec{}, o_qkv_enc{}, o_qkv_dec{}, o_mlp_enc{}, o_mlp_dec{};
 };

@@ -160,6 +160,55 @@ revo_status revo_op_layernorm(const float* x, const float* gamma, const float* b
                      "revo_op_layernorm");
 }
 
+revo_status revo_op_quantize_rows_e4m3(const float* x, int rows, int cols, uint8_t* q, float* scale, void* stream) {
+  if (!x || !q || !scale || rows < 0 || cols <= 0 || cols % 4) {
+    set_last_error("revo_op_quantize_rows_e4m3: bad argument (cols must be a positive multiple of 4)");
+    return REVO_EINVAL;
+  }
+  return cuda_status(launch_quantize_rows_e4m3(x, rows, cols, q, scale, static_cast<cudaStream_t>(stream)),
+                     "revo_op_quantize_rows_e4m3");
+}
+
+revo_status revo_op_layernorm_e4m3(const float* x, const float* gamma, const float* beta, uint8_t* out,
+                                   float* row_scale, int M, int D, void* stream) {
+  if (!x || !gamma || !beta || !out || !row_scale || M < 0 || D <= 0) {
+    set_last_error("revo_op_layernorm_e4m3: bad argument");
+    return REVO_EINVAL;
+  }
+  return cuda_status(launch_layernorm_e4m3(x, gamma, beta, out, row_scale, M, D, static_cast<cudaStream_t>(stream)),
+                     "revo_op_layernorm_e4m3");
+}
+
+revo_status revo_op_linear_fp8(int epilogue, const uint8_t* A, const float* a_scale, const uint8_t* W,
+                               const float* w_scale, const float* bias, void* out, int M, int N, int K, int tile_n,
+                               void* stream) {
+  if (!A || !a_scale || !W || !w_scale || !out || M < 0 || N <= 0 || K <= 0 ||
+      (epilogue != kEpiBf16 && epilogue != kEpiGeluBf16)) {
+    set_last_error("revo_op_linear_fp8: bad argument (epilogue must be 1 or 2)");
+    return REVO_EINVAL;
+  }
+  if (K % 128 || N % 64) {
+    set_last_error("revo_op_linear_fp8: needs K %% 128 == 0 and N %% 64 == 0");
+    return REVO_EINVAL;
+  }
+  const int bn = tile_n == 256 && N >= 256 ? 256 : 128;
+  CUtensorMap ma, mb, mc;
+  const uint64_t rows = M > 0 ? M : 1;
+  if (!encode_tmap_u8_2d(&ma, A, rows, K, K, 128) || !encode_tmap_u8_2d(&mb, W, N, K, K, bn) ||
+      !encode_tmap_out_2d(&mc, out, false, rows, N, N)) {
+    set_last_error("revo_op_linear_fp8: tensor map encoding failed (alignment?)");
+    return REVO_EINVAL;
+  }
+  int* err = op_error_word();
+  if (!err) {
+    set_last_error("revo_op_linear_fp8: no device error word");
+    return REVO_ECUDA;
+  }
+  return cuda_status(launch_gemm_tc_fp8(ma, mb, mc, bn, epilogue, bias, a_scale, w_scale, M, N, K, err,
+                                        device_sm_count(), static_cast<cudaStream_t>(stream)),
+                     "revo_op_linear_fp8");
+}
+
 revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D, int heads,
                               const int* seg_start, int n_seg, void* stream) {
   if (!qkv || !out || !seg_start || n_seg <= 0 || n_seg > kMaxSegments || heads <= 0 || D != 64 * heads) {

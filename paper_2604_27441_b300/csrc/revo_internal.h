@@ -37,11 +37,27 @@ bool encode_tmap_bf16_2d(CUtensorMap* map, const void* base, uint64_t rows, uint
 bool encode_tmap_out_2d(CUtensorMap* map, const void* base, bool f32, uint64_t rows, uint64_t cols,
                         uint64_t row_stride_elems);
 
+bool encode_tmap_u8_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t row_stride_elems,
+                       uint32_t box_rows);
+
 // ---- GEMMs
 // `c` is the output map (encode_tmap_out_2d): float32 for kEpiF32 and
 // kEpiResidF32 (the residual epilogue adds into it), bf16 otherwise.
 cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
                            const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st);
+// FP8 (E4M3) operands with per-row scales of A (`row_scale`, M entries: one per
+// token) and per-output-channel scales of W (`col_scale`, N entries):
+// Y = epilogue(row_scale[m] * col_scale[n] * (A8 W8^T)[m][n] + b[n]).  `a` and
+// `b` are encode_tmap_u8_2d maps (128-row / bn-row boxes).  K % 128 == 0;
+// epilogues kEpiBf16 and kEpiGeluBf16.
+cudaError_t launch_gemm_tc_fp8(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
+                               const float* bias, const float* row_scale, const float* col_scale, int M, int N, int K,
+                               int* err, int num_sms, cudaStream_t st);
+
+// Per-row E4M3 quantisation: scale[r] = max_k |x[r][k]| / 448 (1 for an
+// all-zero row), q[r][k] = e4m3_satfinite(x[r][k] * (448 / max)).  x float32
+// [rows][cols] (cols % 4 == 0), q [rows][cols].
+cudaError_t launch_quantize_rows_e4m3(const float* x, int rows, int cols, uint8_t* q, float* scale, cudaStream_t st);
 cudaError_t launch_gemm_simt(int epi, const float* A, const float* W, const float* bias, void* out, int ldo, int M,
                              int N, int K, cudaStream_t st);
 
@@ -72,6 +88,10 @@ cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, 
 
 cudaError_t launch_layernorm(const float* x, const float* g, const float* b, void* out, int M, int D, int out_bf16,
                              cudaStream_t st);
+// LayerNorm whose output row is quantised to E4M3 with a per-row scale, the
+// same rule as launch_quantize_rows_e4m3 applied to the float32 LN output.
+cudaError_t launch_layernorm_e4m3(const float* x, const float* g, const float* b, uint8_t* out, float* row_scale,
+                                  int M, int D, cudaStream_t st);
 
 size_t depth_stats_scratch_bytes();
 cudaError_t launch_depth_stats(const uint16_t* d, int H, int W, size_t pitch, float* mu_sigma, void* scratch,

@@ -39,6 +39,23 @@ bool encode_tmap_bf16_2d(CUtensorMap* map, const void* base, uint64_t rows, uint
   return r == CUDA_SUCCESS;
 }
 
+// 2-D map over a row-major [rows][row_stride] matrix of 8-bit elements (FP8
+// operands); box = box_rows x 128 columns (one 128-byte swizzle atom per row).
+bool encode_tmap_u8_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t row_stride_elems,
+                       uint32_t box_rows) {
+  std::call_once(g_once, resolve);
+  if (!g_encode) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || row_stride_elems % 16) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {row_stride_elems};
+  cuuint32_t box[2] = {128, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // Output map of a GEMM epilogue: rows x cols of float32 (32-column box) or
 // bf16 (64-column box), 32-row box, 128-byte swizzle (one 128-byte row per
 // box row).

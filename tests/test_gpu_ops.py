@@ -104,6 +104,67 @@ def test_layernorm(M, D, out_bf16):
         np.testing.assert_allclose(f64(out), ref, rtol=0, atol=5e-5)
 
 
+# --------------------------------------------------------------------- fp8
+
+from oracle import fp8 as F8  # noqa: E402
+
+
+@pytest.mark.parametrize("rows,cols", [(300, 768), (1, 384), (1000, 3072), (77, 128)])
+def test_quantize_rows_e4m3_bit_exact(rows, cols):
+    """Codes and scales equal the oracle's on the same float32 input: the
+    scale and the scaled value are float32 operations on both sides, the
+    rounding to E4M3 is the format's."""
+    x = synth.normal(rows + cols, (rows, cols), 2.0)
+    x[rows // 2] = 0.0
+    x[-1, :7] = [1e-7, -3e-6, 5e3, -5e3, 0.0, 1.0, 448.0]
+    q = torch.zeros((rows, cols), dtype=torch.uint8, device="cuda")
+    sc = torch.zeros(rows, dtype=torch.float32, device="cuda")
+    R.op_quantize_rows_e4m3(dev(x), rows, cols, q, sc)
+    torch.cuda.synchronize()
+    q_ref, s_ref = F8.quantise_rows(x)
+    np.testing.assert_array_equal(sc.cpu().numpy(), s_ref)
+    np.testing.assert_array_equal(q.cpu().numpy(), q_ref)
+
+
+@pytest.mark.parametrize("M,D", [(333, 768), (1000, 384), (1, 128)])
+def test_layernorm_e4m3(M, D):
+    """Dequantised codes are within one E4M3 rounding (2^-4 relative, or half a
+    subnormal step) of the FP64 LayerNorm, plus the float32 LN error."""
+    x = synth.normal(M + D, (M, D), 3.0) + 0.5
+    g = 1 + synth.normal(M + D + 1, (D,), 0.1)
+    b = synth.normal(M + D + 2, (D,), 0.1)
+    q = torch.zeros((M, D), dtype=torch.uint8, device="cuda")
+    sc = torch.zeros(M, dtype=torch.float32, device="cuda")
+    R.op_layernorm_e4m3(dev(x), dev(g), dev(b), q, sc, M, D)
+    torch.cuda.synchronize()
+    ref = O.layer_norm(x.astype(np.float64), g.astype(np.float64), b.astype(np.float64))
+    s = sc.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(s, np.abs(ref).max(axis=1) / 448.0, rtol=1e-5)
+    deq = F8.dequantise_rows(q.cpu().numpy(), s)
+    bound = np.maximum(np.abs(ref) * 2.0 ** -4, s[:, None] * 2.0 ** -10) * (1 + 1e-3) + 5e-5
+    assert (np.abs(deq - ref) <= bound).all()
+
+
+@pytest.mark.parametrize("M,N,K,bn", [(300, 256, 768, 128), (1000, 2304, 768, 256), (517, 1536, 384, 256),
+                                      (3600, 3072, 768, 0), (1, 64, 128, 128), (129, 384, 384, 128)])
+@pytest.mark.parametrize("epi", [1, 2])
+def test_linear_fp8_tcgen05(M, N, K, bn, epi):
+    """E4M3 operands decode exactly, so the oracle multiplies the decoded
+    values (times the row and channel scales) in float64; the tolerance
+    covers float32 accumulation and the bf16 output rounding."""
+    seed = M * 5 + N + K
+    a_codes, a_scale = F8.quantise_rows(synth.normal(seed, (M, K), 1.5))
+    w_codes, w_scale = F8.quantise_rows(synth.normal(seed + 1, (N, K), 1.0 / np.sqrt(K)))
+    b = synth.normal(seed + 2, (N,), 0.1)
+    ref = O.linear(F8.dequantise_rows(a_codes, a_scale), F8.dequantise_rows(w_codes, w_scale), b.astype(np.float64))
+    if epi == 2:
+        ref = O.gelu(ref)
+    out = torch.zeros((M, N), dtype=torch.bfloat16, device="cuda")
+    R.op_linear_fp8(epi, dev(a_codes), dev(a_scale), dev(w_codes), dev(w_scale), dev(b), out, M, N, K, bn)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(f64(out), ref, rtol=8e-3, atol=8e-3)
+
+
 # --------------------------------------------------------------- attention
 
 def _oracle_segments(qkv, heads, seg):

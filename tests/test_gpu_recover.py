@@ -4,8 +4,8 @@ oracle on seeded synthetic RGB-D frames.
 Tolerances on the de-normalised float outputs (every pixel of the network
 output, before the blend):
   FP32 path: max |error| <= 1e-4 on [0, 1] RGB and <= 1 mm on depth;
-  BF16 path: PSNR >= 45 dB on [0, 1] RGB and on depth / 65535, max depth
-             error <= 8 mm.
+  BF16 and FP8 paths: PSNR >= 45 dB on [0, 1] RGB and on depth / 65535, max
+             depth error <= 8 mm.
 Blended codes: received pixels bit-exact; a lost pixel's code differs from the
 oracle's by at most floor(|float error| * scale) + 1 and is equal wherever the
 oracle's value is farther than the observed error from a rounding boundary.
@@ -183,7 +183,7 @@ def test_small_network_parity(precision):
     check(precision, got, oracle(SMALL, rgb, dep, "small"), rgb, dep)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_vitb_320x240_parity(precision):
     rgb, dep = synth.make_request(1001, "320x240")
     with make_ctx(VITB, precision, (240, 320)) as ctx:
@@ -191,7 +191,7 @@ def test_vitb_320x240_parity(precision):
     check(precision, got, oracle(VITB, rgb, dep, "320"), rgb, dep)
 
 
-@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("precision", [1, 0, 2])
 def test_vitb_640x480_parity(precision):
     rgb, dep = synth.make_request(2001, "640x480", loss_rate=0.2)
     with make_ctx(VITB, precision, (480, 640)) as ctx:
