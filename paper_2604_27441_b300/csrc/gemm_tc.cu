@@ -7,8 +7,9 @@
 // and BN x 64 tiles with the 128-byte swizzle straight into the operand layout
 // tcgen05.mma reads.  The accumulator (128 lanes x BN f32 columns) lives in
 // TMEM, double-buffered so the epilogue of one tile overlaps the main loop of
-// the next.  The epilogue adds the bias, applies the erf-form GELU (erf by
-// Abramowitz & Stegun 7.1.26) and the bf16 downcast in registers, stages 32-row chunks in 128-byte-swizzled shared
+// the next.  The epilogue adds the bias, applies GELU (the tanh form: within
+// 4.8e-4 of the erf form, below the bf16 rounding of the output) and the bf16
+// downcast in registers, stages 32-row chunks in 128-byte-swizzled shared
 // memory and hands them to TMA: a bulk store, or for the residual layers a
 // bulk f32 add-reduction into the residual stream (one rounding per element,
 // exactly as x += y).
@@ -102,19 +103,20 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
       pieces[k] = make_uint4(__float_as_uint(v[4 * k]), __float_as_uint(v[4 * k + 1]), __float_as_uint(v[4 * k + 2]),
                              __float_as_uint(v[4 * k + 3]));
   } else {
+    uint32_t rr[2][32];
+    tmem_ld32(taddr + c0, rr[0]);
+    tmem_ld32(taddr + c0 + 32, rr[1]);
+    tmem_wait_ld();
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-      uint32_t r[32];
-      tmem_ld32(taddr + c0 + 32 * half, r);
-      tmem_wait_ld();
       float v[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+      for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(rr[half][i]);
       if (F8) apply_scales(v, rs, cs, n0 + c0 + 32 * half);
       add_bias(v, bias, n0 + c0 + 32 * half);
       if (EPI == kEpiGeluBf16) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = gelu_as7126(v[i]);
+        for (int i = 0; i < 32; ++i) v[i] = gelu_tanh(v[i]);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k)
