@@ -4,28 +4,26 @@
 // no token dropping), computed flash-style with an online softmax.
 //
 // One CTA owns two 128-row query tiles (256 queries) of one head of one
-// segment; both tiles share every K/V tile it streams in.  TMA reads the
-// head's 64-column slices of Q, K and V straight out of the qkv matrix
-// [M][3D] (128-byte swizzle), so no head-split pass is needed.  Per KV tile j
-// and query tile t:
-//   S_t  = Q_t K_j^T          tcgen05.mma M=128 N=128 K=64 -> TMEM
-//   P_t  = exp2(S_t c - m_t)  softmax warpgroup t, bf16, written back to TMEM
-//                             (tcgen05.st; one row per lane, two keys per column)
-//   O_t += P_t V_j            tcgen05.mma M=128 N=64 K=128 with A = P from TMEM
-//                             and V read N-major from shared memory,
-//                             accumulated in TMEM across the KV tiles
-// Keeping P in TMEM spares shared memory a write and a read of every P tile,
-// the traffic that otherwise bounds this kernel.
-// The running row maximum m_t only moves when a row's maximum grows by more
-// than 2^8 (then O_t and the row sum are rescaled in place), so P stays below
-// 256 and rescaling is rare; the result is the same softmax.  The softmax
-// threads read S once per tile and release it at once, so the MMA of the next
-// tile overlaps their exponentials, and the two warpgroups give every SM
-// sub-partition two independent softmax instruction streams.
+// segment; both tiles share every K/V tile it streams in (96 keys each).  TMA
+// reads the head's 64-column slices of Q, K and V straight out of the qkv
+// matrix [M][3D] (128-byte swizzle), so no head-split pass is needed.  Per
+// K/V tile j and query tile t:
+//   S_t(j) = Q_t K_j^T         tcgen05.mma M=128 N=96 K=64 -> TMEM region j%2
+//   P_t(j) = exp2(S c - m_t)   softmax warpgroup t, bf16, written over the
+//                              S_t(j) columns it has just read (tcgen05.st)
+//   O_t  += P_t(j) V_j         tcgen05.mma M=128 N=64 K=96, A = P from TMEM,
+//                              V read N-major from shared memory
+// Each query tile has two S/P regions (96 columns each) and O (64 columns):
+// 256 of TMEM's 512 columns.  S_t(j+2) reuses region j%2 once PV_t(j) has
+// finished, so S runs up to two tiles ahead and the softmax never waits for
+// the previous PV (only a rescale of O does, and rescales are rare: the
+// running row maximum m_t only moves when a row's maximum grows by more than
+// 2^8, so P stays below 256; the result is the same softmax).
 //
-// Warp roles (320 threads): warp 0 TMA, warp 1 TMEM allocator + MMA issuer,
-// warps 2..5 softmax of tile 0, warps 6..9 softmax of tile 1 (warp w owns rows
-// 32*(w%4) .. +31 of its tile, the TMEM lanes it may access).
+// Warp roles (352 threads): warp 0 TMA, warp 1 TMEM allocator + MMA issuer
+// of tile 0, warps 2..5 softmax of tile 0, warps 6..9 softmax of tile 1 (warp
+// w owns rows 32*(w%4) .. +31 of its tile, the TMEM lanes it may access),
+// warp 10 MMA issuer of tile 1.
 #include "common.cuh"
 #include "revo_internal.h"
 
@@ -35,15 +33,18 @@ namespace {
 
 constexpr int kQ = 128;
 constexpr int kTiles = 2;  // query tiles per CTA
-constexpr int kKV = 128;
+constexpr int kKV = 96;    // keys per K/V tile
 constexpr int kHD = 64;
-constexpr int kKvStages = 4;
-constexpr int kThreads = 64 + kTiles * 128;
-constexpr int kTileBytes = kQ * kHD * 2;  // 16 KB: 128 rows x 128 B
-constexpr int kSmemBytes = 1024 + kTileBytes * (kTiles + 2 * kKvStages) + 512;
-constexpr uint32_t kTmemCols = 512;  // per tile: S 128 + P 64 + O 64 columns
-constexpr uint32_t kTileCols = 256;
-constexpr uint32_t kPCol = 128;
+constexpr int kKvStages = 6;
+constexpr int kBoxRows = 32;  // TMA box height: Q = 4 boxes, a K or V tile = 3
+constexpr int kThreads = 64 + kTiles * 128 + 32;  // + the second tile's MMA warp
+constexpr int kQBytes = kQ * kHD * 2;    // 16 KB: 128 rows x 128 B
+constexpr int kKVBytes = kKV * kHD * 2;  // 12 KB
+constexpr int kBoxBytes = kBoxRows * kHD * 2;
+constexpr int kSmemBytes = 1024 + kQBytes * kTiles + 2 * kKVBytes * kKvStages + 1024;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kTileCols = 256;   // per tile: S/P regions at 0 and 96, O at 192
+constexpr uint32_t kRegionCols = 96;
 constexpr uint32_t kOCol = 192;
 constexpr float kRescaleLog2 = 8.0f;  // rescale once a row max grows by more than 2^8
 
@@ -128,18 +129,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const __grid_constant__ TcAttnParams P, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sQ = smem;                         // kTiles x 16 KB
-  uint8_t* sK = sQ + kTiles * kTileBytes;     // kKvStages x 16 KB
-  uint8_t* sV = sK + kKvStages * kTileBytes;  // kKvStages x 16 KB
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sV + kKvStages * kTileBytes);
+  uint8_t* sQ = smem;                        // kTiles x 16 KB
+  uint8_t* sK = sQ + kTiles * kQBytes;       // kKvStages x 12 KB
+  uint8_t* sV = sK + kKvStages * kKVBytes;   // kKvStages x 12 KB
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sV + kKvStages * kKVBytes);
   uint64_t* q_full = bars;
   uint64_t* kv_full = q_full + 1;
   uint64_t* kv_empty = kv_full + kKvStages;
-  uint64_t* s_full = kv_empty + kKvStages;  // [kTiles] S ready in TMEM
-  uint64_t* s_empty = s_full + kTiles;      // [kTiles] S read by the softmax
-  uint64_t* p_full = s_empty + kTiles;      // [kTiles] P written, O rescaled
-  uint64_t* p_done = p_full + kTiles;       // [kTiles] PV accumulated (P free, O stable)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(p_done + kTiles);
+  uint64_t* s_full = kv_empty + kKvStages;  // [kTiles][2] S_t(j) ready in region j%2
+  uint64_t* p_full = s_full + 2 * kTiles;   // [kTiles][2] P_t(j) written in region j%2, O rescaled
+  uint64_t* p_done = p_full + 2 * kTiles;   // [kTiles] PV_t(j) accumulated (O stable)
+  uint64_t* p_reg = p_done + kTiles;        // [kTiles][2] PV_t(j) done: region j%2 free
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(p_reg + 2 * kTiles);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -159,13 +160,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(q_full, 1);
     for (int s = 0; s < kKvStages; ++s) {
       mbar_init(&kv_full[s], 1);
-      mbar_init(&kv_empty[s], 1);
+      mbar_init(&kv_empty[s], ntiles);  // one release per query tile's MMA thread
     }
     for (int t = 0; t < kTiles; ++t) {
-      mbar_init(&s_full[t], 1);
-      mbar_init(&s_empty[t], 4);
-      mbar_init(&p_full[t], 4);
+      mbar_init(&s_full[2 * t], 1);
+      mbar_init(&s_full[2 * t + 1], 1);
+      mbar_init(&p_full[2 * t], 4);
+      mbar_init(&p_full[2 * t + 1], 4);
       mbar_init(&p_done[t], 1);
+      mbar_init(&p_reg[2 * t], 1);
+      mbar_init(&p_reg[2 * t + 1], 1);
     }
     fence_mbarrier_init();
   }
@@ -180,80 +184,70 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      mbar_arrive_expect_tx(q_full, ntiles * kTileBytes);
-      for (int t = 0; t < ntiles; ++t) tma_load_2d(sQ + t * kTileBytes, &tm, h * kHD, q0 + t * kQ, q_full);
+      mbar_arrive_expect_tx(q_full, ntiles * kQBytes);
+      for (int t = 0; t < ntiles; ++t)
+        for (int b = 0; b < kQ / kBoxRows; ++b)
+          tma_load_2d(sQ + t * kQBytes + b * kBoxBytes, &tm, h * kHD, q0 + t * kQ + b * kBoxRows, q_full);
       for (int j = 0; j < nkv; ++j) {
         const int st = j % kKvStages;
         if (!mbar_wait(&kv_empty[st], ((j / kKvStages) & 1) ^ 1u, err, kDevTimeoutProducer)) break;
-        mbar_arrive_expect_tx(&kv_full[st], 2 * kTileBytes);
-        tma_load_2d(sK + st * kTileBytes, &tm, D + h * kHD, s0 + j * kKV, &kv_full[st]);
-        tma_load_2d(sV + st * kTileBytes, &tm, 2 * D + h * kHD, s0 + j * kKV, &kv_full[st]);
+        mbar_arrive_expect_tx(&kv_full[st], 2 * kKVBytes);
+        for (int b = 0; b < kKV / kBoxRows; ++b) {
+          const int row = s0 + j * kKV + b * kBoxRows;
+          tma_load_2d(sK + st * kKVBytes + b * kBoxBytes, &tm, D + h * kHD, row, &kv_full[st]);
+          tma_load_2d(sV + st * kKVBytes + b * kBoxBytes, &tm, 2 * D + h * kHD, row, &kv_full[st]);
+        }
       }
     }
-  } else if (warp == 1) {
-    if (lane == 0) {
+  } else if (warp == 1 || warp == kThreads / 32 - 1) {
+    // One MMA thread per query tile (warp 1: tile 0, the last warp: tile 1),
+    // each in a fixed order with blocking waits on its own tile's barriers:
+    // S(0), S(1), then per K/V tile j: PV(j) once P(j) is written, S(j+2)
+    // once PV(j) has finished with region j%2.  The two threads' MMAs touch
+    // disjoint TMEM columns.  Every wait is on the phase the other side cannot
+    // pass before this thread's next issue, so no barrier runs ahead.
+    const int t = warp == 1 ? 0 : 1;
+    if (lane == 0 && t < ntiles) {
       constexpr uint32_t kIdS = idesc_bf16(kQ, kKV);
       constexpr uint32_t kIdPV = idesc_bf16(kQ, kHD, /*b_mn_major=*/true);
-      // Issue in readiness order: per tile t the next S (needs its K tile and
-      // the softmax to have read the previous S) and the next PV (needs P),
-      // polled without blocking so one tile's softmax never holds up the
-      // other tile's MMAs.  A K/V stage is released once every tile's PV that
-      // reads it has been issued.
+      const uint32_t tbase = tmem + t * kTileCols;
+      const uint32_t q_lo = sw128_lo(smem_u32(sQ + t * kQBytes));
+      auto issue_s = [&](int j) {
+        const uint32_t k_lo = sw128_lo(smem_u32(sK + (j % kKvStages) * kKVBytes));
+#pragma unroll
+        for (int kk = 0; kk < kHD / 16; ++kk)  // 16 dims: 32 B of the swizzled rows
+          mma_f16_hl(tbase + (j & 1) * kRegionCols, q_lo + kk * 2, kSw128Hi, k_lo + kk * 2, kSw128Hi, kIdS,
+                     kk > 0 ? 1u : 0u);
+        mma_commit(&s_full[2 * t + (j & 1)]);
+      };
       bool ok = mbar_wait(q_full, 0, err, kDevTimeoutMma);
-      int ns[kTiles] = {0, 0}, np[kTiles] = {0, 0};
-      int released = 0, kv_seen = 0;  // KV tiles released / observed loaded
-      long long t_last = clock64();
-      uint32_t idle = 0;
-      while (ok) {
-        bool progress = false, all_done = true;
-        for (int t = 0; t < ntiles; ++t) {
-          if (np[t] < ns[t] && mbar_test(smem_u32(&p_full[t]), np[t] & 1)) {
-            const int jj = np[t];
+      for (int j = 0; ok && j < 2 && j < nkv; ++j) {
+        ok = mbar_wait(&kv_full[j % kKvStages], (j / kKvStages) & 1, err, kDevTimeoutMma);
+        if (ok) {
+          tc_fence_after();
+          issue_s(j);
+        }
+      }
+      for (int j = 0; ok && j < nkv; ++j) {
+        ok = mbar_wait(&p_full[2 * t + (j & 1)], (j >> 1) & 1, err, kDevTimeoutMma);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t v_lo = sw128_lo(smem_u32(sV + (j % kKvStages) * kKVBytes));
+        const uint32_t p_tmem = tbase + (j & 1) * kRegionCols;
+#pragma unroll
+        for (int kk = 0; kk < kKV / 16; ++kk)  // 16 keys: 8 TMEM columns of P, 2048 B of V
+          mma_f16_tmem_a_hl(tbase + kOCol, p_tmem + kk * 8, v_lo + kk * 128, kSw128Hi, kIdPV,
+                            (j > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&p_done[t]);
+        mma_commit(&p_reg[2 * t + (j & 1)]);
+        mma_commit(&kv_empty[j % kKvStages]);  // this tile is done with K_j, V_j
+        const int jn = j + 2;
+        if (jn < nkv) {
+          ok = mbar_wait(&p_reg[2 * t + (j & 1)], (j >> 1) & 1, err, kDevTimeoutMma) &&
+               mbar_wait(&kv_full[jn % kKvStages], (jn / kKvStages) & 1, err, kDevTimeoutMma);
+          if (ok) {
             tc_fence_after();
-            const uint32_t v_addr = smem_u32(sV + (jj % kKvStages) * kTileBytes);
-#pragma unroll
-            for (int kk = 0; kk < kKV / 16; ++kk)
-              mma_f16_tmem_a(tmem + t * kTileCols + kOCol, tmem + t * kTileCols + kPCol + kk * 8,
-                             sw128_desc(v_addr + kk * 2048), kIdPV, (jj > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(&p_done[t]);
-            ++np[t];
-            progress = true;
-          }
-          if (ns[t] < nkv) {
-            const int j = ns[t];
-            if (kv_seen <= j && mbar_test(smem_u32(&kv_full[j % kKvStages]), (j / kKvStages) & 1))
-              kv_seen = j + 1;
-            if (kv_seen > j && mbar_test(smem_u32(&s_empty[t]), (j & 1) ^ 1u)) {
-              tc_fence_after();
-              const uint32_t k_addr = smem_u32(sK + (j % kKvStages) * kTileBytes);
-              const uint32_t q_addr = smem_u32(sQ + t * kTileBytes);
-#pragma unroll
-              for (int kk = 0; kk < kHD / 16; ++kk)
-                mma_f16(tmem + t * kTileCols, sw128_desc(q_addr + kk * 32), sw128_desc(k_addr + kk * 32), kIdS,
-                        kk > 0 ? 1u : 0u);
-              mma_commit(&s_full[t]);
-              ++ns[t];
-              progress = true;
-            }
-          }
-          all_done = all_done && np[t] == nkv;
-        }
-        int min_np = np[0];
-        if (ntiles > 1) min_np = min(min_np, np[1]);
-        while (released < min_np) {
-          mma_commit(&kv_empty[released % kKvStages]);
-          ++released;
-        }
-        if (all_done) break;
-        // The failure checks (a global load and the clock) only run every 256
-        // idle polls: on the polling path they would delay every issue.
-        if (progress) {
-          idle = 0;
-        } else if ((++idle & 255u) == 0) {
-          if (idle == 256u) t_last = clock64();
-          if (clock64() - t_last > kWaitLimitCycles || *reinterpret_cast<volatile int*>(err) != 0) {
-            atomicCAS(err, 0, static_cast<int>(kDevTimeoutMma));
-            ok = false;
+            issue_s(jn);
           }
         }
       }
@@ -264,36 +258,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = q * 32 + lane;    // row within the tile
     if (t < ntiles) {
       const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-      const uint32_t s_addr = tmem + t * kTileCols + lane_off;
-      const uint32_t o_addr = tmem + t * kTileCols + kOCol + lane_off;
+      const uint32_t tbase = tmem + t * kTileCols + lane_off;
+      const uint32_t o_addr = tbase + kOCol;
+      const uint64_t c2 = pk2(P.scale_log2, P.scale_log2);
       const float c = P.scale_log2;
       float m = -INFINITY;  // the maximum P is taken relative to (log2 units)
       float l = 0.f;
       bool ok = true;
-      const uint32_t p_addr = tmem + t * kTileCols + kPCol + lane_off;
 
       for (int j = 0; j < nkv; ++j) {
-        if (!mbar_wait_warp(&s_full[t], j & 1, err, kDevTimeoutSoftmax, lane)) {
+        const uint32_t s_addr = tbase + (j & 1) * kRegionCols;
+        if (!mbar_wait_warp(&s_full[2 * t + (j & 1)], (j >> 1) & 1, err, kDevTimeoutSoftmax, lane)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        uint32_t v0[32], v1[32], v2[32], v3[32];
+        uint32_t v0[32], v1[32], v2[32];
         tmem_ld32(s_addr, v0);
         tmem_ld32(s_addr + 32, v1);
         tmem_ld32(s_addr + 64, v2);
-        tmem_ld32(s_addr + 96, v3);
         tmem_wait_ld();
-        // S is in registers: the MMA may write the next tile's scores now.
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[t]);
         const int nvalid = min(kKV, s1 - (s0 + j * kKV));
         if (nvalid < kKV) {
           mask_chunk(v0, 0, nvalid);
           mask_chunk(v1, 32, nvalid);
           mask_chunk(v2, 64, nvalid);
-          mask_chunk(v3, 96, nvalid);
         }
         float mx8[8];
 #pragma unroll
@@ -301,33 +290,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         max_chunk(v0, mx8);
         max_chunk(v1, mx8);
         max_chunk(v2, mx8);
-        max_chunk(v3, mx8);
         const float cand = reduce8_max(mx8) * c;
         const float m_new = cand > m + kRescaleLog2 ? cand : m;
         const float alpha = ex2_approx(m - m_new);  // 1 when m is kept, 0 on the first tile
-        // The exponentials only need S; they overlap the previous P*V.
         uint64_t sum2[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) sum2[i] = 0ull;  // +0.0f pairs
-        const uint64_t c2 = pk2(c, c), negm2 = pk2(-m_new, -m_new);
+        const uint64_t negm2 = pk2(-m_new, -m_new);
         uint32_t pk0[32], pk1[32];
         exp_chunk(v0, c2, negm2, pk0, 0, sum2);
         exp_chunk(v1, c2, negm2, pk0, 16, sum2);
         exp_chunk(v2, c2, negm2, pk1, 0, sum2);
-        exp_chunk(v3, c2, negm2, pk1, 16, sum2);
         float sum8[8];
 #pragma unroll
         for (int i = 0; i < 4; ++i) unpk2(sum2[i], sum8[2 * i], sum8[2 * i + 1]);
         const float sum = reduce8_sum(sum8);
-        // The previous P*V has finished: its P columns are free and O is stable.
-        if (j > 0 && !mbar_wait_warp(&p_done[t], (j - 1) & 1, err, kDevTimeoutSoftmax, lane)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        tmem_st32(p_addr, pk0);
-        tmem_st32(p_addr + 32, pk1);
+        // P over the S columns just read (S_t(j+2) waits for PV_t(j)).
+        tmem_st32(s_addr, pk0);
+        tmem_st16(s_addr + 32, pk1);
         if (j > 0 && __any_sync(0xffffffffu, alpha != 1.f)) {
+          // O must hold every PV up to j-1 before it is rescaled.  p_done has
+          // j-1 or j completions here (S(j) waited for PV(j-2); PV(j) needs
+          // this block's P), so the parity of completion j-1 is unambiguous.
+          if (!mbar_wait_warp(&p_done[t], (j - 1) & 1, err, kDevTimeoutSoftmax, lane)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
           tmem_ld32(o_addr, v0);
           tmem_ld32(o_addr + 32, v1);
           tmem_wait_ld();
@@ -341,9 +330,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         m = m_new;
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&p_full[t]);
+        if (lane == 0) mbar_arrive(&p_full[2 * t + (j & 1)]);
       }
-      if (ok && nkv > 0 && mbar_wait_warp(&p_done[t], (nkv - 1) & 1, err, kDevTimeoutSoftmax, lane)) {
+      // The last PV: waited on its region's barrier.  p_done may still lack
+      // two completions here (the softmax can finish while PV(nkv-2) is
+      // pending), where its parity would be ambiguous; the region barrier has
+      // already seen PV(nkv-3) (S(nkv-1) waited for it), so it lacks at most
+      // the awaited one.  Its commit also covers every earlier MMA.
+      const int last = nkv - 1;
+      if (ok && nkv > 0 &&
+          mbar_wait_warp(&p_reg[2 * t + (last & 1)], (last >> 1) & 1, err, kDevTimeoutSoftmax, lane)) {
         tc_fence_after();
         uint32_t o0[32], o1[32];
         tmem_ld32(o_addr, o0);
@@ -381,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 bool encode_attention_tmap(CUtensorMap* map, const void* qkv, int M, int D) {
-  return encode_tmap_bf16_2d(map, qkv, static_cast<uint64_t>(M), 3ull * D, 3ull * D, kKV, kHD);
+  return encode_tmap_bf16_2d(map, qkv, static_cast<uint64_t>(M), 3ull * D, 3ull * D, kBoxRows, kHD);
 }
 
 cudaError_t launch_attention_tc(const CUtensorMap& qkv_map, void* out, int M, int D, int heads, const Segments& seg,

@@ -234,16 +234,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t a_addr = smem_u32(sA + stage * Cfg::kABytes);
-          const uint32_t b_addr = smem_u32(sB + stage * Cfg::kBBytes);
+          const uint32_t a_lo = sw128_lo(smem_u32(sA + stage * Cfg::kABytes));
+          const uint32_t b_lo = sw128_lo(smem_u32(sB + stage * Cfg::kBBytes));
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {  // 4 x 32 bytes of K per stage
             if (F8)
-              mma_f8(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
-                     (kb | kk) != 0 ? 1u : 0u);
+              mma_f8_hl(d_tmem, a_lo + kk * 2, kSw128Hi, b_lo + kk * 2, kSw128Hi, kIdesc, (kb | kk) != 0 ? 1u : 0u);
             else
-              mma_f16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
-                      (kb | kk) != 0 ? 1u : 0u);
+              mma_f16_hl(d_tmem, a_lo + kk * 2, kSw128Hi, b_lo + kk * 2, kSw128Hi, kIdesc, (kb | kk) != 0 ? 1u : 0u);
           }
           mma_commit(&empty[stage]);
           if (++stage == S) {
