@@ -44,7 +44,7 @@ PRECISIONS = {"bf16": lambda R: R.BF16, "fp32": lambda R: R.FP32, "fp8": lambda 
 DTYPE_NAMES = {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3 (encoder fc1; per-token x per-channel scales) + bf16"}
 # DRAM bytes (read + write) of one attn_tc_kernel launch at N = 3600, 12 heads,
 # from an ncu capture of the current kernel version (None once it changes).
-ATTN_DRAM_BYTES_PER_LAUNCH = 16629504
+ATTN_DRAM_BYTES_PER_LAUNCH = None
 
 
 def flops_per_model(C: int, h: int, w: int) -> dict:
@@ -718,6 +718,49 @@ def run_serving(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_kt(args) -> None:
+    """Latency per 640x480 RGB-D frame against the number of clean references
+    k and the tubelet length T (the paper's ablation over k and T): the same
+    kernels at the token counts (k + 1) / T * 1200 each pair gives, batch 1,
+    graph replay, device-timed."""
+    import torch
+
+    import paper_2604_27441_b300 as R
+    import synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    precision = PRECISIONS[args.precision](R)
+    rows = []
+    for k, T in ((1, 1), (1, 2), (3, 1), (3, 2), (5, 1), (5, 2), (7, 1), (7, 2)):
+        shape = dict(VITB, k=k, tubelet=T)
+        cfgs = [synth.ModelConfig(channels=C, k=k, tubelet=T) for C in (3, 1)]
+        ctx = R.Context(R.config(**shape, precision=precision, max_height=H, max_width=W, max_streams=2,
+                                 max_batch=1, lanes=1, use_graphs=1, autotune=1),
+                        synth.flatten(synth.weights(cfgs[0], seed=0)), synth.flatten(synth.weights(cfgs[1], seed=1)),
+                        stream=stream)
+        io = StreamIO(R, torch, ctx, 0, WORKLOAD, 7000 + 10 * k + T, 0.2, 1, True)
+        req = io.reqs[0]
+        for _ in range(args.warmup):
+            ctx.poll(ctx.submit(req))
+        torch.cuda.synchronize()
+        n = max(10, args.steps // 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            r = ctx.poll(ctx.submit(req))
+            assert r.status == R.REVO_OK, R.last_error()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        tokens = (k + 1) // T * (H // 16) * (W // 16)
+        rows.append({"k": k, "T": T, "tokens": tokens, "ms_per_frame": ms, "frames_per_s": 1e3 / ms})
+        ctx.close()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+                      "dtype": DTYPE_NAMES[args.precision], "data": "synthetic",
+                      "config": {"workload": f"k/T sweep, {WORKLOAD} RGB-D, batch 1"}, "rows": rows}), flush=True)
+
+
 def run_profile_kernel(args) -> None:
     """Launches one kernel of the step at the bench's shape (for ncu captures):
     W warm-up + K timed launches on one stream, CUDA-event timed."""
@@ -774,7 +817,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="plain kernel launches instead of graph replay")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
-    ap.add_argument("--workload", choices=["640x480", "mixed16", "serving"], default="640x480",
+    ap.add_argument("--workload", choices=["640x480", "mixed16", "serving", "kt"], default="640x480",
                     help="640x480: the headline batch-1 step; mixed16: one batch of 16 mixed-size streams; "
                          "serving: real-time arrivals from --streams streams")
     ap.add_argument("--streams", type=int, default=4)
@@ -793,6 +836,8 @@ def main():
         run_mixed(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "kt":
+        run_kt(args)
     else:
         run_ours(args)
 

@@ -297,6 +297,18 @@ def test_hold_batches_mixed_sizes_with_autotuned_tiles():
         np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("k,T", [(3, 1), (7, 2), (1, 2)])
+def test_k_and_tubelet_variants(k, T):
+    """Other reference counts and tubelet sizes (the paper's ablation over k
+    and T, Section 4 / Appendix B.3) through the same kernels, BF16 against
+    the FP64 oracle at 320x240."""
+    shape = dict(VITB, k=k, tubelet=T)
+    rgb, dep = synth.make_request(1200 + 10 * k + T, "320x240", k=k)
+    with make_ctx(shape, R.BF16, (240, 320)) as ctx:
+        got = run(ctx, 0, rgb, dep)
+    check(R.BF16, got, oracle(shape, rgb, dep, f"kt{k}{T}"), rgb, dep)
+
+
 def test_two_lanes_interleaved_streams():
     reqs = [synth.make_request(1010 + i, "320x240") for i in range(4)]
     alone = []
