@@ -463,14 +463,14 @@ class StreamIO:
     """One conference stream's buffers: k clean references pushed once, then a
     few corrupted frames (seeded, same size) to recover in turn."""
 
-    def __init__(self, R, torch, ctx, sid, workload, seed, loss_rate, frames, on_device, p_gb=None):
+    def __init__(self, R, torch, ctx, sid, workload, seed, loss_rate, frames, on_device, p_gb=None, k=5):
         import synth
         self.R, self.sid, self.workload = R, sid, workload
         self.reqs, self.keep, self.planes = [], [], []
         self.on_device = on_device
         for f in range(frames):
             kw = dict(loss_rate=loss_rate) if loss_rate is not None else {}
-            rgb, dep = synth.make_request(seed + 7919 * f, workload, index=100 + f, **kw)
+            rgb, dep = synth.make_request(seed + 7919 * f, workload, index=100 + f, k=k, **kw)
             self.planes.append((rgb, dep))
         rgb0, dep0 = self.planes[0]
         self.shape = ((rgb0.height, rgb0.width), (dep0.height, dep0.width))
@@ -739,7 +739,7 @@ def run_kt(args) -> None:
                                  max_batch=1, lanes=1, use_graphs=1, autotune=1),
                         synth.flatten(synth.weights(cfgs[0], seed=0)), synth.flatten(synth.weights(cfgs[1], seed=1)),
                         stream=stream)
-        io = StreamIO(R, torch, ctx, 0, WORKLOAD, 7000 + 10 * k + T, 0.2, 1, True)
+        io = StreamIO(R, torch, ctx, 0, WORKLOAD, 7000 + 10 * k + T, 0.2, 1, True, k=k)
         req = io.reqs[0]
         for _ in range(args.warmup):
             ctx.poll(ctx.submit(req))

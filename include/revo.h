@@ -328,6 +328,27 @@ REVO_API revo_status revo_op_linear_fp8(int epilogue, const uint8_t* A, const fl
                                         int tile_n, void* stream);
 
 /*
+ * Frame-quality metrics of the paper's evaluation (Section 5, Metrics: SSIM
+ * and PSNR of a reconstructed frame against the original).  a, b: device
+ * frames of height x width samples, `channels` (1 or 3) interleaved,
+ * `sample_bytes` 1 (uint8) or 2 (uint16), row pitches in bytes.  data_range =
+ * L (255 for 8-bit RGB; the caller's choice for depth, e.g. 65535).  SSIM:
+ * normalised 11 x 11 Gaussian window (sigma 1.5), C1 = (0.01 L)^2,
+ * C2 = (0.03 L)^2, mean over the positions where the window lies inside the
+ * frame, channels averaged (the paper cites SSIM without parameters; this is
+ * the original definition).  PSNR = 10 log10(L^2 / MSE) over every sample.
+ * out (device, 3 floats): mean SSIM, MSE, PSNR in dB (inf for equal frames).
+ * scratch: device memory of revo_frame_metrics_scratch_bytes() bytes, owned by
+ * the caller (no two calls in flight may share it).  Frames must be larger
+ * than 10 x 10.  Deterministic (fixed-order reductions).
+ * Errors: REVO_EINVAL, REVO_ECUDA.
+ */
+REVO_API size_t revo_frame_metrics_scratch_bytes(int height, int width, int channels);
+REVO_API revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const void* b, size_t pitch_b, int height,
+                                           int width, int channels, int sample_bytes, float data_range,
+                                           void* scratch, float* out, void* stream);
+
+/*
  * Multi-head softmax attention over segments of tokens (the exact scaled
  * dot-product attention of Appendix B.1, point 4).  qkv is [M][3D] (q | k | v,
  * head h owns columns h*64 .. h*64+63 of each part); seg_start[n_seg + 1] is a

@@ -96,6 +96,9 @@ _SIGS = {
                                 C.c_void_p]),
     "revo_op_take_device_error": (C.c_int, []),
     "revo_op_quantize_rows_e4m3": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "revo_frame_metrics_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+    "revo_op_frame_metrics": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_int,
+                                        C.c_int, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
     "revo_op_layernorm_e4m3": (C.c_int, [C.c_void_p] * 5 + [C.c_int, C.c_int, C.c_void_p]),
     "revo_op_linear_fp8": (C.c_int, [C.c_int] + [C.c_void_p] * 6 + [C.c_int] * 4 + [C.c_void_p]),
     "revo_op_depth_stats_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_size_t, C.c_void_p, C.c_void_p]),
@@ -199,6 +202,19 @@ def op_layernorm_e4m3(x, gamma, beta, out, row_scale, M, D, stream=None):
 def op_linear_fp8(epilogue, A, a_scale, W, w_scale, bias, out, M, N, K, tile_n=0, stream=None):
     return _check(lib().revo_op_linear_fp8(epilogue, ptr(A), ptr(a_scale), ptr(W), ptr(w_scale), ptr(bias), ptr(out),
                                            M, N, K, tile_n, _stream(stream)), "revo_op_linear_fp8")
+
+
+def frame_metrics_scratch_bytes(height, width, channels) -> int:
+    return int(lib().revo_frame_metrics_scratch_bytes(height, width, channels))
+
+
+def op_frame_metrics(a, b, height, width, channels, sample_bytes, data_range, scratch, out, stream=None,
+                     pitch_a=None, pitch_b=None):
+    """SSIM / MSE / PSNR of device frame a against b into out (device, 3 floats)."""
+    row = width * channels * sample_bytes
+    return _check(lib().revo_op_frame_metrics(ptr(a), pitch_a or row, ptr(b), pitch_b or row, height, width, channels,
+                                              sample_bytes, float(data_range), ptr(scratch), ptr(out),
+                                              _stream(stream)), "revo_op_frame_metrics")
 
 
 def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None):

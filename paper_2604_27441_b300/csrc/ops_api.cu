@@ -209,6 +209,25 @@ revo_status revo_op_linear_fp8(int epilogue, const uint8_t* A, const float* a_sc
                      "revo_op_linear_fp8");
 }
 
+size_t revo_frame_metrics_scratch_bytes(int height, int width, int channels) {
+  return frame_metrics_scratch_bytes(height, width, channels);
+}
+
+revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const void* b, size_t pitch_b, int height, int width,
+                                  int channels, int sample_bytes, float data_range, void* scratch, float* out,
+                                  void* stream) {
+  if (!a || !b || !scratch || !out || height <= 10 || width <= 10 || (channels != 1 && channels != 3) ||
+      (sample_bytes != 1 && sample_bytes != 2) || !(data_range > 0.f) ||
+      pitch_a < static_cast<size_t>(width) * channels * sample_bytes ||
+      pitch_b < static_cast<size_t>(width) * channels * sample_bytes) {
+    set_last_error("revo_op_frame_metrics: bad argument");
+    return REVO_EINVAL;
+  }
+  return cuda_status(launch_frame_metrics(a, pitch_a, b, pitch_b, height, width, channels, sample_bytes, data_range, out,
+                                          scratch, static_cast<cudaStream_t>(stream)),
+                     "revo_op_frame_metrics");
+}
+
 revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D, int heads,
                               const int* seg_start, int n_seg, void* stream) {
   if (!qkv || !out || !seg_start || n_seg <= 0 || n_seg > kMaxSegments || heads <= 0 || D != 64 * heads) {

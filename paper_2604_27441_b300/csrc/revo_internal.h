@@ -113,6 +113,12 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st, const BlendArgs* d
 
 cudaError_t launch_f32_to_bf16(const float* in, void* out, size_t n, cudaStream_t st);
 
+// SSIM and PSNR of frame a against frame b (uint8 or uint16 samples, C = 1
+// or 3 interleaved): out[0] = mean SSIM, out[1] = MSE, out[2] = PSNR (dB).
+size_t frame_metrics_scratch_bytes(int H, int W, int C);
+cudaError_t launch_frame_metrics(const void* a, size_t pitch_a, const void* b, size_t pitch_b, int H, int W, int C,
+                                 int sample_bytes, float data_range, float* out, void* scratch, cudaStream_t st);
+
 int device_sm_count();
 
 // Raises a kernel's dynamic shared-memory limit once per device (the attribute

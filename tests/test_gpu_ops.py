@@ -295,3 +295,42 @@ def test_blend_codes_bit_exact(modality, H, W):
     np.testing.assert_array_equal(got, expect)
     np.testing.assert_array_equal(got[~pl.lost], pl.decoded[~pl.lost])
     np.testing.assert_array_equal(values.cpu().numpy(), vals)
+
+
+# ------------------------------------------------------------ frame metrics
+
+from oracle import metrics as MX  # noqa: E402
+
+
+@pytest.mark.parametrize("kind,H,W", [("rgb", 240, 320), ("rgb", 37, 53), ("depth", 480, 640), ("depth", 11, 11),
+                                      ("rgb", 720, 1280)])
+def test_frame_metrics_ssim_psnr(kind, H, W):
+    """SSIM (mean over the valid window positions, channels averaged) and PSNR
+    against the float64 oracle: |dSSIM| <= 2e-5, |dPSNR| <= 1e-3 dB."""
+    rng = np.random.default_rng(H * W)
+    if kind == "rgb":
+        x = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
+        y = np.clip(x.astype(np.int32) + rng.integers(-20, 21, x.shape), 0, 255).astype(np.uint8)
+        L, C, sb = 255.0, 3, 1
+        tx, ty = dev(x), dev(y)
+    else:
+        x = rng.integers(500, 4001, (H, W), dtype=np.uint16)
+        y = np.clip(x.astype(np.int32) + rng.integers(-60, 61, x.shape), 0, 65535).astype(np.uint16)
+        L, C, sb = 65535.0, 1, 2
+        tx, ty = dev(x.view(np.int16)), dev(y.view(np.int16))
+    scratch = torch.zeros(R.frame_metrics_scratch_bytes(H, W, C) // 4 + 1, dtype=torch.float32, device="cuda")
+    out = torch.zeros(3, dtype=torch.float32, device="cuda")
+    R.op_frame_metrics(tx, ty, H, W, C, sb, L, scratch, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    assert abs(got[0] - MX.ssim(x, y, L)) <= 2e-5
+    assert abs(got[1] - MX.mse(x, y)) <= 1e-5 * MX.mse(x, y)
+    assert abs(got[2] - MX.psnr(x, y, L)) <= 1e-3
+    # identical frames: SSIM 1, PSNR infinite; a second call gives the same bits
+    R.op_frame_metrics(tx, tx, H, W, C, sb, L, scratch, out)
+    torch.cuda.synchronize()
+    same = out.cpu().numpy()
+    assert abs(same[0] - 1.0) < 1e-6 and same[1] == 0 and np.isinf(same[2])
+    R.op_frame_metrics(tx, ty, H, W, C, sb, L, scratch, out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), got.astype(np.float32))
