@@ -328,6 +328,33 @@ REVO_API revo_status revo_op_linear_fp8(int epilogue, const uint8_t* A, const fl
                                         int tile_n, void* stream);
 
 /*
+ * Reed-Solomon erasure coding of I-frame packets (Section 3.2: an I-frame is
+ * cut into n data packets, r parity packets are added (the paper: r = n/2),
+ * and any n of the n + r packets rebuild the frame).  The paper fixes no
+ * matrix; this is a systematic code over GF(2^8) with field polynomial
+ * x^8 + x^4 + x^3 + x^2 + 1 whose parity packet i is, byte by byte,
+ * sum_j data[j] / ((n + i) + j) (Cauchy rows; + is XOR in the field).
+ * Packets are device buffers of packet_bytes bytes (a multiple of 4; pad the
+ * last one), rows `pitch` bytes apart (multiples of 4); 1 <= n, n + r <= 256.
+ *
+ * revo_fec_encode: data [n] -> parity [r].
+ * revo_fec_decode: received [n] = the packets with indices present[0..n-1]
+ *   (host array; data packets are 0..n-1, parity packets n..n+r-1), in that
+ *   order -> data_out [n].  Arrived data packets are copied, missing ones
+ *   rebuilt; the inverse is computed on the host (O(n^3) field operations).
+ *   scratch: device memory of revo_fec_decode_scratch_bytes(n) bytes (needed
+ *   when a data packet is missing), owned by the caller.
+ * Errors: REVO_EINVAL (shape, pointers, repeated or out-of-range indices),
+ * REVO_ECUDA.
+ */
+REVO_API revo_status revo_fec_encode(int n, int r, size_t packet_bytes, const uint8_t* data, size_t data_pitch,
+                                     uint8_t* parity, size_t parity_pitch, void* stream);
+REVO_API size_t revo_fec_decode_scratch_bytes(int n);
+REVO_API revo_status revo_fec_decode(int n, int r, size_t packet_bytes, const int* present, const uint8_t* received,
+                                     size_t received_pitch, uint8_t* data_out, size_t out_pitch, void* scratch,
+                                     void* stream);
+
+/*
  * Frame-quality metrics of the paper's evaluation (Section 5, Metrics: SSIM
  * and PSNR of a reconstructed frame against the original).  a, b: device
  * frames of height x width samples, `channels` (1 or 3) interleaved,

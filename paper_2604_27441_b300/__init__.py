@@ -97,6 +97,11 @@ _SIGS = {
     "revo_op_take_device_error": (C.c_int, []),
     "revo_op_quantize_rows_e4m3": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "revo_frame_metrics_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+    "revo_fec_encode": (C.c_int, [C.c_int, C.c_int, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t,
+                                  C.c_void_p]),
+    "revo_fec_decode_scratch_bytes": (C.c_size_t, [C.c_int]),
+    "revo_fec_decode": (C.c_int, [C.c_int, C.c_int, C.c_size_t, C.POINTER(C.c_int), C.c_void_p, C.c_size_t,
+                                  C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
     "revo_op_frame_metrics": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_int,
                                         C.c_int, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
     "revo_op_layernorm_e4m3": (C.c_int, [C.c_void_p] * 5 + [C.c_int, C.c_int, C.c_void_p]),
@@ -202,6 +207,23 @@ def op_layernorm_e4m3(x, gamma, beta, out, row_scale, M, D, stream=None):
 def op_linear_fp8(epilogue, A, a_scale, W, w_scale, bias, out, M, N, K, tile_n=0, stream=None):
     return _check(lib().revo_op_linear_fp8(epilogue, ptr(A), ptr(a_scale), ptr(W), ptr(w_scale), ptr(bias), ptr(out),
                                            M, N, K, tile_n, _stream(stream)), "revo_op_linear_fp8")
+
+
+def fec_encode(n, r, packet_bytes, data, parity, stream=None):
+    """Parity [r][packet_bytes] of data [n][packet_bytes] (device, dense rows)."""
+    return _check(lib().revo_fec_encode(n, r, packet_bytes, ptr(data), packet_bytes, ptr(parity), packet_bytes,
+                                        _stream(stream)), "revo_fec_encode")
+
+
+def fec_decode_scratch_bytes(n) -> int:
+    return int(lib().revo_fec_decode_scratch_bytes(n))
+
+
+def fec_decode(n, r, packet_bytes, present, received, data_out, scratch, stream=None):
+    """Data [n][packet_bytes] from the n packets `present` (indices) stacked in `received`."""
+    arr = (C.c_int * n)(*[int(p) for p in present])
+    return _check(lib().revo_fec_decode(n, r, packet_bytes, arr, ptr(received), packet_bytes, ptr(data_out),
+                                        packet_bytes, ptr(scratch), _stream(stream)), "revo_fec_decode")
 
 
 def frame_metrics_scratch_bytes(height, width, channels) -> int:

@@ -8,6 +8,8 @@
 
 #include "common.cuh"
 #include "revo.h"
+#include <vector>
+
 #include "revo_internal.h"
 
 namespace revo {
@@ -207,6 +209,46 @@ revo_status revo_op_linear_fp8(int epilogue, const uint8_t* A, const float* a_sc
   return cuda_status(launch_gemm_tc_fp8(ma, mb, mc, bn, epilogue, bias, a_scale, w_scale, M, N, K, err,
                                         device_sm_count(), static_cast<cudaStream_t>(stream)),
                      "revo_op_linear_fp8");
+}
+
+revo_status revo_fec_encode(int n, int r, size_t packet_bytes, const uint8_t* data, size_t data_pitch,
+                            uint8_t* parity, size_t parity_pitch, void* stream) {
+  if (!data || (r > 0 && !parity) || n < 1 || r < 0 || n + r > 256 || packet_bytes == 0 || packet_bytes % 4 ||
+      data_pitch < packet_bytes || (r > 0 && parity_pitch < packet_bytes) || data_pitch % 4 || parity_pitch % 4) {
+    set_last_error("revo_fec_encode: bad argument (1 <= n, n + r <= 256, packet_bytes and pitches multiples of 4)");
+    return REVO_EINVAL;
+  }
+  return cuda_status(fec_encode(n, r, packet_bytes, data, data_pitch, parity, parity_pitch,
+                                static_cast<cudaStream_t>(stream)),
+                     "revo_fec_encode");
+}
+
+size_t revo_fec_decode_scratch_bytes(int n) { return fec_decode_scratch_bytes(n); }
+
+revo_status revo_fec_decode(int n, int r, size_t packet_bytes, const int* present, const uint8_t* received,
+                            size_t received_pitch, uint8_t* data_out, size_t out_pitch, void* scratch, void* stream) {
+  if (!present || !received || !data_out || n < 1 || r < 0 || n + r > 256 || packet_bytes == 0 || packet_bytes % 4 ||
+      received_pitch < packet_bytes || out_pitch < packet_bytes || received_pitch % 4 || out_pitch % 4) {
+    set_last_error("revo_fec_decode: bad argument");
+    return REVO_EINVAL;
+  }
+  std::vector<char> seen(static_cast<size_t>(n + r), 0);
+  int missing = 0;
+  for (int a = 0; a < n; ++a) {
+    if (present[a] < 0 || present[a] >= n + r || seen[present[a]]) {
+      set_last_error("revo_fec_decode: present[] must hold n distinct packet indices in [0, n + r)");
+      return REVO_EINVAL;
+    }
+    seen[present[a]] = 1;
+  }
+  for (int d = 0; d < n; ++d) missing += !seen[d];
+  if (missing > 0 && !scratch) {
+    set_last_error("revo_fec_decode: scratch (revo_fec_decode_scratch_bytes(n) bytes) needed");
+    return REVO_EINVAL;
+  }
+  return cuda_status(fec_decode(n, r, packet_bytes, present, received, received_pitch, data_out, out_pitch, scratch,
+                                static_cast<cudaStream_t>(stream)),
+                     "revo_fec_decode");
 }
 
 size_t revo_frame_metrics_scratch_bytes(int height, int width, int channels) {

@@ -113,6 +113,16 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st, const BlendArgs* d
 
 cudaError_t launch_f32_to_bf16(const float* in, void* out, size_t n, cudaStream_t st);
 
+// Reed-Solomon erasure code of I-frame packets over GF(2^8) (systematic,
+// Cauchy parity rows): encode n data packets into r parity packets; decode n
+// received packets (indices `present`, data 0..n-1, parity n..n+r-1) into the
+// n data packets.  packet_bytes and pitches multiples of 4; n + r <= 256.
+cudaError_t fec_encode(int n, int r, size_t packet_bytes, const uint8_t* data, size_t data_pitch, uint8_t* parity,
+                       size_t parity_pitch, cudaStream_t st);
+size_t fec_decode_scratch_bytes(int n);
+cudaError_t fec_decode(int n, int r, size_t packet_bytes, const int* present, const uint8_t* received,
+                       size_t received_pitch, uint8_t* data_out, size_t out_pitch, void* scratch, cudaStream_t st);
+
 // SSIM and PSNR of frame a against frame b (uint8 or uint16 samples, C = 1
 // or 3 interleaved): out[0] = mean SSIM, out[1] = MSE, out[2] = PSNR (dB).
 size_t frame_metrics_scratch_bytes(int H, int W, int C);

@@ -80,6 +80,12 @@ def test_null_arguments_are_rejected_before_any_device_work(lib):
     assert lib.revo_recover_submit(None, None, None) == R.REVO_EINVAL
     assert lib.revo_recover_poll(None, 1, 0, None) == R.REVO_EINVAL
     assert lib.revo_recover_stats(None, None) == R.REVO_EINVAL
+    assert lib.revo_fec_encode(0, 1, 8, None, 8, None, 8, None) == R.REVO_EINVAL
+    assert lib.revo_fec_encode(200, 100, 8, 1, 8, 1, 8, None) == R.REVO_EINVAL  # n + r > 256
+    assert lib.revo_fec_encode(4, 2, 6, 1, 8, 1, 8, None) == R.REVO_EINVAL     # packet not a multiple of 4
+    dup = (C.c_int * 2)(0, 0)
+    assert lib.revo_fec_decode(2, 1, 8, dup, 1, 8, 1, 8, 1, None) == R.REVO_EINVAL
+    assert lib.revo_op_frame_metrics(None, 8, None, 8, 4, 4, 1, 1, 255.0, None, None, None) == R.REVO_EINVAL
     lib.revo_recover_destroy(None)
 
 

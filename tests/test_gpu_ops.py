@@ -334,3 +334,58 @@ def test_frame_metrics_ssim_psnr(kind, H, W):
     R.op_frame_metrics(tx, ty, H, W, C, sb, L, scratch, out)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy(), got.astype(np.float32))
+
+
+# ---------------------------------------------------------------------- fec
+
+from oracle import fec as FEC  # noqa: E402
+
+_GF_TABLE = None
+
+
+def gf_table():
+    """256 x 256 products from the oracle's field multiplication (built once)."""
+    global _GF_TABLE
+    if _GF_TABLE is None:
+        _GF_TABLE = np.array([[FEC.gf_mul(a, b) for b in range(256)] for a in range(256)], np.uint8)
+    return _GF_TABLE
+
+
+def oracle_parity(data, r):
+    """The oracle's parity rows, evaluated with its product table (vectorised)."""
+    T = gf_table()
+    n = data.shape[0]
+    C = FEC.cauchy(n, r)
+    out = np.zeros((r, data.shape[1]), np.uint8)
+    for i in range(r):
+        for j in range(n):
+            out[i] ^= T[C[i][j]][data[j]]
+    return out
+
+
+@pytest.mark.parametrize("n,r,S", [(8, 4, 1200), (84, 42, 1200), (170, 85, 64), (1, 0, 4), (255, 1, 1004),
+                                    (3, 253, 12)])
+def test_fec_encode_decode(n, r, S):
+    """Parity bit-exact against the oracle; every data packet rebuilt bit for
+    bit from random n-subsets of the n + r packets (all parity, no parity,
+    mixed)."""
+    rng = np.random.default_rng(n * 1000 + r)
+    data = rng.integers(0, 256, (n, S), dtype=np.uint8)
+    parity = torch.zeros((max(r, 1), S), dtype=torch.uint8, device="cuda")
+    d_data = dev(data)
+    R.fec_encode(n, r, S, d_data, parity)
+    torch.cuda.synchronize()
+    if r > 0:
+        np.testing.assert_array_equal(parity.cpu().numpy()[:r], oracle_parity(data, r))
+    shards = np.concatenate([data, parity.cpu().numpy()[:r]])
+    scratch = torch.zeros(max(R.fec_decode_scratch_bytes(n), 1), dtype=torch.uint8, device="cuda")
+    subsets = [list(range(n))]
+    if r > 0:
+        subsets.append(sorted(rng.choice(n + r, n, replace=False).tolist()))
+        subsets.append(list(range(max(0, n - r), n + r))[-n:] if r >= n else list(range(r, n + r)))
+        subsets.append(rng.permutation(n + r)[:n].tolist())  # unsorted order
+    for present in subsets:
+        out = torch.zeros((n, S), dtype=torch.uint8, device="cuda")
+        R.fec_decode(n, r, S, present, dev(shards[present]), out, scratch)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), data)
