@@ -23,8 +23,8 @@ the order written above (products and sums of R x + t left to right), so a
 float32 implementation that rounds each step the same way agrees bit for bit.
 Pinned by tests: the identity pose reproduces the input frame exactly, a pure
 translation along z shifts depth by the translation, a rotation by pi about
-the optical axis mirrors the frame, and a brute-force per-point loop on tiny
-frames.
+the optical axis mirrors the frame, and hand-worked occlusion, tie and
+resampling cases on tiny frames.
 """
 from __future__ import annotations
 
@@ -69,17 +69,26 @@ def render(rgb: np.ndarray, depth: np.ndarray, K_src, R, t, K_dst, out_hw, splat
     keep &= np.isfinite(u) & np.isfinite(v) & (np.abs(u) < 1e9) & (np.abs(v) < 1e9)
     pu = np.rint(np.where(keep, u, 0)).astype(np.int64)
     pv = np.rint(np.where(keep, v, 0)).astype(np.int64)
-    best_z = np.full((Ho, Wo), np.inf, np.float64)
-    best_i = np.full((Ho, Wo), -1, np.int64)
-    zz = Z.astype(np.float64)
-    for k in np.nonzero(keep)[0]:
-        for dv in range(-splat, splat + 1):
-            for du in range(-splat, splat + 1):
-                a, b = pv[k] + dv, pu[k] + du
-                if 0 <= a < Ho and 0 <= b < Wo:
-                    if zz[k] < best_z[a, b] or (zz[k] == best_z[a, b] and idx[k] < idx[best_i[a, b]]):
-                        best_z[a, b] = zz[k]
-                        best_i[a, b] = k
+    # Every (point, covered pixel) pair, then per pixel the smallest (z', index).
+    pts = np.nonzero(keep)[0]
+    cand_pix, cand_z, cand_k = [], [], []
+    for dv in range(-splat, splat + 1):
+        for du in range(-splat, splat + 1):
+            a, b = pv[pts] + dv, pu[pts] + du
+            ok = (a >= 0) & (a < Ho) & (b >= 0) & (b < Wo)
+            cand_pix.append(a[ok] * Wo + b[ok])
+            cand_z.append(Z[pts[ok]].astype(np.float64))
+            cand_k.append(pts[ok])
+    pix = np.concatenate(cand_pix) if cand_pix else np.zeros(0, np.int64)
+    cz = np.concatenate(cand_z) if cand_z else np.zeros(0)
+    ck = np.concatenate(cand_k) if cand_k else np.zeros(0, np.int64)
+    order = np.lexsort((idx[ck], cz, pix))  # by pixel, then z', then point index
+    pix, ck = pix[order], ck[order]
+    first = np.ones(pix.size, bool)
+    first[1:] = pix[1:] != pix[:-1]
+    best_i = np.full(Ho * Wo, -1, np.int64)
+    best_i[pix[first]] = ck[first]
+    best_i = best_i.reshape(Ho, Wo)
     out_rgb = np.zeros((Ho, Wo, 3), np.uint8)
     out_d = np.zeros((Ho, Wo), np.uint16)
     hit = best_i >= 0
