@@ -355,6 +355,42 @@ REVO_API revo_status revo_fec_decode(int n, int r, size_t packet_bytes, const in
                                      void* stream);
 
 /*
+ * RGB-D rendering: unprojection + point splatting of a (recovered) RGB-D
+ * frame into the viewer's camera (the receiver's rendering step; RGB-D frames
+ * are 2-D projections of the scene, Section 2).  The paper fixes no camera
+ * model; this is a pinhole model: intrinsics {fx, fy, cx, cy}, pixel (i, j) at
+ * u = i, v = j; a depth sample d (mm, 0 = none) is the point ((u - cx) d / fx,
+ * (v - cy) d / fy, d); the pose maps it to x' = R x + t (R row-major, t in
+ * mm); it lands on pixel (round(fx' x'/z' + cx'), round(fy' y'/z' + cy')) of the
+ * target (round half to even; z' <= 0 dropped) and covers the
+ * (2 splat_radius + 1)^2 pixels around it; per pixel the nearest z' wins (ties:
+ * the lower row-major depth index).  Output: out_rgb uint8 [out_h][out_w][3]
+ * (the winner's colour: RGB pixel (i rgb_w / w, j rgb_h / h), nearest sample),
+ * out_depth uint16 [out_h][out_w] (z' rounded half to even, clamped); empty
+ * pixels 0.  Every float step is separately rounded in a fixed order, so the
+ * result is reproducible bit for bit.  All buffers device; pitches in bytes.
+ * scratch: revo_render_scratch_bytes(out_h, out_w) bytes of device memory (the
+ * 64-bit z-buffer), owned by the caller.  splat_radius 0..16.
+ * Errors: REVO_EINVAL, REVO_ECUDA.
+ */
+typedef struct {
+  float fx, fy, cx, cy;
+} revo_intrinsics;
+
+typedef struct {
+  float r[9]; /* row-major rotation */
+  float t[3]; /* translation, mm */
+} revo_pose;
+
+REVO_API size_t revo_render_scratch_bytes(int out_h, int out_w);
+REVO_API revo_status revo_render_rgbd(const uint8_t* rgb, int rgb_h, int rgb_w, size_t rgb_pitch,
+                                      const uint16_t* depth, int h, int w, size_t depth_pitch,
+                                      const revo_intrinsics* src, const revo_pose* pose, const revo_intrinsics* dst,
+                                      int out_h, int out_w, int splat_radius, void* scratch, uint8_t* out_rgb,
+                                      size_t out_rgb_pitch, uint16_t* out_depth, size_t out_depth_pitch,
+                                      void* stream);
+
+/*
  * Frame-quality metrics of the paper's evaluation (Section 5, Metrics: SSIM
  * and PSNR of a reconstructed frame against the original).  a, b: device
  * frames of height x width samples, `channels` (1 or 3) interleaved,

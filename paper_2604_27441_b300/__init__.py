@@ -8,6 +8,8 @@ Tensors may be passed as torch tensors, numpy arrays or raw integer pointers.
 from __future__ import annotations
 
 import ctypes as C
+
+import numpy as np
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -56,6 +58,14 @@ class Request(C.Structure):
                 ("rgb_values", C.c_void_p), ("depth_values", C.c_void_p)]
 
 
+class Intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float)]
+
+
+class Pose(C.Structure):
+    _fields_ = [("r", C.c_float * 9), ("t", C.c_float * 3)]
+
+
 class Stats(C.Structure):
     _fields_ = [("device_bytes", C.c_size_t), ("batches", C.c_uint64), ("graph_replays", C.c_uint64),
                 ("graphs_captured", C.c_int), ("tuned_shapes", C.c_int), ("tuned_wide", C.c_int),
@@ -97,6 +107,10 @@ _SIGS = {
     "revo_op_take_device_error": (C.c_int, []),
     "revo_op_quantize_rows_e4m3": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "revo_frame_metrics_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+    "revo_render_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "revo_render_rgbd": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_size_t, C.c_void_p, C.c_int, C.c_int, C.c_size_t,
+                                   C.POINTER(Intrinsics), C.POINTER(Pose), C.POINTER(Intrinsics), C.c_int, C.c_int,
+                                   C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p]),
     "revo_fec_encode": (C.c_int, [C.c_int, C.c_int, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t,
                                   C.c_void_p]),
     "revo_fec_decode_scratch_bytes": (C.c_size_t, [C.c_int]),
@@ -224,6 +238,23 @@ def fec_decode(n, r, packet_bytes, present, received, data_out, scratch, stream=
     arr = (C.c_int * n)(*[int(p) for p in present])
     return _check(lib().revo_fec_decode(n, r, packet_bytes, arr, ptr(received), packet_bytes, ptr(data_out),
                                         packet_bytes, ptr(scratch), _stream(stream)), "revo_fec_decode")
+
+
+def render_scratch_bytes(out_h, out_w) -> int:
+    return int(lib().revo_render_scratch_bytes(out_h, out_w))
+
+
+def render_rgbd(rgb, depth, K_src, R, t, K_dst, out_hw, splat, scratch, out_rgb, out_depth, stream=None):
+    """Unproject + splat a device RGB-D frame into the target view (dense rows)."""
+    rh, rw = rgb.shape[:2]
+    h, w = depth.shape
+    oh, ow = out_hw
+    src, dst = Intrinsics(*K_src), Intrinsics(*K_dst)
+    pose = Pose((C.c_float * 9)(*[float(v) for v in np.asarray(R).reshape(-1)]),
+                (C.c_float * 3)(*[float(v) for v in t]))
+    return _check(lib().revo_render_rgbd(ptr(rgb), rh, rw, rw * 3, ptr(depth), h, w, w * 2, C.byref(src),
+                                         C.byref(pose), C.byref(dst), oh, ow, splat, ptr(scratch), ptr(out_rgb),
+                                         ow * 3, ptr(out_depth), ow * 2, _stream(stream)), "revo_render_rgbd")
 
 
 def frame_metrics_scratch_bytes(height, width, channels) -> int:

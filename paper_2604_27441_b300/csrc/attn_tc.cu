@@ -24,6 +24,8 @@
 // of tile 0, warps 2..5 softmax of tile 0, warps 6..9 softmax of tile 1 (warp
 // w owns rows 32*(w%4) .. +31 of its tile, the TMEM lanes it may access),
 // warp 10 MMA issuer of tile 1.
+#include <algorithm>
+
 #include "common.cuh"
 #include "revo_internal.h"
 
@@ -49,11 +51,20 @@ constexpr uint32_t kOCol = 192;
 constexpr float kRescaleLog2 = 8.0f;  // rescale once a row max grows by more than 2^8
 
 struct TcAttnParams {
-  int D, n_seg;
+  int D, n_seg, heads, items;
   float scale_log2;
   int start[kMaxSegments + 1];
   int item_prefix[kMaxSegments + 1];  // work items (256-query blocks) before each segment
+  // Work unit u = head * items + item; this launch covers units
+  // [unit_base, unit_base + gridDim.x / chunks), each split into `chunks`
+  // contiguous K/V ranges.  part == null: whole rows, bf16 out; else each CTA
+  // writes its rows' unnormalised O, reference maximum and sum to slot
+  // blockIdx.x of `part` for attn_combine_kernel.
+  int unit_base, chunks;
+  float* part;  // [slots][256][64] O, then [slots][256][2] (m, l)
 };
+
+constexpr int kPartRows = kTiles * kQ;  // 256 rows per partial slot
 
 // Keys at or beyond `nvalid` in columns [col0, col0 + 32) get a score of -inf.
 REVO_DEVI void mask_chunk(uint32_t (&v)[32], int col0, int nvalid) {
@@ -144,14 +155,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int h = blockIdx.y;
-  const int item = blockIdx.x;
+  const int unit = P.unit_base + static_cast<int>(blockIdx.x) / P.chunks;
+  const int chunk = static_cast<int>(blockIdx.x) % P.chunks;
+  const int h = unit / P.items;
+  const int item = unit % P.items;
   int g = 0;
   while (g + 1 < P.n_seg && P.item_prefix[g + 1] <= item) ++g;
   const int s0 = P.start[g];
   const int s1 = P.start[g + 1];
   const int q0 = s0 + (item - P.item_prefix[g]) * (kTiles * kQ);
-  const int nkv = (s1 - s0 + kKV - 1) / kKV;
+  const int nkv_all = (s1 - s0 + kKV - 1) / kKV;
+  const int per = (nkv_all + P.chunks - 1) / P.chunks;
+  const int kv0 = chunk * per;                             // first K/V tile of this CTA
+  const int nkv = max(0, min(nkv_all, kv0 + per) - kv0);   // K/V tiles of this CTA
   const int ntiles = (s1 - q0) > kQ ? kTiles : 1;  // the second tile may lie past the segment end
   const int D = P.D;
 
@@ -193,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(&kv_empty[st], ((j / kKvStages) & 1) ^ 1u, err, kDevTimeoutProducer)) break;
         mbar_arrive_expect_tx(&kv_full[st], 2 * kKVBytes);
         for (int b = 0; b < kKV / kBoxRows; ++b) {
-          const int row = s0 + j * kKV + b * kBoxRows;
+          const int row = s0 + (kv0 + j) * kKV + b * kBoxRows;
           tma_load_2d(sK + st * kKVBytes + b * kBoxBytes, &tm, D + h * kHD, row, &kv_full[st]);
           tma_load_2d(sV + st * kKVBytes + b * kBoxBytes, &tm, 2 * D + h * kHD, row, &kv_full[st]);
         }
@@ -278,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld32(s_addr + 32, v1);
         tmem_ld32(s_addr + 64, v2);
         tmem_wait_ld();
-        const int nvalid = min(kKV, s1 - (s0 + j * kKV));
+        const int nvalid = min(kKV, s1 - (s0 + (kv0 + j) * kKV));
         if (nvalid < kKV) {
           mask_chunk(v0, 0, nvalid);
           mask_chunk(v1, 32, nvalid);
@@ -338,13 +354,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       // already seen PV(nkv-3) (S(nkv-1) waited for it), so it lacks at most
       // the awaited one.  Its commit also covers every earlier MMA.
       const int last = nkv - 1;
+      uint32_t o0[32], o1[32];
+      bool have_o = false;
       if (ok && nkv > 0 &&
           mbar_wait_warp(&p_reg[2 * t + (last & 1)], (last >> 1) & 1, err, kDevTimeoutSoftmax, lane)) {
         tc_fence_after();
-        uint32_t o0[32], o1[32];
         tmem_ld32(o_addr, o0);
         tmem_ld32(o_addr + 32, o1);
         tmem_wait_ld();
+        have_o = true;
+      }
+      if (P.part) {
+        // Partial: unnormalised O, the reference maximum m (log2 units) and
+        // the sum l of this CTA's K/V range (an empty range: O = 0, l = 0).
+        const size_t slot_row = static_cast<size_t>(blockIdx.x) * kPartRows + t * kQ + r;
+        float4* po = reinterpret_cast<float4*>(P.part + slot_row * kHD);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          po[u] = have_o ? make_float4(__uint_as_float(o0[4 * u]), __uint_as_float(o0[4 * u + 1]),
+                                       __uint_as_float(o0[4 * u + 2]), __uint_as_float(o0[4 * u + 3]))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+          po[8 + u] = have_o ? make_float4(__uint_as_float(o1[4 * u]), __uint_as_float(o1[4 * u + 1]),
+                                           __uint_as_float(o1[4 * u + 2]), __uint_as_float(o1[4 * u + 3]))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float* pml = P.part + static_cast<size_t>(gridDim.x) * kPartRows * kHD + slot_row * 2;
+        pml[0] = have_o ? m : -INFINITY;
+        pml[1] = have_o ? l : 0.f;
+      } else if (have_o) {
         const int row = q0 + t * kQ + r;
         if (row < s1) {
           const float inv = 1.f / l;
@@ -374,34 +411,122 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Merges the `chunks` partial results of each split work unit: per query row
+// O = sum_c 2^(m_c - M) O_c, l = sum_c 2^(m_c - M) l_c with M = max_c m_c, and
+// writes O / l as bf16.  One thread per (unit, row, 4 columns).
+__global__ void attn_combine_kernel(const __grid_constant__ TcAttnParams P, __nv_bfloat16* __restrict__ out,
+                                    int nunits) {
+  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (idx >= static_cast<long long>(nunits) * kPartRows * (kHD / 4)) return;
+  const int c4 = static_cast<int>(idx % (kHD / 4));
+  const int row = static_cast<int>((idx / (kHD / 4)) % kPartRows);
+  const int ul = static_cast<int>(idx / (kHD / 4) / kPartRows);
+  const int unit = P.unit_base + ul;
+  const int h = unit / P.items;
+  const int item = unit % P.items;
+  int g = 0;
+  while (g + 1 < P.n_seg && P.item_prefix[g + 1] <= item) ++g;
+  const int q = P.start[g] + (item - P.item_prefix[g]) * kPartRows + row;
+  if (q >= P.start[g + 1]) return;
+  const size_t slots = static_cast<size_t>(nunits) * P.chunks;
+  const float* ml = P.part + slots * kPartRows * kHD;
+  float M = -INFINITY;
+  for (int c = 0; c < P.chunks; ++c) {
+    const size_t sr = (static_cast<size_t>(ul) * P.chunks + c) * kPartRows + row;
+    M = fmaxf(M, ml[sr * 2]);
+  }
+  float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+  float L = 0.f;
+  for (int c = 0; c < P.chunks; ++c) {
+    const size_t sr = (static_cast<size_t>(ul) * P.chunks + c) * kPartRows + row;
+    const float mc = ml[sr * 2];
+    if (mc == -INFINITY) continue;
+    const float w = ex2_approx(mc - M);
+    const float4 oc = reinterpret_cast<const float4*>(P.part + sr * kHD)[c4];
+    o.x = fmaf(w, oc.x, o.x);
+    o.y = fmaf(w, oc.y, o.y);
+    o.z = fmaf(w, oc.z, o.z);
+    o.w = fmaf(w, oc.w, o.w);
+    L = fmaf(w, ml[sr * 2 + 1], L);
+  }
+  const float inv = 1.f / L;
+  uint2* dst = reinterpret_cast<uint2*>(out + static_cast<size_t>(q) * P.D + h * kHD + c4 * 4);
+  *dst = make_uint2(pack_bf16x2(o.x * inv, o.y * inv), pack_bf16x2(o.z * inv, o.w * inv));
+}
+
 }  // namespace
+
+size_t attention_partial_bytes(int num_sms) {
+  return static_cast<size_t>(num_sms) * kPartRows * (kHD + 2) * sizeof(float);
+}
 
 bool encode_attention_tmap(CUtensorMap* map, const void* qkv, int M, int D) {
   return encode_tmap_bf16_2d(map, qkv, static_cast<uint64_t>(M), 3ull * D, 3ull * D, kBoxRows, kHD);
 }
 
 cudaError_t launch_attention_tc(const CUtensorMap& qkv_map, void* out, int M, int D, int heads, const Segments& seg,
-                                int* err, cudaStream_t st) {
+                                int* err, cudaStream_t st, float* part, int num_sms, int* launched) {
+  if (launched) *launched = 0;
   if (seg.n <= 0 || seg.n > kMaxSegments || D != heads * kHD) return cudaErrorInvalidValue;
   TcAttnParams P{};
   P.D = D;
   P.n_seg = seg.n;
+  P.heads = heads;
   P.scale_log2 = 1.4426950408889634f * 0.125f;  // log2(e) / sqrt(64)
-  int items = 0;
+  int items = 0, min_nkv = 1 << 30;
   for (int g = 0; g < seg.n; ++g) {
     const int len = seg.start[g + 1] - seg.start[g];
     if (len < 0 || seg.start[g] < 0 || seg.start[g + 1] > M) return cudaErrorInvalidValue;
     P.start[g] = seg.start[g];
     P.item_prefix[g] = items;
     items += (len + kTiles * kQ - 1) / (kTiles * kQ);
+    if (len > 0) min_nkv = std::min(min_nkv, (len + kKV - 1) / kKV);
   }
   P.start[seg.n] = seg.start[seg.n];
   P.item_prefix[seg.n] = items;
   if (items == 0) return cudaSuccess;
+  P.items = items;
   static std::atomic<unsigned long long> attr_done{0};
   cudaError_t e = ensure_smem_attr(attn_tc_kernel, kSmemBytes, attr_done);
   if (e != cudaSuccess) return e;
-  attn_tc_kernel<<<dim3(items, heads), kThreads, kSmemBytes, st>>>(qkv_map, static_cast<__nv_bfloat16*>(out), P, err);
+  // Work units (head, 256-query item).  Whole waves of units run with their
+  // full K/V range; the units of a last, partly filled wave (or all of them,
+  // when there are fewer units than SMs) are split into `chunks` K/V ranges so
+  // that wave fills the SMs, and their partial results are merged after.
+  const int units = items * heads;
+  const int G = num_sms > 0 ? num_sms : 148;
+  int full = units, chunks = 1;
+  if (part) {
+    const int base = units >= G ? (units / G) * G : 0;
+    const int rest = units - base;
+    if (rest > 0) {
+      int c = std::min(std::min(G / rest, 8), min_nkv);
+      if (c >= 2) {
+        full = base;
+        chunks = c;
+      }
+    }
+  }
+  int n = 0;
+  if (full > 0) {
+    P.unit_base = 0;
+    P.chunks = 1;
+    P.part = nullptr;
+    attn_tc_kernel<<<full, kThreads, kSmemBytes, st>>>(qkv_map, static_cast<__nv_bfloat16*>(out), P, err);
+    ++n;
+  }
+  if (full < units) {
+    const int rest = units - full;
+    P.unit_base = full;
+    P.chunks = chunks;
+    P.part = part;
+    attn_tc_kernel<<<rest * chunks, kThreads, kSmemBytes, st>>>(qkv_map, static_cast<__nv_bfloat16*>(out), P, err);
+    const long long threads = static_cast<long long>(rest) * kPartRows * (kHD / 4);
+    attn_combine_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(
+        P, static_cast<__nv_bfloat16*>(out), rest);
+    n += 2;
+  }
+  if (launched) *launched = n;
   return cudaGetLastError();
 }
 

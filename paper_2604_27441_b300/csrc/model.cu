@@ -209,7 +209,7 @@ void net_destroy(Net* n) {
 
 namespace {
 struct WsLayout {
-  size_t tok, x, h, qkv, att, mlp, head, err, h8, h8s, total;
+  size_t tok, x, h, qkv, att, mlp, head, err, h8, h8s, part, total;
 };
 WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp) {
   const size_t e = precision != REVO_FP32 ? 2 : 4;
@@ -229,6 +229,7 @@ WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp) {
   l.mlp = put(static_cast<size_t>(cap) * s.r * D * e);
   l.head = put(static_cast<size_t>(capp) * s.head_dim_out() * 4);
   l.err = put(256);
+  if (precision != REVO_FP32) l.part = put(attention_partial_bytes(device_sm_count()));
   if (precision == REVO_FP8) {
     l.h8 = put(static_cast<size_t>(cap) * D);
     l.h8s = put(static_cast<size_t>(cap) * 4);
@@ -266,6 +267,8 @@ Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, in
   w->mlp = base + l.mlp;
   w->head = reinterpret_cast<float*>(base + l.head);
   w->err = reinterpret_cast<int*>(base + l.err);
+  w->sms = device_sm_count();
+  if (precision != REVO_FP32) w->attn_part = reinterpret_cast<float*>(base + l.part);
   if (precision == REVO_FP8) {
     w->h8 = base + l.h8;
     w->h8_scale = reinterpret_cast<float*>(base + l.h8s);
@@ -289,6 +292,7 @@ struct Fwd {
   int sms;
   bool tc;
   size_t e;  // activation element size
+  int extra_launches = 0;  // kernels beyond one per attention (split waves)
 
   // `amap` / `cmap`: the A operand and output tensor maps (tensor-core path).
   cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M,
@@ -410,7 +414,11 @@ struct Fwd {
         cudaSuccess)
       return e;
     if (tc)
-      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st);
+    {
+      int nl = 1;
+      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st, ws->attn_part, ws->sms, &nl);
+      extra_launches += nl - 1;
+    }
     else
       e = launch_attention_simt(static_cast<const float*>(ws->qkv), static_cast<float*>(ws->att), M, d, heads, seg,
                                 st);
@@ -578,7 +586,7 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
   }
   // One kernel per step: per request assemble, 2 embeddings, final LN, head, blend;
   // tubelet embedding, encoder LN, encoder->decoder; 7 per transformer block.
-  if (launches) *launches = 3 + 7 * (s.L + s.Ld) + 6 * n;
+  if (launches) *launches = 3 + 7 * (s.L + s.Ld) + 6 * n + f.extra_launches;
   return cudaSuccess;
 }
 

@@ -95,6 +95,8 @@ struct Workspace {
   float* head = nullptr; // [cap_patches][C*p*p]
   uint8_t* h8 = nullptr;  // [cap][max width] E4M3 LayerNorm output (FP8 precision)
   float* h8_scale = nullptr;  // [cap] its per-token scales
+  float* attn_part = nullptr;  // split-wave partial results of the tensor-core attention
+  int sms = 0;
   int* err = nullptr;    // device error word of the tensor-core kernels
   size_t bytes = 0;
   // Tensor maps of the A operands, valid for `maps_rows` rows.

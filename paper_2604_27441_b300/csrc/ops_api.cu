@@ -50,6 +50,21 @@ int* op_error_word() {
   return g_err_word[dev];
 }
 
+// The split-wave scratch of the step-level attention (one per device,
+// allocated on first use; calls on one device run in stream order).
+float* op_attention_partial() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  static float* bufs[64] = {};
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!bufs[dev]) {
+    float* p = nullptr;
+    if (cudaMalloc(&p, attention_partial_bytes(device_sm_count())) != cudaSuccess) return nullptr;
+    bufs[dev] = p;
+  }
+  return bufs[dev];
+}
+
 }  // namespace revo
 
 using namespace revo;
@@ -251,6 +266,51 @@ revo_status revo_fec_decode(int n, int r, size_t packet_bytes, const int* presen
                      "revo_fec_decode");
 }
 
+size_t revo_render_scratch_bytes(int out_h, int out_w) { return render_scratch_bytes(out_h, out_w); }
+
+revo_status revo_render_rgbd(const uint8_t* rgb, int rgb_h, int rgb_w, size_t rgb_pitch, const uint16_t* depth, int h,
+                             int w, size_t depth_pitch, const revo_intrinsics* src, const revo_pose* pose,
+                             const revo_intrinsics* dst, int out_h, int out_w, int splat_radius, void* scratch,
+                             uint8_t* out_rgb, size_t out_rgb_pitch, uint16_t* out_depth, size_t out_depth_pitch,
+                             void* stream) {
+  if (!rgb || !depth || !src || !pose || !dst || !scratch || !out_rgb || !out_depth || h <= 0 || w <= 0 ||
+      rgb_h <= 0 || rgb_w <= 0 || out_h <= 0 || out_w <= 0 || splat_radius < 0 || splat_radius > 16 ||
+      rgb_pitch < static_cast<size_t>(rgb_w) * 3 || depth_pitch < static_cast<size_t>(w) * 2 ||
+      out_rgb_pitch < static_cast<size_t>(out_w) * 3 || out_depth_pitch < static_cast<size_t>(out_w) * 2 ||
+      depth_pitch % 2 || out_depth_pitch % 2 || static_cast<long long>(h) * w > 0xFFFFFFFFll) {
+    set_last_error("revo_render_rgbd: bad argument");
+    return REVO_EINVAL;
+  }
+  RenderCall c{};
+  c.rgb = rgb;
+  c.rgb_pitch = rgb_pitch;
+  c.rgb_h = rgb_h;
+  c.rgb_w = rgb_w;
+  c.depth = depth;
+  c.depth_pitch = depth_pitch;
+  c.h = h;
+  c.w = w;
+  c.src[0] = src->fx;
+  c.src[1] = src->fy;
+  c.src[2] = src->cx;
+  c.src[3] = src->cy;
+  for (int i = 0; i < 9; ++i) c.r[i] = pose->r[i];
+  for (int i = 0; i < 3; ++i) c.t[i] = pose->t[i];
+  c.dst[0] = dst->fx;
+  c.dst[1] = dst->fy;
+  c.dst[2] = dst->cx;
+  c.dst[3] = dst->cy;
+  c.out_h = out_h;
+  c.out_w = out_w;
+  c.splat = splat_radius;
+  c.scratch = scratch;
+  c.out_rgb = out_rgb;
+  c.out_rgb_pitch = out_rgb_pitch;
+  c.out_depth = out_depth;
+  c.out_depth_pitch = out_depth_pitch;
+  return cuda_status(launch_render(c, static_cast<cudaStream_t>(stream)), "revo_render_rgbd");
+}
+
 size_t revo_frame_metrics_scratch_bytes(int height, int width, int channels) {
   return frame_metrics_scratch_bytes(height, width, channels);
 }
@@ -301,7 +361,8 @@ revo_status revo_op_attention(revo_precision precision, const void* qkv, void* o
   }
   int* err = op_error_word();
   if (!err) return REVO_ECUDA;
-  return cuda_status(launch_attention_tc(m, out, M, D, heads, seg, err, st), "revo_op_attention");
+  return cuda_status(launch_attention_tc(m, out, M, D, heads, seg, err, st, op_attention_partial(), device_sm_count()),
+                     "revo_op_attention");
 }
 
 revo_status revo_op_add_position(float* x, int slots, int grid_h, int grid_w, int D, const int* taus, void* stream) {

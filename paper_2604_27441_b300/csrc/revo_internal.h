@@ -64,8 +64,13 @@ cudaError_t launch_gemm_simt(int epi, const float* A, const float* W, const floa
 // ---- attention (qkv [M][3D] row-major; out [M][D])
 cudaError_t launch_attention_simt(const float* qkv, float* out, int M, int D, int heads, const Segments& seg,
                                   cudaStream_t st);
+// `part` (optional, attention_partial_bytes(num_sms) bytes): lets the units of
+// a last, partly filled wave split their K/V range over the idle SMs (two more
+// launches: the split part and a combine).  *launched: kernels enqueued.
 cudaError_t launch_attention_tc(const CUtensorMap& qkv_map, void* out, int M, int D, int heads, const Segments& seg,
-                                int* err, cudaStream_t st);
+                                int* err, cudaStream_t st, float* part = nullptr, int num_sms = 0,
+                                int* launched = nullptr);
+size_t attention_partial_bytes(int num_sms);
 bool encode_attention_tmap(CUtensorMap* map, const void* qkv, int M, int D);
 
 // ---- element-wise stages
@@ -122,6 +127,25 @@ cudaError_t fec_encode(int n, int r, size_t packet_bytes, const uint8_t* data, s
 size_t fec_decode_scratch_bytes(int n);
 cudaError_t fec_decode(int n, int r, size_t packet_bytes, const int* present, const uint8_t* received,
                        size_t received_pitch, uint8_t* data_out, size_t out_pitch, void* scratch, cudaStream_t st);
+
+// RGB-D unprojection + point splatting (render.cu).
+struct RenderCall {
+  const uint8_t* rgb;
+  size_t rgb_pitch;
+  int rgb_h, rgb_w;
+  const uint16_t* depth;
+  size_t depth_pitch;
+  int h, w;
+  float src[4], r[9], t[3], dst[4];  // intrinsics (fx, fy, cx, cy), pose x' = R x + t
+  int out_h, out_w, splat;
+  void* scratch;  // render_scratch_bytes(out_h, out_w)
+  uint8_t* out_rgb;
+  size_t out_rgb_pitch;
+  uint16_t* out_depth;
+  size_t out_depth_pitch;
+};
+size_t render_scratch_bytes(int out_h, int out_w);
+cudaError_t launch_render(const RenderCall& c, cudaStream_t st);
 
 // SSIM and PSNR of frame a against frame b (uint8 or uint16 samples, C = 1
 // or 3 interleaved): out[0] = mean SSIM, out[1] = MSE, out[2] = PSNR (dB).

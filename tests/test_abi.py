@@ -48,7 +48,7 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
     """The binding's ctypes structs have the C compiler's sizes and offsets."""
     src = tmp_path / "layout.c"
     fields = {"revo_config": R.Config, "revo_plane": R.Plane, "revo_request": R.Request, "revo_result": R.Result,
-              "revo_stats": R.Stats}
+              "revo_stats": R.Stats, "revo_intrinsics": R.Intrinsics, "revo_pose": R.Pose}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "revo.h"', "int main(void) {"]
     for cname, py in fields.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')

@@ -389,3 +389,52 @@ def test_fec_encode_decode(n, r, S):
         R.fec_decode(n, r, S, present, dev(shards[present]), out, scratch)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(out.cpu().numpy(), data)
+
+
+# ------------------------------------------------------------------- render
+
+from oracle import render as RD  # noqa: E402
+
+
+def _rot(ax, ay, az):
+    cx, sx, cy, sy, cz, sz = np.cos(ax), np.sin(ax), np.cos(ay), np.sin(ay), np.cos(az), np.sin(az)
+    Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+    return (Rz @ Ry @ Rx).astype(np.float32)
+
+
+@pytest.mark.parametrize("case", ["identity", "turn", "shift", "splat2", "sizes", "upscale"])
+def test_render_rgbd_bit_exact(case):
+    """Unprojection + splatting against the oracle, bit for bit (the same
+    float32 steps, nearest-z with index ties)."""
+    rgb, dep = synth.make_request(4242, "640x480")
+    depth = dep.clean.copy()
+    depth[::7, ::5] = 0  # holes
+    color = rgb.clean
+    H, W = depth.shape
+    K = (525.0, 525.0, 319.5, 239.5)
+    rot, t, Kd, out_hw, s = np.eye(3, dtype=np.float32), (0.0, 0.0, 0.0), K, (H, W), 0
+    if case == "turn":
+        rot, t = _rot(0.05, -0.12, 0.02), (40.0, -25.0, 120.0)
+    elif case == "shift":
+        t = (0.0, 0.0, -300.0)
+    elif case == "splat2":
+        rot, t, s = _rot(0.0, 0.2, 0.0), (150.0, 0.0, 0.0), 2
+    elif case == "sizes":
+        rgb2, _ = synth.make_request(4243, "1280x720+640x576")
+        color = rgb2.clean  # 1280x720 colour over the 640x480 depth
+        rot, t = _rot(0.0, -0.08, 0.0), (-60.0, 10.0, 0.0)
+    elif case == "upscale":  # twice the resolution: 3 x 3 splats close the gaps
+        Kd, out_hw, s = (1050.0, 1050.0, 639.5, 359.5), (720, 1280), 1
+    ref_rgb, ref_d = RD.render(color, depth, K, rot, t, Kd, out_hw, splat=s)
+    nbytes = R.render_scratch_bytes(*out_hw)
+    assert nbytes == out_hw[0] * out_hw[1] * 8
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out_rgb = torch.zeros((*out_hw, 3), dtype=torch.uint8, device="cuda")
+    out_d = torch.zeros(out_hw, dtype=torch.int16, device="cuda")
+    R.render_rgbd(dev(color), dev(depth.view(np.int16)), K, rot, t, Kd, out_hw, s, scratch, out_rgb, out_d)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out_d.cpu().numpy().view(np.uint16), ref_d)
+    np.testing.assert_array_equal(out_rgb.cpu().numpy(), ref_rgb)
+    assert (ref_d > 0).mean() > 0.3  # the view actually shows the scene
