@@ -349,8 +349,16 @@ def run_ours(args) -> None:
             for _ in range(reps):
                 R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream)
             e1.record(stream)
+            e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(3):
+                R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream, split_tail=True)
+            e2.record(stream)
+            for _ in range(reps):
+                R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream, split_tail=True)
+            e3.record(stream)
         torch.cuda.synchronize()
         per_launch = e0.elapsed_time(e1) / 1e3 / reps
+        split_us = e2.elapsed_time(e3) * 1e3 / reps
         pk = peaks()
         peak = pk.get("bf16_tflops")
         achieved = fl["attn_enc_per_block"] / per_launch / 1e12
@@ -359,7 +367,13 @@ def run_ours(args) -> None:
                 "frac": (achieved / peak) if peak else None, "traffic": ATTN_DRAM_BYTES_PER_LAUNCH,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)" if peak else None,
-                "flops_per_launch": fl["attn_enc_per_block"], "us_per_launch": per_launch * 1e6}
+                "flops_per_launch": fl["attn_enc_per_block"], "us_per_launch": per_launch * 1e6,
+                "note": "the form the step runs (RGB and depth in flight together: no tail split); alone, with "
+                        "the last wave's key ranges split over idle SMs (REVO_ATTN_SPLIT_TAIL)",
+                "alone_split_tail": {"us_per_launch": split_us,
+                                     "achieved": fl["attn_enc_per_block"] / (split_us * 1e-6) / 1e12,
+                                     "frac": (fl["attn_enc_per_block"] / (split_us * 1e-6) / 1e12 / peak)
+                                     if peak else None}}
         assert R.take_device_error() == 0
 
     # Quality of the timed configuration against the FP64 oracle (RGB plane of the
@@ -775,6 +789,12 @@ def run_profile_kernel(args) -> None:
         out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
         launch = lambda: R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream)  # noqa: E731
         flops = fl["attn_enc_per_block"]
+    elif args.profile_kernel == "attention_split":
+        qkv = torch.randn((N, 3 * D), device="cuda").to(torch.bfloat16)
+        out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
+        launch = lambda: R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream,  # noqa: E731
+                                        split_tail=True)
+        flops = fl["attn_enc_per_block"]
     elif args.profile_kernel == "fc1_fp8":  # the same fc1 with E4M3 operands
         a = torch.randint(0, 120, (N, D), dtype=torch.uint8, device="cuda")
         w = torch.randint(0, 120, (4 * D, D), dtype=torch.uint8, device="cuda")
@@ -807,7 +827,7 @@ def run_profile_kernel(args) -> None:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-kernel", choices=["attention", "fc1", "fc1_fp8"], default=None,
+    ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "fc1", "fc1_fp8"], default=None,
                     help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)

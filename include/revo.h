@@ -418,9 +418,15 @@ REVO_API revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const 
  * host array of segment boundaries in [0, M]; tokens attend only within their
  * segment.  out [M][D].  REVO_FP32: float32 in and out.  REVO_BF16: qkv and out
  * bf16, tcgen05 tensor cores, float32 softmax.  n_seg <= 64.
+ * flags (REVO_BF16): bit 0 (REVO_ATTN_SPLIT_TAIL) lets the work units of a
+ * last, partly filled wave of CTAs split their key range over the idle SMs
+ * (partial results merged by a second kernel); it pays when nothing else runs
+ * on the GPU and changes the summation order (results equal within rounding,
+ * not bit for bit).  0: one launch, whole key range per unit.
  */
+#define REVO_ATTN_SPLIT_TAIL 1
 REVO_API revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D,
-                              int heads, const int* seg_start, int n_seg, void* stream);
+                              int heads, const int* seg_start, int n_seg, int flags, void* stream);
 
 /*
  * x[(s*Hp + r)*Wp + c][:] += the sinusoidal embedding of (taus[s], r, c), each

@@ -98,7 +98,7 @@ _SIGS = {
                                  C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "revo_op_layernorm": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "revo_op_attention": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
-                                    C.POINTER(C.c_int), C.c_int, C.c_void_p]),
+                                    C.POINTER(C.c_int), C.c_int, C.c_int, C.c_void_p]),
     "revo_op_add_position": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                        C.c_void_p]),
     "revo_op_blend": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
@@ -270,10 +270,11 @@ def op_frame_metrics(a, b, height, width, channels, sample_bytes, data_range, sc
                                               _stream(stream)), "revo_op_frame_metrics")
 
 
-def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None):
+def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None, split_tail=False):
     n = len(seg_start) - 1
     arr = (C.c_int * len(seg_start))(*[int(v) for v in seg_start])
-    return _check(lib().revo_op_attention(precision, ptr(qkv), ptr(out), M, D, heads, arr, n, _stream(stream)),
+    return _check(lib().revo_op_attention(precision, ptr(qkv), ptr(out), M, D, heads, arr, n, int(bool(split_tail)),
+                                          _stream(stream)),
                   "revo_op_attention")
 
 

@@ -293,6 +293,7 @@ struct Fwd {
   bool tc;
   size_t e;  // activation element size
   int extra_launches = 0;  // kernels beyond one per attention (split waves)
+  bool split_tail = false;  // let attention's last wave split its key range
 
   // `amap` / `cmap`: the A operand and output tensor maps (tensor-core path).
   cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M,
@@ -416,7 +417,8 @@ struct Fwd {
     if (tc)
     {
       int nl = 1;
-      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st, ws->attn_part, ws->sms, &nl);
+      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st, split_tail ? ws->attn_part : nullptr,
+                              ws->sms, &nl);
       extra_launches += nl - 1;
     }
     else
@@ -524,12 +526,13 @@ cudaError_t prepare_job_args(const Net* net, const Workspace* ws, const PlaneJob
 }
 
 cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
-                        int* launches, const JobArgs* dev_args) {
+                        int* launches, const JobArgs* dev_args, bool split_tail) {
   const NetShape& s = net->s;
   if (launches) *launches = 0;
   if (n <= 0) return cudaSuccess;
   if (n > kMaxSegments) return cudaErrorInvalidValue;
   Fwd f{net, ws, st, num_sms, net->precision != REVO_FP32, net->precision != REVO_FP32 ? 2u : 4u};
+  f.split_tail = split_tail;
   Segments seg{};
   int patches = 0;
   if (!batch_segments(s, jobs, n, &seg, &patches)) return cudaErrorInvalidValue;

@@ -138,7 +138,9 @@ cudaError_t prepare_job_args(const Net* net, const Workspace* ws, const PlaneJob
 // prepare_job_args' output, written before the kernels run) the per-request
 // kernels read their arguments from it instead of taking them by value, so the
 // enqueued work depends on the request sizes only and can be captured once.
+// split_tail: let attention's last, partly filled wave split its key range
+// (worth it when nothing else shares the GPU; changes the rounding order).
 cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
-                        int* launches, const JobArgs* dev_args = nullptr);
+                        int* launches, const JobArgs* dev_args = nullptr, bool split_tail = false);
 
 }  // namespace revo

@@ -331,7 +331,7 @@ revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const void* b, 
 }
 
 revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D, int heads,
-                              const int* seg_start, int n_seg, void* stream) {
+                              const int* seg_start, int n_seg, int flags, void* stream) {
   if (!qkv || !out || !seg_start || n_seg <= 0 || n_seg > kMaxSegments || heads <= 0 || D != 64 * heads) {
     set_last_error("revo_op_attention: bad argument (head width must be 64, n_seg <= 64)");
     return REVO_EINVAL;
@@ -361,7 +361,8 @@ revo_status revo_op_attention(revo_precision precision, const void* qkv, void* o
   }
   int* err = op_error_word();
   if (!err) return REVO_ECUDA;
-  return cuda_status(launch_attention_tc(m, out, M, D, heads, seg, err, st, op_attention_partial(), device_sm_count()),
+  float* part = (flags & REVO_ATTN_SPLIT_TAIL) ? op_attention_partial() : nullptr;
+  return cuda_status(launch_attention_tc(m, out, M, D, heads, seg, err, st, part, device_sm_count()),
                      "revo_op_attention");
 }
 

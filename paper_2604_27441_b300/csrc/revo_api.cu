@@ -207,12 +207,13 @@ bool lane_idle(revo_ctx* c, int l) {
 // request sizes is replayed.  A size pattern runs eagerly (reading the same
 // table) the first time it is seen, so every kernel's one-time set-up happens
 // outside a capture, and is captured the second time.
-cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob>& jobs, int* launches) {
+cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob>& jobs, bool split, int* launches) {
   Net* net = c->net[m];
   Workspace* ws = L.ws[m];
   cudaStream_t s = L.st[m];
   const int n = static_cast<int>(jobs.size());
-  if (!c->cfg.use_graphs || !L.dev_args[m]) return net_forward(net, ws, jobs.data(), n, s, c->sms, launches);
+  if (!c->cfg.use_graphs || !L.dev_args[m])
+    return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, nullptr, split);
 
   const int r = L.args_next[m];
   L.args_next[m] = (r + 1) % kArgRing;
@@ -224,7 +225,7 @@ cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob
     return e;
   if ((e = cudaEventRecord(L.args_ev[m][r], s)) != cudaSuccess) return e;
 
-  std::vector<int> key;
+  std::vector<int> key{split ? 1 : 0};
   for (const PlaneJob& j : jobs) {
     key.push_back(j.H);
     key.push_back(j.W);
@@ -232,15 +233,16 @@ cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob
   auto it = L.graphs[m].find(key);
   if (it == L.graphs[m].end()) {
     if (static_cast<int>(L.graphs[m].size()) >= kMaxGraphs)
-      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m]);
+      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m], split);
     it = L.graphs[m].emplace(key, GraphEntry{}).first;
   }
   GraphEntry& g = it->second;
   if (!g.exec) {
-    if (g.failed || g.seen++ == 0) return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m]);
+    if (g.failed || g.seen++ == 0)
+      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m], split);
     if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     int nl = 0;
-    const cudaError_t ef = net_forward(net, ws, jobs.data(), n, s, c->sms, &nl, L.dev_args[m]);
+    const cudaError_t ef = net_forward(net, ws, jobs.data(), n, s, c->sms, &nl, L.dev_args[m], split);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(s, &graph);
     cudaError_t ei = cudaErrorUnknown;
@@ -252,7 +254,7 @@ cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob
       (void)cudaGetLastError();
       g.exec = nullptr;
       g.failed = true;
-      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m]);
+      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m], split);
     }
     g.launches = nl;
   }
@@ -313,7 +315,10 @@ revo_status launch_batch(revo_ctx* c, int count) {
     cudaStream_t s = L.st[m];
     cudaMemsetAsync(L.ws[m]->err, 0, sizeof(int), s);
     int nl = 0;
-    e = lane_forward(c, L, m, jobs[m], &nl);
+    // Attention's last wave splits its key range only when this modality has
+    // the GPU to itself: with both models in flight the other stream's
+    // kernels fill the tail, and the split would only add work.
+    e = lane_forward(c, L, m, jobs[m], jobs[1 - m].empty(), &nl);
     b.launches += nl;
     if (e != cudaSuccess) st = cuda_status(e, "forward launch");
     cudaMemcpyAsync(b.err_host + m, L.ws[m]->err, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -71,8 +71,8 @@ def test_null_arguments_are_rejected_before_any_device_work(lib):
     assert lib.revo_op_linear(R.FP32, 0, None, None, None, None, 4, 4, 8, 0, None) == R.REVO_EINVAL
     assert lib.revo_op_layernorm(None, None, None, None, 4, 8, 0, None) == R.REVO_EINVAL
     seg = (C.c_int * 2)(0, 4)
-    assert lib.revo_op_attention(R.FP32, None, None, 4, 64, 1, seg, 1, None) == R.REVO_EINVAL
-    assert lib.revo_op_attention(R.FP32, 1, 1, 4, 96, 1, seg, 1, None) == R.REVO_EINVAL  # head width 96
+    assert lib.revo_op_attention(R.FP32, None, None, 4, 64, 1, seg, 1, 0, None) == R.REVO_EINVAL
+    assert lib.revo_op_attention(R.FP32, 1, 1, 4, 96, 1, seg, 1, 0, None) == R.REVO_EINVAL  # head width 96
     assert lib.revo_op_depth_stats(None, 4, 4, 8, None, None, None) == R.REVO_EINVAL
     assert "bad argument" in R.last_error() or R.last_error()
     h = C.c_void_p()

@@ -179,12 +179,15 @@ ATT_CASES = [((0, 300, 1000), 2), ((0, 5, 5, 133, 900), 3), ((0, 3600), 12), ((0
              ((0, 900, 1800, 2700), 6)]
 
 
-@pytest.mark.parametrize("seg,heads", ATT_CASES)
-def test_attention_bf16_tcgen05(seg, heads):
+@pytest.mark.parametrize("split_tail", [False, True])
+@pytest.mark.parametrize("seg,heads", ATT_CASES + [((0, 900), 12), ((0, 10800), 2)])
+def test_attention_bf16_tcgen05(seg, heads, split_tail):
+    """With split_tail the units of a partly filled last wave (or all units,
+    when fewer than the SMs) split their key range; the partials are merged."""
     M, D = seg[-1], 64 * heads
     qkv = bf16(synth.normal(M + heads, (M, 3 * D)))
     out = torch.zeros((M, D), dtype=torch.bfloat16, device="cuda")
-    R.op_attention(R.BF16, qkv.cuda(), out, M, D, heads, seg)
+    R.op_attention(R.BF16, qkv.cuda(), out, M, D, heads, seg, split_tail=split_tail)
     torch.cuda.synchronize()
     ref = _oracle_segments(f64(qkv), heads, seg)
     np.testing.assert_allclose(f64(out), ref, rtol=2e-2, atol=1.5e-2)
