@@ -44,7 +44,7 @@ PRECISIONS = {"bf16": lambda R: R.BF16, "fp32": lambda R: R.FP32, "fp8": lambda 
 DTYPE_NAMES = {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3 (encoder fc1; per-token x per-channel scales) + bf16"}
 # DRAM bytes (read + write) of one attn_tc_kernel launch at N = 3600, 12 heads,
 # from an ncu capture of the current kernel version (None once it changes).
-ATTN_DRAM_BYTES_PER_LAUNCH = None
+ATTN_DRAM_BYTES_PER_LAUNCH = 16631040
 
 
 def flops_per_model(C: int, h: int, w: int) -> dict:
@@ -222,6 +222,49 @@ def run_reference(args) -> None:
 
 # -------------------------------------------------------------- our arm --
 
+def elementwise_roofline(R, torch, stream) -> dict:
+    """The HBM-bound stages alone at the largest frame of the workloads (1280x720
+    RGB): the fused unpack + normalise + tubelet gather (assemble) and the
+    de-normalise + masked blend.  L2 is flushed (a 256 MB write) before every
+    timed launch; achieved = algorithmic bytes / CUDA-event time."""
+    Hh, Ww, k, T, p = 720, 1280, 5, 2, 16
+    frame = Hh * Ww * 3
+    refs = [torch.randint(0, 256, (Hh, Ww, 3), dtype=torch.uint8, device="cuda") for _ in range(k)]
+    cur = torch.randint(0, 256, (Hh, Ww, 3), dtype=torch.uint8, device="cuda")
+    P = (Hh // p) * (Ww // p)
+    tokens = torch.empty(((k + 1) // T * P, T * 3 * p * p), dtype=torch.bfloat16, device="cuda")
+    head = torch.randn((P, 3 * p * p), device="cuda")
+    mask = torch.randint(-2 ** 31, 2 ** 31 - 1, (Hh, (Ww + 31) // 32), dtype=torch.int32, device="cuda")
+    out = torch.empty((Hh, Ww, 3), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stats = torch.zeros(2, device="cuda")
+
+    def timed(fn, reps=10):
+        tot = 0.0
+        for i in range(reps + 2):
+            flush.fill_(i & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                tot += e0.elapsed_time(e1) * 1e3
+        return tot / reps
+
+    us_a = timed(lambda: R.op_assemble(3, k, T, p, Hh, Ww, refs, cur, Ww * 3, stats, tokens, 1, stream=stream))
+    us_b = timed(lambda: R.op_blend(3, p, Hh, Ww, head, cur, Ww * 3, mask, (Ww + 31) // 32, stats, out, Ww * 3,
+                                    stream=stream))
+    bytes_a = (k + 1) * frame + tokens.numel() * 2
+    bytes_b = head.numel() * 4 + frame + mask.numel() * 4 + frame
+    hbm = peaks().get("hbm_gbs")
+    mk = lambda us, b: {"us": us, "bytes": b, "gbs": b / us / 1e3,  # noqa: E731
+                        "frac_of_measured_hbm": (b / us / 1e3 / hbm) if hbm else None}
+    return {"assemble_rgb_1280x720": mk(us_a, bytes_a), "blend_rgb_1280x720": mk(us_b, bytes_b),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hbm else None}
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -376,6 +419,8 @@ def run_ours(args) -> None:
                                      if peak else None}}
         assert R.take_device_error() == 0
 
+    elementwise = elementwise_roofline(R, torch, stream) if rank == 0 else None
+
     # Quality of the timed configuration against the FP64 oracle (RGB plane of the
     # 20 %-loss stream) + the CPU baseline from the same oracle run.
     quality, cpu = None, None
@@ -449,7 +494,7 @@ def run_ours(args) -> None:
                            "budget": FRAME_BUDGET_MS},
             "flops_per_step": flops_per_model(3, H, W)["total"] + flops_per_model(1, H, W)["total"],
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-            "cpu_baseline": cpu, "quality": quality, "precisions": compare,
+            "cpu_baseline": cpu, "quality": quality, "precisions": compare, "elementwise": elementwise,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
