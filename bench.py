@@ -44,7 +44,7 @@ PRECISIONS = {"bf16": lambda R: R.BF16, "fp32": lambda R: R.FP32, "fp8": lambda 
 DTYPE_NAMES = {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3 (encoder fc1; per-token x per-channel scales) + bf16"}
 # DRAM bytes (read + write) of one attn_tc_kernel launch at N = 3600, 12 heads,
 # from an ncu capture of the current kernel version (None once it changes).
-ATTN_DRAM_BYTES_PER_LAUNCH = 16631040
+ATTN_DRAM_BYTES_PER_LAUNCH = 16631808
 
 
 def flops_per_model(C: int, h: int, w: int) -> dict:
@@ -225,8 +225,9 @@ def run_reference(args) -> None:
 def elementwise_roofline(R, torch, stream) -> dict:
     """The HBM-bound stages alone at the largest frame of the workloads (1280x720
     RGB): the fused unpack + normalise + tubelet gather (assemble) and the
-    de-normalise + masked blend.  L2 is flushed (a 256 MB write) before every
-    timed launch; achieved = algorithmic bytes / CUDA-event time."""
+    de-normalise + masked blend.  L2 is flushed (a 256 MB write, then a read of
+    it) before every timed launch; achieved = algorithmic bytes / CUDA-event
+    time."""
     Hh, Ww, k, T, p = 720, 1280, 5, 2, 16
     frame = Hh * Ww * 3
     refs = [torch.randint(0, 256, (Hh, Ww, 3), dtype=torch.uint8, device="cuda") for _ in range(k)]
@@ -237,14 +238,19 @@ def elementwise_roofline(R, torch, stream) -> dict:
     mask = torch.randint(-2 ** 31, 2 ** 31 - 1, (Hh, (Ww + 31) // 32), dtype=torch.int32, device="cuda")
     out = torch.empty((Hh, Ww, 3), dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush_sum = torch.zeros((), dtype=torch.int64, device="cuda")
     stats = torch.zeros(2, device="cuda")
 
     def timed(fn, reps=10):
         tot = 0.0
         for i in range(reps + 2):
-            flush.fill_(i & 255)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(stream):
+                # Evict the operands: write a buffer larger than L2, then read
+                # it, so the lines left in L2 are clean and the timed launch
+                # does not pay for writing back the flush's dirty lines.
+                flush.fill_(i & 255)
+                flush_sum.copy_(flush.view(torch.int64).sum())
                 e0.record(stream)
                 fn()
                 e1.record(stream)
@@ -840,6 +846,24 @@ def run_profile_kernel(args) -> None:
         launch = lambda: R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream,  # noqa: E731
                                         split_tail=True)
         flops = fl["attn_enc_per_block"]
+    elif args.profile_kernel in ("assemble", "blend"):  # the HBM-bound stages at 1280x720 RGB, k = 5, T = 2
+        Hh, Ww, k, T, p = 720, 1280, 5, 2, 16
+        frames = [torch.randint(0, 256, (Hh, Ww, 3), dtype=torch.uint8, device="cuda") for _ in range(k + 1)]
+        P = (Hh // p) * (Ww // p)
+        stats = torch.zeros(2, device="cuda")
+        if args.profile_kernel == "assemble":
+            tokens = torch.empty(((k + 1) // T * P, T * 3 * p * p), dtype=torch.bfloat16, device="cuda")
+            launch = lambda: R.op_assemble(3, k, T, p, Hh, Ww, frames[:k], frames[k], Ww * 3, stats,  # noqa: E731
+                                           tokens, 1, stream=stream)
+            nbytes = (k + 1) * Hh * Ww * 3 + tokens.numel() * 2
+        else:
+            head = torch.randn((P, 3 * p * p), device="cuda")
+            mask = torch.randint(-2 ** 31, 2 ** 31 - 1, (Hh, (Ww + 31) // 32), dtype=torch.int32, device="cuda")
+            out = torch.empty((Hh, Ww, 3), dtype=torch.uint8, device="cuda")
+            launch = lambda: R.op_blend(3, p, Hh, Ww, head, frames[k], Ww * 3, mask, (Ww + 31) // 32,  # noqa: E731
+                                        stats, out, Ww * 3, stream=stream)
+            nbytes = head.numel() * 4 + 2 * Hh * Ww * 3 + mask.numel() * 4
+        flops = None
     elif args.profile_kernel == "fc1_fp8":  # the same fc1 with E4M3 operands
         a = torch.randint(0, 120, (N, D), dtype=torch.uint8, device="cuda")
         w = torch.randint(0, 120, (4 * D, D), dtype=torch.uint8, device="cuda")
@@ -866,13 +890,15 @@ def run_profile_kernel(args) -> None:
     e1.record(stream)
     torch.cuda.synchronize()
     us = e0.elapsed_time(e1) * 1e3 / args.steps
-    print(json.dumps({"kernel": args.profile_kernel, "us_per_launch": us, "tflops": flops / us / 1e6,
+    rate = {"tflops": flops / us / 1e6} if flops else {"gbs": nbytes / us / 1e3, "bytes": nbytes}
+    print(json.dumps({"kernel": args.profile_kernel, "us_per_launch": us, **rate,
                       "device_error": R.take_device_error()}))
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "fc1", "fc1_fp8"], default=None,
+    ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "fc1", "fc1_fp8", "assemble", "blend"],
+                    default=None,
                     help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)

@@ -23,7 +23,10 @@
 // Warp roles (352 threads): warp 0 TMA, warp 1 TMEM allocator + MMA issuer
 // of tile 0, warps 2..5 softmax of tile 0, warps 6..9 softmax of tile 1 (warp
 // w owns rows 32*(w%4) .. +31 of its tile, the TMEM lanes it may access),
-// warp 10 MMA issuer of tile 1.
+// warp 10 MMA issuer of tile 1.  Handoffs: K/V tiles, S ready and PV done are
+// mbarriers (TMA transaction counts, tcgen05.commit); P ready is a named
+// barrier on which the MMA warp waits suspended, so no polling thread takes
+// issue slots from the softmax warps of its SM sub-partition.
 #include <algorithm>
 
 #include "common.cuh"
@@ -122,6 +125,36 @@ REVO_DEVI void exp_chunk(const uint32_t (&v)[32], uint64_t c2, uint64_t negm2, u
   }
 }
 
+// P_t(j) handoff from the softmax warpgroup of tile t to its MMA warp: named
+// barrier 1 + 2 t + (j & 1), 128 softmax threads arrive, the 32 threads of
+// the MMA warp wait (suspended in hardware: a polling MMA thread would take
+// issue and MIO slots from the softmax warps of its SM sub-partition).
+// Alternating by K/V tile parity keeps the arrivals for j + 2 (which need
+// S(j + 2), issued after the wait for j) from mixing with those for j.
+constexpr uint32_t kPReadyThreads = 128 + 32;
+REVO_DEVI uint32_t p_ready_id(int t, int j) { return 1u + 2u * static_cast<uint32_t>(t) + (static_cast<uint32_t>(j) & 1u); }
+REVO_DEVI void p_ready_arrive(uint32_t id) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kPReadyThreads) : "memory"); }
+REVO_DEVI void p_ready_wait(uint32_t id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kPReadyThreads) : "memory"); }
+
+// Producer wait for a free K/V stage: polls with a short sleep in between
+// (the ring runs kKvStages tiles ahead, so a late wake-up costs nothing),
+// leaving the issue slots of its sub-partition to the softmax warps there.
+REVO_DEVI bool mbar_wait_sleepy(uint64_t* bar, uint32_t parity, int* err, int code) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_test(a, parity)) return true;
+    __nanosleep(128);
+    if ((it & 63u) == 63u) {
+      if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+      if (clock64() - t0 > kWaitLimitCycles) {
+        atomicCAS(err, 0, code);
+        return false;
+      }
+    }
+  }
+}
+
 REVO_DEVI float reduce8_max(const float (&a)[8]) {
   return fmaxf(fmaxf(fmaxf(a[0], a[1]), fmaxf(a[2], a[3])), fmaxf(fmaxf(a[4], a[5]), fmaxf(a[6], a[7])));
 }
@@ -148,8 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* kv_full = q_full + 1;
   uint64_t* kv_empty = kv_full + kKvStages;
   uint64_t* s_full = kv_empty + kKvStages;  // [kTiles][2] S_t(j) ready in region j%2
-  uint64_t* p_full = s_full + 2 * kTiles;   // [kTiles][2] P_t(j) written in region j%2, O rescaled
-  uint64_t* p_done = p_full + 2 * kTiles;   // [kTiles] PV_t(j) accumulated (O stable)
+  uint64_t* p_done = s_full + 2 * kTiles;   // [kTiles] PV_t(j) accumulated (O stable)
   uint64_t* p_reg = p_done + kTiles;        // [kTiles][2] PV_t(j) done: region j%2 free
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(p_reg + 2 * kTiles);
 
@@ -181,8 +213,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int t = 0; t < kTiles; ++t) {
       mbar_init(&s_full[2 * t], 1);
       mbar_init(&s_full[2 * t + 1], 1);
-      mbar_init(&p_full[2 * t], 4);
-      mbar_init(&p_full[2 * t + 1], 4);
       mbar_init(&p_done[t], 1);
       mbar_init(&p_reg[2 * t], 1);
       mbar_init(&p_reg[2 * t + 1], 1);
@@ -206,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tma_load_2d(sQ + t * kQBytes + b * kBoxBytes, &tm, h * kHD, q0 + t * kQ + b * kBoxRows, q_full);
       for (int j = 0; j < nkv; ++j) {
         const int st = j % kKvStages;
-        if (!mbar_wait(&kv_empty[st], ((j / kKvStages) & 1) ^ 1u, err, kDevTimeoutProducer)) break;
+        if (!mbar_wait_sleepy(&kv_empty[st], ((j / kKvStages) & 1) ^ 1u, err, kDevTimeoutProducer)) break;
         mbar_arrive_expect_tx(&kv_full[st], 2 * kKVBytes);
         for (int b = 0; b < kKV / kBoxRows; ++b) {
           const int row = s0 + (kv0 + j) * kKV + b * kBoxRows;
@@ -216,14 +246,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1 || warp == kThreads / 32 - 1) {
-    // One MMA thread per query tile (warp 1: tile 0, the last warp: tile 1),
-    // each in a fixed order with blocking waits on its own tile's barriers:
-    // S(0), S(1), then per K/V tile j: PV(j) once P(j) is written, S(j+2)
-    // once PV(j) has finished with region j%2.  The two threads' MMAs touch
-    // disjoint TMEM columns.  Every wait is on the phase the other side cannot
-    // pass before this thread's next issue, so no barrier runs ahead.
+    // One MMA warp per query tile (warp 1: tile 0, the last warp: tile 1);
+    // lane 0 issues in a fixed order with blocking waits on its own tile's
+    // barriers: S(0), S(1), then per K/V tile j: PV(j) once P(j) is written
+    // (the whole warp waits on the P-ready barrier), S(j+2) once PV(j) has
+    // finished with region j%2.  The two warps' MMAs touch disjoint TMEM
+    // columns.  Every wait is on the phase the other side cannot pass before
+    // this warp's next issue, so no barrier runs ahead.  The warp takes part
+    // in the P-ready barrier for every j, also after a failed wait.
     const int t = warp == 1 ? 0 : 1;
-    if (lane == 0 && t < ntiles) {
+    if (t < ntiles) {
       constexpr uint32_t kIdS = idesc_bf16(kQ, kKV);
       constexpr uint32_t kIdPV = idesc_bf16(kQ, kHD, /*b_mn_major=*/true);
       const uint32_t tbase = tmem + t * kTileCols;
@@ -236,17 +268,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                      kk > 0 ? 1u : 0u);
         mma_commit(&s_full[2 * t + (j & 1)]);
       };
-      bool ok = mbar_wait(q_full, 0, err, kDevTimeoutMma);
-      for (int j = 0; ok && j < 2 && j < nkv; ++j) {
-        ok = mbar_wait(&kv_full[j % kKvStages], (j / kKvStages) & 1, err, kDevTimeoutMma);
-        if (ok) {
-          tc_fence_after();
-          issue_s(j);
+      bool ok = true;
+      if (lane == 0) {
+        ok = mbar_wait(q_full, 0, err, kDevTimeoutMma);
+        for (int j = 0; ok && j < 2 && j < nkv; ++j) {
+          ok = mbar_wait(&kv_full[j % kKvStages], (j / kKvStages) & 1, err, kDevTimeoutMma);
+          if (ok) {
+            tc_fence_after();
+            issue_s(j);
+          }
         }
       }
-      for (int j = 0; ok && j < nkv; ++j) {
-        ok = mbar_wait(&p_full[2 * t + (j & 1)], (j >> 1) & 1, err, kDevTimeoutMma);
-        if (!ok) break;
+      for (int j = 0; j < nkv; ++j) {
+        __syncwarp();
+        p_ready_wait(p_ready_id(t, j));
+        if (lane != 0 || !ok) continue;
         tc_fence_after();
         const uint32_t v_lo = sw128_lo(smem_u32(sV + (j % kKvStages) * kKVBytes));
         const uint32_t p_tmem = tbase + (j & 1) * kRegionCols;
@@ -267,6 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      __syncwarp();
     }
   } else {
     const int t = (warp - 2) >> 2;  // query tile of this warpgroup
@@ -282,7 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       float l = 0.f;
       bool ok = true;
 
-      for (int j = 0; j < nkv; ++j) {
+      int j = 0;
+      for (; j < nkv; ++j) {
         const uint32_t s_addr = tbase + (j & 1) * kRegionCols;
         if (!mbar_wait_warp(&s_full[2 * t + (j & 1)], (j >> 1) & 1, err, kDevTimeoutSoftmax, lane)) {
           ok = false;
@@ -346,7 +384,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         m = m_new;
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&p_full[2 * t + (j & 1)]);
+        p_ready_arrive(p_ready_id(t, j));
+      }
+      // After a failed wait: take part in the remaining P-ready barriers,
+      // waiting on each (arriving ahead could complete a later phase early).
+      for (; j < nkv; ++j) {
+        __syncwarp();
+        p_ready_wait(p_ready_id(t, j));
       }
       // The last PV: waited on its region's barrier.  p_done may still lack
       // two completions here (the softmax can finish while PV(nkv-2) is

@@ -87,6 +87,103 @@ REVO_DEVI void assemble_body(const AssembleArgs& a) {
 __global__ void assemble_kernel(const __grid_constant__ AssembleArgs a) { assemble_body(a); }
 __global__ void assemble_kernel_dev(const AssembleArgs* __restrict__ a) { assemble_body(*a); }
 
+// Patch size 16 (the model's): one warp per (frame, token); lane 2y + h
+// handles pixels [8h, 8h + 8) of the token's patch row y.  For each channel
+// the warp's 32 lanes then write the token's 16 x 16 plane (512 contiguous
+// bytes in bf16) with one 16-byte store each, and read 16 row segments of
+// 48 (RGB) or 32 (depth) bytes.  RGB codes are normalised as
+// x * (1 / (255 std_c)) + (-mean_c / std_c) in one FMA (constants rounded
+// once from their exact values; within 2 ulp of (x / 255 - mean_c) / std_c),
+// depth as (d - mu) * (1 / sigma).  A row that is not 8-byte aligned falls
+// back to byte loads.
+__constant__ float kRgbScale[3] = {0.0171247534f, 0.0175070036f, 0.0174291935f};
+__constant__ float kRgbShift[3] = {-2.11790395f, -2.03571439f, -1.80444443f};
+constexpr int kAsmThreads = 256;
+
+REVO_DEVI float byte_to_float(uint32_t word, int byte) {
+  // 2^23 + b as a float, minus 2^23: exact for a byte.
+  uint32_t bits;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(bits) : "r"(word), "r"(0x4B000000u), "r"(0x7650u | static_cast<uint32_t>(byte)));
+  return __uint_as_float(bits) - 8388608.f;
+}
+
+REVO_DEVI void assemble16_body(const AssembleArgs& a) {
+  const int C = a.C, T = a.T, H = a.H;
+  const int Wp = a.W >> 4, Hp = H >> 4;
+  const long long gw = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+  if (gw >= static_cast<long long>(a.F) * Hp * Wp) return;
+  const int lane = threadIdx.x & 31;
+  const int y = lane >> 1, hx = lane & 1;
+  const int tx = static_cast<int>(gw % Wp);
+  const long long ft = gw / Wp;
+  const int ty = static_cast<int>(ft % Hp);
+  const int f = static_cast<int>(ft / Hp);
+  const int s = f / T, t = f % T;
+  const size_t n = static_cast<size_t>(s * Hp + ty) * Wp + tx;
+  const size_t K = static_cast<size_t>(T) * C * 256;
+  const uint8_t* src = static_cast<const uint8_t*>(a.frames[f]) + static_cast<size_t>(ty * 16 + y) * a.pitch[f];
+  float v[3][8];
+  if (C == 3) {
+    const uint8_t* p3 = src + tx * 48 + hx * 24;
+    uint32_t b[6];
+    if ((reinterpret_cast<uintptr_t>(p3) & 7u) == 0) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(p3) + i);
+        b[2 * i] = w.x;
+        b[2 * i + 1] = w.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        b[i] = p3[4 * i] | (p3[4 * i + 1] << 8) | (p3[4 * i + 2] << 16) | (static_cast<uint32_t>(p3[4 * i + 3]) << 24);
+    }
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int byte = 3 * x + c;
+        v[c][x] = fmaf(byte_to_float(b[byte >> 2], byte & 3), kRgbScale[c], kRgbShift[c]);
+      }
+  } else {
+    const uint8_t* p1 = src + tx * 32 + hx * 16;
+    uint32_t w16[4];
+    if ((reinterpret_cast<uintptr_t>(p1) & 15u) == 0) {
+      const uint4 w = __ldg(reinterpret_cast<const uint4*>(p1));
+      w16[0] = w.x, w16[1] = w.y, w16[2] = w.z, w16[3] = w.w;
+    } else {
+      const uint16_t* q = reinterpret_cast<const uint16_t*>(p1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) w16[i] = q[2 * i] | (static_cast<uint32_t>(q[2 * i + 1]) << 16);
+    }
+    const float mu = a.mu_sigma[0], inv = 1.f / a.mu_sigma[1];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+      v[0][x] = (static_cast<float>((w16[x >> 1] >> (16 * (x & 1))) & 0xFFFFu) - mu) * inv;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (c >= C) break;
+    const size_t o = n * K + static_cast<size_t>((t * C + c) * 16 + y) * 16 + hx * 8;
+    if (a.out_bf16) {
+      *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) + o) =
+          make_uint4(pack_bf16x2(v[c][0], v[c][1]), pack_bf16x2(v[c][2], v[c][3]), pack_bf16x2(v[c][4], v[c][5]),
+                     pack_bf16x2(v[c][6], v[c][7]));
+    } else {
+      float4* d4 = reinterpret_cast<float4*>(static_cast<float*>(a.out) + o);
+      d4[0] = make_float4(v[c][0], v[c][1], v[c][2], v[c][3]);
+      d4[1] = make_float4(v[c][4], v[c][5], v[c][6], v[c][7]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kAsmThreads) assemble16_kernel(const __grid_constant__ AssembleArgs a) {
+  assemble16_body(a);
+}
+__global__ void __launch_bounds__(kAsmThreads) assemble16_kernel_dev(const AssembleArgs* __restrict__ a) {
+  assemble16_body(*a);
+}
+
 // ------------------------------------------------------------------- PE --
 struct PeArgs {
   float omega[128];  // 10000^(-2i/part), i < part / 2
@@ -389,6 +486,116 @@ REVO_DEVI void blend_body(const BlendArgs& a) {
 __global__ void blend_kernel(const __grid_constant__ BlendArgs a) { blend_body(a); }
 __global__ void blend_kernel_dev(const BlendArgs* __restrict__ a) { blend_body(*a); }
 
+// Patch size 16: one thread per (row, 8-pixel run) with all channels.  The
+// head's 8 values per channel are 32 contiguous bytes of the token's row; the
+// decoded and output pixels are 24 (RGB) or 16 (depth) contiguous bytes,
+// moved with 8- or 16-byte accesses when aligned (bytes otherwise).  All loads
+// are issued before the arithmetic, which is blend_body's.
+constexpr int kBlendThreads = 128;
+
+REVO_DEVI void blend16_body(const BlendArgs& a) {
+  const int C = a.C, W = a.W;
+  const int runs = W >> 3;
+  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (idx >= static_cast<long long>(a.H) * runs) return;
+  const int r8 = static_cast<int>(idx % runs);
+  const int y = static_cast<int>(idx / runs);
+  const int x0 = r8 * 8;
+  const uint32_t bits = (__ldg(a.mask + static_cast<size_t>(y) * a.mask_pitch + (x0 >> 5)) >> (x0 & 31)) & 0xFFu;
+  const size_t n = static_cast<size_t>(y >> 4) * (W >> 4) + (x0 >> 4);
+  const float* hrow = a.head + n * (C * 256) + (y & 15) * 16 + (x0 & 15);
+  const bool hvec = (reinterpret_cast<uintptr_t>(hrow) & 15u) == 0;
+  const int bpp = C == 3 ? 3 : 2;  // bytes per pixel
+  const uint8_t* dec = static_cast<const uint8_t*>(a.decoded) + static_cast<size_t>(y) * a.pitch + x0 * bpp;
+  uint8_t* out = static_cast<uint8_t*>(a.out) + static_cast<size_t>(y) * a.out_pitch + x0 * bpp;
+  float h[3][8];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (c >= C) break;
+    if (hvec) {
+      const float4 q0 = __ldg(reinterpret_cast<const float4*>(hrow + c * 256));
+      const float4 q1 = __ldg(reinterpret_cast<const float4*>(hrow + c * 256) + 1);
+      h[c][0] = q0.x, h[c][1] = q0.y, h[c][2] = q0.z, h[c][3] = q0.w;
+      h[c][4] = q1.x, h[c][5] = q1.y, h[c][6] = q1.z, h[c][7] = q1.w;
+    } else {
+#pragma unroll
+      for (int x = 0; x < 8; ++x) h[c][x] = __ldg(hrow + c * 256 + x);
+    }
+  }
+  if (C == 3) {
+    uint32_t dw[6], ow[6];
+    const bool dvec = ((reinterpret_cast<uintptr_t>(dec) | reinterpret_cast<uintptr_t>(out)) & 7u) == 0;
+    if (dvec) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(dec) + i);
+        dw[2 * i] = w.x, dw[2 * i + 1] = w.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        dw[i] = dec[4 * i] | (dec[4 * i + 1] << 8) | (dec[4 * i + 2] << 16) | (static_cast<uint32_t>(dec[4 * i + 3]) << 24);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ow[i] = 0u;
+    float* vals = a.values ? a.values + (static_cast<size_t>(y) * W + x0) * 3 : nullptr;
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v = __fadd_rn(__fmul_rn(h[c][x], kRgbStd[c]), kRgbMean[c]);
+        if (vals) vals[x * 3 + c] = v;
+        const float q = fminf(fmaxf(rintf(__fmul_rn(v, 255.0f)), 0.f), 255.f);
+        const int byte = 3 * x + c;
+        const uint32_t code =
+            ((bits >> x) & 1u) ? static_cast<uint32_t>(q) : (dw[byte >> 2] >> (8 * (byte & 3))) & 0xFFu;
+        ow[byte >> 2] |= code << (8 * (byte & 3));
+      }
+    if (dvec) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) reinterpret_cast<uint2*>(out)[i] = make_uint2(ow[2 * i], ow[2 * i + 1]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 24; ++i) out[i] = static_cast<uint8_t>(ow[i >> 2] >> (8 * (i & 3)));
+    }
+  } else {
+    uint32_t dw[4], ow[4];
+    const bool dvec = ((reinterpret_cast<uintptr_t>(dec) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
+    if (dvec) {
+      const uint4 w = __ldg(reinterpret_cast<const uint4*>(dec));
+      dw[0] = w.x, dw[1] = w.y, dw[2] = w.z, dw[3] = w.w;
+    } else {
+      const uint16_t* d16 = reinterpret_cast<const uint16_t*>(dec);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dw[i] = d16[2 * i] | (static_cast<uint32_t>(d16[2 * i + 1]) << 16);
+    }
+    const float mu = a.mu_sigma[0], sg = a.mu_sigma[1];
+    float* vals = a.values ? a.values + static_cast<size_t>(y) * W + x0 : nullptr;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ow[i] = 0u;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const float v = __fadd_rn(__fmul_rn(h[0][x], sg), mu);
+      if (vals) vals[x] = v;
+      const float q = fminf(fmaxf(rintf(v), 0.f), 65535.f);
+      const uint32_t code = ((bits >> x) & 1u) ? static_cast<uint32_t>(q) : (dw[x >> 1] >> (16 * (x & 1))) & 0xFFFFu;
+      ow[x >> 1] |= code << (16 * (x & 1));
+    }
+    if (dvec) {
+      *reinterpret_cast<uint4*>(out) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+    } else {
+      uint16_t* o16 = reinterpret_cast<uint16_t*>(out);
+#pragma unroll
+      for (int x = 0; x < 8; ++x) o16[x] = static_cast<uint16_t>(ow[x >> 1] >> (16 * (x & 1)));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlendThreads) blend16_kernel(const __grid_constant__ BlendArgs a) { blend16_body(a); }
+__global__ void __launch_bounds__(kBlendThreads) blend16_kernel_dev(const BlendArgs* __restrict__ a) {
+  blend16_body(*a);
+}
+
 __global__ void f32_to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {
   const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
   if (i < n) out[i] = __float2bfloat16_rn(in[i]);
@@ -400,6 +607,16 @@ cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st, const Assemb
   if (a.T <= 0 || a.F % a.T != 0 || a.p <= 0 || a.p > 16 || a.H % a.p || a.W % a.p || a.F > kMaxRefs + 1 ||
       (a.C != 1 && a.C != 3))
     return cudaErrorInvalidValue;
+  if (a.p == 16) {
+    const long long threads = static_cast<long long>(a.F) * (a.H / 16) * (a.W / 16) * 32;  // a warp per token-frame
+    if (threads == 0) return cudaSuccess;
+    const unsigned grid = static_cast<unsigned>((threads + kAsmThreads - 1) / kAsmThreads);
+    if (dev)
+      assemble16_kernel_dev<<<grid, kAsmThreads, 0, st>>>(dev);
+    else
+      assemble16_kernel<<<grid, kAsmThreads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const long long runs = static_cast<long long>(a.F / a.T) * (a.H / a.p) * (a.W / a.p) * a.T * a.C * a.p;
   if (runs == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((runs + 255) / 256);
@@ -471,6 +688,16 @@ cudaError_t launch_depth_stats(const uint16_t* d, int H, int W, size_t pitch, fl
 
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st, const BlendArgs* dev) {
   if (a.p <= 0 || a.H % a.p || a.W % a.p || (a.C != 1 && a.C != 3)) return cudaErrorInvalidValue;
+  if (a.p == 16) {
+    const long long threads = static_cast<long long>(a.H) * (a.W / 8);
+    if (threads == 0) return cudaSuccess;
+    const unsigned grid = static_cast<unsigned>((threads + kBlendThreads - 1) / kBlendThreads);
+    if (dev)
+      blend16_kernel_dev<<<grid, kBlendThreads, 0, st>>>(dev);
+    else
+      blend16_kernel<<<grid, kBlendThreads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const long long warps = static_cast<long long>(a.H) * ((a.W + 31) / 32);
   if (warps == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((warps * 32 + 255) / 256);
