@@ -330,24 +330,6 @@ REVO_DEVI uint32_t pack_bf16x2(float lo, float hi) {
 
 REVO_DEVI float gelu_exact(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
-// erf by the rational approximation of Abramowitz & Stegun, Handbook of
-// Mathematical Functions, formula 7.1.26: erf(z) = 1 - t (a1 + t (a2 + t (a3 +
-// t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z) for z >= 0, odd extension;
-// absolute error <= 1.5e-7, far below the bf16 rounding of the outputs it
-// feeds.  Cheaper than erff in the tensor-core GEMM epilogue.
-REVO_DEVI float erf_as7126(float z) {
-  const float a = fabsf(z);
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, a, 1.0f));
-  float poly = fmaf(t, 1.061405429f, -1.453152027f);
-  poly = fmaf(t, poly, 1.421413741f);
-  poly = fmaf(t, poly, -0.284496736f);
-  poly = fmaf(t, poly, 0.254829592f);
-  const float e = ex2_approx(-a * a * 1.4426950408889634f);
-  return copysignf(1.0f - t * poly * e, z);
-}
-
-REVO_DEVI float gelu_as7126(float x) { return 0.5f * x * (1.0f + erf_as7126(x * 0.70710678118654752f)); }
-
 REVO_DEVI float tanh_approx(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
