@@ -83,24 +83,6 @@ REVO_DEVI float max3(float a, float b, float c) {
   return d;
 }
 
-// Packed pair arithmetic on the f32x2 path: d = a * b + c and d = a + b.
-REVO_DEVI uint64_t pk2(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-REVO_DEVI void unpk2(uint64_t v, float& lo, float& hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
-REVO_DEVI uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-REVO_DEVI uint64_t add2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-
 // Running maxima in 8 independent lanes (short dependency chains), two new
 // values per instruction.
 REVO_DEVI void max_chunk(const uint32_t (&v)[32], float (&mx)[8]) {

@@ -57,30 +57,47 @@ REVO_DEVI void stage_row(uint8_t* chunk, int row, const uint4 (&pieces)[8]) {
   for (int k = 0; k < 8; ++k) *reinterpret_cast<uint4*>(base + ((k ^ (row & 7)) << 4)) = pieces[k];
 }
 
+// The epilogue works on 16 packed pairs (columns 2i, 2i + 1) so that each
+// multiply, add and FMA issues once per two values; every operation rounds
+// exactly as its scalar form would.
+
 // v[i] *= rs * cs[col + i] (FP8 dequantisation: token scale x channel scale).
-REVO_DEVI void apply_scales(float (&v)[32], float rs, const float* __restrict__ cs, int col) {
+REVO_DEVI void apply_scales(uint64_t (&v)[16], float rs, const float* __restrict__ cs, int col) {
   const float4* c4 = reinterpret_cast<const float4*>(cs + col);
+  const uint64_t rs2 = pk2(rs, rs);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const float4 c = __ldg(c4 + i);
-    v[4 * i] *= rs * c.x;
-    v[4 * i + 1] *= rs * c.y;
-    v[4 * i + 2] *= rs * c.z;
-    v[4 * i + 3] *= rs * c.w;
+    v[2 * i] = mul2(v[2 * i], mul2(rs2, pk2(c.x, c.y)));
+    v[2 * i + 1] = mul2(v[2 * i + 1], mul2(rs2, pk2(c.z, c.w)));
   }
 }
 
-REVO_DEVI void add_bias(float (&v)[32], const float* __restrict__ bias, int col) {
+REVO_DEVI void add_bias(uint64_t (&v)[16], const float* __restrict__ bias, int col) {
   if (bias == nullptr) return;
   const float4* b4 = reinterpret_cast<const float4*>(bias + col);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const float4 b = __ldg(b4 + i);
-    v[4 * i] += b.x;
-    v[4 * i + 1] += b.y;
-    v[4 * i + 2] += b.z;
-    v[4 * i + 3] += b.w;
+    v[2 * i] = add2(v[2 * i], pk2(b.x, b.y));
+    v[2 * i + 1] = add2(v[2 * i + 1], pk2(b.z, b.w));
   }
+}
+
+// gelu_tanh on a pair: the same operations as the scalar form, paired.
+REVO_DEVI uint64_t gelu_tanh2(uint64_t x) {
+  const uint64_t u = mul2(x, fma2(mul2(x, x), pk2(0.0356774081363001f, 0.0356774081363001f),
+                                   pk2(0.7978845608028654f, 0.7978845608028654f)));
+  const uint64_t hx = mul2(pk2(0.5f, 0.5f), x);
+  float u0, u1;
+  unpk2(u, u0, u1);
+  return fma2(hx, pk2(tanh_approx(u0), tanh_approx(u1)), hx);
+}
+
+REVO_DEVI uint32_t pack_bf16_pair(uint64_t v) {
+  float lo, hi;
+  unpk2(v, lo, hi);
+  return pack_bf16x2(lo, hi);
 }
 
 // One epilogue chunk: 32 rows (this warp's lanes) x 128 bytes of output
@@ -93,15 +110,18 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
     uint32_t r[32];
     tmem_ld32(taddr + c0, r);
     tmem_wait_ld();
-    float v[32];
+    uint64_t v[16];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = pk2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
     if (F8) apply_scales(v, rs, cs, n0 + c0);
     add_bias(v, bias, n0 + c0);
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-      pieces[k] = make_uint4(__float_as_uint(v[4 * k]), __float_as_uint(v[4 * k + 1]), __float_as_uint(v[4 * k + 2]),
-                             __float_as_uint(v[4 * k + 3]));
+    for (int k = 0; k < 8; ++k) {
+      float a, b, c, d;
+      unpk2(v[2 * k], a, b);
+      unpk2(v[2 * k + 1], c, d);
+      pieces[k] = make_uint4(__float_as_uint(a), __float_as_uint(b), __float_as_uint(c), __float_as_uint(d));
+    }
   } else {
     uint32_t rr[2][32];
     tmem_ld32(taddr + c0, rr[0]);
@@ -109,20 +129,19 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
     tmem_wait_ld();
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-      float v[32];
+      uint64_t v[16];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(rr[half][i]);
+      for (int i = 0; i < 16; ++i) v[i] = pk2(__uint_as_float(rr[half][2 * i]), __uint_as_float(rr[half][2 * i + 1]));
       if (F8) apply_scales(v, rs, cs, n0 + c0 + 32 * half);
       add_bias(v, bias, n0 + c0 + 32 * half);
       if (EPI == kEpiGeluBf16) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = gelu_tanh(v[i]);
+        for (int i = 0; i < 16; ++i) v[i] = gelu_tanh2(v[i]);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        pieces[4 * half + k] =
-            make_uint4(pack_bf16x2(v[8 * k], v[8 * k + 1]), pack_bf16x2(v[8 * k + 2], v[8 * k + 3]),
-                       pack_bf16x2(v[8 * k + 4], v[8 * k + 5]), pack_bf16x2(v[8 * k + 6], v[8 * k + 7]));
+        pieces[4 * half + k] = make_uint4(pack_bf16_pair(v[4 * k]), pack_bf16_pair(v[4 * k + 1]),
+                                          pack_bf16_pair(v[4 * k + 2]), pack_bf16_pair(v[4 * k + 3]));
     }
   }
   // The staging chunk is free once the previous bulk copy has read it.

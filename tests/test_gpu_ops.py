@@ -232,6 +232,74 @@ def test_assemble(modality, k, out_bf16):
         np.testing.assert_allclose(f64(out), ref, rtol=2e-6, atol=2e-6)
 
 
+def pitched(frame, pad, offset):
+    """A frame copied into rows of len(row) + pad bytes, starting `offset` bytes
+    into a device buffer (rows and base then lack 8/16-byte alignment)."""
+    rows = np.ascontiguousarray(frame).view(np.uint8).reshape(frame.shape[0], -1)
+    H, rb = rows.shape
+    pitch = rb + pad
+    buf = np.zeros(offset + H * pitch + 16, np.uint8)
+    for y in range(H):
+        buf[offset + y * pitch: offset + y * pitch + rb] = rows[y]
+    t = dev(buf)
+    return t[offset:], pitch
+
+
+@pytest.mark.parametrize("modality", ["rgb", "depth"])
+def test_assemble_unaligned_rows(modality):
+    """Frames whose rows are not 8/16-byte aligned take the kernel's scalar
+    loads; the tokens are the same as from aligned frames."""
+    H, W, T, p, k = 48, 80, 2, 16, 3
+    pl = synth.make_tiny_plane(77 + len(modality), modality, H, W, k)
+    C = 3 if modality == "rgb" else 1
+    if modality == "rgb":
+        frames = np.stack([O.normalise_rgb(f) for f in pl.refs] + [O.normalise_rgb(pl.decoded)])
+        mu_sigma = None
+    else:
+        mu, sg = O.depth_stats(pl.refs[-1])
+        frames = np.stack([O.normalise_depth(f, mu, sg) for f in pl.refs] + [O.normalise_depth(pl.decoded, mu, sg)])
+        mu_sigma = dev(np.array([mu, sg], np.float32))
+    ref = O.tubelets(frames, T, p)
+    offset = 4 if modality == "rgb" else 2
+    pad = 4 if modality == "rgb" else 6
+    refs_d, pitch = zip(*[pitched(f, pad, offset) for f in pl.refs])
+    cur_d, pitch_c = pitched(pl.decoded, pad, offset)
+    assert len(set(pitch)) == 1 and pitch[0] == pitch_c
+    out = torch.zeros(ref.shape, dtype=torch.float32, device="cuda")
+    R.op_assemble(C, k, T, p, H, W, list(refs_d), cur_d, pitch_c, mu_sigma, out, 0)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(f64(out), ref, rtol=2e-6, atol=2e-6)
+
+
+@pytest.mark.parametrize("modality", ["rgb", "depth"])
+def test_blend_unaligned_rows(modality):
+    """Decoded / output rows and the head not 16-byte aligned: scalar paths,
+    same bit-exact codes."""
+    H, W, p = 32, 48, 16
+    C = 3 if modality == "rgb" else 1
+    pl = synth.make_tiny_plane(H * W + 5, modality, H, W, 1)
+    Hp, Wp = H // p, W // p
+    head = synth.normal(H + W, (Hp * Wp, C * p * p), 1.5 if modality == "rgb" else 0.8)
+    y = O.untubelet_frame(head.astype(np.float64), C, 1, p, Hp, Wp, 0).astype(np.float32)
+    if modality == "rgb":
+        codes = O.quantise_rgb(O.denormalise_rgb(y, np.float32), np.float32)
+        ms = None
+    else:
+        mu, sg = 2500.0, 700.0
+        codes = O.quantise_depth(O.denormalise_depth(y, mu, sg, np.float32), np.float32)
+        ms = dev(np.array([mu, sg], np.float32))
+    expect = O.blend(pl.decoded, O.unpack_mask(pl.mask, W), codes)
+    offset = 4 if modality == "rgb" else 2
+    dec_d, pitch = pitched(pl.decoded, 4, offset)
+    out_d, _ = pitched(np.zeros_like(pl.decoded), 4, offset)
+    head_buf = dev(np.concatenate([np.zeros(1, np.float32), head.ravel()]))[1:]  # 4 bytes past a 16-byte boundary
+    R.op_blend(C, p, H, W, head_buf, dec_d, pitch, dev(pl.mask), pl.mask.shape[1], ms, out_d, pitch)
+    torch.cuda.synchronize()
+    rows = out_d.cpu().numpy()[: H * pitch].reshape(H, pitch)[:, : W * (3 if modality == "rgb" else 2)]
+    got = rows.copy().view(np.uint8 if modality == "rgb" else np.uint16).reshape(pl.decoded.shape)
+    np.testing.assert_array_equal(got, expect)
+
+
 @pytest.mark.parametrize("case", ["synthetic", "zeros", "constant", "two_values"])
 def test_depth_stats(case):
     if case == "synthetic":
