@@ -864,21 +864,23 @@ def run_profile_kernel(args) -> None:
                                         stats, out, Ww * 3, stream=stream)
             nbytes = head.numel() * 4 + 2 * Hh * Ww * 3 + mask.numel() * 4
         flops = None
-    elif args.profile_kernel == "fc1_fp8":  # the same fc1 with E4M3 operands
+    elif args.profile_kernel in ("fc1_fp8", "fc1_fp8_pair"):  # the same fc1 with E4M3 operands
         a = torch.randint(0, 120, (N, D), dtype=torch.uint8, device="cuda")
         w = torch.randint(0, 120, (4 * D, D), dtype=torch.uint8, device="cuda")
         sa = torch.full((N,), 0.01, device="cuda")
         sw = torch.full((4 * D,), 0.01, device="cuda")
         b = torch.zeros(4 * D, device="cuda")
         out = torch.empty((N, 4 * D), dtype=torch.bfloat16, device="cuda")
-        launch = lambda: R.op_linear_fp8(2, a, sa, w, sw, b, out, N, 4 * D, D, 256, stream=stream)  # noqa: E731
+        tile = 256 | (R.TILE_PAIR if args.profile_kernel == "fc1_fp8_pair" else 0)
+        launch = lambda: R.op_linear_fp8(2, a, sa, w, sw, b, out, N, 4 * D, D, tile, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
-    else:  # fc1 of an encoder block: [N, 768] x [3072, 768]^T + GELU
+    else:  # fc1 of an encoder block: [N, 768] x [3072, 768]^T + GELU (fc1_pair: 256-row tiles on CTA pairs)
         a = torch.randn((N, D), device="cuda").to(torch.bfloat16)
         w = (torch.randn((4 * D, D), device="cuda") / 28).to(torch.bfloat16)
         b = torch.zeros(4 * D, device="cuda")
         out = torch.empty((N, 4 * D), dtype=torch.bfloat16, device="cuda")
-        launch = lambda: R.op_linear(R.BF16, 2, a, w, b, out, N, 4 * D, D, 256, stream=stream)  # noqa: E731
+        tile = 256 | (R.TILE_PAIR if args.profile_kernel == "fc1_pair" else 0)
+        launch = lambda: R.op_linear(R.BF16, 2, a, w, b, out, N, 4 * D, D, tile, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
     torch.cuda.synchronize()
     for _ in range(args.warmup):
@@ -897,7 +899,8 @@ def run_profile_kernel(args) -> None:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "fc1", "fc1_fp8", "assemble", "blend"],
+    ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "fc1", "fc1_pair", "fc1_fp8", "fc1_fp8_pair",
+                             "assemble", "blend"],
                     default=None,
                     help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)

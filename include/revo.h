@@ -209,9 +209,10 @@ typedef struct {
   uint64_t graph_replays;   /* of those modality forwards, replays of a captured graph */
   int graphs_captured;      /* captured forwards held (all lanes, both modalities) */
   int tuned_shapes;         /* GEMM shapes the autotuner has timed                 */
-  int tuned_wide;           /* of those, shapes where the 256-wide tile won        */
+  int tuned_wide;           /* of those, shapes where a 256-wide tile won          */
   int pending;              /* submitted requests not yet in a batch               */
   int in_flight;            /* batches launched and not yet retired                */
+  int tuned_pair;           /* tuned shapes where a CTA-pair tile (REVO_TILE_PAIR) won */
 } revo_stats;
 
 /* Fills *out.  Errors: REVO_EINVAL (null argument). */
@@ -281,12 +282,22 @@ REVO_API revo_status revo_op_depth_stats_noalloc(const uint16_t* depth, int heig
                                                  size_t pitch_bytes, float* mu_sigma, void* stream);
 
 /*
+ * Tile choice for the tensor-core Linear entry points: the tile width (128 or
+ * 256 output columns), optionally ORed with REVO_TILE_PAIR for 256-row tiles
+ * computed by a pair of CTAs on two SMs (one tcgen05 MMA with .cta_group::2
+ * over both SMs' shared memory and TMEM).  Results are the same for every
+ * choice (each output is one float32 dot product in the same K order).
+ */
+#define REVO_TILE_PAIR 0x1000
+
+/*
  * Y = epilogue(A W^T + b) with A [M][K], W [N][K] (Linear [out][in]), b [N]
  * (b may be NULL).
  *   precision REVO_FP32: A, W float32, SIMT FMA (K % 8 == 0).  REVO_BF16: A, W
  *   bf16 on the tcgen05 tensor cores with float32 accumulation (K % 64 == 0,
  *   N % 32 == 0, N % 64 == 0 for the bf16 epilogues 1 and 2); `tile_n` picks
- *   the 128- or 256-column tile (other values: 128).
+ *   the 128- or 256-column tile (other widths: 128), | REVO_TILE_PAIR for the
+ *   CTA-pair tiles.
  *   epilogue 0: out = acc + b (float32 out)
  *   epilogue 1: out = acc + b (bf16 out; FP32 precision writes float32)
  *   epilogue 2: out = gelu(acc + b) (bf16 out; FP32 precision writes float32)
@@ -317,7 +328,7 @@ REVO_API revo_status revo_op_layernorm(const float* x, const float* gamma, const
  * + bias[n]) with A [M][K] and W [N][K] E4M3 codes (decoded exactly), the sum
  * accumulated in float32 on the tensor cores.  epilogue 1 (bf16 out) or 2
  * (GELU, bf16 out); out bf16 [M][N].  K % 128 == 0, N % 64 == 0; tile_n 128
- * or 256.  Errors: REVO_EINVAL, REVO_ECUDA.
+ * or 256, | REVO_TILE_PAIR for CTA-pair tiles.  Errors: REVO_EINVAL, REVO_ECUDA.
  */
 REVO_API revo_status revo_op_quantize_rows_e4m3(const float* x, int rows, int cols, uint8_t* q, float* scale,
                                                 void* stream);

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "REVO_OK", 1: "REVO_EAGAIN", -1: "REVO_EINVAL", -2: "REVO_ENO
 FP32, BF16, FP8 = 0, 1, 2
 RGB, DEPTH, CLEAN, HOLD = 1, 2, 4, 8
 EPI_F32, EPI_BF16, EPI_GELU_BF16, EPI_RESID_F32 = 0, 1, 2, 3
+TILE_PAIR = 0x1000  # REVO_TILE_PAIR: OR into tile_n for 256-row tiles on a CTA pair
 
 
 class RevoError(RuntimeError):
@@ -69,7 +70,7 @@ class Pose(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("device_bytes", C.c_size_t), ("batches", C.c_uint64), ("graph_replays", C.c_uint64),
                 ("graphs_captured", C.c_int), ("tuned_shapes", C.c_int), ("tuned_wide", C.c_int),
-                ("pending", C.c_int), ("in_flight", C.c_int)]
+                ("pending", C.c_int), ("in_flight", C.c_int), ("tuned_pair", C.c_int)]
 
 
 class Result(C.Structure):

@@ -19,11 +19,17 @@
 // same) and multiplies each accumulator by its row's activation scale and its
 // column's weight scale before the bias.
 //
+// A second form runs 256-row tiles on a CTA pair (a two-CTA cluster on two
+// SMs issuing one tcgen05.mma.cta_group::2 per K step; see gemm_tc_pair_kernel).
+// The autotuner times both forms per shape; the results are bit-identical.
+//
 // Warp roles (320 threads, one CTA per SM, persistent over output tiles):
 //   warp 0      TMA producer (one thread)
 //   warp 1      TMEM allocator + MMA issuer (one thread)
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (tile rows);
 //               warps 2..5 take the left half of the tile's columns, 6..9 the right.
+#include <algorithm>
+
 #include "common.cuh"
 #include "revo_internal.h"
 
@@ -306,6 +312,182 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---- CTA-pair form: a cluster of two CTAs computes 256 x BN output tiles with
+// tcgen05.mma.cta_group::2 (M = 256).  Each CTA holds 128 rows of A and BN/2
+// rows of W per stage (32 KB at BN = 256 instead of 48 KB), so the same shared
+// memory holds 6 stages instead of 4 and every SM reads a third less operand
+// data per FLOP; rank 0 issues the MMAs for both SMs (half the issue work per
+// SM).  Both CTAs' loads complete on rank 0's stage barrier; the MMA commits
+// release the stage in both CTAs and hand each CTA's epilogue its 128
+// accumulator rows (its own TMEM, same column address); the epilogue warps of
+// both CTAs free an accumulator buffer on rank 0's barrier.
+template <int BN>
+struct TcGemmPairCfg {
+  static constexpr int kABytes = kBM * 128;         // 128 rows x 128 B of K
+  static constexpr int kBBytes = (BN / 2) * 128;    // this CTA's half of the W rows
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kStages = (192 * 1024) / kStageBytes;  // BN 256: 6, BN 128: 8
+  static constexpr int kTmemCols = 2 * BN;
+  static constexpr int kSmemBytes =
+      1024 /*align slack*/ + kStages * kStageBytes + kEpiWarps * kOutChunkBytes + 256 /*barriers*/;
+};
+
+template <int BN, int EPI, bool F8>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmC, const float* __restrict__ bias,
+                        const float* __restrict__ row_scale, const float* __restrict__ col_scale, int M, int N, int K,
+                        int* err) {
+  using Cfg = TcGemmPairCfg<BN>;
+  constexpr int S = Cfg::kStages;
+  constexpr uint32_t kIdesc = F8 ? idesc_e4m3(2 * kBM, BN) : idesc_bf16(2 * kBM, BN);
+  constexpr int kKe = F8 ? kBK8 : kBK;
+  constexpr int kChunkCols = (EPI == kEpiF32 || EPI == kEpiResidF32) ? 32 : 64;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + S * Cfg::kABytes;
+  uint8_t* sOut = sB + S * Cfg::kBBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sOut + kEpiWarps * kOutChunkBytes);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int pair = static_cast<int>(blockIdx.x) >> 1;
+  const int npairs = static_cast<int>(gridDim.x) >> 1;
+  const int m_tiles = (M + 2 * kBM - 1) / (2 * kBM);
+  const int n_tiles = (N + BN - 1) / BN;
+  const int num_tiles = m_tiles * n_tiles;
+  const int num_kb = K / kKe;
+
+  if (threadIdx.x == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+    tma_prefetch_desc(&tmC);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);   // rank 0's: its producer's arrival + both CTAs' bytes
+      mbar_init(&empty[s], 1);  // one multicast commit per use
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 2 * kEpiWarps);  // rank 0's: the epilogue warps of both CTAs
+    }
+    fence_mbarrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc_pair(tmem_slot, Cfg::kTmemCols);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // both CTAs' barriers initialised before any remote completion
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint32_t full0 = mapa_shared(smem_u32(&full[0]), 0);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int tile = pair; tile < num_tiles && ok; tile += npairs) {
+        const int m0 = (tile % m_tiles) * (2 * kBM) + kBM * static_cast<int>(rank);
+        const int n0 = (tile / m_tiles) * BN + (BN / 2) * static_cast<int>(rank);
+        for (int kb = 0; kb < num_kb; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, err, kDevTimeoutProducer)) {
+            ok = false;
+            break;
+          }
+          if (rank == 0) mbar_arrive_expect_tx(&full[stage], 2 * Cfg::kStageBytes);
+          const uint32_t bar = full0 + stage * static_cast<uint32_t>(sizeof(uint64_t));
+          tma_load_2d_pair(sA + stage * Cfg::kABytes, &tmA, kb * kKe, m0, bar);
+          tma_load_2d_pair(sB + stage * Cfg::kBBytes, &tmB, kb * kKe, n0, bar);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int t_local = 0;
+      bool ok = true;
+      for (int tile = pair; tile < num_tiles && ok; tile += npairs, ++t_local) {
+        const int acc = t_local & 1;
+        const uint32_t acc_phase = (t_local >> 1) & 1;
+        if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, err, kDevTimeoutMma)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * BN;
+        for (int kb = 0; kb < num_kb; ++kb) {
+          if (!mbar_wait(&full[stage], phase, err, kDevTimeoutMma)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_lo = sw128_lo(smem_u32(sA + stage * Cfg::kABytes));
+          const uint32_t b_lo = sw128_lo(smem_u32(sB + stage * Cfg::kBBytes));
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {  // 4 x 32 bytes of K per stage
+            if (F8)
+              mma_f8_pair(d_tmem, a_lo + kk * 2, kSw128Hi, b_lo + kk * 2, kSw128Hi, kIdesc, (kb | kk) != 0 ? 1u : 0u);
+            else
+              mma_f16_pair(d_tmem, a_lo + kk * 2, kSw128Hi, b_lo + kk * 2, kSw128Hi, kIdesc,
+                           (kb | kk) != 0 ? 1u : 0u);
+          }
+          mma_commit_pair(&empty[stage], 0x3);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (ok) mma_commit_pair(&tfull[acc], 0x3);
+      }
+    }
+  } else {
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int half = e >> 2;
+    uint8_t* chunk = sOut + e * kOutChunkBytes;
+    int t_local = 0;
+    for (int tile = pair; tile < num_tiles; tile += npairs, ++t_local) {
+      const int acc = t_local & 1;
+      const uint32_t acc_phase = (t_local >> 1) & 1;
+      if (!mbar_wait(&tfull[acc], acc_phase, err, kDevTimeoutEpilogue)) break;
+      tc_fence_after();
+      const int m0 = (tile % m_tiles) * (2 * kBM) + kBM * static_cast<int>(rank);
+      const int n0 = (tile / m_tiles) * BN;
+      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BN;
+      const int my_row = m0 + q * 32 + lane;
+      const float rs = (F8 && my_row < M) ? __ldg(row_scale + my_row) : 0.f;
+#pragma unroll 1
+      for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2) && m0 + q * 32 < M; c0 += kChunkCols) {
+        if (n0 + c0 >= N) break;
+        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[acc]), 0));
+    }
+    if (lane == 0) bulk_wait_all();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // no CTA leaves while its peer's MMAs may read its shared memory
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, Cfg::kTmemCols);
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -325,6 +507,45 @@ cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const CUte
   return cudaGetLastError();
 }
 
+template <int BN, int EPI, bool F8 = false>
+cudaError_t launch_pair_epi(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const float* bias, int M,
+                            int N, int K, int* err, int num_sms, cudaStream_t st, const float* row_scale = nullptr,
+                            const float* col_scale = nullptr) {
+  using Cfg = TcGemmPairCfg<BN>;
+  auto kern = gemm_tc_pair_kernel<BN, EPI, F8>;
+  static std::atomic<unsigned long long> attr_done{0};  // one per template instance
+  cudaError_t e = ensure_smem_attr(kern, Cfg::kSmemBytes, attr_done);
+  if (e != cudaSuccess) return e;
+  const int tiles = ((M + 2 * kBM - 1) / (2 * kBM)) * ((N + BN - 1) / BN);
+  const int pairs = std::min(tiles, num_sms / 2);
+  if (pairs < 1) return cudaErrorInvalidValue;
+  kern<<<2 * pairs, kThreads, Cfg::kSmemBytes, st>>>(a, b, c, bias, row_scale, col_scale, M, N, K, err);
+  return cudaGetLastError();
+}
+
+template <bool F8>
+cudaError_t launch_any(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
+                       const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st,
+                       const float* row_scale, const float* col_scale) {
+#define REVO_GEMM_CASE(W, E)                                                                                 \
+  if (bn == (W) && epi == (E)) return launch_bn_epi<W, E, F8>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, \
+                                                             col_scale);                                          \
+  if (bn == ((W) | kTilePair) && epi == (E))                                                                 \
+    return launch_pair_epi<W, E, F8>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, col_scale);
+  if (!F8) {
+    REVO_GEMM_CASE(128, kEpiF32)
+    REVO_GEMM_CASE(256, kEpiF32)
+    REVO_GEMM_CASE(128, kEpiResidF32)
+    REVO_GEMM_CASE(256, kEpiResidF32)
+  }
+  REVO_GEMM_CASE(128, kEpiBf16)
+  REVO_GEMM_CASE(256, kEpiBf16)
+  REVO_GEMM_CASE(128, kEpiGeluBf16)
+  REVO_GEMM_CASE(256, kEpiGeluBf16)
+#undef REVO_GEMM_CASE
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
@@ -332,22 +553,7 @@ cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUt
   if (M <= 0 || N <= 0) return cudaSuccess;
   const bool bf16_out = epi == kEpiBf16 || epi == kEpiGeluBf16;
   if (K % kBK != 0 || N % (bf16_out ? 64 : 32) != 0) return cudaErrorInvalidValue;
-  if (bn == 256) {
-    switch (epi) {
-      case kEpiF32: return launch_bn_epi<256, kEpiF32>(a, b, c, bias, M, N, K, err, num_sms, st);
-      case kEpiBf16: return launch_bn_epi<256, kEpiBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
-      case kEpiGeluBf16: return launch_bn_epi<256, kEpiGeluBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
-      case kEpiResidF32: return launch_bn_epi<256, kEpiResidF32>(a, b, c, bias, M, N, K, err, num_sms, st);
-    }
-  } else {
-    switch (epi) {
-      case kEpiF32: return launch_bn_epi<128, kEpiF32>(a, b, c, bias, M, N, K, err, num_sms, st);
-      case kEpiBf16: return launch_bn_epi<128, kEpiBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
-      case kEpiGeluBf16: return launch_bn_epi<128, kEpiGeluBf16>(a, b, c, bias, M, N, K, err, num_sms, st);
-      case kEpiResidF32: return launch_bn_epi<128, kEpiResidF32>(a, b, c, bias, M, N, K, err, num_sms, st);
-    }
-  }
-  return cudaErrorInvalidValue;
+  return launch_any<false>(a, b, c, bn, epi, bias, M, N, K, err, num_sms, st, nullptr, nullptr);
 }
 
 cudaError_t launch_gemm_tc_fp8(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
@@ -355,22 +561,7 @@ cudaError_t launch_gemm_tc_fp8(const CUtensorMap& a, const CUtensorMap& b, const
                                int* err, int num_sms, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (K % kBK8 != 0 || N % 64 != 0 || !row_scale || !col_scale) return cudaErrorInvalidValue;
-  if (bn == 256) {
-    switch (epi) {
-      case kEpiBf16: return launch_bn_epi<256, kEpiBf16, true>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale,
-                                                                col_scale);
-      case kEpiGeluBf16: return launch_bn_epi<256, kEpiGeluBf16, true>(a, b, c, bias, M, N, K, err, num_sms, st,
-                                                                        row_scale, col_scale);
-    }
-  } else {
-    switch (epi) {
-      case kEpiBf16: return launch_bn_epi<128, kEpiBf16, true>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale,
-                                                                col_scale);
-      case kEpiGeluBf16: return launch_bn_epi<128, kEpiGeluBf16, true>(a, b, c, bias, M, N, K, err, num_sms, st,
-                                                                        row_scale, col_scale);
-    }
-  }
-  return cudaErrorInvalidValue;
+  return launch_any<true>(a, b, c, bn, epi, bias, M, N, K, err, num_sms, st, row_scale, col_scale);
 }
 
 }  // namespace revo

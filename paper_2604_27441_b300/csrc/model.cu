@@ -27,9 +27,14 @@ int pick_bn(int /*M*/, int N, int /*sms*/) { return N >= 256 ? 256 : 128; }
 
 bool make_weight_maps(LinearW& w) {
   if (!w.w16) return true;
+  // 64-row boxes serve the CTA-pair tiles of width 128 (each CTA loads half
+  // of the W rows), 128-row boxes the single tiles of width 128 and the pair
+  // tiles of width 256, 256-row boxes the single tiles of width 256.
+  if (!encode_tmap_bf16_2d(&w.map64, w.w16, w.out, w.in, w.in, 64, 64)) return false;
   if (!encode_tmap_bf16_2d(&w.map128, w.w16, w.out, w.in, w.in, 128, 64)) return false;
   if (w.out >= 256 && !encode_tmap_bf16_2d(&w.map256, w.w16, w.out, w.in, w.in, 256, 64)) return false;
   if (w.w8) {
+    if (!encode_tmap_u8_2d(&w.map8_64, w.w8, w.out, w.in, w.in, 64)) return false;
     if (!encode_tmap_u8_2d(&w.map8_128, w.w8, w.out, w.in, w.in, 128)) return false;
     if (w.out >= 256 && !encode_tmap_u8_2d(&w.map8_256, w.w8, w.out, w.in, w.in, 256)) return false;
   }
@@ -317,14 +322,15 @@ struct Fwd {
     return launch(amap, w, epi, M, true, bn, cmap);
   }
 
-  // One launch of width bn writing through `dst`.
+  // One launch of tile width bn (see kTilePair) writing through `dst`.
   cudaError_t launch(const CUtensorMap* amap, const LinearW& w, int epi, int M, bool f8, int bn,
                      const CUtensorMap* dst) {
+    const int rows = (bn & kTilePair) ? (bn & ~kTilePair) / 2 : bn;  // W rows per CTA and tile
     if (f8)
-      return launch_gemm_tc_fp8(*amap, bn == 256 ? w.map8_256 : w.map8_128, *dst, bn, epi, w.b, ws->h8_scale,
-                                w.w8_scale, M, w.out, w.in, ws->err, sms, st);
-    return launch_gemm_tc(*amap, bn == 256 ? w.map256 : w.map128, *dst, bn, epi, w.b, M, w.out, w.in, ws->err, sms,
-                          st);
+      return launch_gemm_tc_fp8(*amap, rows == 256 ? w.map8_256 : rows == 128 ? w.map8_128 : w.map8_64, *dst, bn,
+                                epi, w.b, ws->h8_scale, w.w8_scale, M, w.out, w.in, ws->err, sms, st);
+    return launch_gemm_tc(*amap, rows == 256 ? w.map256 : rows == 128 ? w.map128 : w.map64, *dst, bn, epi, w.b, M,
+                          w.out, w.in, ws->err, sms, st);
   }
 
   // The autotuner's choice for this shape, timing the candidates if it has none
@@ -362,8 +368,8 @@ struct Fwd {
     }
     float best = 0.f;
     int best_bn = *bn;
-    for (int cand : {128, 256}) {
-      if (cand == 256 && w.out < 256) continue;
+    for (int cand : {128, 256, kTilePair | 128, kTilePair | 256}) {
+      if ((cand & ~kTilePair) == 256 && w.out < 256) continue;
       for (int rep = 0; rep < 4 && rc == cudaSuccess; ++rep) {
         if (rep == 1) rc = cudaEventRecord(ev[0], st);
         if (rc == cudaSuccess) rc = launch(amap, w, epi, M, f8, cand, dst);
@@ -382,7 +388,8 @@ struct Fwd {
     cudaEventDestroy(ev[1]);
     if (rc != cudaSuccess) return rc;
     net->tuned_bn[key] = best_bn;
-    ++(best_bn == 256 ? net->tuned_shapes_256 : net->tuned_shapes_128);
+    ++((best_bn & ~kTilePair) == 256 ? net->tuned_shapes_256 : net->tuned_shapes_128);
+    if (best_bn & kTilePair) ++net->tuned_shapes_pair;
     *bn = best_bn;
     return cudaSuccess;
   }

@@ -35,12 +35,12 @@ struct LinearW {
   const float* b = nullptr;
   const __nv_bfloat16* w16 = nullptr;
   int out = 0, in = 0;
-  CUtensorMap map128{}, map256{};
+  CUtensorMap map64{}, map128{}, map256{};  // W boxes of 64 / 128 / 256 rows
   // FP8 precision, the LayerNorm-fed layers (qkv, fc1): E4M3 codes with one
   // scale per output channel, and their maps.
   const uint8_t* w8 = nullptr;
   const float* w8_scale = nullptr;
-  CUtensorMap map8_128{}, map8_256{};
+  CUtensorMap map8_64{}, map8_128{}, map8_256{};
 };
 
 struct BlockW {
@@ -67,7 +67,7 @@ struct Net {
   // qkv, 3 decoder fc1).
   int fp8_mask = 0;
   std::map<uint64_t, int> tuned_bn;
-  int tuned_shapes_256 = 0, tuned_shapes_128 = 0;
+  int tuned_shapes_256 = 0, tuned_shapes_128 = 0, tuned_shapes_pair = 0;
 };
 
 // One request of one modality inside a batch (all pointers are device pointers).

@@ -150,10 +150,13 @@ revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A
     set_last_error("revo_op_linear: BF16 path needs K %% 64 == 0 and N %% 32 == 0 (N %% 64 == 0 for bf16 outputs)");
     return REVO_EINVAL;
   }
-  const int bn = tile_n == 256 ? 256 : 128;
+  const bool pair = (tile_n & REVO_TILE_PAIR) != 0;
+  const int width = (tile_n & ~REVO_TILE_PAIR) == 256 ? 256 : 128;
+  const int bn = pair ? (width | kTilePair) : width;
   CUtensorMap ma, mb, mc;
   const uint64_t rows = M > 0 ? M : 1;
-  if (!encode_tmap_bf16_2d(&ma, A, rows, K, K, 128, 64) || !encode_tmap_bf16_2d(&mb, W, N, K, K, bn, 64) ||
+  if (!encode_tmap_bf16_2d(&ma, A, rows, K, K, 128, 64) ||
+      !encode_tmap_bf16_2d(&mb, W, N, K, K, pair ? width / 2 : width, 64) ||
       !encode_tmap_out_2d(&mc, out, f32_out, rows, N, N)) {
     set_last_error("revo_op_linear: tensor map encoding failed (alignment?)");
     return REVO_EINVAL;
@@ -208,10 +211,12 @@ revo_status revo_op_linear_fp8(int epilogue, const uint8_t* A, const float* a_sc
     set_last_error("revo_op_linear_fp8: needs K %% 128 == 0 and N %% 64 == 0");
     return REVO_EINVAL;
   }
-  const int bn = tile_n == 256 && N >= 256 ? 256 : 128;
+  const bool pair = (tile_n & REVO_TILE_PAIR) != 0;
+  const int width = (tile_n & ~REVO_TILE_PAIR) == 256 && N >= 256 ? 256 : 128;
+  const int bn = pair ? (width | kTilePair) : width;
   CUtensorMap ma, mb, mc;
   const uint64_t rows = M > 0 ? M : 1;
-  if (!encode_tmap_u8_2d(&ma, A, rows, K, K, 128) || !encode_tmap_u8_2d(&mb, W, N, K, K, bn) ||
+  if (!encode_tmap_u8_2d(&ma, A, rows, K, K, 128) || !encode_tmap_u8_2d(&mb, W, N, K, K, pair ? width / 2 : width) ||
       !encode_tmap_out_2d(&mc, out, false, rows, N, N)) {
     set_last_error("revo_op_linear_fp8: tensor map encoding failed (alignment?)");
     return REVO_EINVAL;

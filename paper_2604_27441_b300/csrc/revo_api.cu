@@ -762,6 +762,7 @@ revo_status revo_recover_stats(revo_ctx* c, revo_stats* out) {
     if (c->net[m]) {
       out->tuned_shapes += static_cast<int>(c->net[m]->tuned_bn.size());
       out->tuned_wide += c->net[m]->tuned_shapes_256;
+      out->tuned_pair += c->net[m]->tuned_shapes_pair;
     }
   out->pending = static_cast<int>(c->pending.size());
   for (const auto& kv : c->batches) out->in_flight += kv.second.lane >= 0 && !kv.second.done;

@@ -20,6 +20,12 @@ enum Epilogue : int {
   kEpiResidF32 = 3,  // float32 out += .
 };
 
+// GEMM tile widths: 128 or 256 output columns per tile of 128 rows (one CTA);
+// kTilePair | 128 or kTilePair | 256: tiles of 256 rows on a CTA pair (two
+// SMs, tcgen05.mma.cta_group::2), whose W tensor map has width/2-row boxes.
+constexpr int kTilePair = 0x1000;
+static_assert(kTilePair == REVO_TILE_PAIR, "internal and public pair flags agree");
+
 constexpr int kMaxSegments = 64;
 constexpr int kMaxRefs = 7;  // k <= 7
 
@@ -42,7 +48,9 @@ bool encode_tmap_u8_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64
 
 // ---- GEMMs
 // `c` is the output map (encode_tmap_out_2d): float32 for kEpiF32 and
-// kEpiResidF32 (the residual epilogue adds into it), bf16 otherwise.
+// kEpiResidF32 (the residual epilogue adds into it), bf16 otherwise.  `bn` is a
+// tile width (see kTilePair); `a` has 128-row boxes, `b` bn-row boxes, or
+// bn/2-row boxes for a pair width.
 cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
                            const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st);
 // FP8 (E4M3) operands with per-row scales of A (`row_scale`, M entries: one per

@@ -67,6 +67,45 @@ def test_linear_bf16_tcgen05(M, N, K, bn, epi):
         np.testing.assert_allclose(got, ref, rtol=8e-3, atol=8e-3)
 
 
+PAIR_SHAPES = [(300, 256, 192), (1000, 768, 768), (517, 384, 128), (3600, 3072, 768), (1, 64, 64), (129, 2304, 768),
+               (256, 512, 256), (5000, 1536, 384)]
+
+
+@pytest.mark.parametrize("M,N,K", PAIR_SHAPES)
+@pytest.mark.parametrize("epi", [0, 1, 2, 3])
+def test_linear_bf16_cta_pair_tiles(M, N, K, epi):
+    """256-row tiles on a CTA pair (tcgen05.mma.cta_group::2): the oracle's
+    values, and bit for bit the single-CTA tile of the same width (same
+    float32 dot products, same K order, same epilogue)."""
+    seed = M * 3 + N * 5 + K
+    A = bf16(synth.normal(seed, (M, K))).cuda()
+    W = bf16(synth.normal(seed + 1, (N, K), 1.0 / np.sqrt(K))).cuda()
+    b = synth.normal(seed + 2, (N,), 0.1)
+    ref = O.linear(f64(A), f64(W), b.astype(np.float64))
+    if epi == 2:
+        ref = O.gelu(ref)
+    out_dtype = torch.float32 if epi in (0, 3) else torch.bfloat16
+    base = synth.normal(seed + 3, (M, N)) if epi == 3 else np.zeros((M, N), np.float32)
+    if epi == 3:
+        ref = ref + base
+    for width in (128, 256):
+        if width > N:
+            continue
+        outs = []
+        for tile in (width, width | R.TILE_PAIR):
+            out = torch.from_numpy(base).to(out_dtype).cuda()
+            R.op_linear(R.BF16, epi, A, W, dev(b), out, M, N, K, tile)
+            torch.cuda.synchronize()
+            outs.append(out)
+        got = f64(outs[1])
+        if out_dtype == torch.float32:
+            np.testing.assert_allclose(got, ref, rtol=1e-4, atol=2e-4)
+        else:
+            np.testing.assert_allclose(got, ref, rtol=8e-3, atol=8e-3)
+        assert torch.equal(outs[0], outs[1]), f"width {width}: pair tile differs from the single tile"
+    assert R.take_device_error() == 0
+
+
 @pytest.mark.parametrize("M,N,K", [(300, 256, 192), (1000, 768, 768), (77, 96, 24)])
 @pytest.mark.parametrize("epi", [0, 2, 3])
 def test_linear_fp32_simt(M, N, K, epi):
@@ -163,6 +202,33 @@ def test_linear_fp8_tcgen05(M, N, K, bn, epi):
     R.op_linear_fp8(epi, dev(a_codes), dev(a_scale), dev(w_codes), dev(w_scale), dev(b), out, M, N, K, bn)
     torch.cuda.synchronize()
     np.testing.assert_allclose(f64(out), ref, rtol=8e-3, atol=8e-3)
+
+
+@pytest.mark.parametrize("M,N,K", [(300, 256, 768), (1000, 2304, 768), (3600, 3072, 768), (1, 64, 128),
+                                   (517, 1536, 384)])
+@pytest.mark.parametrize("epi", [1, 2])
+def test_linear_fp8_cta_pair_tiles(M, N, K, epi):
+    """E4M3 pair tiles: the oracle's values and the single tile's bits."""
+    seed = M * 11 + N + K
+    a_codes, a_scale = F8.quantise_rows(synth.normal(seed, (M, K), 1.5))
+    w_codes, w_scale = F8.quantise_rows(synth.normal(seed + 1, (N, K), 1.0 / np.sqrt(K)))
+    b = synth.normal(seed + 2, (N,), 0.1)
+    ref = O.linear(F8.dequantise_rows(a_codes, a_scale), F8.dequantise_rows(w_codes, w_scale), b.astype(np.float64))
+    if epi == 2:
+        ref = O.gelu(ref)
+    args = [dev(a_codes), dev(a_scale), dev(w_codes), dev(w_scale), dev(b)]
+    for width in (128, 256):
+        if width > N:
+            continue
+        outs = []
+        for tile in (width, width | R.TILE_PAIR):
+            out = torch.zeros((M, N), dtype=torch.bfloat16, device="cuda")
+            R.op_linear_fp8(epi, *args[:5], out, M, N, K, tile)
+            torch.cuda.synchronize()
+            outs.append(out)
+        np.testing.assert_allclose(f64(outs[1]), ref, rtol=8e-3, atol=8e-3)
+        assert torch.equal(outs[0], outs[1])
+    assert R.take_device_error() == 0
 
 
 # --------------------------------------------------------------- attention
