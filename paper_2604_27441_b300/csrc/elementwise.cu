@@ -192,21 +192,33 @@ struct PeArgs {
   int Hp, Wp, D, part;
 };
 
-__global__ void add_pe_kernel(float* __restrict__ x, long long total, const __grid_constant__ PeArgs a) {
-  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (idx >= total) return;
-  const int d = static_cast<int>(idx % a.D);
-  const long long n = idx / a.D;
-  const int s = static_cast<int>(n / (a.Hp * a.Wp));
-  const int rem = static_cast<int>(n % (a.Hp * a.Wp));
-  const int which = d / a.part;
-  const int j = d % a.part;
+// One thread per (token, part, i < part / 2): sin(pos w_i) goes to column
+// part * which + i and cos(pos w_i) to column part * which + part / 2 + i, both
+// from one sincosf.  The frequencies are staged in shared memory (indexing the
+// parameter array per lane would serialise the warp's constant loads).
+__global__ void add_pe_kernel(float* __restrict__ x, int rows, const __grid_constant__ PeArgs a) {
+  __shared__ float om[128];
   const int half = a.part / 2;
+  for (int i = threadIdx.x; i < half; i += blockDim.x) om[i] = a.omega[i];
+  __syncthreads();
+  const int per_row = 3 * half;
+  const int idx = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+  if (idx >= rows * per_row) return;
+  const int n = idx / per_row;
+  const int r = idx - n * per_row;
+  const int which = r / half;
+  const int i = r - which * half;
+  const int hw = a.Hp * a.Wp;
+  const int s = n / hw;
+  const int rem = n - s * hw;
   const int tau = a.taus_dev ? __ldg(a.taus_dev + s) : a.taus[s];
   const float pos = which == 0 ? static_cast<float>(tau) : which == 1 ? static_cast<float>(rem / a.Wp)
-                                                                            : static_cast<float>(rem % a.Wp);
-  const float arg = pos * a.omega[j % half];
-  x[idx] += (j < half) ? sinf(arg) : cosf(arg);
+                                                                       : static_cast<float>(rem % a.Wp);
+  float sv, cv;
+  sincosf(pos * om[i], &sv, &cv);
+  float* row = x + static_cast<size_t>(n) * a.D + which * a.part;
+  row[i] += sv;
+  row[half + i] += cv;
 }
 
 // ------------------------------------------------------------ LayerNorm --
@@ -639,9 +651,11 @@ cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, 
   for (int i = 0; i < a.part / 2; ++i) a.omega[i] = static_cast<float>(pow(10000.0, -2.0 * i / a.part));
   if (!taus_dev)
     for (int s = 0; s < slots; ++s) a.taus[s] = taus[s];
-  const long long total = static_cast<long long>(slots) * Hp * Wp * D;
-  if (total == 0) return cudaSuccess;
-  add_pe_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(x, total, a);
+  const long long rows = static_cast<long long>(slots) * Hp * Wp;
+  const long long threads = rows * (D / 2);
+  if (threads == 0) return cudaSuccess;
+  if (threads > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+  add_pe_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(x, static_cast<int>(rows), a);
   return cudaGetLastError();
 }
 
