@@ -4,29 +4,28 @@
 // no token dropping), computed flash-style with an online softmax.
 //
 // One CTA owns two 128-row query tiles (256 queries) of one head of one
-// segment; both tiles share every K/V tile it streams in (96 keys each).  TMA
+// segment; both tiles share every K/V tile it streams in (128 keys each).  TMA
 // reads the head's 64-column slices of Q, K and V straight out of the qkv
 // matrix [M][3D] (128-byte swizzle), so no head-split pass is needed.  Per
 // K/V tile j and query tile t:
-//   S_t(j) = Q_t K_j^T         tcgen05.mma M=128 N=96 K=64 -> TMEM region j%2
-//   P_t(j) = exp2(S c - m_t)   softmax warpgroup t, bf16, written over the
-//                              S_t(j) columns it has just read (tcgen05.st)
-//   O_t  += P_t(j) V_j         tcgen05.mma M=128 N=64 K=96, A = P from TMEM,
+//   S_t(j) = Q_t K_j^T         tcgen05.mma M=128 N=128 K=64 -> the S columns
+//   P_t(j) = exp2(S c - m_t)   softmax warpgroup t, bf16, into the P columns
+//   O_t  += P_t(j) V_j         tcgen05.mma M=128 N=64 K=128, A = P from TMEM,
 //                              V read N-major from shared memory
-// Each query tile has two S/P regions (96 columns each) and O (64 columns):
-// 256 of TMEM's 512 columns.  S_t(j+2) reuses region j%2 once PV_t(j) has
-// finished, so S runs up to two tiles ahead and the softmax never waits for
-// the previous PV (only a rescale of O does, and rescales are rare: the
-// running row maximum m_t only moves when a row's maximum grows by more than
-// 2^8, so P stays below 256; the result is the same softmax).
+// Each query tile has S (128 columns), P (64: bf16 pairs) and O (64): 256 of
+// TMEM's 512 columns.  S and P live apart, so S_t(j+1) is issued as soon as the
+// softmax has loaded S_t(j) into registers (it runs during that block's
+// exponentials) and PV_t(j) during the next block's; the softmax only waits
+// for PV_t(j-1) before it writes P_t(j), by which time it has finished.  A
+// rescale of O happens only when a row's maximum grows by more than 2^8 (P
+// stays below 256; the result is the same softmax).
 //
 // Warp roles (352 threads): warp 0 TMA, warp 1 TMEM allocator + MMA issuer
 // of tile 0, warps 2..5 softmax of tile 0, warps 6..9 softmax of tile 1 (warp
 // w owns rows 32*(w%4) .. +31 of its tile, the TMEM lanes it may access),
 // warp 10 MMA issuer of tile 1.  Handoffs: K/V tiles, S ready and PV done are
-// mbarriers (TMA transaction counts, tcgen05.commit); P ready is a named
-// barrier on which the MMA warp waits suspended, so no polling thread takes
-// issue slots from the softmax warps of its SM sub-partition.
+// mbarriers (TMA transaction counts, tcgen05.commit); S free and P ready are
+// named barriers on which the MMA warp waits suspended.
 #include <algorithm>
 
 #include "common.cuh"
@@ -38,18 +37,19 @@ namespace {
 
 constexpr int kQ = 128;
 constexpr int kTiles = 2;  // query tiles per CTA
-constexpr int kKV = 96;    // keys per K/V tile
+constexpr int kKV = 128;   // keys per K/V tile
 constexpr int kHD = 64;
-constexpr int kKvStages = 6;
-constexpr int kBoxRows = 32;  // TMA box height: Q = 4 boxes, a K or V tile = 3
+constexpr int kKvStages = 5;
+constexpr int kBoxRows = 32;  // TMA box height: Q = 4 boxes, a K or V tile = 4
 constexpr int kThreads = 64 + kTiles * 128 + 32;  // + the second tile's MMA warp
 constexpr int kQBytes = kQ * kHD * 2;    // 16 KB: 128 rows x 128 B
-constexpr int kKVBytes = kKV * kHD * 2;  // 12 KB
+constexpr int kKVBytes = kKV * kHD * 2;  // 16 KB
 constexpr int kBoxBytes = kBoxRows * kHD * 2;
 constexpr int kSmemBytes = 1024 + kQBytes * kTiles + 2 * kKVBytes * kKvStages + 1024;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kTileCols = 256;   // per tile: S/P regions at 0 and 96, O at 192
-constexpr uint32_t kRegionCols = 96;
+constexpr uint32_t kTileCols = 256;   // per tile: S at 0 (128 columns), P at 128 (64), O at 192 (64)
+constexpr uint32_t kSCol = 0;
+constexpr uint32_t kPCol = 128;
 constexpr uint32_t kOCol = 192;
 constexpr float kRescaleLog2 = 8.0f;  // rescale once a row max grows by more than 2^8
 
@@ -107,16 +107,19 @@ REVO_DEVI void exp_chunk(const uint32_t (&v)[32], uint64_t c2, uint64_t negm2, u
   }
 }
 
-// P_t(j) handoff from the softmax warpgroup of tile t to its MMA warp: named
-// barrier 1 + 2 t + (j & 1), 128 softmax threads arrive, the 32 threads of
-// the MMA warp wait (suspended in hardware: a polling MMA thread would take
-// issue and MIO slots from the softmax warps of its SM sub-partition).
-// Alternating by K/V tile parity keeps the arrivals for j + 2 (which need
-// S(j + 2), issued after the wait for j) from mixing with those for j.
-constexpr uint32_t kPReadyThreads = 128 + 32;
-REVO_DEVI uint32_t p_ready_id(int t, int j) { return 1u + 2u * static_cast<uint32_t>(t) + (static_cast<uint32_t>(j) & 1u); }
-REVO_DEVI void p_ready_arrive(uint32_t id) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kPReadyThreads) : "memory"); }
-REVO_DEVI void p_ready_wait(uint32_t id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kPReadyThreads) : "memory"); }
+// Handoffs from the softmax warpgroup of tile t to its MMA warp, on named
+// barriers (128 softmax threads arrive, the 32 threads of the MMA warp wait
+// suspended in hardware: a polling MMA thread would take issue and MIO slots
+// from the softmax warps of its SM sub-partition).  S-free (1 + 2 t): S(j) is
+// in the softmax registers, the S columns may take S(j + 1).  P-ready (2 + 2 t):
+// P(j) is in the P columns.  One barrier of each kind per tile suffices: the
+// arrivals for j + 1 need S(j + 1) (issued after the MMA warp passed S-free(j))
+// and, for P-ready, PV(j) (issued after it passed P-ready(j)).
+constexpr uint32_t kSoftmaxPlusMma = 128 + 32;
+REVO_DEVI uint32_t s_free_id(int t) { return 1u + 2u * static_cast<uint32_t>(t); }
+REVO_DEVI uint32_t p_ready_id(int t) { return 2u + 2u * static_cast<uint32_t>(t); }
+REVO_DEVI void bar_arrive_named(uint32_t id, uint32_t n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+REVO_DEVI void bar_sync_named(uint32_t id, uint32_t n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 // Producer wait for a free K/V stage: polls with a short sleep in between
 // (the ring runs kKvStages tiles ahead, so a late wake-up costs nothing),
@@ -145,27 +148,21 @@ REVO_DEVI float reduce8_sum(const float (&a)[8]) {
   return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
-REVO_DEVI void scale_chunk(uint32_t (&v)[32], float a) {
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __float_as_uint(__uint_as_float(v[i]) * a);
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
     attn_tc_kernel(const __grid_constant__ CUtensorMap tm, __nv_bfloat16* __restrict__ out,
                    const __grid_constant__ TcAttnParams P, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sQ = smem;                        // kTiles x 16 KB
-  uint8_t* sK = sQ + kTiles * kQBytes;       // kKvStages x 12 KB
-  uint8_t* sV = sK + kKvStages * kKVBytes;   // kKvStages x 12 KB
+  uint8_t* sK = sQ + kTiles * kQBytes;       // kKvStages x 16 KB
+  uint8_t* sV = sK + kKvStages * kKVBytes;   // kKvStages x 16 KB
   uint64_t* bars = reinterpret_cast<uint64_t*>(sV + kKvStages * kKVBytes);
   uint64_t* q_full = bars;
   uint64_t* kv_full = q_full + 1;
   uint64_t* kv_empty = kv_full + kKvStages;
-  uint64_t* s_full = kv_empty + kKvStages;  // [kTiles][2] S_t(j) ready in region j%2
-  uint64_t* p_done = s_full + 2 * kTiles;   // [kTiles] PV_t(j) accumulated (O stable)
-  uint64_t* p_reg = p_done + kTiles;        // [kTiles][2] PV_t(j) done: region j%2 free
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(p_reg + 2 * kTiles);
+  uint64_t* s_full = kv_empty + kKvStages;  // [kTiles] S_t(j) in the S columns
+  uint64_t* pv_done = s_full + kTiles;      // [kTiles] PV_t(j) accumulated: P columns free, O stable
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pv_done + kTiles);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -193,11 +190,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&kv_empty[s], ntiles);  // one release per query tile's MMA thread
     }
     for (int t = 0; t < kTiles; ++t) {
-      mbar_init(&s_full[2 * t], 1);
-      mbar_init(&s_full[2 * t + 1], 1);
-      mbar_init(&p_done[t], 1);
-      mbar_init(&p_reg[2 * t], 1);
-      mbar_init(&p_reg[2 * t + 1], 1);
+      mbar_init(&s_full[t], 1);
+      mbar_init(&pv_done[t], 1);
     }
     fence_mbarrier_init();
   }
@@ -229,13 +223,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1 || warp == kThreads / 32 - 1) {
     // One MMA warp per query tile (warp 1: tile 0, the last warp: tile 1);
-    // lane 0 issues in a fixed order with blocking waits on its own tile's
-    // barriers: S(0), S(1), then per K/V tile j: PV(j) once P(j) is written
-    // (the whole warp waits on the P-ready barrier), S(j+2) once PV(j) has
-    // finished with region j%2.  The two warps' MMAs touch disjoint TMEM
-    // columns.  Every wait is on the phase the other side cannot pass before
-    // this warp's next issue, so no barrier runs ahead.  The warp takes part
-    // in the P-ready barrier for every j, also after a failed wait.
+    // lane 0 issues, in a fixed order per K/V tile j: S(j+1) once the softmax
+    // has read S(j) out of the S columns (S-free barrier), PV(j) once it has
+    // written P(j) (P-ready barrier).  The whole warp takes part in both named
+    // barriers for every j, also after a failed wait.
     const int t = warp == 1 ? 0 : 1;
     if (t < ntiles) {
       constexpr uint32_t kIdS = idesc_bf16(kQ, kKV);
@@ -246,43 +237,39 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t k_lo = sw128_lo(smem_u32(sK + (j % kKvStages) * kKVBytes));
 #pragma unroll
         for (int kk = 0; kk < kHD / 16; ++kk)  // 16 dims: 32 B of the swizzled rows
-          mma_f16_hl(tbase + (j & 1) * kRegionCols, q_lo + kk * 2, kSw128Hi, k_lo + kk * 2, kSw128Hi, kIdS,
-                     kk > 0 ? 1u : 0u);
-        mma_commit(&s_full[2 * t + (j & 1)]);
+          mma_f16_hl(tbase + kSCol, q_lo + kk * 2, kSw128Hi, k_lo + kk * 2, kSw128Hi, kIdS, kk > 0 ? 1u : 0u);
+        mma_commit(&s_full[t]);
       };
       bool ok = true;
       if (lane == 0) {
-        ok = mbar_wait(q_full, 0, err, kDevTimeoutMma);
-        for (int j = 0; ok && j < 2 && j < nkv; ++j) {
-          ok = mbar_wait(&kv_full[j % kKvStages], (j / kKvStages) & 1, err, kDevTimeoutMma);
-          if (ok) {
-            tc_fence_after();
-            issue_s(j);
-          }
+        ok = mbar_wait(q_full, 0, err, kDevTimeoutMma) && (nkv == 0 || mbar_wait(&kv_full[0], 0, err, kDevTimeoutMma));
+        if (ok && nkv > 0) {
+          tc_fence_after();
+          issue_s(0);
         }
       }
       for (int j = 0; j < nkv; ++j) {
         __syncwarp();
-        p_ready_wait(p_ready_id(t, j));
-        if (lane != 0 || !ok) continue;
-        tc_fence_after();
-        const uint32_t v_lo = sw128_lo(smem_u32(sV + (j % kKvStages) * kKVBytes));
-        const uint32_t p_tmem = tbase + (j & 1) * kRegionCols;
-#pragma unroll
-        for (int kk = 0; kk < kKV / 16; ++kk)  // 16 keys: 8 TMEM columns of P, 2048 B of V
-          mma_f16_tmem_a_hl(tbase + kOCol, p_tmem + kk * 8, v_lo + kk * 128, kSw128Hi, kIdPV,
-                            (j > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(&p_done[t]);
-        mma_commit(&p_reg[2 * t + (j & 1)]);
-        mma_commit(&kv_empty[j % kKvStages]);  // this tile is done with K_j, V_j
-        const int jn = j + 2;
-        if (jn < nkv) {
-          ok = mbar_wait(&p_reg[2 * t + (j & 1)], (j >> 1) & 1, err, kDevTimeoutMma) &&
-               mbar_wait(&kv_full[jn % kKvStages], (jn / kKvStages) & 1, err, kDevTimeoutMma);
+        bar_sync_named(s_free_id(t), kSoftmaxPlusMma);
+        if (lane == 0 && ok && j + 1 < nkv) {
+          const int jn = j + 1;
+          ok = mbar_wait(&kv_full[jn % kKvStages], (jn / kKvStages) & 1, err, kDevTimeoutMma);
           if (ok) {
             tc_fence_after();
             issue_s(jn);
           }
+        }
+        __syncwarp();
+        bar_sync_named(p_ready_id(t), kSoftmaxPlusMma);
+        if (lane == 0 && ok) {
+          tc_fence_after();
+          const uint32_t v_lo = sw128_lo(smem_u32(sV + (j % kKvStages) * kKVBytes));
+#pragma unroll
+          for (int kk = 0; kk < kKV / 16; ++kk)  // 16 keys: 8 TMEM columns of P, 2048 B of V
+            mma_f16_tmem_a_hl(tbase + kOCol, tbase + kPCol + kk * 8, v_lo + kk * 128, kSw128Hi, kIdPV,
+                              (j > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&pv_done[t]);
+          mma_commit(&kv_empty[j % kKvStages]);  // this tile is done with K_j, V_j
         }
       }
       __syncwarp();
@@ -294,31 +281,40 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (t < ntiles) {
       const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
       const uint32_t tbase = tmem + t * kTileCols + lane_off;
+      const uint32_t s_addr = tbase + kSCol;
+      const uint32_t p_addr = tbase + kPCol;
       const uint32_t o_addr = tbase + kOCol;
       const uint64_t c2 = pk2(P.scale_log2, P.scale_log2);
       const float c = P.scale_log2;
       float m = -INFINITY;  // the maximum P is taken relative to (log2 units)
       float l = 0.f;
       bool ok = true;
-
       int j = 0;
+      int passed = 0;  // named barriers of tile j already arrived at (0, 1: S-free)
       for (; j < nkv; ++j) {
-        const uint32_t s_addr = tbase + (j & 1) * kRegionCols;
-        if (!mbar_wait_warp(&s_full[2 * t + (j & 1)], (j >> 1) & 1, err, kDevTimeoutSoftmax, lane)) {
+        passed = 0;
+        if (!mbar_wait_warp(&s_full[t], j & 1, err, kDevTimeoutSoftmax, lane)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        uint32_t v0[32], v1[32], v2[32];
+        uint32_t v0[32], v1[32], v2[32], v3[32];
         tmem_ld32(s_addr, v0);
         tmem_ld32(s_addr + 32, v1);
         tmem_ld32(s_addr + 64, v2);
+        tmem_ld32(s_addr + 96, v3);
         tmem_wait_ld();
+        // S(j) is in registers: the S columns may take S(j+1).
+        tc_fence_before();
+        __syncwarp();
+        bar_arrive_named(s_free_id(t), kSoftmaxPlusMma);
+        passed = 1;
         const int nvalid = min(kKV, s1 - (s0 + (kv0 + j) * kKV));
         if (nvalid < kKV) {
           mask_chunk(v0, 0, nvalid);
           mask_chunk(v1, 32, nvalid);
           mask_chunk(v2, 64, nvalid);
+          mask_chunk(v3, 96, nvalid);
         }
         float mx8[8];
 #pragma unroll
@@ -326,6 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         max_chunk(v0, mx8);
         max_chunk(v1, mx8);
         max_chunk(v2, mx8);
+        max_chunk(v3, mx8);
         const float cand = reduce8_max(mx8) * c;
         const float m_new = cand > m + kRescaleLog2 ? cand : m;
         const float alpha = ex2_approx(m - m_new);  // 1 when m is kept, 0 on the first tile
@@ -333,57 +330,64 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int i = 0; i < 4; ++i) sum2[i] = 0ull;  // +0.0f pairs
         const uint64_t negm2 = pk2(-m_new, -m_new);
+        // Keys 0..63 first, so that their registers are free before the
+        // second half is computed; each half is stored as soon as the P
+        // columns are free.
         uint32_t pk0[32], pk1[32];
         exp_chunk(v0, c2, negm2, pk0, 0, sum2);
         exp_chunk(v1, c2, negm2, pk0, 16, sum2);
-        exp_chunk(v2, c2, negm2, pk1, 0, sum2);
-        float sum8[8];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) unpk2(sum2[i], sum8[2 * i], sum8[2 * i + 1]);
-        const float sum = reduce8_sum(sum8);
-        // P over the S columns just read (S_t(j+2) waits for PV_t(j)).
-        tmem_st32(s_addr, pk0);
-        tmem_st16(s_addr + 32, pk1);
-        if (j > 0 && __any_sync(0xffffffffu, alpha != 1.f)) {
-          // O must hold every PV up to j-1 before it is rescaled.  p_done has
-          // j-1 or j completions here (S(j) waited for PV(j-2); PV(j) needs
-          // this block's P), so the parity of completion j-1 is unambiguous.
-          if (!mbar_wait_warp(&p_done[t], (j - 1) & 1, err, kDevTimeoutSoftmax, lane)) {
+        if (j > 0) {
+          // PV(j-1) must have read P(j-1) before P(j) replaces it, and O must
+          // hold it before a rescale.  pv_done has j-1 or j completions here
+          // (PV(j) needs this block's P), so the parity is unambiguous.
+          if (!mbar_wait_warp(&pv_done[t], (j - 1) & 1, err, kDevTimeoutSoftmax, lane)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          tmem_ld32(o_addr, v0);
-          tmem_ld32(o_addr + 32, v1);
-          tmem_wait_ld();
-          scale_chunk(v0, alpha);
-          scale_chunk(v1, alpha);
-          tmem_st32(o_addr, v0);
-          tmem_st32(o_addr + 32, v1);
+          if (__any_sync(0xffffffffu, alpha != 1.f)) {
+            // Rare: O *= alpha, 16 columns at a time (few live registers).
+#pragma unroll 1
+            for (int c16 = 0; c16 < kHD; c16 += 16) {
+              uint32_t o16[16];
+              tmem_ld16(o_addr + c16, o16);
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 16; ++i) o16[i] = __float_as_uint(__uint_as_float(o16[i]) * alpha);
+              tmem_st16(o_addr + c16, o16);
+              tmem_wait_st();
+            }
+          }
         }
+        tmem_st32(p_addr, pk0);
+        exp_chunk(v2, c2, negm2, pk1, 0, sum2);
+        exp_chunk(v3, c2, negm2, pk1, 16, sum2);
+        tmem_st32(p_addr + 32, pk1);
+        float sum8[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) unpk2(sum2[i], sum8[2 * i], sum8[2 * i + 1]);
+        const float sum = reduce8_sum(sum8);
         tmem_wait_st();
         l = l * alpha + sum;
         m = m_new;
         tc_fence_before();
         __syncwarp();
-        p_ready_arrive(p_ready_id(t, j));
+        bar_arrive_named(p_ready_id(t), kSoftmaxPlusMma);
       }
-      // After a failed wait: take part in the remaining P-ready barriers,
-      // waiting on each (arriving ahead could complete a later phase early).
+      // After a failed wait: take part in the remaining named barriers in
+      // order, waiting on each (arriving ahead could complete a later phase).
       for (; j < nkv; ++j) {
         __syncwarp();
-        p_ready_wait(p_ready_id(t, j));
+        if (passed == 0) bar_sync_named(s_free_id(t), kSoftmaxPlusMma);
+        passed = 0;
+        __syncwarp();
+        bar_sync_named(p_ready_id(t), kSoftmaxPlusMma);
       }
-      // The last PV: waited on its region's barrier.  p_done may still lack
-      // two completions here (the softmax can finish while PV(nkv-2) is
-      // pending), where its parity would be ambiguous; the region barrier has
-      // already seen PV(nkv-3) (S(nkv-1) waited for it), so it lacks at most
-      // the awaited one.  Its commit also covers every earlier MMA.
+      // The last PV: completion nkv-1 of pv_done (nothing later is issued).
       const int last = nkv - 1;
       uint32_t o0[32], o1[32];
       bool have_o = false;
-      if (ok && nkv > 0 &&
-          mbar_wait_warp(&p_reg[2 * t + (last & 1)], (last >> 1) & 1, err, kDevTimeoutSoftmax, lane)) {
+      if (ok && nkv > 0 && mbar_wait_warp(&pv_done[t], last & 1, err, kDevTimeoutSoftmax, lane)) {
         tc_fence_after();
         tmem_ld32(o_addr, o0);
         tmem_ld32(o_addr + 32, o1);
