@@ -44,7 +44,7 @@ PRECISIONS = {"bf16": lambda R: R.BF16, "fp32": lambda R: R.FP32, "fp8": lambda 
 DTYPE_NAMES = {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3 (encoder fc1; per-token x per-channel scales) + bf16"}
 # DRAM bytes (read + write) of one attn_tc_kernel launch at N = 3600, 12 heads,
 # from an ncu capture of the current kernel version (None once it changes).
-ATTN_DRAM_BYTES_PER_LAUNCH = None
+ATTN_DRAM_BYTES_PER_LAUNCH = 16629760
 
 
 def flops_per_model(C: int, h: int, w: int) -> dict:
