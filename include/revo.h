@@ -469,6 +469,16 @@ REVO_API revo_status revo_op_blend(int channels, int p, int height, int width, c
  */
 REVO_API int revo_op_take_device_error(void);
 
+/*
+ * Diagnostic of the bounded waits: launches one thread that waits on a
+ * barrier nothing completes.  After `limit_cycles` SM clocks (1000 ..
+ * 2e9) the wait gives up, records code 5 in the step-level device error word
+ * (read it with revo_op_take_device_error) and the kernel returns; the device
+ * stays usable.  The pipeline kernels give up the same way (codes 1-4).
+ * Errors: REVO_EINVAL (limit out of range), REVO_ECUDA.
+ */
+REVO_API revo_status revo_op_wait_selftest(long long limit_cycles, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,7 @@ _SIGS = {
                                 C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
                                 C.c_void_p]),
     "revo_op_take_device_error": (C.c_int, []),
+    "revo_op_wait_selftest": (C.c_int, [C.c_longlong, C.c_void_p]),
     "revo_op_quantize_rows_e4m3": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "revo_frame_metrics_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
     "revo_render_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int]),
@@ -294,6 +295,11 @@ def op_blend(channels, p, height, width, head, decoded, pitch_bytes, mask, mask_
 
 def take_device_error() -> int:
     return lib().revo_op_take_device_error()
+
+
+def op_wait_selftest(limit_cycles, stream=None):
+    """One bounded wait that runs out: sets device error code 5 (see take_device_error)."""
+    return _check(lib().revo_op_wait_selftest(int(limit_cycles), _stream(stream)), "revo_op_wait_selftest")
 
 
 # ------------------------------------------------------------------ context

@@ -19,6 +19,7 @@ enum DeviceError : int {
   kDevTimeoutMma = 2,
   kDevTimeoutEpilogue = 3,
   kDevTimeoutSoftmax = 4,
+  kDevTimeoutSelftest = 5,  // revo_op_wait_selftest
 };
 
 // A wait gives up after this many SM clocks (about 1-2 s at B300 clocks), sets
@@ -79,7 +80,7 @@ REVO_DEVI bool mbar_test(uint32_t bar, uint32_t parity) {
 
 // Waits for the phase of the given parity to complete.  Returns false (after
 // recording `code` in *err) if the wait ran out or another role already failed.
-REVO_DEVI bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+REVO_DEVI bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code, long long limit = kWaitLimitCycles) {
   const uint32_t a = smem_u32(bar);
   if (mbar_try_wait(a, parity)) return true;
   const long long t0 = clock64();
@@ -87,7 +88,7 @@ REVO_DEVI bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
     if (mbar_try_wait(a, parity)) return true;
     if ((it & 255u) == 0) {
       if (*reinterpret_cast<volatile int*>(err) != 0) return false;
-      if (clock64() - t0 > kWaitLimitCycles) {
+      if (clock64() - t0 > limit) {
         atomicCAS(err, 0, code);
         return false;
       }

@@ -73,6 +73,39 @@ extern "C" {
 
 const char* revo_last_error(void) { return g_last_error.c_str(); }
 
+}  // extern "C"
+
+namespace revo {
+namespace {
+// One thread waits on an mbarrier that nothing completes: the bounded wait
+// every pipeline kernel uses gives up after `limit` clocks, records its code
+// in the error word and returns.
+__global__ void wait_selftest_kernel(int* err, long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbarrier_init();
+  mbar_wait(&bar, 0, err, kDevTimeoutSelftest, limit);
+}
+}  // namespace
+}  // namespace revo
+
+extern "C" {
+
+revo_status revo_op_wait_selftest(long long limit_cycles, void* stream) {
+  if (limit_cycles < 1000 || limit_cycles > kWaitLimitCycles) {
+    set_last_error("revo_op_wait_selftest: limit_cycles outside [1000, %lld]", kWaitLimitCycles);
+    return REVO_EINVAL;
+  }
+  int* err = op_error_word();
+  if (!err) {
+    set_last_error("revo_op_wait_selftest: no device error word");
+    return REVO_ECUDA;
+  }
+  wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(err, limit_cycles);
+  return cuda_status(cudaGetLastError(), "revo_op_wait_selftest");
+}
+
 int revo_op_take_device_error(void) {
   int* w = op_error_word();
   if (!w) return -1;

@@ -575,3 +575,24 @@ def test_render_rgbd_bit_exact(case):
     np.testing.assert_array_equal(out_d.cpu().numpy().view(np.uint16), ref_d)
     np.testing.assert_array_equal(out_rgb.cpu().numpy(), ref_rgb)
     assert (ref_d > 0).mean() > 0.3  # the view actually shows the scene
+
+
+# ------------------------------------------------------------ bounded waits
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable():
+    """A wait that nothing completes gives up after its limit, records its
+    code in the device error word and returns; the next kernels run normally."""
+    assert R.take_device_error() == 0
+    R.op_wait_selftest(2_000_000)  # about 1 ms of SM clocks
+    torch.cuda.synchronize()
+    assert R.take_device_error() == 5
+    assert R.take_device_error() == 0  # taking the word clears it
+    M, D = 64, 192
+    x = synth.normal(9, (M, D))
+    out = torch.zeros((M, D), dtype=torch.float32, device="cuda")
+    R.op_layernorm(dev(x), dev(np.ones(D, np.float32)), dev(np.zeros(D, np.float32)), out, M, D, 0)
+    torch.cuda.synchronize()
+    ref = O.layer_norm(x.astype(np.float64), np.ones(D), np.zeros(D))
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=5e-5)
+    with pytest.raises(R.RevoError):
+        R.op_wait_selftest(10)  # below the accepted range: rejected on the host
