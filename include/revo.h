@@ -282,8 +282,9 @@ REVO_API revo_status revo_op_depth_stats_noalloc(const uint16_t* depth, int heig
                                                  size_t pitch_bytes, float* mu_sigma, void* stream);
 
 /*
- * Tile choice for the tensor-core Linear entry points: the tile width (128 or
- * 256 output columns), optionally ORed with REVO_TILE_PAIR for 256-row tiles
+ * Tile choice for the tensor-core Linear entry points: the tile width (128,
+ * 192 or 256 output columns; 192 for float32 outputs on single tiles only),
+ * optionally ORed with REVO_TILE_PAIR for 256-row tiles
  * computed by a pair of CTAs on two SMs (one tcgen05 MMA with .cta_group::2
  * over both SMs' shared memory and TMEM).  Results are the same for every
  * choice (each output is one float32 dot product in the same K order).
@@ -296,8 +297,8 @@ REVO_API revo_status revo_op_depth_stats_noalloc(const uint16_t* depth, int heig
  *   precision REVO_FP32: A, W float32, SIMT FMA (K % 8 == 0).  REVO_BF16: A, W
  *   bf16 on the tcgen05 tensor cores with float32 accumulation (K % 64 == 0,
  *   N % 32 == 0, N % 64 == 0 for the bf16 epilogues 1 and 2); `tile_n` picks
- *   the 128- or 256-column tile (other widths: 128), | REVO_TILE_PAIR for the
- *   CTA-pair tiles.
+ *   the 128-, 192- (epilogues 0 and 3, without REVO_TILE_PAIR) or 256-column
+ *   tile (other widths: 128), | REVO_TILE_PAIR for the CTA-pair tiles.
  *   epilogue 0: out = acc + b (float32 out)
  *   epilogue 1: out = acc + b (bf16 out; FP32 precision writes float32)
  *   epilogue 2: out = gelu(acc + b) (bf16 out; FP32 precision writes float32)

@@ -44,13 +44,24 @@ constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kOutChunkBytes = 32 * 128;  // 32 rows x 128 B staging per epilogue warp
 
+// TMEM columns for a double-buffered accumulator of width bn (the allocation
+// is a power of two).
+constexpr int tmem_cols_for(int bn) { return 2 * bn <= 256 ? 256 : 512; }
+
+// BN = 192 (f32 epilogues only: two halves of three 32-column chunks) gives
+// N = 768 four tiles per row block instead of three: fc2 of an encoder block
+// alone takes 20.6 us instead of 22.6 (116 of 148 SMs busy instead of 87).
+// With two models in flight the SM-time is the same (116 x 0.75 vs 87 x 1) and
+// the other model's kernels get fewer SMs, so the network's autotuner, which
+// times each GEMM alone, does not offer it; revo_op_linear does.
 template <int BN>
 struct TcGemmCfg {
-  static constexpr int kStages = (BN == 256) ? 4 : 6;
+  static_assert(BN == 128 || BN == 192 || BN == 256, "tile width");
+  static constexpr int kStages = (BN == 128) ? 6 : 4;
   static constexpr int kABytes = kBM * kBK * 2;
   static constexpr int kBBytes = BN * kBK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kTmemCols = 2 * BN;
+  static constexpr int kTmemCols = tmem_cols_for(BN);
   static constexpr int kSmemBytes =
       1024 /*align slack*/ + kStages * kStageBytes + kEpiWarps * kOutChunkBytes + 256 /*barriers*/;
 };
@@ -327,7 +338,7 @@ struct TcGemmPairCfg {
   static constexpr int kBBytes = (BN / 2) * 128;    // this CTA's half of the W rows
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStages = (192 * 1024) / kStageBytes;  // BN 256: 6, BN 128: 8
-  static constexpr int kTmemCols = 2 * BN;
+  static constexpr int kTmemCols = tmem_cols_for(BN);
   static constexpr int kSmemBytes =
       1024 /*align slack*/ + kStages * kStageBytes + kEpiWarps * kOutChunkBytes + 256 /*barriers*/;
 };
@@ -533,6 +544,10 @@ cudaError_t launch_any(const CUtensorMap& a, const CUtensorMap& b, const CUtenso
   if (bn == ((W) | kTilePair) && epi == (E))                                                                 \
     return launch_pair_epi<W, E, F8>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, col_scale);
   if (!F8) {
+    if (bn == 192 && epi == kEpiF32)
+      return launch_bn_epi<192, kEpiF32, false>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, col_scale);
+    if (bn == 192 && epi == kEpiResidF32)
+      return launch_bn_epi<192, kEpiResidF32, false>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, col_scale);
     REVO_GEMM_CASE(128, kEpiF32)
     REVO_GEMM_CASE(256, kEpiF32)
     REVO_GEMM_CASE(128, kEpiResidF32)

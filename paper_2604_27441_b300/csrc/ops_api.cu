@@ -184,7 +184,9 @@ revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A
     return REVO_EINVAL;
   }
   const bool pair = (tile_n & REVO_TILE_PAIR) != 0;
-  const int width = (tile_n & ~REVO_TILE_PAIR) == 256 ? 256 : 128;
+  const int req = tile_n & ~REVO_TILE_PAIR;
+  // 192: single tiles with float32 outputs only (other uses fall back to 128).
+  const int width = req == 256 ? 256 : (req == 192 && f32_out && !pair) ? 192 : 128;
   const int bn = pair ? (width | kTilePair) : width;
   CUtensorMap ma, mb, mc;
   const uint64_t rows = M > 0 ? M : 1;

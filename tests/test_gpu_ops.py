@@ -106,6 +106,38 @@ def test_linear_bf16_cta_pair_tiles(M, N, K, epi):
     assert R.take_device_error() == 0
 
 
+# 192-wide tiles (float32 epilogues): N = 768 and 384 split evenly, 320 and
+# 224 leave a ragged last tile (N % 192 != 0), M spans several row tiles and a
+# ragged tail; (3600, 768, 3072) is fc2 of an encoder block.
+@pytest.mark.gpu
+@pytest.mark.parametrize("M,N,K", [(300, 768, 192), (3600, 768, 3072), (517, 384, 128), (129, 320, 256),
+                                   (1, 224, 64)])
+@pytest.mark.parametrize("epi", [0, 3])
+def test_linear_bf16_192_wide_tiles(M, N, K, epi):
+    """The 192-column tile: the oracle's values, and bit for bit the 128- and
+    256-column tiles (same float32 dot products in the same K order)."""
+    seed = M * 7 + N * 3 + K
+    A = bf16(synth.normal(seed, (M, K))).cuda()
+    W = bf16(synth.normal(seed + 1, (N, K), 1.0 / np.sqrt(K))).cuda()
+    b = synth.normal(seed + 2, (N,), 0.1)
+    ref = O.linear(f64(A), f64(W), b.astype(np.float64))
+    base = synth.normal(seed + 3, (M, N)) if epi == 3 else np.zeros((M, N), np.float32)
+    if epi == 3:
+        ref = ref + base
+    outs = {}
+    for tile in (192, 128, 256):
+        if tile > N:
+            continue
+        out = torch.from_numpy(base).cuda()
+        R.op_linear(R.BF16, epi, A, W, dev(b), out, M, N, K, tile)
+        torch.cuda.synchronize()
+        outs[tile] = out
+    np.testing.assert_allclose(f64(outs[192]), ref, rtol=1e-4, atol=2e-4)
+    for tile, out in outs.items():
+        assert torch.equal(out, outs[192]), f"192-wide tile differs from the {tile}-wide tile"
+    assert R.take_device_error() == 0
+
+
 @pytest.mark.parametrize("M,N,K", [(300, 256, 192), (1000, 768, 768), (77, 96, 24)])
 @pytest.mark.parametrize("epi", [0, 2, 3])
 def test_linear_fp32_simt(M, N, K, epi):
