@@ -47,6 +47,14 @@ DTYPE_NAMES = {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3 (encoder fc1; per-tok
 ATTN_DRAM_BYTES_PER_LAUNCH = 16629760
 
 
+def workload_config(world: int, seq_len: int) -> dict:
+    """The headline workload, as both arms name it in `config`."""
+    return {"workload": f"{WORKLOAD} RGB uint8 + {WORKLOAD} depth uint16, batch 1, "
+                        "loss 5/10/20/40% (4 streams in turn)",
+            "model": "ViT-B enc-dec (768x12 / 384x4), k=5, T=2, p=16", "global_batch": world,
+            "seq_len": seq_len, "parallelism": f"replicas x{world}"}
+
+
 def flops_per_model(C: int, h: int, w: int) -> dict:
     """Algorithmic FLOPs of one forward (2 per multiply-add), exact savings applied:
     the pixel head runs on the target frame's rows of the last slot only."""
@@ -213,8 +221,7 @@ def run_reference(args) -> None:
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " RGB + " + WORKLOAD + " depth, batch 1", "model": "ViT-B enc-dec",
-                   "global_batch": 1},
+        "config": workload_config(1, flops_per_model(3, H, W)["N"]),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -489,10 +496,7 @@ def run_ours(args) -> None:
             "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[args.precision],
             "data": "synthetic (seeded RGB-D frames, Gilbert-Elliott slice loss, random-init ViT-B weights)",
-            "config": {"workload": f"{WORKLOAD} RGB uint8 + {WORKLOAD} depth uint16, batch 1, "
-                                   "loss 5/10/20/40% (4 streams in turn)",
-                       "model": "ViT-B enc-dec (768x12 / 384x4), k=5, T=2, p=16", "global_batch": world,
-                       "seq_len": fl["N"], "parallelism": f"replicas x{world}",
+            "config": {**workload_config(world, fl["N"]),
                        "launch": "kernels" if args.no_graphs else "CUDA graph replay per request-size pattern, "
                                  "autotuned GEMM tile widths",
                        "l2": "working set > L2: bf16 weights of both models (0.37 GB) stream every step"},
