@@ -80,6 +80,14 @@ struct Batch {
   int launches = 0;
 };
 
+// A retired batch's events and pinned error words, kept for the next batch:
+// creating events and pinned memory per frame costs host time, and freeing
+// pinned memory can synchronise the device.
+struct BatchRes {
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  int* err_host = nullptr;
+};
+
 struct TicketInfo {
   uint64_t batch = 0;  // 0 = still pending
   uint32_t stream_id = 0;
@@ -139,6 +147,7 @@ struct revo_ctx {
   uint64_t n_batches = 0, graph_replays = 0;
   size_t bytes = 0;
   std::vector<void*> allocs;
+  std::vector<revo::BatchRes> batch_pool;  // resources of retired batches
 };
 
 namespace revo {
@@ -178,7 +187,7 @@ bool batch_check(revo_ctx* c, Batch& b, bool block) {
     set_last_error("batch failed: %s", cudaGetErrorString(e));
   } else {
     float ms = 0.f;
-    if (b.ev_start) cudaEventElapsedTime(&ms, b.ev_start, b.ev_end);
+    if (b.lane >= 0 && b.ev_start) cudaEventElapsedTime(&ms, b.ev_start, b.ev_end);  // copy-only batches: 0
     b.device_ms = ms;
     if (b.err_host && (b.err_host[0] || b.err_host[1])) b.status = REVO_ETIMEDOUT;
   }
@@ -186,13 +195,42 @@ bool batch_check(revo_ctx* c, Batch& b, bool block) {
   return true;
 }
 
+void free_batch_res(const BatchRes& r) {
+  if (r.ev_start) cudaEventDestroy(r.ev_start);
+  if (r.ev_end) cudaEventDestroy(r.ev_end);
+  if (r.err_host) cudaFreeHost(r.err_host);
+}
+
+// Events and pinned error words for a new batch: a retired batch's, else new ones.
+cudaError_t acquire_batch_res(revo_ctx* c, Batch& b) {
+  BatchRes r;
+  if (!c->batch_pool.empty()) {
+    r = c->batch_pool.back();
+    c->batch_pool.pop_back();
+  } else {
+    cudaError_t e;
+    if ((e = cudaEventCreate(&r.ev_start)) != cudaSuccess || (e = cudaEventCreate(&r.ev_end)) != cudaSuccess ||
+        (e = cudaMallocHost(&r.err_host, 2 * sizeof(int))) != cudaSuccess) {
+      free_batch_res(r);
+      return e;
+    }
+  }
+  b.ev_start = r.ev_start;
+  b.ev_end = r.ev_end;
+  b.err_host = r.err_host;
+  b.err_host[0] = b.err_host[1] = 0;
+  return cudaSuccess;
+}
+
 void retire_if_empty(revo_ctx* c, uint64_t bid) {
   auto it = c->batches.find(bid);
   if (it == c->batches.end() || !it->second.tickets.empty() || !it->second.done) return;
   Batch& b = it->second;
-  if (b.ev_start) cudaEventDestroy(b.ev_start);
-  if (b.ev_end) cudaEventDestroy(b.ev_end);
-  if (b.err_host) cudaFreeHost(b.err_host);
+  const BatchRes r{b.ev_start, b.ev_end, b.err_host};
+  if (r.ev_start && r.ev_end && r.err_host)
+    c->batch_pool.push_back(r);
+  else
+    free_batch_res(r);
   c->batches.erase(it);
 }
 
@@ -283,10 +321,7 @@ revo_status launch_batch(revo_ctx* c, int count) {
   b.id = c->next_batch++;
   b.lane = lane;
   cudaError_t e;
-  if ((e = cudaEventCreate(&b.ev_start)) != cudaSuccess || (e = cudaEventCreate(&b.ev_end)) != cudaSuccess ||
-      (e = cudaMallocHost(&b.err_host, 2 * sizeof(int))) != cudaSuccess)
-    return cuda_status(e, "batch setup");
-  b.err_host[0] = b.err_host[1] = 0;
+  if ((e = acquire_batch_res(c, b)) != cudaSuccess) return cuda_status(e, "batch setup");
 
   std::vector<PlaneJob> jobs[2];
   std::vector<Pending> taken;
@@ -465,12 +500,8 @@ void revo_recover_destroy(revo_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   for (auto& kv : c->batches) batch_check(c, kv.second, true);
-  for (auto& kv : c->batches) {
-    Batch& b = kv.second;
-    if (b.ev_start) cudaEventDestroy(b.ev_start);
-    if (b.ev_end) cudaEventDestroy(b.ev_end);
-    if (b.err_host) cudaFreeHost(b.err_host);
-  }
+  for (auto& kv : c->batches) free_batch_res(BatchRes{kv.second.ev_start, kv.second.ev_end, kv.second.err_host});
+  for (const BatchRes& r : c->batch_pool) free_batch_res(r);
   if (c->copy_st) cudaStreamSynchronize(c->copy_st);
   for (int l = 0; l < c->n_lanes; ++l) {
     Lane& L = c->lanes[l];
@@ -658,7 +689,8 @@ revo_status revo_recover_submit(revo_ctx* c, const revo_request* r, uint64_t* ti
     Batch b;
     b.id = c->next_batch++;
     b.lane = -1;
-    cudaEventCreate(&b.ev_end);
+    cudaError_t e = acquire_batch_res(c, b);
+    if (e != cudaSuccess) return cuda_status(e, "clean frame batch");
     cudaEventRecord(b.ev_end, c->copy_st);
     cudaEventRecord(c->copy_ev, c->copy_st);
     c->copy_ev_valid = true;
