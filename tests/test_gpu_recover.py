@@ -327,6 +327,41 @@ def test_two_lanes_interleaved_streams():
             np.testing.assert_array_equal(x, y)
 
 
+def test_frames_in_flight_reuse_batch_resources():
+    """Two lanes with two frames in flight and clean-frame pushes in between:
+    retired batches hand their events and pinned error words to later ones
+    (copy-only batches of clean frames included), and every frame still
+    equals the same frame recovered alone, bit for bit."""
+    reqs = [synth.make_request(1040 + i, "320x240") for i in range(4)]
+    alone = []
+    with make_ctx(VITB, R.BF16, (240, 320)) as ctx:
+        for sid, (rgb, dep) in enumerate(reqs):
+            alone.append(run(ctx, sid, rgb, dep))
+    with make_ctx(VITB, R.BF16, (240, 320), lanes=2, use_graphs=1) as ctx:
+        keep = [push_refs(ctx, sid, *reqs[sid]) for sid in (0, 1)]
+        outs = [Outputs(rgb, dep) for rgb, dep in reqs]
+        inflight = []
+
+        def submit(sid):
+            inflight.append(ctx.submit(outs[sid].request(sid, *reqs[sid])))
+            if len(inflight) == 2:
+                assert ctx.poll(inflight.pop(0)).status == R.REVO_OK
+
+        for i in range(6):  # streams 0 and 1 only, two in flight
+            submit(i % 2)
+        keep += [push_refs(ctx, sid, *reqs[sid]) for sid in (2, 3)]  # copy-only batches while one is in flight
+        for i in range(12):
+            submit(i % 4)
+        while inflight:
+            assert ctx.poll(inflight.pop(0)).status == R.REVO_OK
+        st = ctx.stats()
+        assert st["pending"] == 0 and st["in_flight"] == 0
+        del keep
+    for a, o in zip(alone, outs):
+        for x, y in zip(a, o.numpy()):
+            np.testing.assert_array_equal(x, y)
+
+
 def test_temporal_distance_reaches_the_network():
     """Same references at a larger distance to the target (Section 3.4.1) give
     another output, matching the oracle's."""
