@@ -897,6 +897,14 @@ def run_profile_kernel(args) -> None:
         tile = 256 | (R.TILE_PAIR if args.profile_kernel == "fc1_fp8_pair" else 0)
         launch = lambda: R.op_linear_fp8(2, a, sa, w, sw, b, out, N, 4 * D, D, tile, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
+    elif args.profile_kernel in ("fc2", "fc2_pair"):  # fc2 of an encoder block: residual f32 += [N, 3072] x [768, 3072]^T
+        a = torch.randn((N, 4 * D), device="cuda").to(torch.bfloat16)
+        w = (torch.randn((D, 4 * D), device="cuda") / 56).to(torch.bfloat16)
+        b = torch.zeros(D, device="cuda")
+        out = torch.zeros((N, D), device="cuda")
+        tile = 256 | (R.TILE_PAIR if args.profile_kernel == "fc2_pair" else 0)
+        launch = lambda: R.op_linear(R.BF16, 3, a, w, b, out, N, D, 4 * D, tile, stream=stream)  # noqa: E731
+        flops = 2 * N * D * 4 * D
     else:  # fc1 of an encoder block: [N, 768] x [3072, 768]^T + GELU (fc1_pair: 256-row tiles on CTA pairs)
         a = torch.randn((N, D), device="cuda").to(torch.bfloat16)
         w = (torch.randn((4 * D, D), device="cuda") / 28).to(torch.bfloat16)
@@ -923,6 +931,7 @@ def run_profile_kernel(args) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "fc1", "fc1_pair", "fc1_fp8", "fc1_fp8_pair",
+                                                 "fc2", "fc2_pair",
                              "assemble", "blend"],
                     default=None,
                     help="only launch one kernel of the step (for profiler captures)")
