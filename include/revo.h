@@ -251,8 +251,10 @@ REVO_API revo_status revo_op_assemble(int channels, int k, int T, int p, int hei
  * Depth statistics of one uint16 frame: mean and biased standard deviation of
  * the non-zero pixels, written as float32 to mu_sigma[0..1] (device).  No valid
  * pixel gives (0, 1); the deviation is floored at 1 mm.  scratch is a device
- * buffer of revo_depth_stats_scratch_bytes() bytes that only one call at a time
- * may use.
+ * buffer of revo_depth_stats_scratch_bytes() bytes, 8-byte aligned, that only
+ * one call at a time may use.  Frames up to 2^24 pixels (height * width), so
+ * that the pixel count is exact in float32 where it divides the sum; larger
+ * frames and a misaligned scratch return REVO_EINVAL.
  */
 REVO_API size_t revo_depth_stats_scratch_bytes(void);
 REVO_API revo_status revo_op_depth_stats(const uint16_t* depth, int height, int width, size_t pitch_bytes,
@@ -267,11 +269,15 @@ REVO_API revo_status revo_op_depth_stats(const uint16_t* depth, int height, int 
  * convenience.  It allocates nothing: the scratch is a fixed 8 KB array inside
  * the library, held by every GPU that loads the library until the process
  * exits.  The caller still passes the frame and the output pair.
- *  - Frames up to 2^24 pixels (height * width); larger frames return
- *    REVO_EINVAL with a message.
- *  - The first call on a device looks up the array's device address (once per
- *    device, with that device current); make that first call before any CUDA
- *    stream capture.
+ *  - Frames up to 2^24 pixels (height * width), the same limit as
+ *    revo_op_depth_stats (the pixel count stays exact in float32); larger
+ *    frames return REVO_EINVAL with a message.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current) and keeps it for that device's current CUDA context; a
+ *    call in another context (after cudaDeviceReset, or under a context the
+ *    caller made current) looks it up again.  Make the first call on a device,
+ *    and the first after such a context change, before any CUDA stream
+ *    capture.
  *  - Every call shares the one array.  Calls whose work overlaps on the GPU
  *    (other streams, other host threads) race on it and give wrong results;
  *    order them on one stream or serialise them.  Each call clears the

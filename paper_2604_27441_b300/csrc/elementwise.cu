@@ -686,6 +686,7 @@ cudaError_t launch_quantize_rows_e4m3(const float* x, int rows, int cols, uint8_
 }
 
 size_t depth_stats_scratch_bytes() { return sizeof(StatsScratch); }
+size_t depth_stats_scratch_align() { return alignof(StatsScratch); }
 
 cudaError_t launch_depth_stats(const uint16_t* d, int H, int W, size_t pitch, float* mu_sigma, void* scratch,
                                cudaStream_t st) {

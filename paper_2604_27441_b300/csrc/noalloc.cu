@@ -6,6 +6,8 @@
 // variant keeps it in a fixed array of this file instead, so nothing is
 // allocated at call time.  Every GPU that loads the library holds the array
 // (kNoAllocScratchBytes) until the process exits.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -17,19 +19,62 @@ namespace revo {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 8192;
-// The exact float32 division by the pixel count in the statistics needs
-// count < 2^24, which bounds the frames this variant accepts.
-constexpr long long kNoAllocMaxPixels = 1LL << 24;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_depth_stats_scratch[kNoAllocScratchBytes];
 
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+// The array's device address is a property of the context the module was
+// loaded into: a cudaDeviceReset (or a caller switching to a context of its
+// own) loads the module again, possibly elsewhere.  So the address kept for a
+// device is tagged with the unique id of the context it was taken in
+// (cuCtxGetId: unique for the life of the process, unlike the handle, which a
+// re-created primary context can reuse) and looked up again when it differs.
+struct Cached {
+  unsigned long long ctx_id = 0;
+  void* addr = nullptr;
+};
 
-// Device address of the array on the current device (looked up once per device;
-// the host-side name is only a stand-in for it).
+std::mutex g_mu;
+Cached g_cache[kMaxDevices];
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
+std::once_flag g_once;
+
+void resolve_driver() {
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+  fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+}
+
+// Id of the calling thread's current context; 0 if there is none yet.
+revo_status current_ctx_id(unsigned long long* id) {
+  *id = 0;
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS) {
+    set_last_error("revo_op_depth_stats_noalloc: cuCtxGetCurrent failed");
+    return REVO_ECUDA;
+  }
+  if (ctx && g_ctx_id(ctx, id) != CUDA_SUCCESS) {
+    set_last_error("revo_op_depth_stats_noalloc: cuCtxGetId failed");
+    return REVO_ECUDA;
+  }
+  return REVO_OK;
+}
+
+// Device address of the array in the current context of the current device
+// (the host-side name is only a stand-in for it).
 revo_status scratch_address(void** out) {
+  std::call_once(g_once, resolve_driver);
+  if (!g_ctx_current || !g_ctx_id) {
+    set_last_error("revo_op_depth_stats_noalloc: the driver lacks cuCtxGetCurrent / cuCtxGetId");
+    return REVO_ENOTSUP;
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e, "revo_op_depth_stats_noalloc: cudaGetDevice");
@@ -37,14 +82,21 @@ revo_status scratch_address(void** out) {
     set_last_error("revo_op_depth_stats_noalloc: device ordinal %d beyond %d", dev, kMaxDevices - 1);
     return REVO_ENOTSUP;
   }
+  unsigned long long id = 0;
+  revo_status s = current_ctx_id(&id);
+  if (s != REVO_OK) return s;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
+  Cached& c = g_cache[dev];
+  if (id == 0 || c.ctx_id != id || !c.addr) {
+    // Also makes the runtime's context current when the thread has none yet.
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_depth_stats_scratch);
     if (e != cudaSuccess || !p) return cuda_status(e, "revo_op_depth_stats_noalloc: cudaGetSymbolAddress");
-    g_scratch_addr[dev] = p;
+    if (id == 0 && (s = current_ctx_id(&id)) != REVO_OK) return s;
+    c.ctx_id = id;
+    c.addr = p;
   }
-  *out = g_scratch_addr[dev];
+  *out = c.addr;
   return REVO_OK;
 }
 
@@ -60,9 +112,9 @@ extern "C" revo_status revo_op_depth_stats_noalloc(const uint16_t* depth, int he
     set_last_error("revo_op_depth_stats_noalloc: bad argument");
     return REVO_EINVAL;
   }
-  if (static_cast<long long>(height) * width > kNoAllocMaxPixels) {
+  if (static_cast<long long>(height) * width > kDepthStatsMaxPixels) {
     set_last_error("revo_op_depth_stats_noalloc: frame of %d x %d pixels exceeds the maximum of %lld pixels", height,
-                   width, kNoAllocMaxPixels);
+                   width, kDepthStatsMaxPixels);
     return REVO_EINVAL;
   }
   if (depth_stats_scratch_bytes() > kNoAllocScratchBytes) {

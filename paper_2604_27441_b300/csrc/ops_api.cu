@@ -153,6 +153,15 @@ revo_status revo_op_depth_stats(const uint16_t* depth, int height, int width, si
     set_last_error("revo_op_depth_stats: bad argument");
     return REVO_EINVAL;
   }
+  if (reinterpret_cast<uintptr_t>(scratch) % depth_stats_scratch_align()) {
+    set_last_error("revo_op_depth_stats: scratch must be %zu-byte aligned", depth_stats_scratch_align());
+    return REVO_EINVAL;
+  }
+  if (static_cast<long long>(height) * width > kDepthStatsMaxPixels) {
+    set_last_error("revo_op_depth_stats: frame of %d x %d pixels exceeds the maximum of %lld pixels", height, width,
+                   kDepthStatsMaxPixels);
+    return REVO_EINVAL;
+  }
   return cuda_status(
       launch_depth_stats(depth, height, width, pitch_bytes, mu_sigma, scratch, static_cast<cudaStream_t>(stream)),
       "revo_op_depth_stats");

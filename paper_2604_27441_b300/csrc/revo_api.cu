@@ -535,6 +535,8 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
   if (cfg->max_batch < 1 || cfg->max_batch > kMaxSegments || cfg->lanes < 1 || cfg->lanes > kMaxLanes ||
       cfg->max_streams < 1 || cfg->max_height <= 0 || cfg->max_width <= 0)
     return fail(REVO_EINVAL, "max_batch must be 1..64, lanes 1..8, max_streams and max size positive%s");
+  if (static_cast<long long>(cfg->max_height) * cfg->max_width > kDepthStatsMaxPixels)
+    return fail(REVO_EINVAL, "max_height x max_width above 2^24 pixels%s");
   if (cfg->precision != REVO_FP32 && cfg->precision != REVO_BF16 && cfg->precision != REVO_FP8)
     return fail(REVO_ENOTSUP, "precision not supported%s");
   if (cfg->precision == REVO_FP8 && (cfg->enc_dim % 128 || cfg->dec_dim % 128))

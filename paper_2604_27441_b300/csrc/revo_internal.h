@@ -107,6 +107,10 @@ cudaError_t launch_layernorm_e4m3(const float* x, const float* g, const float* b
                                   int M, int D, cudaStream_t st);
 
 size_t depth_stats_scratch_bytes();
+size_t depth_stats_scratch_align();
+// Largest frame (height * width) the statistics accept: the pixel count must be
+// exact in float32, where it divides the sum.
+constexpr long long kDepthStatsMaxPixels = 1LL << 24;
 cudaError_t launch_depth_stats(const uint16_t* d, int H, int W, size_t pitch, float* mu_sigma, void* scratch,
                                cudaStream_t st);
 

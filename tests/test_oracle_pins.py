@@ -352,6 +352,111 @@ def test_depth_stats_closed_forms():
     assert O.depth_stats(g) == (2000.0, 1000.0)
 
 
+def test_rgb_denormalise_inverts_normalise_for_every_code():
+    """De-normalisation is the inverse of the input normalisation: for every
+    uint8 code, on a frame whose height, width and channel count all differ,
+    normalise then de-normalise gives the code / 255 in [H, W, 3] layout.  A
+    swapped mean and std, a division in place of the product, or a transposed
+    axis fails here."""
+    codes = np.arange(256, dtype=np.uint8)
+    rng = np.random.default_rng(31)
+    f = rng.permutation(np.concatenate([codes, codes, codes, codes[:12]]))[:4 * 5 * 3 * 13].reshape(4 * 13, 5, 3)
+    f = np.ascontiguousarray(f[:20]).astype(np.uint8)      # [20, 5, 3]: H != W != C
+    for frame in (f, np.ascontiguousarray(np.broadcast_to(codes[:, None, None], (256, 2, 3)))):
+        y = O.normalise_rgb(frame)
+        assert y.shape == (3,) + frame.shape[:2]
+        np.testing.assert_allclose(O.denormalise_rgb(y), frame / 255.0, rtol=0, atol=1e-15)
+
+
+def test_rgb_denormalise_closed_forms():
+    """y = 0 gives each channel's mean, y = 1 its mean plus its deviation, at
+    every pixel of the [H, W, 3] result (ImageNet statistics)."""
+    mean, std = np.array([0.485, 0.456, 0.406]), np.array([0.229, 0.224, 0.225])
+    z = O.denormalise_rgb(np.zeros((3, 2, 7)))
+    o = O.denormalise_rgb(np.ones((3, 2, 7)))
+    assert z.shape == (2, 7, 3)
+    np.testing.assert_allclose(z, np.broadcast_to(mean, (2, 7, 3)), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(o, np.broadcast_to(mean + std, (2, 7, 3)), rtol=0, atol=1e-15)
+    # one channel at a time: channel c of y lands in the last axis at c
+    for c in range(3):
+        y = np.zeros((3, 2, 7))
+        y[c] = 1.0
+        want = mean.copy()
+        want[c] += std[c]
+        np.testing.assert_allclose(O.denormalise_rgb(y), np.broadcast_to(want, (2, 7, 3)), rtol=0, atol=1e-15)
+
+
+def test_depth_normalise_closed_forms_and_inverse():
+    """(d - mu) / sigma with a non-trivial (mu, sigma): d = mu -> 0,
+    d = mu + sigma -> 1, d = 0 (no measurement) -> -mu / sigma; de-normalising
+    gives the millimetres back for every code of a range, in [H, W] layout."""
+    mu, sigma = 1234.5, 321.25
+    d = np.array([[1234, 1235, 0], [1555, 1556, 913]], np.uint16)
+    y = O.normalise_depth(d, mu, sigma)
+    assert y.shape == (1, 2, 3)
+    np.testing.assert_allclose(y[0, 1, 0], (1555 - mu) / sigma, atol=1e-15)
+    np.testing.assert_allclose(y[0, 0, 2], -mu / sigma, atol=1e-15)
+    e = np.array([[mu, mu + sigma, mu - sigma]])
+    np.testing.assert_allclose(O.normalise_depth(e, mu, sigma)[0], [[0.0, 1.0, -1.0]], atol=1e-15)
+    np.testing.assert_allclose(O.denormalise_depth(np.array([[[0.0, 1.0, -2.0]]]), mu, sigma),
+                               [[mu, mu + sigma, mu - 2 * sigma]], atol=1e-12)
+    codes = np.arange(0, 65536, 7, dtype=np.uint16)[:9000].reshape(90, 100)
+    back = O.denormalise_depth(O.normalise_depth(codes, mu, sigma), mu, sigma)
+    assert back.shape == codes.shape
+    np.testing.assert_allclose(back, codes.astype(np.float64), rtol=0, atol=1e-10)
+
+
+def _constant_output_weights(cfg, head_bias):
+    """Weights whose network output is head_bias at every pixel, whatever the
+    input: every matrix and every LayerNorm gain is zero (each LayerNorm then
+    outputs its shift, zero), so the pixel head sees zeros and adds its bias."""
+    w = synth.weights(cfg, seed=3)
+    for n in w:
+        w[n] = np.zeros_like(w[n])
+    w["head.b"] = np.full_like(w["head.b"], head_bias)
+    return w
+
+
+@pytest.mark.parametrize("head_bias", [0.0, 1.0, -0.5])
+def test_recover_depth_statistics_come_from_the_newest_reference(head_bias):
+    """recover() normalises depth with the statistics of the newest reference
+    (the last clean frame), not of the current frame or an older reference.
+    With a network whose normalised output is the constant y, every recovered
+    depth is y * sigma + mu of that frame: here mu = 2000, sigma = 1000 (half
+    the valid pixels at 1000 mm, half at 3000, zeros excluded), while the
+    current frame and the older references have mean 500 (sigma floored to 1)."""
+    cfg = synth.tiny(1, k=3)
+    w = _constant_output_weights(cfg, head_bias)
+    H, W = 8, 12
+    old = np.full((H, W), 500, np.uint16)
+    newest = np.zeros((H, W), np.uint16)
+    newest[:, 0::2] = 1000
+    newest[:, 1::2] = 3000
+    newest[0, :4] = 0
+    newest[1, :2] = 0   # zeros are excluded; 46 pixels of each value remain
+    refs = np.stack([old, old, newest])
+    decoded = np.full((H, W), 500, np.uint16)
+    lost = np.zeros((H, W), bool)
+    lost[:4] = True
+    decoded[lost] = 0
+    codes, values = O.recover("depth", w, cfg, refs, [7, 8, 9], decoded, synth.pack_mask(lost), 10)
+    np.testing.assert_allclose(values, np.full((H, W), head_bias * 1000.0 + 2000.0), rtol=0, atol=1e-9)
+    np.testing.assert_array_equal(codes[lost], np.full(lost.sum(), round(head_bias * 1000 + 2000), np.uint16))
+    np.testing.assert_array_equal(codes[~lost], decoded[~lost])
+
+
+@pytest.mark.parametrize("head_bias", [0.0, 1.0])
+def test_recover_rgb_denormalises_per_channel(head_bias):
+    """recover() for RGB: a constant normalised output y gives y std_c + mean_c
+    in channel c of every pixel (ImageNet statistics), whatever the frames."""
+    cfg = synth.tiny(3, k=1)
+    w = _constant_output_weights(cfg, head_bias)
+    pl = synth.make_tiny_plane(9, "rgb", 8, 12, 1, lost_rows=[2, 3])
+    _, values = O.recover("rgb", w, cfg, pl.refs, pl.ref_index, pl.decoded, pl.mask, pl.index)
+    want = np.array([0.485, 0.456, 0.406]) + head_bias * np.array([0.229, 0.224, 0.225])
+    np.testing.assert_allclose(values, np.broadcast_to(want, (8, 12, 3)), rtol=0, atol=1e-14)
+
+
 def test_quantisation_round_half_even_and_clamp():
     v = np.array([0.5, 1.5, 2.5, -3.0, 300.0, 254.5]) / 255.0
     np.testing.assert_array_equal(O.quantise_rgb(v * 255.0 / 255.0), [0, 2, 2, 0, 255, 254])
