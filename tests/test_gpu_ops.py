@@ -277,6 +277,34 @@ ATT_CASES = [((0, 300, 1000), 2), ((0, 5, 5, 133, 900), 3), ((0, 3600), 12), ((0
              ((0, 900, 1800, 2700), 6)]
 
 
+def check_attention_bf16(got, qkv64, heads, seg):
+    """Checks a bf16 attention output against the FP64 oracle on the same
+    bf16-rounded q, k, v, with tolerances derived from the kernel's roundings:
+    P = exp(...) rounded to bf16 before the PV product (relative error <= 2^-8
+    per weight, so |error| <= 2^-8 sum_j a_ij |v_j| with a = softmax), and the
+    output rounded to bf16 (<= 2^-8 |O|); plus 2^-12 sum_j a_ij |v_j| for the
+    float32 accumulations.  Element by element within that bound, and over the
+    whole output and each long segment a relative RMS error below 4e-3 (the
+    roundings give ~2e-3; one dropped 128-key tile at N = 3600 gives ~0.2, a 10%
+    error in the softmax scale ~0.1)."""
+    D = qkv64.shape[1] // 3
+    ref = _oracle_segments(qkv64, heads, seg)
+    absv = qkv64.copy()
+    absv[:, 2 * D:] = np.abs(absv[:, 2 * D:])
+    av = _oracle_segments(absv, heads, seg)
+    bound = 2.0 ** -8 * av + 2.0 ** -8 * np.abs(ref) + 2.0 ** -12 * av + 1e-6
+    err = np.abs(got - ref)
+    bad = err > bound
+    assert not bad.any(), (int(bad.sum()), float(err[bad].max()), float(bound[bad].min()))
+
+    def rel_rms(a, b):
+        return float(np.sqrt(np.mean((a - b) ** 2)) / max(np.sqrt(np.mean(b ** 2)), 1e-30))
+    assert rel_rms(got, ref) < 4e-3, rel_rms(got, ref)
+    for a, b in zip(seg[:-1], seg[1:]):
+        if b - a >= 64:
+            assert rel_rms(got[a:b], ref[a:b]) < 4e-3, (a, b, rel_rms(got[a:b], ref[a:b]))
+
+
 @pytest.mark.parametrize("split_tail", [False, True])
 @pytest.mark.parametrize("seg,heads", ATT_CASES + [((0, 900), 12), ((0, 10800), 2)])
 def test_attention_bf16_tcgen05(seg, heads, split_tail):
@@ -287,8 +315,7 @@ def test_attention_bf16_tcgen05(seg, heads, split_tail):
     out = torch.zeros((M, D), dtype=torch.bfloat16, device="cuda")
     R.op_attention(R.BF16, qkv.cuda(), out, M, D, heads, seg, split_tail=split_tail)
     torch.cuda.synchronize()
-    ref = _oracle_segments(f64(qkv), heads, seg)
-    np.testing.assert_allclose(f64(out), ref, rtol=2e-2, atol=1.5e-2)
+    check_attention_bf16(f64(out), f64(qkv), heads, seg)
 
 
 @pytest.mark.parametrize("seg,heads", ATT_CASES[:2] + [((0, 700), 4)])

@@ -199,6 +199,25 @@ def test_vitb_640x480_parity(precision):
     check(precision, got, oracle(VITB, rgb, dep, "640"), rgb, dep)
 
 
+# The 1280x720 RGB + 640x576 depth request shared by the decoupled-size test
+# and the mixed batch below (one oracle run serves both).
+SEED_720 = 3001
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_vitb_1280x720_rgb_640x576_depth_parity(precision):
+    """Decoupled streams at different sizes (Section 3.4.2: a model per
+    modality): 1280x720 RGB (N = 10800 tokens) with a 640x576 depth stream
+    (N = 4320; 300-5000 mm, 2% invalid zero pixels), 20% bursty slice loss,
+    BF16 and FP8 against the FP64 oracle."""
+    rgb, dep = synth.make_request(SEED_720, "1280x720+640x576", loss_rate=0.2)
+    assert (rgb.height, rgb.width, dep.height, dep.width) == (720, 1280, 576, 640)
+    assert (dep.clean == 0).mean() > 0.01
+    with make_ctx(VITB, precision, (720, 1280)) as ctx:
+        got = run(ctx, 0, rgb, dep)
+    check(precision, got, oracle(VITB, rgb, dep, "720"), rgb, dep)
+
+
 def test_host_buffers_match_device_buffers():
     rgb, dep = synth.make_request(1002, "320x240")
     with make_ctx(VITB, R.BF16, (240, 320)) as ctx:
@@ -263,7 +282,7 @@ def test_hold_batches_mixed_sizes_with_autotuned_tiles():
     """REVO_HOLD admits requests without launching; the batch starts when it is
     full.  Tile widths chosen by the autotuner leave every output unchanged (a
     tile width changes which CTA computes an element, not its arithmetic)."""
-    reqs = [synth.make_request(3100 + i, wl, loss_rate=0.2)
+    reqs = [synth.make_request(SEED_720 if wl.startswith("1280") else 3100 + i, wl, loss_rate=0.2)
             for i, wl in enumerate(("640x480", "320x240", "1280x720+640x576", "320x240"))]
     got = {}
     for tune in (0, 1):
@@ -295,6 +314,8 @@ def test_hold_batches_mixed_sizes_with_autotuned_tiles():
         alone = run(ctx, 0, *reqs[0])
     for x, y in zip(alone, got[1, 2][0]):
         np.testing.assert_array_equal(x, y)
+    # and its 1280x720 + 640x576 member matches the FP64 oracle
+    check(R.BF16, got[1, 2][2], oracle(VITB, *reqs[2], "720"), *reqs[2])
 
 
 @pytest.mark.parametrize("k,T", [(3, 1), (7, 2), (1, 2)])
