@@ -1,20 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the ReVo neural loss-recovery hot path on B300.
 
-One step = recovery of one corrupted RGB-D frame (640x480 RGB uint8 +
-640x480 depth uint16, batch 1): tubelet assembly + normalisation, the ViT-B
-encoder-decoder forward of both modality models (run concurrently on two CUDA
-streams), the pixel head and the masked blend, through the library's C ABI
-(revo_recover_submit + revo_recover_poll).  Four conference streams, one per
-Gilbert-Elliott slice-loss rate (5/10/20/40 %), each with five clean
-references resident on the device, take turns.  Random-init weights and
-seeded synthetic frames.  Two frames are kept in flight (--in-flight, one
-lane each), as a receiver serving several conference streams would: each
-frame is still its own batch-1 launch, and its latency (submit -> poll) is
-reported against the 33 ms frame budget.
+The headline step is the batched mixed-resolution tick: 16 conference
+streams (6 x 320x240, 6 x 640x480, 4 x 1280x720 RGB + 640x576 depth), one
+corrupted RGB-D frame each with independent Gilbert-Elliott slice loss, all
+recovered in one batch per modality (one CUDA-graph replay each, autotuned
+GEMM tiles) through the library's C ABI (revo_recover_submit with REVO_HOLD +
+revo_recover_poll): tubelet assembly + normalisation, the ViT-B
+encoder-decoder forward of both modality models (two CUDA streams), the pixel
+head and the masked blend.  `value` = recovered frames/s of that tick (BF16),
+inputs resident on the device.  Beside it, in the same JSON line:
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
-  python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
+  latency_ms   p50/p99 of the real-time serving loop (8 streams x 30 frames/s
+               of the same resolution mix, 20 s, pinned host inputs), BF16;
+               `serving` has BF16 and FP8
+  e2e          the tick with pinned host buffers (copies inside the timing)
+  batch1_640x480  one 640x480 RGB-D frame per launch (two in flight) at BF16,
+               FP8 and FP32 -- the FP32 batch-1 path is the one to beat --
+               with RGB and depth error against the FP64 oracle
+  roofline     the dominant kernel (the tick's batched encoder attention)
+  cpu_baseline the FP64 oracle on 320x240 RGB-D frames, scaled to the tick
+
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, same metric and workload
+  python bench.py --workload 640x480 | serving | kt   # single measurements
 
 Prints one JSON line (rank 0).
 """
@@ -37,17 +46,25 @@ if ROOT not in sys.path:
 
 METRIC = "recovered RGB-D frames/s + p99 latency, BF16/FP8 vs FP32, at ≥45 dB vs FP64 oracle"
 UNIT = "frames/s"
-WORKLOAD = "640x480"
-H, W = 480, 640
+H, W = 480, 640  # the batch-1 comparison frame
 LOSS_RATES = (0.05, 0.10, 0.20, 0.40)
 VITB = dict(k=5, tubelet=2, patch=16, enc_dim=768, enc_depth=12, enc_heads=12, dec_dim=384, dec_depth=4,
             dec_heads=6, mlp_ratio=4)
 FRAME_BUDGET_MS = 33.0
 PRECISIONS = {"bf16": lambda R: R.BF16, "fp32": lambda R: R.FP32, "fp8": lambda R: R.FP8}
-DTYPE_NAMES = {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3 (encoder fc1; per-token x per-channel scales) + bf16"}
-# DRAM bytes (read + write) of one attn_tc_kernel launch at N = 3600, 12 heads,
-# from an ncu capture of the current kernel version (None once it changes).
-ATTN_DRAM_BYTES_PER_LAUNCH = 16629760
+DTYPE_NAMES = {"bf16": "bf16", "fp32": "f32",
+               "fp8": "e4m3 (RGB model: encoder and decoder qkv + fc1; per-token x per-channel scales) + bf16"}
+# The 16-participant resolution mix: 6 x 320x240, 6 x 640x480, 4 x (1280x720
+# RGB + 640x576 depth), interleaved so the first n streams keep the proportions.
+MIX16 = ["320x240", "640x480", "1280x720+640x576", "320x240", "640x480", "1280x720+640x576", "320x240",
+         "640x480", "1280x720+640x576", "320x240", "640x480", "1280x720+640x576", "320x240", "640x480",
+         "320x240", "640x480"]
+TICK_WORKLOAD = ("mixed16: 16 participant streams (6 x 320x240, 6 x 640x480, 4 x 1280x720 RGB + 640x576 depth), "
+                 "independent Gilbert-Elliott slice loss, one batch per modality per step")
+# DRAM bytes (read + write) of one attn_tc_kernel launch of the tick's batched
+# RGB encoder attention, from an ncu capture of the current kernel version
+# (None once the kernel changes).
+ATTN_DRAM_BYTES_PER_LAUNCH = None
 
 
 def run_pipelined(R, ctx, req_list, n: int, depth: int, start: int = 0):
@@ -76,12 +93,10 @@ def run_pipelined(R, ctx, req_list, n: int, depth: int, start: int = 0):
     return lat, launches
 
 
-def workload_config(world: int, seq_len: int) -> dict:
+def tick_config(world: int) -> dict:
     """The headline workload, as both arms name it in `config`."""
-    return {"workload": f"{WORKLOAD} RGB uint8 + {WORKLOAD} depth uint16, batch 1, "
-                        "loss 5/10/20/40% (4 streams in turn)",
-            "model": "ViT-B enc-dec (768x12 / 384x4), k=5, T=2, p=16", "global_batch": world,
-            "seq_len": seq_len, "parallelism": f"replicas x{world}"}
+    return {"workload": TICK_WORKLOAD, "model": "ViT-B enc-dec (768x12 / 384x4), k=5, T=2, p=16",
+            "global_batch": 16 * world, "seq_len": 10800, "parallelism": f"replicas x{world}"}
 
 
 def flops_per_model(C: int, h: int, w: int) -> dict:
@@ -100,6 +115,13 @@ def flops_per_model(C: int, h: int, w: int) -> dict:
     attn_dec = 4 * N * N * Dd
     return dict(N=N, linear=lin, attn_enc_per_block=attn_enc, attn=L * attn_enc + Ld * attn_dec,
                 total=lin + L * attn_enc + Ld * attn_dec)
+
+
+def request_flops(workload: str) -> float:
+    import synth
+    wl = synth.WORKLOADS[workload]
+    (hr, wr), (hd, wd) = wl["rgb"], wl["depth"]
+    return flops_per_model(3, hr, wr)["total"] + flops_per_model(1, hd, wd)["total"]
 
 
 def peaks() -> dict:
@@ -131,9 +153,9 @@ def rank_max(v: float, world: int) -> float:
     return float(t.item())
 
 
-def whole_job_rate(steps_per_rank: int, max_seconds: float, world: int) -> float:
+def whole_job_rate(steps_per_rank: int, max_seconds: float, world: int, frames_per_step: int = 1) -> float:
     """Frames/s of the whole job: every rank's frames over the slowest rank's time."""
-    return world * steps_per_rank / max_seconds
+    return world * steps_per_rank * frames_per_step / max_seconds
 
 
 # --------------------------------------------------------------- clocks --
@@ -192,66 +214,68 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ oracle arm --
+# One oracle measurement serves both CPU figures (the main arm's cpu_baseline
+# and the --impl reference arm): seconds per 320x240 RGB-D frame of the FP64
+# oracle (both modality models), scaled to the tick by FLOP count.
 
-def oracle_rgb_sample(seed: int = 2002):
-    """Times the FP64 oracle recovering the RGB plane of one 640x480 frame (the
-    bounded sample); returns (seconds, the oracle's values, the plane)."""
+ORACLE_SAMPLE = "320x240"
+
+
+def oracle_sample_inputs():
+    import synth
+    rgb, dep = synth.make_request(1001, ORACLE_SAMPLE)
+    return rgb, dep, synth.weights(synth.RGB, seed=0), synth.weights(synth.DEPTH, seed=1)
+
+
+def oracle_frame_seconds(inputs) -> float:
+    """One 320x240 RGB-D frame through the FP64 oracle, as it stands."""
     import synth
     from oracle import revo_oracle as O
-    rgb, _ = synth.make_request(seed, WORKLOAD, loss_rate=0.2)
-    w = synth.weights(synth.RGB, seed=0)
+    rgb, dep, wr, wd = inputs
     t0 = time.perf_counter()
-    codes, values = O.recover("rgb", w, synth.RGB, rgb.refs, rgb.ref_index, rgb.decoded, rgb.mask, rgb.index)
-    return time.perf_counter() - t0, values, rgb
+    O.recover("rgb", wr, synth.RGB, rgb.refs, rgb.ref_index, rgb.decoded, rgb.mask, rgb.index)
+    O.recover("depth", wd, synth.DEPTH, dep.refs, dep.ref_index, dep.decoded, dep.mask, dep.index)
+    return time.perf_counter() - t0
 
 
-def cpu_baseline(seconds_rgb: float) -> dict:
-    f_rgb = flops_per_model(3, H, W)["total"]
-    f_dep = flops_per_model(1, H, W)["total"]
-    per_frame = seconds_rgb * (f_rgb + f_dep) / f_rgb
-    return {"value": 1.0 / per_frame, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 oracle recovering the RGB plane of one {WORKLOAD} frame "
-                      f"({seconds_rgb:.1f} s), scaled to an RGB-D frame by the FLOP ratio "
-                      f"{(f_rgb + f_dep) / f_rgb:.3f}"}
+def oracle_scale() -> tuple[float, float]:
+    """(FLOPs of the tick, FLOPs of one oracle sample frame)."""
+    return sum(request_flops(wl) for wl in MIX16), request_flops(ORACLE_SAMPLE)
+
+
+def oracle_tick_rate(seconds_per_frame: float) -> float:
+    tick, frame = oracle_scale()
+    return len(MIX16) / (seconds_per_frame * tick / frame)
+
+
+def oracle_sample_text(seconds_per_frame: float, frames: int) -> str:
+    tick, frame = oracle_scale()
+    return (f"FP64 oracle recovering {frames} whole {ORACLE_SAMPLE} RGB-D frame(s) (both models), "
+            f"{seconds_per_frame:.2f} s per frame, scaled to the 16-frame tick by FLOPs ({tick / frame:.1f} such "
+            f"frames; the oracle's softmax makes its larger frames slower per FLOP, so the scaled figure favours "
+            f"the CPU)")
 
 
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import revo_oracle as O
-    import synth
-    # Each step: one oracle encoder block of the RGB model on the token count
-    # of a 320x240 frame (N = 900; a bounded sample, ~0.3-0.5 s on 8 cores, so
-    # the default 210 steps end within minutes); a 640x480 RGB-D frame costs
-    # `blocks_per_frame` such blocks by FLOP count.  At N = 900 the attention
-    # share is smaller than at N = 3600, where the oracle's per-FLOP speed is
-    # lower (softmax), so the scaled figure favours the CPU.
-    fr = flops_per_model(3, H, W)
-    fd = flops_per_model(1, H, W)
-    N, D = flops_per_model(3, 240, 320)["N"], 768
-    block_flops = 2 * N * (3 * D * D + D * D + 8 * D * D) + 4 * N * N * D
-    blocks_per_frame = (fr["total"] + fd["total"]) / block_flops
-    cfg = synth.RGB
-    w = {n: a.astype(np.float64) for n, a in synth.weights(cfg, seed=0).items() if n.startswith("enc.0.")}
-    x = synth.normal(7, (N, D)).astype(np.float64)
+    inputs = oracle_sample_inputs()
     times = []
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        O.block(x, w, "enc.0.", cfg.enc_heads)
-        dt = time.perf_counter() - t0
+        dt = oracle_frame_seconds(inputs)
         if i >= args.warmup:
             times.append(dt)
-    per_frame = statistics.mean(times) * blocks_per_frame
-    value = 1.0 / per_frame
-    sample = (f"per step one FP64 oracle encoder block at N={N} tokens; an RGB-D frame = "
-              f"{blocks_per_frame:.2f} such blocks by FLOP count")
+    per_frame = statistics.mean(times)
+    value = oracle_tick_rate(per_frame)
+    cores = os.cpu_count()
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_frame,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(1, flops_per_model(3, H, W)["N"]),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+        "config": tick_config(1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "per step: " + oracle_sample_text(per_frame, 1)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -307,254 +331,72 @@ def elementwise_roofline(R, torch, stream) -> dict:
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hbm else None}
 
 
-def run_ours(args) -> None:
-    import torch
-    import torch.distributed as dist
-
-    import paper_2604_27441_b300 as R
+def tick_segments(wl_rgb: bool = True) -> list:
+    """Token counts of the tick's RGB (or depth) requests, in MIX16 order."""
     import synth
+    out = []
+    for wl in MIX16:
+        h, w = synth.WORKLOADS[wl]["rgb" if wl_rgb else "depth"]
+        out.append(3 * (h // 16) * (w // 16))
+    return out
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        rank_barrier(world)
+def attention_roofline(R, torch, stream) -> dict:
+    """The dominant kernel of the tick, timed alone on the same stream with CUDA
+    events: the batched tcgen05 attention of one RGB encoder block over the 16
+    requests' token segments (N = 900 x 6, 3600 x 6, 10800 x 4; 12 heads x 64).
+    Achieved = 4 N^2 D summed over the segments / launch time.  Beside it the
+    same kernel on one 640x480 request (N = 3600) and its one-CTA-per-unit form."""
+    D, heads = 768, 12
+    lens = tick_segments(True)
+    seg = np.concatenate([[0], np.cumsum(lens)]).astype(int).tolist()
+    M = seg[-1]
+    qkv = torch.randn((M, 3 * D), device="cuda").to(torch.bfloat16)
+    out = torch.empty((M, D), dtype=torch.bfloat16, device="cuda")
 
-    def max_over_ranks(v: float) -> float:
-        return rank_max(v, world)
-
-    precision = PRECISIONS[args.precision](R)
-    stream = torch.cuda.Stream()
-    w_rgb = synth.flatten(synth.weights(synth.RGB, seed=0))
-    w_dep = synth.flatten(synth.weights(synth.DEPTH, seed=1))
-    depth = max(1, min(8, args.in_flight))  # frames in flight, one lane each
-    cfg = R.config(**VITB, precision=precision, device=local, max_height=H, max_width=W, max_streams=8,
-                   max_batch=1, lanes=depth, use_graphs=0 if args.no_graphs else 1, autotune=1)
-    ctx = R.Context(cfg, w_rgb, w_dep, stream=stream)
-
-    # Four conference streams (one per loss rate), references pushed once.
-    reqs = [synth.make_request(2000 + 100 * rank + i, WORKLOAD, loss_rate=r) for i, r in enumerate(LOSS_RATES)]
-    keep = []
-    dev_req, host_req, dev_bufs = [], [], []
-    for sid, (rgb, dep) in enumerate(reqs):
-        for j in range(rgb.refs.shape[0]):
-            fr = torch.from_numpy(rgb.refs[j]).cuda()
-            fd = torch.from_numpy(dep.refs[j].view(np.int16)).cuda()
-            keep += [fr, fd]
-            ctx.poll(ctx.submit(R.request(sid, int(rgb.ref_index[j]), R.RGB | R.DEPTH | R.CLEAN, on_device=True,
-                                          rgb=(fr, H, W), depth=(fd, H, W))))
-        d = dict(ri=torch.from_numpy(rgb.decoded).cuda(), di=torch.from_numpy(dep.decoded.view(np.int16)).cuda(),
-                 rm=torch.from_numpy(rgb.mask.view(np.int32)).cuda(), dm=torch.from_numpy(dep.mask.view(np.int32)).cuda(),
-                 ro=torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda"),
-                 do=torch.zeros((H, W), dtype=torch.int16, device="cuda"),
-                 rv=torch.zeros((H, W, 3), dtype=torch.float32, device="cuda"))
-        keep.append(d)
-        dev_bufs.append(d)
-        dev_req.append(R.request(sid, rgb.index, R.RGB | R.DEPTH, on_device=True, rgb=(d["ri"], H, W),
-                                 rgb_mask=d["rm"], depth=(d["di"], H, W), depth_mask=d["dm"], rgb_out=d["ro"],
-                                 depth_out=d["do"], rgb_values=d["rv"] if sid == 2 else None))
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
-        h = dict(ri=pin(rgb.decoded), di=pin(dep.decoded.view(np.int16)), rm=pin(rgb.mask.view(np.int32)),
-                 dm=pin(dep.mask.view(np.int32)), ro=torch.zeros((H, W, 3), dtype=torch.uint8).pin_memory(),
-                 do=torch.zeros((H, W), dtype=torch.int16).pin_memory())
-        keep.append(h)
-        host_req.append(R.request(sid, rgb.index, R.RGB | R.DEPTH, on_device=False, rgb=(h["ri"], H, W),
-                                  rgb_mask=h["rm"], depth=(h["di"], H, W), depth_mask=h["dm"], rgb_out=h["ro"],
-                                  depth_out=h["do"]))
-    h2d = H * W * 3 + H * W * 2 + 2 * H * ((W + 31) // 32) * 4
-    d2h = H * W * 3 + H * W * 2
-
-    run_pipelined(R, ctx, dev_req, args.warmup, depth)
-    torch.cuda.synchronize()
-    barrier()
-
-    # Timed region: device-resident inputs and outputs.
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat, launches = [], 0
-    # REVO_PROFILE_RANGE=1 marks the timed region for a profiler started with
-    # --profile-from-start off (it changes nothing else).
-    mark = os.environ.get("REVO_PROFILE_RANGE") == "1"
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        barrier()
-        if mark:
-            torch.cuda.profiler.start()
-        # With `depth` frames in flight the other lanes run on the context's
-        # own streams: the end event is recorded once every frame has been
-        # polled (complete), so the span covers all of them.
-        start.record(stream)
-        lat, launches = run_pipelined(R, ctx, dev_req, args.steps, depth)
-        end.record(stream)
-        torch.cuda.synchronize()
-        if mark:
-            torch.cuda.profiler.stop()
-        barrier()
-    dev_s = start.elapsed_time(end) / 1e3
-    dev_s_max = max_over_ranks(dev_s)
-    value = whole_job_rate(args.steps, dev_s_max, world)
-    clocks = clk.summary()
-
-    # End to end: host (pinned) buffers, copies inside the timed region, host clock.
-    run_pipelined(R, ctx, host_req, 2 * depth, depth)
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    run_pipelined(R, ctx, host_req, args.steps, depth)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-
-    # Dominant kernel, timed alone on the same stream with CUDA events: the
-    # tcgen05 flash attention of one encoder block at N = 3600 tokens.
-    fl = flops_per_model(3, H, W)
-    N, D = fl["N"], 768
-    roof = None
-    if precision != R.FP32:
-        qkv = (torch.randn((N, 3 * D), device="cuda") * 1.0).to(torch.bfloat16)
-        out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
+    def timed(fn, reps):
         with torch.cuda.stream(stream):
             for _ in range(3):
-                R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream)
+                fn()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 50
             e0.record(stream)
             for _ in range(reps):
-                R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream)
+                fn()
             e1.record(stream)
-            e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            for _ in range(3):
-                R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream, split_tail=True)
-            e2.record(stream)
-            for _ in range(reps):
-                R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream, split_tail=True)
-            e3.record(stream)
         torch.cuda.synchronize()
-        per_launch = e0.elapsed_time(e1) / 1e3 / reps
-        split_us = e2.elapsed_time(e3) * 1e3 / reps
-        pk = peaks()
-        peak = pk.get("bf16_tflops")
-        achieved = fl["attn_enc_per_block"] / per_launch / 1e12
-        roof = {"kernel": "attn_tc_kernel (tcgen05 flash attention, N=3600, 12 heads x 64)", "bound": "tensor",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": ATTN_DRAM_BYTES_PER_LAUNCH,
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)" if peak else None,
-                "flops_per_launch": fl["attn_enc_per_block"], "us_per_launch": per_launch * 1e6,
-                "note": "the form the step runs (RGB and depth in flight together: no tail split); alone, with "
-                        "the last wave's key ranges split over idle SMs (REVO_ATTN_SPLIT_TAIL)",
-                "alone_split_tail": {"us_per_launch": split_us,
-                                     "achieved": fl["attn_enc_per_block"] / (split_us * 1e-6) / 1e12,
-                                     "frac": (fl["attn_enc_per_block"] / (split_us * 1e-6) / 1e12 / peak)
-                                     if peak else None}}
-        assert R.take_device_error() == 0
+        return e0.elapsed_time(e1) / 1e3 / reps
 
-    elementwise = elementwise_roofline(R, torch, stream) if rank == 0 else None
-
-    # Quality of the timed configuration against the FP64 oracle (RGB plane of the
-    # 20 %-loss stream) + the CPU baseline from the same oracle run.
-    quality, cpu = None, None
-    if rank == 0 and not args.no_cpu_baseline:
-        secs, o_vals, pl = oracle_rgb_sample()
-        cpu = cpu_baseline(secs)
-        # stream 2 carries the 20 %-loss frame the oracle recovered (same seed)
-        err = dev_bufs[2]["rv"].cpu().numpy().astype(np.float64) - o_vals
-        mse = float(np.mean(err * err))
-        quality = {"rgb_psnr_db_vs_fp64": 10 * np.log10(1.0 / mse) if mse > 0 else float("inf"),
-                   "rgb_max_abs_err": float(np.abs(err).max()), "gate_db": 45.0}
-
-    # The other precisions on the same four streams and the same device buffers
-    # (each in a context of its own), device-timed, with the same quality check:
-    # the FP32 batch-1 path is the one the reduced-precision paths must beat.
-    compare = {}
-    if world == 1 and not args.no_compare:
-        for name in sorted(PRECISIONS):
-            if name == args.precision:
-                continue
-            c2 = R.Context(R.config(**VITB, precision=PRECISIONS[name](R), device=local, max_height=H, max_width=W,
-                                    max_streams=8, max_batch=1, lanes=depth, use_graphs=0 if args.no_graphs else 1,
-                                    autotune=1),
-                           w_rgb, w_dep, stream=stream)
-            for sid, (rgb, dep) in enumerate(reqs):
-                for j in range(rgb.refs.shape[0]):
-                    fr = torch.from_numpy(rgb.refs[j]).cuda()
-                    fd = torch.from_numpy(dep.refs[j].view(np.int16)).cuda()
-                    keep += [fr, fd]
-                    c2.poll(c2.submit(R.request(sid, int(rgb.ref_index[j]), R.RGB | R.DEPTH | R.CLEAN,
-                                                on_device=True, rgb=(fr, H, W), depth=(fd, H, W))))
-            n2 = 6 if name == "fp32" else 40
-            run_pipelined(R, c2, dev_req, 4, depth)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            run_pipelined(R, c2, dev_req, n2, depth)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            sec = e0.elapsed_time(e1) / 1e3
-            entry = {"frames_per_s": n2 / sec, "ms_per_step": sec * 1e3 / n2, "steps": n2, "batch": 1,
-                     "in_flight": depth}
-            c2.poll(c2.submit(dev_req[2]))
-            if quality is not None:
-                err = dev_bufs[2]["rv"].cpu().numpy().astype(np.float64) - o_vals
-                mse = float(np.mean(err * err))
-                entry["rgb_psnr_db_vs_fp64"] = 10 * np.log10(1.0 / mse) if mse > 0 else float("inf")
-                entry["rgb_max_abs_err"] = float(np.abs(err).max())
-            compare[name] = entry
-            c2.close()
-        if "fp32" in compare:
-            compare["speedup_vs_fp32_batch1"] = value / compare["fp32"]["frames_per_s"]
-
-    if rank == 0:
-        lat_s = sorted(lat)
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[args.precision],
-            "data": "synthetic (seeded RGB-D frames, Gilbert-Elliott slice loss, random-init ViT-B weights)",
-            "config": {**workload_config(world, fl["N"]),
-                       "in_flight": depth, "lanes": depth,
-                       "launch": "kernels" if args.no_graphs else "CUDA graph replay per request-size pattern, "
-                                 "autotuned GEMM tile widths",
-                       "l2": "working set > L2: bf16 weights of both models (0.37 GB) stream every step"},
-            "latency_ms": {"p50": float(np.percentile(lat_s, 50)), "p99": float(np.percentile(lat_s, 99)),
-                           "budget": FRAME_BUDGET_MS},
-            "flops_per_step": flops_per_model(3, H, W)["total"] + flops_per_model(1, H, W)["total"],
-            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-            "cpu_baseline": cpu, "quality": quality, "precisions": compare, "elementwise": elementwise,
-        }
-        print(json.dumps(line), flush=True)
-    ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
-
-
-# ------------------------------------------------ mixed sizes / serving --
-
-# The 16-participant resolution mix: 6 x 320x240, 6 x 640x480, 4 x (1280x720
-# RGB + 640x576 depth), interleaved so the first n streams keep the proportions.
-MIX16 = ["320x240", "640x480", "1280x720+640x576", "320x240", "640x480", "1280x720+640x576", "320x240",
-         "640x480", "1280x720+640x576", "320x240", "640x480", "1280x720+640x576", "320x240", "640x480",
-         "320x240", "640x480"]
-
-
-def request_flops(workload: str) -> float:
-    import synth
-    wl = synth.WORKLOADS[workload]
-    (hr, wr), (hd, wd) = wl["rgb"], wl["depth"]
-    return flops_per_model(3, hr, wr)["total"] + flops_per_model(1, hd, wd)["total"]
+    flops = sum(4 * n * n * D for n in lens)
+    sec = timed(lambda: R.op_attention(R.BF16, qkv, out, M, D, heads, seg, stream=stream), 10)
+    N1 = 3600
+    f1 = 4 * N1 * N1 * D
+    q1, o1 = qkv[:N1].contiguous(), out[:N1]
+    sec1 = timed(lambda: R.op_attention(R.BF16, q1, o1, N1, D, heads, [0, N1], stream=stream), 50)
+    sec1w = timed(lambda: R.op_attention(R.BF16, q1, o1, N1, D, heads, [0, N1], stream=stream, whole_units=True), 50)
+    assert R.take_device_error() == 0
+    peak = peaks().get("bf16_tflops")
+    tf = lambda f, s: f / s / 1e12  # noqa: E731
+    return {"kernel": "attn_tc_kernel + attn_combine_kernel (tcgen05 flash attention; the tick's RGB encoder "
+                      "attention: 16 segments, N = 900 x 6 + 3600 x 6 + 10800 x 4, 12 heads x 64)",
+            "bound": "tensor", "achieved": tf(flops, sec), "peak": peak, "unit": "TFLOP/s",
+            "frac": tf(flops, sec) / peak if peak else None, "traffic": ATTN_DRAM_BYTES_PER_LAUNCH,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)" if peak else None,
+            "flops_per_launch": flops, "us_per_launch": sec * 1e6,
+            "n3600_alone": {"us_per_launch": sec1 * 1e6, "achieved": tf(f1, sec1),
+                            "frac": tf(f1, sec1) / peak if peak else None},
+            "n3600_whole_units": {"us_per_launch": sec1w * 1e6, "achieved": tf(f1, sec1w),
+                                  "frac": tf(f1, sec1w) / peak if peak else None}}
 
 
 class StreamIO:
     """One conference stream's buffers: k clean references pushed once, then a
     few corrupted frames (seeded, same size) to recover in turn."""
 
-    def __init__(self, R, torch, ctx, sid, workload, seed, loss_rate, frames, on_device, p_gb=None, k=5):
+    def __init__(self, R, torch, ctx, sid, workload, seed, loss_rate, frames, on_device, k=5, values=False):
         import synth
         self.R, self.sid, self.workload = R, sid, workload
-        self.reqs, self.keep, self.planes = [], [], []
+        self.reqs, self.keep, self.planes, self.bufs = [], [], [], []
         self.on_device = on_device
         for f in range(frames):
             kw = dict(loss_rate=loss_rate) if loss_rate is not None else {}
@@ -565,7 +407,7 @@ class StreamIO:
         self.push_refs(ctx, rgb0, dep0)
         self.cleans = []
         for rgb, dep in self.planes:
-            self.reqs.append(self._request(torch, rgb, dep))
+            self.reqs.append(self._request(torch, rgb, dep, values))
             self.cleans.append(self._clean(torch, rgb, dep))
 
     def _buf(self, torch, a):
@@ -582,17 +424,21 @@ class StreamIO:
             ctx.poll(ctx.submit(R.request(self.sid, int(rgb.ref_index[j]), R.RGB | R.DEPTH | R.CLEAN, on_device=True,
                                           rgb=(fr, rgb.height, rgb.width), depth=(fd, dep.height, dep.width))))
 
-    def _request(self, torch, rgb, dep):
+    def _request(self, torch, rgb, dep, values):
         R = self.R
         (hr, wr), (hd, wd) = self.shape
         b = dict(ri=self._buf(torch, rgb.decoded), di=self._buf(torch, dep.decoded.view(np.int16)),
                  rm=self._buf(torch, rgb.mask.view(np.int32)), dm=self._buf(torch, dep.mask.view(np.int32)),
                  ro=self._buf(torch, np.zeros((hr, wr, 3), np.uint8)),
                  do=self._buf(torch, np.zeros((hd, wd), np.int16)))
+        if values:
+            b["rv"] = self._buf(torch, np.zeros((hr, wr, 3), np.float32))
+            b["dv"] = self._buf(torch, np.zeros((hd, wd), np.float32))
         self.keep.append(b)
+        self.bufs.append(b)
         return R.request(self.sid, rgb.index, R.RGB | R.DEPTH, on_device=self.on_device, rgb=(b["ri"], hr, wr),
                          rgb_mask=b["rm"], depth=(b["di"], hd, wd), depth_mask=b["dm"], rgb_out=b["ro"],
-                         depth_out=b["do"])
+                         depth_out=b["do"], rgb_values=b.get("rv"), depth_values=b.get("dv"))
 
     def _clean(self, torch, rgb, dep):
         R = self.R
@@ -606,78 +452,11 @@ class StreamIO:
         """An intact frame of this stream (it enters the reference history)."""
         return self.cleans[i % len(self.cleans)]
 
-
-def run_mixed(args) -> None:
-    """The batched mixed-resolution launch: 16 participant streams (6 x 320x240,
-    6 x 640x480, 4 x 1280x720 RGB + 640x576 depth), independent Gilbert-Elliott
-    loss per stream, all 16 frames admitted into one batch per step (one graph
-    replay per modality, autotuned GEMM tiles).  Beside it, the same 16 frames
-    recovered one per launch (batch 1) in the same context."""
-    import torch
-
-    import paper_2604_27441_b300 as R
-    import synth
-
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
-    precision = PRECISIONS[args.precision](R)
-    cfg = R.config(**VITB, precision=precision, max_height=720, max_width=1280, max_streams=16, max_batch=16,
-                   lanes=1, use_graphs=0 if args.no_graphs else 1, autotune=1)
-    ctx = R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
-                    synth.flatten(synth.weights(synth.DEPTH, seed=1)), stream=stream)
-    streams = [StreamIO(R, torch, ctx, sid, wl, 4000 + sid, None, 1, True) for sid, wl in enumerate(MIX16)]
-    flops = sum(request_flops(wl) for wl in MIX16)
-
-    def batched_step():
-        ts = [ctx.submit(_with_flag(R, s.reqs[0], R.HOLD if i < len(streams) - 1 else 0))
-              for i, s in enumerate(streams)]
-        res = [ctx.poll(t) for t in ts]
-        assert all(r.status == R.REVO_OK for r in res), R.last_error()
-        return res
-
-    def single_step():
-        return [ctx.poll(ctx.submit(s.reqs[0])) for s in streams]
-
-    out = {}
-    for name, fn in (("batched", batched_step), ("batch1", single_step)):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        steps = max(3, args.steps // 10)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(0) as clk:
-            e0.record(stream)
-            lat, sizes, launches = [], [], 0
-            for _ in range(steps):
-                res = fn()
-                lat += [r.latency_ms for r in res]
-                sizes += [r.batch_size for r in res]
-                launches += sum(r.kernel_launches for r in res) // max(1, res[0].batch_size) if name == "batched" \
-                    else sum(r.kernel_launches for r in res)
-            e1.record(stream)
-            torch.cuda.synchronize()
-        sec = e0.elapsed_time(e1) / 1e3
-        out[name] = {"frames_per_s": len(streams) * steps / sec, "ms_per_step": sec * 1e3 / steps,
-                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "mean_batch": float(np.mean(sizes)), "gpu_launches": launches, "steps": steps,
-                     "effective_tflops": flops * steps / sec / 1e12, "clocks": clk.summary()}
-    pk = peaks()
-    st = ctx.stats()
-    ctx.close()
-    line = {"metric": METRIC, "value": out["batched"]["frames_per_s"], "unit": UNIT, "n_gpus": 1,
-            "steps": out["batched"]["steps"], "warmup": args.warmup, "ms_per_step": out["batched"]["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE_NAMES[args.precision], "data": "synthetic",
-            "config": {"workload": "mixed16: 6 x 320x240 + 6 x 640x480 + 4 x (1280x720 RGB + 640x576 depth), "
-                                   "one batch of 16 per step", "flops_per_step": flops,
-                       "launch": "kernels" if args.no_graphs else "CUDA graph replay, autotuned GEMM tiles"},
-            "batched": out["batched"], "batch1": out["batch1"],
-            "speedup_vs_batch1": out["batched"]["frames_per_s"] / out["batch1"]["frames_per_s"],
-            "tensor_frac_of_measured_sustained": (out["batched"]["effective_tflops"] /
-                                                  pk["bf16_tflops_sustained"]) if pk.get("bf16_tflops_sustained")
-            else None,
-            "context": st}
-    print(json.dumps(line), flush=True)
+    def io_bytes(self):
+        """(host->device, device->host) bytes of one recovery request."""
+        (hr, wr), (hd, wd) = self.shape
+        h2d = hr * wr * 3 + hd * wd * 2 + 4 * (hr * ((wr + 31) // 32) + hd * ((wd + 31) // 32))
+        return h2d, hr * wr * 3 + hd * wd * 2
 
 
 def _with_flag(R, req, extra):
@@ -685,6 +464,74 @@ def _with_flag(R, req, extra):
     R.C.memmove(R.C.byref(c), R.C.byref(req), R.C.sizeof(R.Request))
     c.flags |= extra
     return c
+
+
+def tick_context(R, precision, stream, graphs=True, lanes=1):
+    import synth
+    cfg = R.config(**VITB, precision=precision, max_height=720, max_width=1280, max_streams=16, max_batch=16,
+                   lanes=lanes, use_graphs=1 if graphs else 0, autotune=1)
+    return R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
+                     synth.flatten(synth.weights(synth.DEPTH, seed=1)), stream=stream)
+
+
+def tick_streams(R, torch, ctx, on_device, base_seed=4000):
+    return [StreamIO(R, torch, ctx, sid, wl, base_seed + sid, None, 1, on_device) for sid, wl in enumerate(MIX16)]
+
+
+def tick_once(R, ctx, streams):
+    """Submits the 16 frames (all but the last with REVO_HOLD, so they form one
+    batch), polls them all."""
+    ts = [ctx.submit(_with_flag(R, s.reqs[0], R.HOLD if i < len(streams) - 1 else 0))
+          for i, s in enumerate(streams)]
+    res = [ctx.poll(t) for t in ts]
+    if not all(r.status == R.REVO_OK for r in res):
+        raise RuntimeError(f"tick failed: {R.last_error()}")
+    return res
+
+
+def measure_tick(R, torch, ctx, streams, stream, steps, warmup, clock_gpu=None):
+    """Device-timed ticks (CUDA events on the context's stream)."""
+    for _ in range(warmup):
+        tick_once(R, ctx, streams)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat, launches = [], 0
+    clk = ClockSampler(clock_gpu) if clock_gpu is not None else None
+    if clk:
+        clk.__enter__()
+    try:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            res = tick_once(R, ctx, streams)
+            lat += [r.latency_ms for r in res]
+            launches += res[0].kernel_launches  # every request of the batch reports the batch's launches
+        e1.record(stream)
+        torch.cuda.synchronize()
+    finally:
+        if clk:
+            clk.__exit__()
+    sec = e0.elapsed_time(e1) / 1e3
+    flops = sum(request_flops(wl) for wl in MIX16)
+    return {"seconds": sec, "frames_per_s": len(streams) * steps / sec, "ms_per_step": sec * 1e3 / steps,
+            "steps": steps, "launches": launches, "tick_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                                                       "p99": float(np.percentile(lat, 99))},
+            "effective_tflops": flops * steps / sec / 1e12, "clocks": clk.summary() if clk else None}
+
+
+def measure_tick_e2e(R, torch, ctx, streams, steps):
+    """The tick through pinned host buffers: the frame and mask copies in at
+    submit and the blended frames out before poll returns, host clock."""
+    tick_once(R, ctx, streams)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        tick_once(R, ctx, streams)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    h2d = sum(s.io_bytes()[0] for s in streams)
+    d2h = sum(s.io_bytes()[1] for s in streams)
+    return sec, h2d, d2h
 
 
 def arrival_schedule(n_streams: int, seconds: float, rng, fps: float = 30.0) -> list:
@@ -707,32 +554,26 @@ def arrival_schedule(n_streams: int, seconds: float, rng, fps: float = 30.0) -> 
     return events
 
 
-def run_serving(args) -> None:
-    """Serving loop: `--streams` conference streams of the mixed resolutions,
+def measure_serving(R, torch, precision, n_streams, seconds, serve_warmup, max_batch=8, lanes=2, graphs=True):
+    """Serving loop: n_streams conference streams of the mixed resolutions,
     each sending 30 frames/s (uniform phase, per-frame jitter
     clip(Poisson(5) - 5, -5, 5) ms), Gilbert-Elliott slice loss at a per-stream
     rate drawn from 10-30 %, every 30th frame intact (REVO_CLEAN, it refreshes
     the stream's references).  Frames are submitted from pinned host memory as
     they arrive and polled without blocking; latency = submit -> completion seen
-    by poll.  The first `--serve-warmup` seconds are not counted."""
-    import torch
-
-    import paper_2604_27441_b300 as R
-
+    by poll.  Frames arriving in the first serve_warmup seconds are not counted."""
     import synth
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(5000 + args.streams)
-    precision = PRECISIONS[args.precision](R)
-    cfg = R.config(**VITB, precision=precision, max_height=720, max_width=1280, max_streams=args.streams,
-                   max_batch=args.max_batch, lanes=args.lanes, use_graphs=0 if args.no_graphs else 1, autotune=1,
+    rng = np.random.default_rng(5000 + n_streams)
+    cfg = R.config(**VITB, precision=precision, max_height=720, max_width=1280, max_streams=n_streams,
+                   max_batch=max_batch, lanes=lanes, use_graphs=1 if graphs else 0, autotune=1,
                    hbm_budget_bytes=40 << 30)
     ctx = R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
                     synth.flatten(synth.weights(synth.DEPTH, seed=1)))
-    wls = [MIX16[i % len(MIX16)] for i in range(args.streams)]
-    rates = rng.uniform(0.10, 0.30, args.streams)
+    wls = [MIX16[i % len(MIX16)] for i in range(n_streams)]
+    rates = rng.uniform(0.10, 0.30, n_streams)
     streams = [StreamIO(R, torch, ctx, sid, wl, 6000 + sid, float(rates[sid]), 3, False)
                for sid, wl in enumerate(wls)]
-    events = arrival_schedule(args.streams, args.seconds, rng)
+    events = arrival_schedule(n_streams, seconds, rng)
     outstanding = {}  # ticket -> (sid, arrival ms, flops)
     lat, done_frames, late, eagain, clean = [], 0, 0, 0, 0
     flops_done = 0.0
@@ -752,7 +593,7 @@ def run_serving(args) -> None:
                 sid, t_arr, fl = outstanding.pop(t)
                 if r.status != R.REVO_OK:
                     raise RuntimeError(f"serving request failed: {R.STATUS_NAMES.get(r.status)} {R.last_error()}")
-                if t_arr >= args.serve_warmup * 1e3:
+                if t_arr >= serve_warmup * 1e3:
                     lat.append(r.latency_ms)
                     done_frames += 1
                     flops_done += fl
@@ -761,7 +602,7 @@ def run_serving(args) -> None:
                 return
             time.sleep(0.0002)
 
-    with ClockSampler(0) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         for t_arr, sid, n in events:
             drain(block_until=t_arr)
             s = streams[sid]
@@ -783,27 +624,215 @@ def run_serving(args) -> None:
             outstanding[tk] = (sid, t_arr, request_flops(s.workload))
         while outstanding:
             drain(block_until=now_ms() + 1.0)
-        wall = now_ms() - args.serve_warmup * 1e3
+        wall = now_ms() - serve_warmup * 1e3
     st = ctx.stats()
     ctx.close()
     lat_s = sorted(lat)
-    offered = sum(1 for t, _, n in events if t >= args.serve_warmup * 1e3 and n % 30 != 29)
-    line = {"metric": METRIC, "value": done_frames / (wall / 1e3), "unit": UNIT, "n_gpus": 1,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE_NAMES[args.precision], "data": "synthetic",
-            "config": {"workload": f"serving: {args.streams} streams at 30 fps, resolutions {sorted(set(wls))}",
-                       "seconds": args.seconds, "warmup_s": args.serve_warmup, "max_batch": args.max_batch,
-                       "lanes": args.lanes, "hbm_budget_gb": 40, "inputs": "pinned host buffers"},
+    offered = sum(1 for t, _, n in events if t >= serve_warmup * 1e3 and n % 30 != 29)
+    return {"frames_per_s": done_frames / (wall / 1e3),
             "latency_ms": {"p50": float(np.percentile(lat_s, 50)) if lat_s else None,
                            "p99": float(np.percentile(lat_s, 99)) if lat_s else None,
                            "max": float(lat_s[-1]) if lat_s else None, "budget": FRAME_BUDGET_MS,
                            "over_budget": late},
+            "streams": n_streams, "seconds": seconds, "warmup_s": serve_warmup, "max_batch": max_batch,
+            "lanes": lanes, "hbm_budget_gb": 40, "inputs": "pinned host buffers",
             "offered_frames": offered, "recovered_frames": done_frames, "rejected_eagain": eagain,
-            "clean_frames": clean, "offered_tflops": sum(request_flops(wls[sid]) for t, sid, n in events
-                                                         if t >= args.serve_warmup * 1e3 and n % 30 != 29)
-            / (wall / 1e3) / 1e12, "achieved_tflops": flops_done / (wall / 1e3) / 1e12,
-            "clocks": clk.summary(), "context": st}
-    print(json.dumps(line), flush=True)
+            "clean_frames": clean,
+            "offered_tflops": sum(request_flops(wls[sid]) for t, sid, n in events
+                                  if t >= serve_warmup * 1e3 and n % 30 != 29) / (wall / 1e3) / 1e12,
+            "achieved_tflops": flops_done / (wall / 1e3) / 1e12, "clocks": clk.summary(), "context": st}
+
+
+def measure_batch1(R, torch, precision, stream, steps, warmup, in_flight=2, graphs=True, local=0, rank=0):
+    """One 640x480 RGB-D frame per launch, `in_flight` frames in flight on as
+    many lanes; four streams (5/10/20/40 % loss) in turn.  Stream 2 (20 %) also
+    writes the de-normalised float outputs for the quality check."""
+    import synth
+    cfg = R.config(**VITB, precision=precision, device=local, max_height=H, max_width=W, max_streams=8,
+                   max_batch=1, lanes=in_flight, use_graphs=1 if graphs else 0, autotune=1)
+    ctx = R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
+                    synth.flatten(synth.weights(synth.DEPTH, seed=1)), stream=stream)
+    streams = [StreamIO(R, torch, ctx, sid, "640x480", 2000 + 100 * rank + sid, r, 1, True, values=sid == 2)
+               for sid, r in enumerate(LOSS_RATES)]
+    reqs = [s.reqs[0] for s in streams]
+    run_pipelined(R, ctx, reqs, warmup, in_flight)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat, launches = run_pipelined(R, ctx, reqs, steps, in_flight)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    lat_s = sorted(lat)
+    out = {"frames_per_s": steps / sec, "ms_per_step": sec * 1e3 / steps, "steps": steps, "batch": 1,
+           "in_flight": in_flight, "latency_ms": {"p50": float(np.percentile(lat_s, 50)),
+                                                  "p99": float(np.percentile(lat_s, 99))},
+           "gpu_launches_per_frame": launches / steps}
+    run_pipelined(R, ctx, [reqs[2]], 1, 1)
+    b = streams[2].bufs[0]
+    values = (b["rv"].cpu().numpy().astype(np.float64), b["dv"].cpu().numpy().astype(np.float64))
+    ctx.close()
+    return out, values, streams[2].planes[0]
+
+
+def oracle_640_values(plane_pair):
+    """The FP64 oracle's de-normalised outputs (RGB in [0, 1] units, depth in
+    mm) for the 640x480 RGB-D frame the batch-1 runs write values for."""
+    import synth
+    from oracle import revo_oracle as O
+    rgb, dep = plane_pair
+    _, vr = O.recover("rgb", synth.weights(synth.RGB, seed=0), synth.RGB, rgb.refs, rgb.ref_index, rgb.decoded,
+                      rgb.mask, rgb.index)
+    _, vd = O.recover("depth", synth.weights(synth.DEPTH, seed=1), synth.DEPTH, dep.refs, dep.ref_index,
+                      dep.decoded, dep.mask, dep.index)
+    return vr, vd
+
+
+def quality(values, ref) -> dict:
+    """Error of one precision's float outputs against the FP64 oracle: PSNR of
+    RGB in [0, 1] units and of depth / 65535, max |error| in [0, 1] units and mm."""
+    er = values[0] - ref[0]
+    ed = values[1] - ref[1]
+
+    def psnr(e, peak):
+        mse = float(np.mean(e * e))
+        return 10 * np.log10(peak * peak / mse) if mse > 0 else float("inf")
+    return {"rgb_psnr_db": psnr(er, 1.0), "rgb_max_abs_err": float(np.abs(er).max()),
+            "depth_psnr_db": psnr(ed / 65535.0, 1.0), "depth_max_abs_err_mm": float(np.abs(ed).max()),
+            "gate": "PSNR >= 45 dB (RGB, depth / 65535), depth max <= 8 mm; FP32: <= 1e-4 RGB, <= 1 mm depth"}
+
+
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    import paper_2604_27441_b300 as R
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    stream = torch.cuda.Stream()
+    precision = PRECISIONS[args.precision](R)
+    ctx = tick_context(R, precision, stream, graphs=not args.no_graphs)
+    streams = tick_streams(R, torch, ctx, True, base_seed=4000 + 100 * rank)
+    for _ in range(2):  # autotuning and graph capture of the batch's size pattern
+        tick_once(R, ctx, streams)
+    torch.cuda.synchronize()
+    rank_barrier(world)
+
+    # Timed region: device-resident inputs and outputs, CUDA events.
+    tick = measure_tick(R, torch, ctx, streams, stream, args.steps, args.warmup, clock_gpu=local)
+    rank_barrier(world)
+    dev_s_max = rank_max(tick["seconds"], world)
+    value = whole_job_rate(args.steps, dev_s_max, world, len(MIX16))
+    ctx_stats = ctx.stats()
+
+    # End to end: the same tick through pinned host buffers.
+    hstreams = tick_streams(R, torch, ctx, False, base_seed=4000 + 100 * rank)
+    e2e_steps = max(3, args.steps // 2)
+    e2e_s, h2d, d2h = measure_tick_e2e(R, torch, ctx, hstreams, e2e_steps)
+    e2e_s = rank_max(e2e_s, world)
+    e2e = {"value": world * e2e_steps * len(MIX16) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+    ctx.close()
+    del streams, hstreams
+
+    extra = {}
+    if world == 1 and not args.quick:
+        roof = attention_roofline(R, torch, stream) if precision != R.FP32 else None
+        # FP8 tick, same workload.
+        if args.precision == "bf16":
+            c8 = tick_context(R, R.FP8, stream, graphs=not args.no_graphs)
+            s8 = tick_streams(R, torch, c8, True)
+            for _ in range(2):
+                tick_once(R, c8, s8)
+            t8 = measure_tick(R, torch, c8, s8, stream, max(5, args.steps // 2), 2)
+            extra["tick_fp8"] = {k: t8[k] for k in ("frames_per_s", "ms_per_step", "steps", "tick_latency_ms",
+                                                     "effective_tflops")}
+            c8.close()
+            del s8
+        # Batch-1 frames at every precision, their error against the FP64 oracle.
+        b1, vals, plane_pair = {}, {}, None
+        for name in ("bf16", "fp8", "fp32"):
+            n = 6 if name == "fp32" else 40
+            b1[name], vals[name], plane_pair = measure_batch1(R, torch, PRECISIONS[name](R), stream, n, 4,
+                                                              graphs=not args.no_graphs)
+        ref = oracle_640_values(plane_pair) if not args.no_cpu_baseline else None
+        if ref is not None:
+            for name in b1:
+                b1[name]["quality_vs_fp64"] = quality(vals[name], ref)
+        b1["speedup_bf16_vs_fp32"] = b1["bf16"]["frames_per_s"] / b1["fp32"]["frames_per_s"]
+        extra["batch1_640x480"] = b1
+        extra["speedup_tick_vs_fp32_batch1"] = value / b1["fp32"]["frames_per_s"]
+        # Real-time serving at 8 streams (BF16 and FP8).
+        serving = {}
+        for name in ("bf16", "fp8"):
+            serving[name] = measure_serving(R, torch, PRECISIONS[name](R), args.serve_streams, args.seconds,
+                                            args.serve_warmup)
+        extra["serving"] = serving
+        extra["latency_ms"] = dict(serving[args.precision if args.precision in serving else "bf16"]["latency_ms"],
+                                   source=f"serving loop, {args.serve_streams} streams x 30 fps of the mix, "
+                                          f"{args.seconds:.0f} s, {args.precision}")
+        extra["roofline"] = roof
+        extra["elementwise"] = elementwise_roofline(R, torch, stream)
+        if not args.no_cpu_baseline:
+            inputs = oracle_sample_inputs()
+            secs = [oracle_frame_seconds(inputs) for _ in range(args.oracle_frames)]
+            per = statistics.mean(secs)
+            extra["cpu_baseline"] = {"value": oracle_tick_rate(per), "unit": UNIT, "cores": os.cpu_count(),
+                                     "kind": "oracle", "sample": oracle_sample_text(per, args.oracle_frames)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tick["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[args.precision],
+            "data": "synthetic (seeded RGB-D frames, Gilbert-Elliott slice loss, random-init ViT-B weights)",
+            "config": {**tick_config(world),
+                       "launch": "kernels" if args.no_graphs else "one CUDA graph replay per modality per tick, "
+                                 "autotuned GEMM tile widths",
+                       "l2": "working set > L2: bf16 weights of both models (0.37 GB) and 1.4 GB of activations "
+                             "per tick"},
+            "flops_per_step": sum(request_flops(wl) for wl in MIX16),
+            "effective_tflops": tick["effective_tflops"], "tick_latency_ms": tick["tick_latency_ms"],
+            "clocks": tick["clocks"], "e2e": e2e, "gpu_launches": tick["launches"],
+            "context": ctx_stats, **extra,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_640(args) -> None:
+    """The batch-1 640x480 RGB-D step alone (one precision), two frames in flight."""
+    import torch
+
+    import paper_2604_27441_b300 as R
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    with ClockSampler(0) as clk:
+        out, _, _ = measure_batch1(R, torch, PRECISIONS[args.precision](R), stream, args.steps, args.warmup,
+                                   in_flight=args.in_flight, graphs=not args.no_graphs)
+    print(json.dumps({"metric": METRIC, "value": out["frames_per_s"], "unit": UNIT, "n_gpus": 1,
+                      "dtype": DTYPE_NAMES[args.precision], "config": {"workload": "640x480 RGB-D batch 1"},
+                      **out, "clocks": clk.summary()}), flush=True)
+
+
+def run_serving(args) -> None:
+    import torch
+
+    import paper_2604_27441_b300 as R
+    torch.cuda.set_device(0)
+    out = measure_serving(R, torch, PRECISIONS[args.precision](R), args.serve_streams, args.seconds,
+                          args.serve_warmup, max_batch=args.max_batch, lanes=args.lanes, graphs=not args.no_graphs)
+    print(json.dumps({"metric": METRIC, "value": out["frames_per_s"], "unit": UNIT, "n_gpus": 1,
+                      "dtype": DTYPE_NAMES[args.precision], "data": "synthetic",
+                      "config": {"workload": f"serving: {args.serve_streams} streams at 30 fps of the mix"},
+                      **out}), flush=True)
 
 
 def run_kt(args) -> None:
@@ -827,7 +856,7 @@ def run_kt(args) -> None:
                                  max_batch=1, lanes=1, use_graphs=1, autotune=1),
                         synth.flatten(synth.weights(cfgs[0], seed=0)), synth.flatten(synth.weights(cfgs[1], seed=1)),
                         stream=stream)
-        io = StreamIO(R, torch, ctx, 0, WORKLOAD, 7000 + 10 * k + T, 0.2, 1, True, k=k)
+        io = StreamIO(R, torch, ctx, 0, "640x480", 7000 + 10 * k + T, 0.2, 1, True, k=k)
         req = io.reqs[0]
         for _ in range(args.warmup):
             ctx.poll(ctx.submit(req))
@@ -846,7 +875,7 @@ def run_kt(args) -> None:
         ctx.close()
     print(json.dumps({"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
                       "dtype": DTYPE_NAMES[args.precision], "data": "synthetic",
-                      "config": {"workload": f"k/T sweep, {WORKLOAD} RGB-D, batch 1"}, "rows": rows}), flush=True)
+                      "config": {"workload": "k/T sweep, 640x480 RGB-D, batch 1"}, "rows": rows}), flush=True)
 
 
 def run_profile_kernel(args) -> None:
@@ -858,17 +887,21 @@ def run_profile_kernel(args) -> None:
     fl = flops_per_model(3, H, W)
     N, D = fl["N"], 768
     stream = torch.cuda.Stream()
-    if args.profile_kernel == "attention":
+    if args.profile_kernel in ("attention", "attention_whole"):
         qkv = torch.randn((N, 3 * D), device="cuda").to(torch.bfloat16)
         out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
-        launch = lambda: R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream)  # noqa: E731
-        flops = fl["attn_enc_per_block"]
-    elif args.profile_kernel == "attention_split":
-        qkv = torch.randn((N, 3 * D), device="cuda").to(torch.bfloat16)
-        out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
+        whole = args.profile_kernel == "attention_whole"
         launch = lambda: R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream,  # noqa: E731
-                                        split_tail=True)
+                                        whole_units=whole)
         flops = fl["attn_enc_per_block"]
+    elif args.profile_kernel == "attention_tick":  # the tick's batched RGB encoder attention
+        lens = tick_segments(True)
+        seg = np.concatenate([[0], np.cumsum(lens)]).astype(int).tolist()
+        M = seg[-1]
+        qkv = torch.randn((M, 3 * D), device="cuda").to(torch.bfloat16)
+        out = torch.empty((M, D), dtype=torch.bfloat16, device="cuda")
+        launch = lambda: R.op_attention(R.BF16, qkv, out, M, D, 12, seg, stream=stream)  # noqa: E731
+        flops = sum(4 * n * n * D for n in lens)
     elif args.profile_kernel in ("assemble", "blend"):  # the HBM-bound stages at 1280x720 RGB, k = 5, T = 2
         Hh, Ww, k, T, p = 720, 1280, 5, 2, 16
         frames = [torch.randint(0, 256, (Hh, Ww, 3), dtype=torch.uint8, device="cuda") for _ in range(k + 1)]
@@ -930,29 +963,28 @@ def run_profile_kernel(args) -> None:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "fc1", "fc1_pair", "fc1_fp8", "fc1_fp8_pair",
-                                                 "fc2", "fc2_pair",
-                             "assemble", "blend"],
-                    default=None,
-                    help="only launch one kernel of the step (for profiler captures)")
+    ap.add_argument("--profile-kernel", choices=["attention", "attention_whole", "attention_tick", "fc1", "fc1_pair",
+                                                 "fc1_fp8", "fc1_fp8_pair", "fc2", "fc2_pair", "assemble", "blend"],
+                    default=None, help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the FP64 oracle (quality and cpu_baseline)")
     ap.add_argument("--no-graphs", action="store_true", help="plain kernel launches instead of graph replay")
-    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
-    ap.add_argument("--workload", choices=["640x480", "mixed16", "serving", "kt"], default="640x480",
-                    help="640x480: the headline batch-1 step; mixed16: one batch of 16 mixed-size streams; "
-                         "serving: real-time arrivals from --streams streams")
-    ap.add_argument("--streams", type=int, default=4)
-    ap.add_argument("--seconds", type=float, default=30.0)
+    ap.add_argument("--quick", action="store_true", help="the tick and its e2e only")
+    ap.add_argument("--workload", choices=["mixed16", "640x480", "serving", "kt"], default="mixed16",
+                    help="mixed16: the headline line; 640x480: batch-1 frames only; serving: the real-time loop "
+                         "only; kt: the k/T latency sweep")
+    ap.add_argument("--serve-streams", "--streams", dest="serve_streams", type=int, default=8)
+    ap.add_argument("--seconds", type=float, default=20.0)
     ap.add_argument("--serve-warmup", type=float, default=3.0)
     ap.add_argument("--max-batch", type=int, default=8)
     ap.add_argument("--lanes", type=int, default=2)
+    ap.add_argument("--oracle-frames", type=int, default=2, help="320x240 RGB-D frames the cpu_baseline times")
     ap.add_argument("--in-flight", type=int, default=2,
-                    help="headline: batch-1 frames in flight (one lane each); 1 = submit, wait, repeat")
+                    help="640x480 workload: batch-1 frames in flight (one lane each); 1 = submit, wait, repeat")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -960,8 +992,8 @@ def main():
         run_profile_kernel(args)
     elif args.impl == "reference":
         run_reference(args)
-    elif args.workload == "mixed16":
-        run_mixed(args)
+    elif args.workload == "640x480":
+        run_640(args)
     elif args.workload == "serving":
         run_serving(args)
     elif args.workload == "kt":

@@ -100,10 +100,13 @@ typedef struct {
   int use_graphs;                /* 1 = replay captured CUDA graphs per batch shape */
   int autotune;                  /* 1 = time the GEMM tile widths per shape on first
                                     use and keep the fastest (tensor-core path)  */
-  int fp8_layers;                /* REVO_FP8: which LayerNorm-fed layers run in E4M3
-                                    (bit 0 encoder qkv, 1 encoder fc1, 2 decoder
-                                    qkv, 3 decoder fc1; the rest stay bf16);
-                                    0 = the default set: encoder fc1 only       */
+  int fp8_layers;                /* REVO_FP8: which LayerNorm-fed layers run in E4M3,
+                                    bits 0-3 for the RGB model, bits 4-7 for the
+                                    depth model (per model: bit 0 encoder qkv, 1
+                                    encoder fc1, 2 decoder qkv, 3 decoder fc1; the
+                                    rest stay bf16); 0 = the default: all four in
+                                    the RGB model, none in the depth model (its
+                                    8 mm gate fails with E4M3 at 300-5000 mm) */
   const float* rgb_weights;      /* host, flat float32, NULL = no RGB model      */
   size_t rgb_weights_count;
   const float* depth_weights;    /* host, flat float32, NULL = no depth model    */
@@ -436,13 +439,16 @@ REVO_API revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const 
  * host array of segment boundaries in [0, M]; tokens attend only within their
  * segment.  out [M][D].  REVO_FP32: float32 in and out.  REVO_BF16: qkv and out
  * bf16, tcgen05 tensor cores, float32 softmax.  n_seg <= 64.
- * flags (REVO_BF16): bit 0 (REVO_ATTN_SPLIT_TAIL) lets the work units of a
- * last, partly filled wave of CTAs split their key range over the idle SMs
- * (partial results merged by a second kernel); it pays when nothing else runs
- * on the GPU and changes the summation order (results equal within rounding,
- * not bit for bit).  0: one launch, whole key range per unit.
+ * REVO_BF16 work split: each segment's (head, 256-query) units are laid end
+ * to end over their 128-key tiles and cut into equal pieces, one per CTA, so
+ * that the segment's pieces fill the GPU's SMs once; units cut in two are
+ * merged by a second kernel.  The cut depends on the segment's length only, so
+ * a segment's output is bit for bit the same alone and among other segments.
+ * flags bit 1 (REVO_ATTN_WHOLE_UNITS): one CTA per unit instead, one launch
+ * (results equal within rounding, not bit for bit).  The step-level entry
+ * point keeps its partial-result buffer per device (grown on demand).
  */
-#define REVO_ATTN_SPLIT_TAIL 1
+#define REVO_ATTN_WHOLE_UNITS 2
 REVO_API revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D,
                               int heads, const int* seg_start, int n_seg, int flags, void* stream);
 

@@ -272,10 +272,14 @@ def op_frame_metrics(a, b, height, width, channels, sample_bytes, data_range, sc
                                               _stream(stream)), "revo_op_frame_metrics")
 
 
-def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None, split_tail=False):
+ATTN_WHOLE_UNITS = 2
+
+
+def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None, whole_units=False):
     n = len(seg_start) - 1
     arr = (C.c_int * len(seg_start))(*[int(v) for v in seg_start])
-    return _check(lib().revo_op_attention(precision, ptr(qkv), ptr(out), M, D, heads, arr, n, int(bool(split_tail)),
+    flags = ATTN_WHOLE_UNITS if whole_units else 0
+    return _check(lib().revo_op_attention(precision, ptr(qkv), ptr(out), M, D, heads, arr, n, flags,
                                           _stream(stream)),
                   "revo_op_attention")
 

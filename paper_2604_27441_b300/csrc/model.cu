@@ -216,7 +216,7 @@ namespace {
 struct WsLayout {
   size_t tok, x, h, qkv, att, mlp, head, err, h8, h8s, part, total;
 };
-WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp) {
+WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_seg) {
   const size_t e = precision != REVO_FP32 ? 2 : 4;
   const size_t D = s.D > s.Dd ? s.D : s.Dd;
   WsLayout l{};
@@ -234,7 +234,13 @@ WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp) {
   l.mlp = put(static_cast<size_t>(cap) * s.r * D * e);
   l.head = put(static_cast<size_t>(capp) * s.head_dim_out() * 4);
   l.err = put(256);
-  if (precision != REVO_FP32) l.part = put(attention_partial_bytes(device_sm_count()));
+  if (precision != REVO_FP32) {
+    // Up to max_seg requests of up to cap / max_seg tokens, at either width.
+    const int seg_len = max_seg > 0 ? (cap + max_seg - 1) / max_seg : cap;
+    const int sms = device_sm_count();
+    l.part = put(std::max(attention_partial_bytes_bound(max_seg, seg_len, s.H, sms),
+                          attention_partial_bytes_bound(max_seg, seg_len, s.Hd, sms)));
+  }
   if (precision == REVO_FP8) {
     l.h8 = put(static_cast<size_t>(cap) * D);
     l.h8s = put(static_cast<size_t>(cap) * 4);
@@ -244,12 +250,13 @@ WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp) {
 }
 }  // namespace
 
-size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches) {
-  return ws_layout(s, precision, cap_tokens, cap_patches).total;
+size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments) {
+  return ws_layout(s, precision, cap_tokens, cap_patches, max_segments).total;
 }
 
-Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, int cap_patches, std::string* err) {
-  const WsLayout l = ws_layout(s, precision, cap_tokens, cap_patches);
+Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments,
+                            std::string* err) {
+  const WsLayout l = ws_layout(s, precision, cap_tokens, cap_patches, max_segments);
   uint8_t* base = nullptr;
   if (cudaMalloc(&base, l.total) != cudaSuccess) {
     *err = "workspace allocation failed";
@@ -297,8 +304,7 @@ struct Fwd {
   int sms;
   bool tc;
   size_t e;  // activation element size
-  int extra_launches = 0;  // kernels beyond one per attention (split waves)
-  bool split_tail = false;  // let attention's last wave split its key range
+  int extra_launches = 0;  // kernels beyond one per attention (the combine of split units)
 
   // `amap` / `cmap`: the A operand and output tensor maps (tensor-core path).
   cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M,
@@ -424,8 +430,7 @@ struct Fwd {
     if (tc)
     {
       int nl = 1;
-      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st, split_tail ? ws->attn_part : nullptr,
-                              ws->sms, &nl);
+      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st, ws->attn_part, ws->sms, &nl);
       extra_launches += nl - 1;
     }
     else
@@ -533,13 +538,12 @@ cudaError_t prepare_job_args(const Net* net, const Workspace* ws, const PlaneJob
 }
 
 cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
-                        int* launches, const JobArgs* dev_args, bool split_tail) {
+                        int* launches, const JobArgs* dev_args) {
   const NetShape& s = net->s;
   if (launches) *launches = 0;
   if (n <= 0) return cudaSuccess;
   if (n > kMaxSegments) return cudaErrorInvalidValue;
   Fwd f{net, ws, st, num_sms, net->precision != REVO_FP32, net->precision != REVO_FP32 ? 2u : 4u};
-  f.split_tail = split_tail;
   Segments seg{};
   int patches = 0;
   if (!batch_segments(s, jobs, n, &seg, &patches)) return cudaErrorInvalidValue;

@@ -95,7 +95,7 @@ struct Workspace {
   float* head = nullptr; // [cap_patches][C*p*p]
   uint8_t* h8 = nullptr;  // [cap][max width] E4M3 LayerNorm output (FP8 precision)
   float* h8_scale = nullptr;  // [cap] its per-token scales
-  float* attn_part = nullptr;  // split-wave partial results of the tensor-core attention
+  float* attn_part = nullptr;  // partial results of the tensor-core attention's split units
   int sms = 0;
   int* err = nullptr;    // device error word of the tensor-core kernels
   size_t bytes = 0;
@@ -112,8 +112,10 @@ Net* net_create(const NetShape& s, int precision, const float* host_weights, std
 void net_destroy(Net* n);
 size_t net_bytes(const NetShape& s, int precision);
 
-size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches);
-Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, int cap_patches, std::string* err);
+// max_segments: requests per batch (sizes the attention's partial results).
+size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments);
+Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments,
+                            std::string* err);
 void workspace_destroy(Workspace* w);
 
 // Tokens of one request of height H and width W.
@@ -138,9 +140,7 @@ cudaError_t prepare_job_args(const Net* net, const Workspace* ws, const PlaneJob
 // prepare_job_args' output, written before the kernels run) the per-request
 // kernels read their arguments from it instead of taking them by value, so the
 // enqueued work depends on the request sizes only and can be captured once.
-// split_tail: let attention's last, partly filled wave split its key range
-// (worth it when nothing else shares the GPU; changes the rounding order).
 cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
-                        int* launches, const JobArgs* dev_args = nullptr, bool split_tail = false);
+                        int* launches, const JobArgs* dev_args = nullptr);
 
 }  // namespace revo

@@ -50,17 +50,26 @@ int* op_error_word() {
   return g_err_word[dev];
 }
 
-// The split-wave scratch of the step-level attention (one per device,
-// allocated on first use; calls on one device run in stream order).
-float* op_attention_partial() {
+// The partial-result scratch of the step-level attention (one per device,
+// grown on demand; calls on one device run in stream order).
+float* op_attention_partial(size_t bytes) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   static float* bufs[64] = {};
+  static size_t sizes[64] = {};
   std::lock_guard<std::mutex> lk(g_err_mu);
-  if (!bufs[dev]) {
+  if (!bufs[dev] || sizes[dev] < bytes) {
+    if (bufs[dev]) {
+      // Earlier launches may still read the old buffer.
+      if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
+      cudaFree(bufs[dev]);
+      bufs[dev] = nullptr;
+      sizes[dev] = 0;
+    }
     float* p = nullptr;
-    if (cudaMalloc(&p, attention_partial_bytes(device_sm_count())) != cudaSuccess) return nullptr;
+    if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) return nullptr;
     bufs[dev] = p;
+    sizes[dev] = bytes;
   }
   return bufs[dev];
 }
@@ -410,7 +419,14 @@ revo_status revo_op_attention(revo_precision precision, const void* qkv, void* o
   }
   int* err = op_error_word();
   if (!err) return REVO_ECUDA;
-  float* part = (flags & REVO_ATTN_SPLIT_TAIL) ? op_attention_partial() : nullptr;
+  float* part = nullptr;
+  if (!(flags & REVO_ATTN_WHOLE_UNITS)) {
+    const size_t need = attention_partial_bytes(M, heads, seg, device_sm_count());
+    if (!(part = op_attention_partial(need))) {
+      set_last_error("revo_op_attention: partial-result buffer allocation failed");
+      return REVO_ENOMEM;
+    }
+  }
   return cuda_status(launch_attention_tc(m, out, M, D, heads, seg, err, st, part, device_sm_count()),
                      "revo_op_attention");
 }

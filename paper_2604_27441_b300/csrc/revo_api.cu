@@ -33,11 +33,13 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kMaxLanes = 8;
-// FP8 precision, layers in E4M3 unless the config names others: the encoder's
-// fc1 (its largest Linear).  With the encoder's qkv as well the 640x480 depth
-// error reached 10.3 mm against the FP64 forward, above the 8 mm gate; fc1
-// alone measured 5.9 mm and 69 dB RGB PSNR.
-constexpr int kDefaultFp8Layers = 0x2;
+// FP8 precision, layers in E4M3 per model unless the config names others.  RGB:
+// all four LayerNorm-fed layers (encoder and decoder qkv and fc1; 64 dB against
+// the FP64 forward at 640x480).  Depth: none -- its millimetre gate is the
+// binding one: the encoder fc1 alone gave 5.9 mm at 640x480 (500-4000 mm) but
+// 17.6 mm on the 640x576 stream of 300-5000 mm, above the 8 mm gate, and every
+// larger set measured worse.
+constexpr int kDefaultFp8Layers[2] = {0xF, 0x0};
 
 struct Ring {
   int H = 0, W = 0;
@@ -245,13 +247,13 @@ bool lane_idle(revo_ctx* c, int l) {
 // request sizes is replayed.  A size pattern runs eagerly (reading the same
 // table) the first time it is seen, so every kernel's one-time set-up happens
 // outside a capture, and is captured the second time.
-cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob>& jobs, bool split, int* launches) {
+cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob>& jobs, int* launches) {
   Net* net = c->net[m];
   Workspace* ws = L.ws[m];
   cudaStream_t s = L.st[m];
   const int n = static_cast<int>(jobs.size());
   if (!c->cfg.use_graphs || !L.dev_args[m])
-    return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, nullptr, split);
+    return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, nullptr);
 
   const int r = L.args_next[m];
   L.args_next[m] = (r + 1) % kArgRing;
@@ -263,7 +265,7 @@ cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob
     return e;
   if ((e = cudaEventRecord(L.args_ev[m][r], s)) != cudaSuccess) return e;
 
-  std::vector<int> key{split ? 1 : 0};
+  std::vector<int> key;
   for (const PlaneJob& j : jobs) {
     key.push_back(j.H);
     key.push_back(j.W);
@@ -271,16 +273,16 @@ cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob
   auto it = L.graphs[m].find(key);
   if (it == L.graphs[m].end()) {
     if (static_cast<int>(L.graphs[m].size()) >= kMaxGraphs)
-      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m], split);
+      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m]);
     it = L.graphs[m].emplace(key, GraphEntry{}).first;
   }
   GraphEntry& g = it->second;
   if (!g.exec) {
     if (g.failed || g.seen++ == 0)
-      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m], split);
+      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m]);
     if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     int nl = 0;
-    const cudaError_t ef = net_forward(net, ws, jobs.data(), n, s, c->sms, &nl, L.dev_args[m], split);
+    const cudaError_t ef = net_forward(net, ws, jobs.data(), n, s, c->sms, &nl, L.dev_args[m]);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(s, &graph);
     cudaError_t ei = cudaErrorUnknown;
@@ -292,7 +294,7 @@ cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob
       (void)cudaGetLastError();
       g.exec = nullptr;
       g.failed = true;
-      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m], split);
+      return net_forward(net, ws, jobs.data(), n, s, c->sms, launches, L.dev_args[m]);
     }
     g.launches = nl;
   }
@@ -350,10 +352,7 @@ revo_status launch_batch(revo_ctx* c, int count) {
     cudaStream_t s = L.st[m];
     cudaMemsetAsync(L.ws[m]->err, 0, sizeof(int), s);
     int nl = 0;
-    // Attention's last wave splits its key range only when this modality has
-    // the GPU to itself: with both models in flight the other stream's
-    // kernels fill the tail, and the split would only add work.
-    e = lane_forward(c, L, m, jobs[m], jobs[1 - m].empty(), &nl);
+    e = lane_forward(c, L, m, jobs[m], &nl);
     b.launches += nl;
     if (e != cudaSuccess) st = cuda_status(e, "forward launch");
     cudaMemcpyAsync(b.err_host + m, L.ws[m]->err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -568,7 +567,7 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
     if (wn[m] != param_count(s)) return fail(REVO_EINVAL, "weight count does not match the network shape%s");
     cap_p[m] = cfg->max_batch * request_patches(s, cfg->max_height, cfg->max_width);
     cap_tok[m] = cfg->max_batch * request_tokens(s, cfg->max_height, cfg->max_width);
-    need += net_bytes(s, cfg->precision) + cfg->lanes * workspace_bytes(s, cfg->precision, cap_tok[m], cap_p[m]);
+    need += net_bytes(s, cfg->precision) + cfg->lanes * workspace_bytes(s, cfg->precision, cap_tok[m], cap_p[m], cfg->max_batch);
     need += static_cast<size_t>(cfg->max_streams) * cfg->k * frame_bytes(m, cfg->max_height, cfg->max_width);
     need += static_cast<size_t>(2 * cfg->max_batch * cfg->lanes) *
             (frame_bytes(m, cfg->max_height, cfg->max_width) * 2 + mask_words(cfg->max_height, cfg->max_width) * 4 +
@@ -582,7 +581,7 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
     c->net[m] = net_create(c->shape[m], cfg->precision, w[m], &err);
     if (!c->net[m]) return fail(REVO_ENOMEM, "network upload: %s", err.c_str());
     c->net[m]->autotune = cfg->autotune != 0 && cfg->precision != REVO_FP32;
-    c->net[m]->fp8_mask = cfg->fp8_layers ? (cfg->fp8_layers & 15) : kDefaultFp8Layers;
+    c->net[m]->fp8_mask = cfg->fp8_layers ? ((cfg->fp8_layers >> (4 * m)) & 15) : kDefaultFp8Layers[m];
     c->bytes += net_bytes(c->shape[m], cfg->precision);
   }
   cudaError_t e;
@@ -601,7 +600,7 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
       return cuda_status(e, "lane setup");
     for (int m = 0; m < 2; ++m) {
       if (!c->net[m]) continue;
-      L.ws[m] = workspace_create(c->shape[m], cfg->precision, cap_tok[m], cap_p[m], &err);
+      L.ws[m] = workspace_create(c->shape[m], cfg->precision, cap_tok[m], cap_p[m], cfg->max_batch, &err);
       if (!L.ws[m]) return fail(REVO_ENOMEM, "workspace: %s", err.c_str());
       c->bytes += L.ws[m]->bytes;
       if (!cfg->use_graphs) continue;

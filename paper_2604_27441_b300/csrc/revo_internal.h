@@ -72,13 +72,17 @@ cudaError_t launch_gemm_simt(int epi, const float* A, const float* W, const floa
 // ---- attention (qkv [M][3D] row-major; out [M][D])
 cudaError_t launch_attention_simt(const float* qkv, float* out, int M, int D, int heads, const Segments& seg,
                                   cudaStream_t st);
-// `part` (optional, attention_partial_bytes(num_sms) bytes): lets the units of
-// a last, partly filled wave split their K/V range over the idle SMs (two more
-// launches: the split part and a combine).  *launched: kernels enqueued.
+// `part` (attention_partial_bytes(...) bytes): each segment's work is cut into
+// pieces that fill the SMs once, chosen from the segment's length alone; split
+// units are merged by a second kernel.  Null: one CTA per (head, 256 queries)
+// unit, no second kernel.  *launched: kernels enqueued.
 cudaError_t launch_attention_tc(const CUtensorMap& qkv_map, void* out, int M, int D, int heads, const Segments& seg,
                                 int* err, cudaStream_t st, float* part = nullptr, int num_sms = 0,
                                 int* launched = nullptr);
-size_t attention_partial_bytes(int num_sms);
+// Partial-result bytes launch_attention_tc needs for these segments (0 if invalid).
+size_t attention_partial_bytes(int M, int heads, const Segments& seg, int num_sms);
+// The most any batch of up to n_seg segments of up to seg_len tokens needs.
+size_t attention_partial_bytes_bound(int n_seg, int seg_len, int heads, int num_sms);
 bool encode_attention_tmap(CUtensorMap* map, const void* qkv, int M, int D);
 
 // ---- element-wise stages
