@@ -101,7 +101,9 @@ def tick_config(world: int) -> dict:
 
 def flops_per_model(C: int, h: int, w: int) -> dict:
     """Algorithmic FLOPs of one forward (2 per multiply-add), exact savings applied:
-    the pixel head runs on the target frame's rows of the last slot only."""
+    the last decoder block's queries, proj and MLP and the pixel head run on the
+    final slot's P rows only (its keys and values on all N), and the head keeps
+    the target frame's outputs only."""
     k, T, p, D, L, Dd, Ld, r = 5, 2, 16, 768, 12, 384, 4, 4
     P = (h // p) * (w // p)
     N = (k + 1) // T * P
@@ -109,12 +111,13 @@ def flops_per_model(C: int, h: int, w: int) -> dict:
     lin = 2 * N * Kt * D
     lin += L * 2 * N * (3 * D * D + D * D + 2 * r * D * D)
     lin += 2 * N * D * Dd
-    lin += Ld * 2 * N * (3 * Dd * Dd + Dd * Dd + 2 * r * Dd * Dd)
+    lin += (Ld - 1) * 2 * N * (3 * Dd * Dd + Dd * Dd + 2 * r * Dd * Dd)
+    lin += 2 * N * 3 * Dd * Dd + 2 * P * (Dd * Dd + 2 * r * Dd * Dd)
     lin += 2 * P * Dd * (C * p * p)
     attn_enc = 4 * N * N * D
-    attn_dec = 4 * N * N * Dd
-    return dict(N=N, linear=lin, attn_enc_per_block=attn_enc, attn=L * attn_enc + Ld * attn_dec,
-                total=lin + L * attn_enc + Ld * attn_dec)
+    attn_dec = (Ld - 1) * 4 * N * N * Dd + 4 * P * N * Dd
+    return dict(N=N, linear=lin, attn_enc_per_block=attn_enc, attn=L * attn_enc + attn_dec,
+                total=lin + L * attn_enc + attn_dec)
 
 
 def request_flops(workload: str) -> float:

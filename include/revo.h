@@ -107,10 +107,23 @@ typedef struct {
                                     rest stay bf16); 0 = the default: all four in
                                     the RGB model, none in the depth model (its
                                     8 mm gate fails with E4M3 at 300-5000 mm) */
-  const float* rgb_weights;      /* host, flat float32, NULL = no RGB model      */
+  const float* rgb_weights;      /* host, flat float32, NULL = see below         */
   size_t rgb_weights_count;
-  const float* depth_weights;    /* host, flat float32, NULL = no depth model    */
+  const float* depth_weights;    /* host, flat float32, NULL = see below         */
   size_t depth_weights_count;
+  /* A model whose array is NULL is read from its file (flat little-endian
+   * float32 in the order above, exactly the model's parameter count), else,
+   * if its bit of random_init is set, gets the random initialisation of
+   * revo_init_weights from seed (RGB) or seed + 1 (depth), else is absent. */
+  const char* rgb_weights_path;
+  const char* depth_weights_path;
+  uint64_t seed;
+  int random_init;               /* bit 0 RGB, bit 1 depth                        */
+  /* Tile choices of the autotuner: with autotune on, create reads this file
+   * (entries of another GPU model or SM count are ignored), times every GEMM
+   * shape it lacks, and writes the file back; NULL = time them all at create.
+   * Requests never wait for tuning. */
+  const char* autotune_cache;
 } revo_config;
 
 typedef struct revo_ctx revo_ctx;
@@ -170,6 +183,21 @@ typedef struct {
 
 /* Fills *cfg with the ViT-B reading above and precision BF16. */
 REVO_API void revo_config_default(revo_config* cfg);
+
+/*
+ * The random initialisation (no trained weights exist for the paper's model):
+ * fills out[0 .. count) with the float32 weights of the model of `channels`
+ * (3 RGB, 1 depth) shaped by cfg, in the order above, drawn from one stream of
+ * uniform doubles u = (x >> 11) 2^-53 of the PCG64 generator (128-bit LCG,
+ * multiplier 0x2360ED051FC65DA44385DF649FCCF645, XSL-RR output) seeded through
+ * the SeedSequence mixing of NumPy's random module: [out][in] matrices
+ * U(-b, b), b = sqrt(6 / (in + out)), the pixel head times 0.1; LayerNorm
+ * gains 1 + U(-0.1, 0.1); every other vector U(-0.02, 0.02); each value in
+ * double, rounded to float32.  Host only (no device work).
+ * Errors: REVO_EINVAL (null pointer, unsupported shape, count differs from
+ * the model's parameter count).
+ */
+REVO_API revo_status revo_init_weights(const revo_config* cfg, int channels, uint64_t seed, float* out, size_t count);
 
 /*
  * Creates a context on cfg->device: uploads both models' weights (float32
@@ -439,6 +467,11 @@ REVO_API revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const 
  * host array of segment boundaries in [0, M]; tokens attend only within their
  * segment.  out [M][D].  REVO_FP32: float32 in and out.  REVO_BF16: qkv and out
  * bf16, tcgen05 tensor cores, float32 softmax.  n_seg <= 64.
+ * q_begin / q_end (host arrays of n_seg, or both NULL): only rows
+ * [q_begin[g], q_end[g]) of segment g are queries -- keys and values are still
+ * the whole segment -- and, at REVO_BF16, only those output rows are written
+ * (REVO_FP32 writes every row).  The recovery network uses it for its last
+ * decoder block, whose only consumer is the pixel head on the final slot.
  * REVO_BF16 work split: each segment's (head, 256-query) units are laid end
  * to end over their 128-key tiles and cut into equal pieces, one per CTA, so
  * that the segment's pieces fill the GPU's SMs once; units cut in two are
@@ -450,7 +483,8 @@ REVO_API revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const 
  */
 #define REVO_ATTN_WHOLE_UNITS 2
 REVO_API revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D,
-                              int heads, const int* seg_start, int n_seg, int flags, void* stream);
+                              int heads, const int* seg_start, const int* q_begin, const int* q_end, int n_seg,
+                              int flags, void* stream);
 
 /*
  * x[(s*Hp + r)*Wp + c][:] += the sinusoidal embedding of (taus[s], r, c), each

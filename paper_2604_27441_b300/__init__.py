@@ -41,7 +41,9 @@ class Config(C.Structure):
                 ("cuda_stream", C.c_void_p), ("use_graphs", C.c_int), ("autotune", C.c_int),
                 ("fp8_layers", C.c_int),
                 ("rgb_weights", C.c_void_p), ("rgb_weights_count", C.c_size_t),
-                ("depth_weights", C.c_void_p), ("depth_weights_count", C.c_size_t)]
+                ("depth_weights", C.c_void_p), ("depth_weights_count", C.c_size_t),
+                ("rgb_weights_path", C.c_char_p), ("depth_weights_path", C.c_char_p),
+                ("seed", C.c_uint64), ("random_init", C.c_int), ("autotune_cache", C.c_char_p)]
 
 
 class Plane(C.Structure):
@@ -99,13 +101,15 @@ _SIGS = {
                                  C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "revo_op_layernorm": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "revo_op_attention": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
-                                    C.POINTER(C.c_int), C.c_int, C.c_int, C.c_void_p]),
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
+                                    C.c_int, C.c_void_p]),
     "revo_op_add_position": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                        C.c_void_p]),
     "revo_op_blend": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
                                 C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
                                 C.c_void_p]),
     "revo_op_take_device_error": (C.c_int, []),
+    "revo_init_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_void_p, C.c_size_t]),
     "revo_op_wait_selftest": (C.c_int, [C.c_longlong, C.c_void_p]),
     "revo_op_quantize_rows_e4m3": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "revo_frame_metrics_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
@@ -275,11 +279,16 @@ def op_frame_metrics(a, b, height, width, channels, sample_bytes, data_range, sc
 ATTN_WHOLE_UNITS = 2
 
 
-def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None, whole_units=False):
+def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None, whole_units=False, queries=None):
+    """queries: optional list of (begin, end) query rows per segment."""
     n = len(seg_start) - 1
     arr = (C.c_int * len(seg_start))(*[int(v) for v in seg_start])
+    qb = qe = None
+    if queries is not None:
+        qb = (C.c_int * n)(*[int(a) for a, _ in queries])
+        qe = (C.c_int * n)(*[int(b) for _, b in queries])
     flags = ATTN_WHOLE_UNITS if whole_units else 0
-    return _check(lib().revo_op_attention(precision, ptr(qkv), ptr(out), M, D, heads, arr, n, flags,
+    return _check(lib().revo_op_attention(precision, ptr(qkv), ptr(out), M, D, heads, arr, qb, qe, n, flags,
                                           _stream(stream)),
                   "revo_op_attention")
 
@@ -309,13 +318,39 @@ def op_wait_selftest(limit_cycles, stream=None):
 # ------------------------------------------------------------------ context
 
 def config(**kw) -> Config:
+    """A revo_config from revo_config_default with the given fields set
+    (str values of the path fields are encoded; the Config keeps them alive)."""
     cfg = Config()
     lib().revo_config_default(C.byref(cfg))
+    keep = []
     for k, v in kw.items():
         if not hasattr(cfg, k):
             raise AttributeError(k)
+        if isinstance(v, str):
+            v = v.encode()
+            keep.append(v)
         setattr(cfg, k, v)
+    cfg._keep_strings = keep
     return cfg
+
+
+def init_weights(cfg: Config, channels: int, seed: int) -> np.ndarray:
+    """revo_init_weights: the library's seeded random initialisation of one model (host)."""
+    n = int(param_count(cfg, channels))
+    out = np.empty(n, np.float32)
+    _check(lib().revo_init_weights(C.byref(cfg), channels, seed, out.ctypes.data, n), "revo_init_weights")
+    return out
+
+
+def param_count(cfg: Config, channels: int) -> int:
+    """Parameters of one model of the configured shape (the order of revo.h)."""
+    D, Dd, r = cfg.enc_dim, cfg.dec_dim, cfg.mlp_ratio
+    K = cfg.tubelet * channels * cfg.patch * cfg.patch
+
+    def block(d):
+        return 2 * d + 3 * d * d + 3 * d + d * d + d + 2 * d + r * d * d + r * d + r * d * d + d
+    return D * K + D + cfg.enc_depth * block(D) + 2 * D + Dd * D + Dd + cfg.dec_depth * block(Dd) + 2 * Dd + \
+        K * Dd + K
 
 
 class Context:

@@ -80,7 +80,8 @@ constexpr int kCombineRows = 16;        // rows per combine block (x 16 column g
 struct TcAttnParams {
   int D, heads, n_slots, pieces;
   float scale_log2;
-  int s0[kMaxSegments], s1[kMaxSegments];     // token range
+  int s0[kMaxSegments], s1[kMaxSegments];     // key rows
+  int qs0[kMaxSegments], qs1[kMaxSegments];   // query rows (within the key rows)
   int items[kMaxSegments], nkv[kMaxSegments]; // 256-query items, 128-key tiles
   int plen[kMaxSegments];                     // steps per piece
   int piece_prefix[kMaxSegments + 1];
@@ -101,8 +102,8 @@ REVO_DEVI SubUnit sub_unit(const TcAttnParams& P, int k, int u, int step0, int s
   const int nkv = P.nkv[k], items = P.items[k];
   SubUnit su;
   su.h = u / items;
-  su.q0 = P.s0[k] + (u % items) * kPartRows;
-  su.ntiles = (P.s1[k] - su.q0) > kQ ? 2 : 1;
+  su.q0 = P.qs0[k] + (u % items) * kPartRows;
+  su.ntiles = (P.qs1[k] - su.q0) > kQ ? 2 : 1;
   su.kb = max(step0 - u * nkv, 0);
   su.ke = min(step1 - u * nkv, nkv);
   su.partial = su.kb > 0 || su.ke < nkv;
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         *reinterpret_cast<float2*>(pml) = make_float2(m, l);
       } else {
         const int row = su.q0 + t * kQ + r;
-        if (row < s1) {
+        if (row < P.qs1[k]) {
           const float inv = 1.f / l;
           uint4* dst = reinterpret_cast<uint4*>(out + static_cast<size_t>(row) * D + su.h * kHD);
 #pragma unroll
@@ -588,8 +589,8 @@ __global__ void __launch_bounds__(256) attn_combine_kernel(const __grid_constant
   const int row = rblk * kCombineRows + static_cast<int>(threadIdx.x) / 16;
   const int c4 = static_cast<int>(threadIdx.x) % 16;
   const int h = u / items;
-  const int q = P.s0[k] + (u % items) * kPartRows + row;
-  if (q >= P.s1[k]) return;
+  const int q = P.qs0[k] + (u % items) * kPartRows + row;
+  if (q >= P.qs1[k]) return;
   const int pf = (u * nkv) / plen;
   const int pl = ((u + 1) * nkv - 1) / plen;
   const float* ml = P.part + static_cast<size_t>(2 * P.pieces) * kPartRows * kHD;
@@ -623,16 +624,19 @@ int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b
 bool plan_pieces(TcAttnParams* P, int M, int heads, const Segments& seg, int num_sms, bool whole_units) {
   const int G = num_sms > 0 ? num_sms : 148;
   struct S {
-    int g, items, nkv, plen, pieces;
+    int g, q0, q1, items, nkv, plen, pieces;
   };
   std::vector<S> v;
   for (int g = 0; g < seg.n; ++g) {
     const int len = seg.start[g + 1] - seg.start[g];
     if (len < 0 || seg.start[g] < 0 || seg.start[g + 1] > M) return false;
-    if (len == 0) continue;
     S s;
     s.g = g;
-    s.items = ceil_div(len, kPartRows);
+    s.q0 = seg.queries ? seg.q_begin[g] : seg.start[g];
+    s.q1 = seg.queries ? seg.q_end[g] : seg.start[g + 1];
+    if (s.q0 < seg.start[g] || s.q1 > seg.start[g + 1] || s.q1 < s.q0) return false;
+    if (s.q1 == s.q0) continue;
+    s.items = ceil_div(s.q1 - s.q0, kPartRows);
     s.nkv = ceil_div(len, kKV);
     const long long work = static_cast<long long>(heads) * s.items * s.nkv;
     if (work > (1LL << 30)) return false;
@@ -647,6 +651,8 @@ bool plan_pieces(TcAttnParams* P, int M, int heads, const Segments& seg, int num
     const S& s = v[i];
     P->s0[i] = seg.start[s.g];
     P->s1[i] = seg.start[s.g + 1];
+    P->qs0[i] = s.q0;
+    P->qs1[i] = s.q1;
     P->items[i] = s.items;
     P->nkv[i] = s.nkv;
     P->plen[i] = s.plen;

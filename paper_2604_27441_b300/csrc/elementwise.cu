@@ -723,6 +723,35 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st, const BlendArgs* d
   return cudaGetLastError();
 }
 
+// One CTA per destination row: the float32 row of x and the row of a
+// (16-byte vectors).
+__global__ void __launch_bounds__(128) gather_rows_kernel(const float* __restrict__ x, const uint8_t* __restrict__ a,
+                                                          int elem_bytes, int D, const __grid_constant__ RowRuns runs,
+                                                          float* __restrict__ xc, uint8_t* __restrict__ ac) {
+  const int row = static_cast<int>(blockIdx.x);
+  int i = 0;
+  while (i + 1 < runs.n && runs.dst[i + 1] <= row) ++i;
+  const size_t src = static_cast<size_t>(runs.src[i] + (row - runs.dst[i]));
+  const uint4* xs = reinterpret_cast<const uint4*>(x + src * D);
+  uint4* xd = reinterpret_cast<uint4*>(xc + static_cast<size_t>(row) * D);
+  for (int c = threadIdx.x; c < D / 4; c += blockDim.x) xd[c] = xs[c];
+  const size_t rb = static_cast<size_t>(D) * elem_bytes;
+  const uint4* as = reinterpret_cast<const uint4*>(a + src * rb);
+  uint4* ad = reinterpret_cast<uint4*>(ac + static_cast<size_t>(row) * rb);
+  for (int c = threadIdx.x; c < static_cast<int>(rb / 16); c += blockDim.x) ad[c] = as[c];
+}
+
+cudaError_t launch_gather_rows(const float* x, const void* a, int elem_bytes, int D, const RowRuns& runs, float* xc,
+                               void* ac, cudaStream_t st) {
+  if (runs.n <= 0 || runs.n > kMaxSegments || D % 8 || (elem_bytes != 2 && elem_bytes != 4))
+    return cudaErrorInvalidValue;
+  const int rows = runs.dst[runs.n];
+  if (rows <= 0) return cudaSuccess;
+  gather_rows_kernel<<<rows, 128, 0, st>>>(x, static_cast<const uint8_t*>(a), elem_bytes, D, runs, xc,
+                                           static_cast<uint8_t*>(ac));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_f32_to_bf16(const float* in, void* out, size_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   f32_to_bf16_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(in, static_cast<__nv_bfloat16*>(out), n);

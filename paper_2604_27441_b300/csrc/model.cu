@@ -20,6 +20,23 @@ size_t block_params(int d, int r) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+}  // namespace
+
+// GEMM row counts share a tile choice within power-of-two buckets (at least
+// 128 rows): a launch of M rows uses the choice timed at the bucket's top.
+int tune_bucket(int M) {
+  int b = 128;
+  while (b < M && b < (1 << 30)) b *= 2;
+  return b;
+}
+
+uint64_t tune_key(int M, int N, int K, bool f8, int epi) {
+  return (static_cast<uint64_t>(tune_bucket(M)) << 36) | (static_cast<uint64_t>(N) << 22) |
+         (static_cast<uint64_t>(K) << 4) | (static_cast<uint64_t>(f8) << 3) | static_cast<uint64_t>(epi);
+}
+
+namespace {
+
 // 128 x 256 tiles halve the A-operand traffic per FLOP and measured faster than
 // 128 x 128 at every Linear shape of the network (also with fewer tiles than
 // SMs), so they are used whenever N allows.
@@ -214,7 +231,7 @@ void net_destroy(Net* n) {
 
 namespace {
 struct WsLayout {
-  size_t tok, x, h, qkv, att, mlp, head, err, h8, h8s, part, total;
+  size_t tok, x, h, qkv, att, mlp, head, xc, attc, err, h8, h8s, part, total;
 };
 WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_seg) {
   const size_t e = precision != REVO_FP32 ? 2 : 4;
@@ -233,6 +250,8 @@ WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_
   l.att = put(static_cast<size_t>(cap) * D * e);
   l.mlp = put(static_cast<size_t>(cap) * s.r * D * e);
   l.head = put(static_cast<size_t>(capp) * s.head_dim_out() * 4);
+  l.xc = put(static_cast<size_t>(capp) * s.Dd * 4);
+  l.attc = put(static_cast<size_t>(capp) * s.Dd * e);
   l.err = put(256);
   if (precision != REVO_FP32) {
     // Up to max_seg requests of up to cap / max_seg tokens, at either width.
@@ -278,6 +297,8 @@ Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, in
   w->att = base + l.att;
   w->mlp = base + l.mlp;
   w->head = reinterpret_cast<float*>(base + l.head);
+  w->xc = reinterpret_cast<float*>(base + l.xc);
+  w->attc = base + l.attc;
   w->err = reinterpret_cast<int*>(base + l.err);
   w->sms = device_sm_count();
   if (precision != REVO_FP32) w->attn_part = reinterpret_cast<float*>(base + l.part);
@@ -339,24 +360,23 @@ struct Fwd {
                           w.out, w.in, ws->err, sms, st);
   }
 
-  // The autotuner's choice for this shape, timing the candidates if it has none
-  // yet and the stream is not being captured.  The timed launches write the
-  // GEMM's own destination (the real launch overwrites it next), except for the
-  // residual epilogue, whose destination accumulates: those write into the
-  // qkv buffer, which holds nothing live between attention and the next block.
+  // The autotuner's choice for this shape.  While serving (tuning == false)
+  // only the choices timed at create are looked up: no request waits for
+  // tuning.  At create (tuning == true) a shape without a choice has its
+  // candidates timed on the stream.  The timed launches write the GEMM's own
+  // destination (the real launch overwrites it next), except for the residual
+  // epilogue, whose destination accumulates: those write into the qkv buffer,
+  // which holds nothing live between attention and the next block.
+  bool tuning = false;
   cudaError_t tuned_width(const CUtensorMap* amap, const LinearW& w, int epi, int M, const CUtensorMap* cmap, bool f8,
                           int* bn) {
-    // Row counts share a choice within buckets (128 rows up to 8192, then 2048),
-    // so a serving mix of batch sizes is not re-timed for every new total.
-    const int step = M <= 8192 ? 128 : 2048;
-    const uint64_t mb = static_cast<uint64_t>((M + step - 1) / step) * step;
-    const uint64_t key = (mb << 36) | (static_cast<uint64_t>(w.out) << 22) | (static_cast<uint64_t>(w.in) << 4) |
-                         (static_cast<uint64_t>(f8) << 3) | static_cast<uint64_t>(epi);
+    const uint64_t key = tune_key(M, w.out, w.in, f8, epi);
     auto it = net->tuned_bn.find(key);
     if (it != net->tuned_bn.end()) {
       *bn = it->second;
       return cudaSuccess;
     }
+    if (!tuning) return cudaSuccess;  // keep the default rule
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t rc = cudaStreamIsCapturing(st, &cap);
     if (rc != cudaSuccess || cap != cudaStreamCaptureStatusNone) return rc;
@@ -410,22 +430,22 @@ struct Fwd {
 
   // LayerNorm then a LayerNorm-fed Linear (qkv, fc1): in E4M3 with per-token
   // and per-channel scales at FP8 precision, else from the bf16 / f32 LN output.
-  cudaError_t ln_linear(const float* g, const float* bb, int d, int M, const LinearW& w, int epi, void* out, int ldo,
-                        const Maps& mp, const CUtensorMap* cmap, int fp8_bit) {
+  cudaError_t ln_linear(const float* x, const float* g, const float* bb, int d, int M, const LinearW& w, int epi,
+                        void* out, int ldo, const Maps& mp, const CUtensorMap* cmap, int fp8_bit) {
     cudaError_t e;
     if (net->precision == REVO_FP8 && (net->fp8_mask >> fp8_bit) & 1) {
-      if ((e = launch_layernorm_e4m3(ws->x, g, bb, ws->h8, ws->h8_scale, M, d, st)) != cudaSuccess) return e;
+      if ((e = launch_layernorm_e4m3(x, g, bb, ws->h8, ws->h8_scale, M, d, st)) != cudaSuccess) return e;
       return linear8(mp.h8, w, epi, M, cmap);
     }
-    if ((e = launch_layernorm(ws->x, g, bb, ws->h, M, d, tc, st)) != cudaSuccess) return e;
+    if ((e = launch_layernorm(x, g, bb, ws->h, M, d, tc, st)) != cudaSuccess) return e;
     return linear(mp.h, ws->h, w, epi, out, ldo, M, cmap);
   }
 
   cudaError_t block(const BlockW& b, int d, int heads, int M, const Segments& seg, const Maps& mp, bool dec) {
     cudaError_t e;
     const int bit = dec ? 2 : 0;
-    if ((e = ln_linear(b.ln1g, b.ln1b, d, M, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, mp, mp.o_qkv, bit)) !=
-        cudaSuccess)
+    if ((e = ln_linear(ws->x, b.ln1g, b.ln1b, d, M, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, mp, mp.o_qkv,
+                       bit)) != cudaSuccess)
       return e;
     if (tc)
     {
@@ -438,10 +458,48 @@ struct Fwd {
                                 st);
     if (e != cudaSuccess) return e;
     if ((e = linear(mp.att, ws->att, b.proj, kEpiResidF32, ws->x, d, M, mp.o_x)) != cudaSuccess) return e;
-    if ((e = ln_linear(b.ln2g, b.ln2b, d, M, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, mp, mp.o_mlp, bit + 1)) !=
-        cudaSuccess)
+    if ((e = ln_linear(ws->x, b.ln2g, b.ln2b, d, M, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, mp, mp.o_mlp,
+                       bit + 1)) != cudaSuccess)
       return e;
     return linear(mp.mlp, ws->mlp, b.fc2, kEpiResidF32, ws->x, d, M, mp.o_x);
+  }
+
+  // The last decoder block on the rows that reach the pixel head (Section
+  // 3.4.1: the output is the target frame, the last frame of the final
+  // tubelet slot): LN1 and qkv on every token (keys and values of the whole
+  // request), attention with the final slot's queries only, then those rows
+  // are stacked (runs.dst: their row in the head output) and proj, LN2, fc1,
+  // fc2 run on them alone.  An exact saving: no other row reaches the head.
+  cudaError_t last_block(const BlockW& b, int d, int heads, int M, const Segments& seg, const Maps& mp,
+                         const RowRuns& runs, const Maps& cm) {
+    cudaError_t e;
+    if ((e = ln_linear(ws->x, b.ln1g, b.ln1b, d, M, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, mp, mp.o_qkv,
+                       2)) != cudaSuccess)
+      return e;
+    Segments q = seg;
+    q.queries = true;
+    for (int i = 0; i < seg.n; ++i) {
+      q.q_begin[i] = runs.src[i];
+      q.q_end[i] = runs.src[i] + (runs.dst[i + 1] - runs.dst[i]);
+    }
+    if (tc) {
+      int nl = 1;
+      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, q, ws->err, st, ws->attn_part, ws->sms, &nl);
+      extra_launches += nl - 1;
+    } else {
+      e = launch_attention_simt(static_cast<const float*>(ws->qkv), static_cast<float*>(ws->att), M, d, heads, seg,
+                                st);
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = launch_gather_rows(ws->x, ws->att, static_cast<int>(this->e), d, runs, ws->xc, ws->attc, st)) !=
+        cudaSuccess)
+      return e;
+    const int P = runs.dst[runs.n];
+    if ((e = linear(cm.att, ws->attc, b.proj, kEpiResidF32, ws->xc, d, P, cm.o_x)) != cudaSuccess) return e;
+    if ((e = ln_linear(ws->xc, b.ln2g, b.ln2b, d, P, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, cm, cm.o_mlp, 3)) !=
+        cudaSuccess)
+      return e;
+    return linear(cm.mlp, ws->mlp, b.fc2, kEpiResidF32, ws->xc, d, P, cm.o_x);
   }
 };
 
@@ -467,6 +525,21 @@ bool encode_maps(const NetShape& s, Workspace* ws, int M) {
     ok = encode_tmap_u8_2d(&ws->m_h8_enc, ws->h8, rows, s.D, s.D, 128) &&
          encode_tmap_u8_2d(&ws->m_h8_dec, ws->h8, rows, s.Dd, s.Dd, 128);
   ws->maps_rows = ok ? M : -1;
+  return ok;
+}
+
+// Maps of the last decoder block's stacked rows (P of them) and the head output.
+bool encode_compact_maps(const NetShape& s, Workspace* ws, int P) {
+  if (ws->maps_rows_c == P) return true;
+  const uint64_t rows = P > 0 ? P : 1;
+  bool ok = encode_tmap_bf16_2d(&ws->c_h, ws->h, rows, s.Dd, s.Dd, 128, 64) &&
+            encode_tmap_bf16_2d(&ws->c_att, ws->attc, rows, s.Dd, s.Dd, 128, 64) &&
+            encode_tmap_bf16_2d(&ws->c_mlp, ws->mlp, rows, s.r * s.Dd, s.r * s.Dd, 128, 64) &&
+            encode_tmap_out_2d(&ws->c_o_x, ws->xc, true, rows, s.Dd, s.Dd) &&
+            encode_tmap_out_2d(&ws->c_o_mlp, ws->mlp, false, rows, s.r * s.Dd, s.r * s.Dd) &&
+            encode_tmap_out_2d(&ws->c_o_head, ws->head, true, rows, s.head_dim_out(), s.head_dim_out());
+  if (ok && ws->h8) ok = encode_tmap_u8_2d(&ws->c_h8, ws->h8, rows, s.Dd, s.Dd, 128);
+  ws->maps_rows_c = ok ? P : -1;
   return ok;
 }
 
@@ -577,31 +650,86 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.Dd, jobs[i].H / s.p, jobs[i].W / s.p,
                            s.slots(), args[i].taus, s.Dd, st, dev_args ? dev_args[i].taus : nullptr)) != cudaSuccess)
       return e;
-  for (const BlockW& b : net->dec)
-    if ((e = f.block(b, s.Dd, s.Hd, M, seg, dec_maps, true)) != cudaSuccess) return e;
-
-  // Final LN and pixel head on the last slot's tokens of each request, then the blend.
-  uint8_t* h = static_cast<uint8_t*>(ws->h);
+  // The final slot's rows of each request, stacked in request order: the rows
+  // the last decoder block, the final LN and the pixel head work on (the head
+  // output is then in the order the blend reads it).
+  RowRuns runs{};
+  runs.n = n;
+  runs.dst[0] = 0;
   for (int i = 0; i < n; ++i) {
     const int P = request_patches(s, jobs[i].H, jobs[i].W);
-    const size_t row0 = static_cast<size_t>(seg.start[i]) + static_cast<size_t>(s.slots() - 1) * P;
-    void* hrows = h + row0 * s.Dd * f.e;
-    if ((e = launch_layernorm(ws->x + row0 * s.Dd, net->dec_norm_g, net->dec_norm_b, hrows, P, s.Dd, f.tc, st)) !=
-        cudaSuccess)
-      return e;
-    float* head = const_cast<float*>(args[i].blend.head);
-    CUtensorMap m_rows, o_head;
-    if (f.tc && (!encode_tmap_bf16_2d(&m_rows, hrows, P, s.Dd, s.Dd, 128, 64) ||
-                 !encode_tmap_out_2d(&o_head, head, true, P, s.head_dim_out(), s.head_dim_out())))
-      return cudaErrorInvalidValue;
-    if ((e = f.linear(&m_rows, hrows, net->head, kEpiF32, head, s.head_dim_out(), P, &o_head)) != cudaSuccess)
-      return e;
-    if ((e = launch_blend(args[i].blend, st, dev_args ? &dev_args[i].blend : nullptr)) != cudaSuccess) return e;
+    runs.src[i] = seg.start[i] + (s.slots() - 1) * P;
+    runs.dst[i + 1] = runs.dst[i] + P;
   }
-  // One kernel per step: per request assemble, 2 embeddings, final LN, head, blend;
-  // tubelet embedding, encoder LN, encoder->decoder; 7 per transformer block.
-  if (launches) *launches = 3 + 7 * (s.L + s.Ld) + 6 * n + f.extra_launches;
+  if (f.tc && !encode_compact_maps(s, ws, patches)) return cudaErrorInvalidValue;
+  const Fwd::Maps last_maps{&ws->c_h, &ws->c_att, &ws->c_mlp, nullptr, &ws->c_o_x, nullptr, &ws->c_o_mlp, &ws->c_h8};
+  for (int i = 0; i < s.Ld; ++i) {
+    const BlockW& b = net->dec[i];
+    if ((e = i + 1 < s.Ld ? f.block(b, s.Dd, s.Hd, M, seg, dec_maps, true)
+                          : f.last_block(b, s.Dd, s.Hd, M, seg, dec_maps, runs, last_maps)) != cudaSuccess)
+      return e;
+  }
+
+  // Final LN and pixel head on the stacked rows, then the blend per request.
+  if ((e = launch_layernorm(ws->xc, net->dec_norm_g, net->dec_norm_b, ws->h, patches, s.Dd, f.tc, st)) != cudaSuccess)
+    return e;
+  if ((e = f.linear(&ws->c_h, ws->h, net->head, kEpiF32, ws->head, s.head_dim_out(), patches, &ws->c_o_head)) !=
+      cudaSuccess)
+    return e;
+  for (int i = 0; i < n; ++i)
+    if ((e = launch_blend(args[i].blend, st, dev_args ? &dev_args[i].blend : nullptr)) != cudaSuccess) return e;
+  // One kernel per step: per request assemble, 2 embeddings, blend; tubelet
+  // embedding, encoder LN, encoder->decoder, final LN, head; 7 per transformer
+  // block, 8 for the last (the row gather).
+  if (launches) *launches = 5 + 7 * (s.L + s.Ld) + 1 + 4 * n + f.extra_launches;
   return cudaSuccess;
+}
+
+cudaError_t net_autotune(Net* net, Workspace* ws, int max_tokens, int max_patches, cudaStream_t st, int num_sms) {
+  const NetShape& s = net->s;
+  if (net->precision == REVO_FP32) return cudaSuccess;
+  Fwd f{net, ws, st, num_sms, true, 2u};
+  f.tuning = true;
+  cudaError_t e = cudaSuccess;
+  int bn = 0;
+  auto tune = [&](const CUtensorMap* amap, const LinearW& w, int epi, int M, const CUtensorMap* cmap, bool f8) {
+    if (e == cudaSuccess) e = f.tuned_width(amap, w, epi, M, cmap, f8, &bn);
+  };
+  const bool f8q_e = net->precision == REVO_FP8 && (net->fp8_mask & 1);
+  const bool f8f_e = net->precision == REVO_FP8 && (net->fp8_mask & 2);
+  const bool f8q_d = net->precision == REVO_FP8 && (net->fp8_mask & 4);
+  const bool f8f_d = net->precision == REVO_FP8 && (net->fp8_mask & 8);
+  // Rows of every token: the tubelet embedding, the blocks (all alike within
+  // the encoder and within the decoder) and the encoder->decoder Linear.
+  for (int b = 128; e == cudaSuccess; b *= 2) {
+    const int M = std::min(b, max_tokens);
+    if (!encode_maps(s, ws, M)) return cudaErrorInvalidValue;
+    tune(&ws->m_tok, net->patch, kEpiF32, M, &ws->o_x_enc, false);
+    if (s.L > 0) {
+      const BlockW& k = net->enc[0];
+      tune(f8q_e ? &ws->m_h8_enc : &ws->m_h_enc, k.qkv, kEpiBf16, M, &ws->o_qkv_enc, f8q_e);
+      tune(&ws->m_att_enc, k.proj, kEpiResidF32, M, &ws->o_x_enc, false);
+      tune(f8f_e ? &ws->m_h8_enc : &ws->m_h_enc, k.fc1, kEpiGeluBf16, M, &ws->o_mlp_enc, f8f_e);
+      tune(&ws->m_mlp_enc, k.fc2, kEpiResidF32, M, &ws->o_x_enc, false);
+    }
+    tune(&ws->m_h_enc, net->enc2dec, kEpiF32, M, &ws->o_x_dec, false);
+    const BlockW& d = net->dec[0];
+    tune(f8q_d ? &ws->m_h8_dec : &ws->m_h_dec, d.qkv, kEpiBf16, M, &ws->o_qkv_dec, f8q_d);
+    tune(&ws->m_att_dec, d.proj, kEpiResidF32, M, &ws->o_x_dec, false);
+    tune(f8f_d ? &ws->m_h8_dec : &ws->m_h_dec, d.fc1, kEpiGeluBf16, M, &ws->o_mlp_dec, f8f_d);
+    tune(&ws->m_mlp_dec, d.fc2, kEpiResidF32, M, &ws->o_x_dec, false);
+    if (M >= max_tokens) break;
+  }
+  // The final slot's rows: the pixel head (the last block's other shapes are
+  // the decoder's, timed above for these row counts).
+  for (int b = 128; e == cudaSuccess; b *= 2) {
+    const int M = std::min(b, max_patches);
+    if (!encode_compact_maps(s, ws, M)) return cudaErrorInvalidValue;
+    tune(&ws->c_h, net->head, kEpiF32, M, &ws->c_o_head, false);
+    if (M >= max_patches) break;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
 }
 
 }  // namespace revo

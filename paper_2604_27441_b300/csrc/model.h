@@ -58,10 +58,9 @@ struct Net {
   LinearW patch, enc2dec, head;     // head: the rows that produce the target frame
   std::vector<BlockW> enc, dec;
   const float *enc_norm_g, *enc_norm_b, *dec_norm_g, *dec_norm_b;
-  // GEMM tile-width autotuner (tensor-core path): the first time a GEMM shape
-  // (M, N, K, epilogue) runs outside a graph capture, each candidate width is
-  // timed on the stream and the fastest is kept for every later launch and
-  // capture of that shape.  Off: a fixed rule (256 when N >= 256).
+  // GEMM tile-width autotuner (tensor-core path): choices per shape key
+  // (tune_key), timed at create by net_autotune or read from a cache file.
+  // Off, or a shape without a choice: a fixed rule (256 when N >= 256).
   bool autotune = false;
   // FP8 precision: E4M3 layers (bit 0 encoder qkv, 1 encoder fc1, 2 decoder
   // qkv, 3 decoder fc1).
@@ -93,6 +92,9 @@ struct Workspace {
   void* att = nullptr;   // [cap][D]
   void* mlp = nullptr;   // [cap][rD]
   float* head = nullptr; // [cap_patches][C*p*p]
+  // The last decoder block's rows (the final slot of each request, stacked):
+  float* xc = nullptr;    // [cap_patches][D'] residual stream
+  void* attc = nullptr;   // [cap_patches][D'] attention output
   uint8_t* h8 = nullptr;  // [cap][max width] E4M3 LayerNorm output (FP8 precision)
   float* h8_scale = nullptr;  // [cap] its per-token scales
   float* attn_part = nullptr;  // partial results of the tensor-core attention's split units
@@ -106,6 +108,9 @@ struct Workspace {
   CUtensorMap m_h8_enc{}, m_h8_dec{};
   // Output maps of the GEMM epilogues.
   CUtensorMap o_x_enc{}, o_x_dec{}, o_qkv_enc{}, o_qkv_dec{}, o_mlp_enc{}, o_mlp_dec{};
+  // Maps of the last decoder block's stacked rows, valid for `maps_rows_c` rows.
+  int maps_rows_c = -1;
+  CUtensorMap c_h{}, c_att{}, c_mlp{}, c_h8{}, c_o_x{}, c_o_mlp{}, c_o_head{};
 };
 
 Net* net_create(const NetShape& s, int precision, const float* host_weights, std::string* err);
@@ -142,5 +147,20 @@ cudaError_t prepare_job_args(const Net* net, const Workspace* ws, const PlaneJob
 // enqueued work depends on the request sizes only and can be captured once.
 cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cudaStream_t st, int num_sms,
                         int* launches, const JobArgs* dev_args = nullptr);
+
+// GEMM tile autotuning (tensor-core path), done once at create: every GEMM
+// shape of the network is timed for row counts 128, 256, ... up to max_tokens
+// (the head up to max_patches) on `ws` and `st`, skipping shapes that already
+// have a choice (from an autotune cache file).  A forward then only looks the
+// choices up (tune_bucket: a launch of M rows uses the choice of the smallest
+// power of two >= M, at least 128).
+cudaError_t net_autotune(Net* net, Workspace* ws, int max_tokens, int max_patches, cudaStream_t st, int num_sms);
+int tune_bucket(int M);
+uint64_t tune_key(int M, int N, int K, bool f8, int epi);
+
+// Host-side weight sources (weights.cu): the documented random initialisation
+// of a model from a seed, and a flat float32 file.
+void init_weights_random(const NetShape& s, uint64_t seed, float* out);
+bool load_weights_file(const char* path, size_t offset_floats, size_t count, float* out, std::string* why);
 
 }  // namespace revo

@@ -389,7 +389,8 @@ revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const void* b, 
 }
 
 revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D, int heads,
-                              const int* seg_start, int n_seg, int flags, void* stream) {
+                              const int* seg_start, const int* q_begin, const int* q_end, int n_seg, int flags,
+                              void* stream) {
   if (!qkv || !out || !seg_start || n_seg <= 0 || n_seg > kMaxSegments || heads <= 0 || D != 64 * heads) {
     set_last_error("revo_op_attention: bad argument (head width must be 64, n_seg <= 64)");
     return REVO_EINVAL;
@@ -401,6 +402,21 @@ revo_status revo_op_attention(revo_precision precision, const void* qkv, void* o
     if (seg.start[i] < 0 || seg.start[i] > M || (i && seg.start[i] < seg.start[i - 1])) {
       set_last_error("revo_op_attention: segment bounds not increasing within [0, M]");
       return REVO_EINVAL;
+    }
+  }
+  if ((q_begin != nullptr) != (q_end != nullptr)) {
+    set_last_error("revo_op_attention: q_begin and q_end go together");
+    return REVO_EINVAL;
+  }
+  if (q_begin) {
+    seg.queries = true;
+    for (int i = 0; i < n_seg; ++i) {
+      seg.q_begin[i] = q_begin[i];
+      seg.q_end[i] = q_end[i];
+      if (q_begin[i] < seg.start[i] || q_end[i] > seg.start[i + 1] || q_end[i] < q_begin[i]) {
+        set_last_error("revo_op_attention: query rows outside their segment");
+        return REVO_EINVAL;
+      }
     }
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);

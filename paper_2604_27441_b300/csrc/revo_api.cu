@@ -13,6 +13,7 @@
 // staging slots free up.  All device work is ordered with events: a batch waits
 // for the copy stream (input uploads, reference pushes); a reference push
 // waits for every lane's last batch.
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -527,6 +528,44 @@ void revo_recover_destroy(revo_ctx* c) {
   delete c;
 }
 
+// Autotune cache file: a header line naming the GPU it was timed on, then one
+// line per choice: modality, shape key (tune_key, hex), tile choice.
+std::string autotune_tag(const cudaDeviceProp& p) {
+  char buf[320];
+  snprintf(buf, sizeof(buf), "revo-autotune 1 sm_%d%d sms=%d %s", p.major, p.minor, p.multiProcessorCount, p.name);
+  for (char* q = buf; *q; ++q)
+    if (*q == '\n') *q = ' ';
+  return buf;
+}
+
+void load_autotune_cache(revo_ctx* c, const char* path, const std::string& tag) {
+  FILE* f = fopen(path, "r");
+  if (!f) return;  // no file yet: everything is timed and the file written
+  char line[512];
+  if (fgets(line, sizeof(line), f) && std::string(line).substr(0, tag.size()) == tag) {
+    int m = 0, choice = 0;
+    unsigned long long key = 0;
+    while (fgets(line, sizeof(line), f))
+      if (sscanf(line, "%d %llx %d", &m, &key, &choice) == 3 && m >= 0 && m < 2 && c->net[m] &&
+          ((choice & ~kTilePair) == 128 || (choice & ~kTilePair) == 256))
+        c->net[m]->tuned_bn[key] = choice;
+  }
+  fclose(f);
+}
+
+bool save_autotune_cache(revo_ctx* c, const char* path, const std::string& tag) {
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  fprintf(f, "%s\n", tag.c_str());
+  for (int m = 0; m < 2; ++m)
+    if (c->net[m])
+      for (const auto& kv : c->net[m]->tuned_bn)
+        fprintf(f, "%d %llx %d\n", m, static_cast<unsigned long long>(kv.first), kv.second);
+  const bool ok = fclose(f) == 0;
+  return ok && rename(tmp.c_str(), path) == 0;
+}
+
 revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
   if (!out) return fail(REVO_EINVAL, "null out%s");
   *out = nullptr;
@@ -540,7 +579,9 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
     return fail(REVO_ENOTSUP, "precision not supported%s");
   if (cfg->precision == REVO_FP8 && (cfg->enc_dim % 128 || cfg->dec_dim % 128))
     return fail(REVO_EINVAL, "the FP8 path needs widths that are multiples of 128%s");
-  if (!cfg->rgb_weights && !cfg->depth_weights) return fail(REVO_EINVAL, "no model weights given%s");
+  if (!cfg->rgb_weights && !cfg->depth_weights && !cfg->rgb_weights_path && !cfg->depth_weights_path &&
+      !(cfg->random_init & 3))
+    return fail(REVO_EINVAL, "no model weights given%s");
   if (cudaSetDevice(cfg->device) != cudaSuccess) return fail(REVO_EINVAL, "bad device ordinal%s");
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, cfg->device) != cudaSuccess) return fail(REVO_ECUDA, "device query failed%s");
@@ -554,7 +595,26 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
   c->n_lanes = cfg->lanes;
   const size_t budget = cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : (40ull << 30);
   const float* w[2] = {cfg->rgb_weights, cfg->depth_weights};
-  const size_t wn[2] = {cfg->rgb_weights_count, cfg->depth_weights_count};
+  size_t wn[2] = {cfg->rgb_weights_count, cfg->depth_weights_count};
+  // Models without an array: from their file, or the seeded random initialisation.
+  std::vector<float> host_w[2];
+  const char* wpath[2] = {cfg->rgb_weights_path, cfg->depth_weights_path};
+  for (int m = 0; m < 2; ++m) {
+    if (w[m] || (!wpath[m] && !((cfg->random_init >> m) & 1))) continue;
+    NetShape s{m == 0 ? 3 : 1, cfg->k, cfg->tubelet, cfg->patch, cfg->enc_dim, cfg->enc_depth, cfg->enc_heads,
+               cfg->dec_dim, cfg->dec_depth, cfg->dec_heads, cfg->mlp_ratio};
+    std::string why = check_shape(s);
+    if (!why.empty()) return fail(REVO_EINVAL, "unsupported network shape: %s", why.c_str());
+    host_w[m].resize(param_count(s));
+    if (wpath[m]) {
+      if (!load_weights_file(wpath[m], 0, host_w[m].size(), host_w[m].data(), &why))
+        return fail(REVO_EINVAL, "%s", why.c_str());
+    } else {
+      init_weights_random(s, cfg->seed + static_cast<uint64_t>(m), host_w[m].data());
+    }
+    w[m] = host_w[m].data();
+    wn[m] = host_w[m].size();
+  }
   int cap_tok[2] = {0, 0}, cap_p[2] = {0, 0};
   size_t need = 0;
   for (int m = 0; m < 2; ++m) {
@@ -646,7 +706,34 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
     }
   }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_status(e, "create");
+  if (cfg->autotune && cfg->precision != REVO_FP32) {
+    // Tile choices: from the cache file where it has them, timed here for the rest.
+    const std::string tag = autotune_tag(prop);
+    if (cfg->autotune_cache) load_autotune_cache(c.get(), cfg->autotune_cache, tag);
+    size_t before = 0, after = 0;
+    for (int m = 0; m < 2; ++m) before += c->net[m] ? c->net[m]->tuned_bn.size() : 0;
+    for (int m = 0; m < 2; ++m) {
+      if (!c->net[m]) continue;
+      if ((e = net_autotune(c->net[m], c->lanes[0].ws[m], cap_tok[m], cap_p[m], c->lanes[0].st[m], c->sms)) !=
+          cudaSuccess)
+        return cuda_status(e, "autotune");
+      after += c->net[m]->tuned_bn.size();
+    }
+    if (cfg->autotune_cache && after != before && !save_autotune_cache(c.get(), cfg->autotune_cache, tag))
+      return fail(REVO_EINVAL, "cannot write the autotune cache file %s", cfg->autotune_cache);
+  }
   *out = c.release();
+  return REVO_OK;
+}
+
+revo_status revo_init_weights(const revo_config* cfg, int channels, uint64_t seed, float* out, size_t count) {
+  if (!cfg || !out || (channels != 1 && channels != 3)) return fail(REVO_EINVAL, "bad argument%s");
+  NetShape s{channels, cfg->k, cfg->tubelet, cfg->patch, cfg->enc_dim, cfg->enc_depth, cfg->enc_heads,
+             cfg->dec_dim, cfg->dec_depth, cfg->dec_heads, cfg->mlp_ratio};
+  const std::string why = check_shape(s);
+  if (!why.empty()) return fail(REVO_EINVAL, "unsupported network shape: %s", why.c_str());
+  if (count != param_count(s)) return fail(REVO_EINVAL, "count differs from the model's parameter count%s");
+  init_weights_random(s, seed, out);
   return REVO_OK;
 }
 

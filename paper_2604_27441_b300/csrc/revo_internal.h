@@ -30,10 +30,14 @@ constexpr int kMaxSegments = 64;
 constexpr int kMaxRefs = 7;  // k <= 7
 
 // Token segments (one per request) for attention: tokens attend within their
-// segment only.
+// segment only.  With `queries` set, only rows [q_begin[g], q_end[g]) of
+// segment g are queries (the keys stay the whole segment) and only those
+// output rows are written (tensor-core path; the FP32 path writes every row).
 struct Segments {
   int n;
   int start[kMaxSegments + 1];
+  bool queries;
+  int q_begin[kMaxSegments], q_end[kMaxSegments];
 };
 
 // ---- tensor maps
@@ -133,6 +137,17 @@ struct BlendArgs {
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st, const BlendArgs* dev = nullptr);
 
 cudaError_t launch_f32_to_bf16(const float* in, void* out, size_t n, cudaStream_t st);
+
+// Row gather: for each of n runs, rows [src[i], src[i] + (dst[i+1] - dst[i]))
+// of x (float32 [.][D]) and a (elem_bytes 2 or 4, [.][D]) go to rows
+// [dst[i], dst[i+1]) of xc and ac.  D % 8 == 0.
+struct RowRuns {
+  int n;
+  int src[kMaxSegments];
+  int dst[kMaxSegments + 1];
+};
+cudaError_t launch_gather_rows(const float* x, const void* a, int elem_bytes, int D, const RowRuns& runs, float* xc,
+                               void* ac, cudaStream_t st);
 
 // Reed-Solomon erasure code of I-frame packets over GF(2^8) (systematic,
 // Cauchy parity rows): encode n data packets into r parity packets; decode n

@@ -71,8 +71,11 @@ def test_null_arguments_are_rejected_before_any_device_work(lib):
     assert lib.revo_op_linear(R.FP32, 0, None, None, None, None, 4, 4, 8, 0, None) == R.REVO_EINVAL
     assert lib.revo_op_layernorm(None, None, None, None, 4, 8, 0, None) == R.REVO_EINVAL
     seg = (C.c_int * 2)(0, 4)
-    assert lib.revo_op_attention(R.FP32, None, None, 4, 64, 1, seg, 1, 0, None) == R.REVO_EINVAL
-    assert lib.revo_op_attention(R.FP32, 1, 1, 4, 96, 1, seg, 1, 0, None) == R.REVO_EINVAL  # head width 96
+    assert lib.revo_op_attention(R.FP32, None, None, 4, 64, 1, seg, None, None, 1, 0, None) == R.REVO_EINVAL
+    assert lib.revo_op_attention(R.FP32, 1, 1, 4, 96, 1, seg, None, None, 1, 0, None) == R.REVO_EINVAL  # width 96
+    qb, qe = (C.c_int * 1)(0), (C.c_int * 1)(5)   # query rows past the segment end
+    assert lib.revo_op_attention(R.FP32, 1, 1, 4, 64, 1, seg, qb, qe, 1, 0, None) == R.REVO_EINVAL
+    assert lib.revo_op_attention(R.FP32, 1, 1, 4, 64, 1, seg, qb, None, 1, 0, None) == R.REVO_EINVAL
     assert lib.revo_op_depth_stats(None, 4, 4, 8, None, None, None) == R.REVO_EINVAL
     assert "bad argument" in R.last_error() or R.last_error()
     h = C.c_void_p()
@@ -117,3 +120,32 @@ def test_synthetic_frames_are_row_major():
     for pl in (rgb, dep, synth.make_tiny_plane(5, "rgb", 48, 80, 5)):
         for name in ("refs", "decoded", "mask", "clean", "lost"):
             assert getattr(pl, name).flags["C_CONTIGUOUS"], name
+
+
+@pytest.mark.parametrize("shape,channels,seed", [
+    (dict(k=1, tubelet=2, enc_dim=192, enc_depth=1, enc_heads=3, dec_dim=192, dec_depth=1, dec_heads=3), 3, 0),
+    (dict(k=3, tubelet=1, enc_dim=384, enc_depth=2, enc_heads=6, dec_dim=192, dec_depth=1, dec_heads=3), 1, 7),
+    (dict(), 3, 0), (dict(), 1, 1), (dict(), 3, 2 ** 40 + 5)])
+def test_seeded_random_init_equals_the_synthetic_weights(shape, channels, seed):
+    """revo_init_weights (C++, host) draws exactly the weights the Python side
+    draws for the same shape and seed (NumPy's PCG64 seeded through
+    SeedSequence, uniform doubles rounded to float32): bit for bit, so a
+    context created from a seed alone computes the same network the oracle
+    is given.  ViT-B shapes included (94 M parameters)."""
+    import numpy as np
+    import synth
+    cfg = R.config(**shape)
+    mc = synth.ModelConfig(channels=channels, k=cfg.k, tubelet=cfg.tubelet, patch=cfg.patch, enc_dim=cfg.enc_dim,
+                           enc_depth=cfg.enc_depth, enc_heads=cfg.enc_heads, dec_dim=cfg.dec_dim,
+                           dec_depth=cfg.dec_depth, dec_heads=cfg.dec_heads, mlp_ratio=cfg.mlp_ratio)
+    want = synth.flatten(synth.weights(mc, seed=seed))
+    got = R.init_weights(cfg, channels, seed)
+    assert got.shape == want.shape
+    np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_init_weights_rejects_a_wrong_count():
+    import numpy as np
+    cfg = R.config()
+    out = np.empty(10, np.float32)
+    assert R.lib().revo_init_weights(C.byref(cfg), 3, 0, out.ctypes.data, 10) == R.REVO_EINVAL

@@ -332,6 +332,29 @@ def test_attention_bf16_tcgen05(seg, heads, whole_units):
     assert R.take_device_error() == 0
 
 
+@pytest.mark.parametrize("seg,queries,heads", [((0, 3600), [(2400, 3600)], 6), ((0, 900, 1800), [(600, 900), (1500, 1800)], 6),
+                                               ((0, 300, 1000), [(0, 17), (700, 1000)], 2)])
+def test_attention_bf16_query_rows(seg, queries, heads):
+    """Queries restricted to some rows of each segment (the last decoder block
+    keeps the final slot's rows only): those rows equal the oracle's full
+    attention there; every other output row is left untouched."""
+    M, D = seg[-1], 64 * heads
+    qkv = bf16(synth.normal(M + 3 * heads, (M, 3 * D)))
+    out = torch.full((M, D), 7.0, dtype=torch.bfloat16, device="cuda")
+    R.op_attention(R.BF16, qkv.cuda(), out, M, D, heads, seg, queries=queries)
+    torch.cuda.synchronize()
+    got = f64(out)
+    rows = np.zeros(M, bool)
+    for a, b in queries:
+        rows[a:b] = True
+    assert (got[~rows] == 7.0).all()
+    full = got.copy()
+    ref = _oracle_segments(f64(qkv), heads, seg)
+    full[~rows] = ref[~rows]   # rows outside the queries compared as exact
+    check_attention_bf16(full, f64(qkv), heads, seg)
+    assert R.take_device_error() == 0
+
+
 def test_attention_segment_alone_equals_in_a_batch():
     """The pieces of a segment depend on its length only: its output inside a
     launch with other segments is bit for bit its output alone."""
