@@ -244,6 +244,8 @@ typedef struct {
   int pending;              /* submitted requests not yet in a batch               */
   int in_flight;            /* batches launched and not yet retired                */
   int tuned_pair;           /* tuned shapes where a CTA-pair tile (REVO_TILE_PAIR) won */
+  int tuned_timed;          /* of the tuned shapes, those this context timed (the rest
+                               came from the autotune cache file)                  */
 } revo_stats;
 
 /* Fills *out.  Errors: REVO_EINVAL (null argument). */
@@ -472,14 +474,14 @@ REVO_API revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const 
  * the whole segment -- and, at REVO_BF16, only those output rows are written
  * (REVO_FP32 writes every row).  The recovery network uses it for its last
  * decoder block, whose only consumer is the pixel head on the final slot.
- * REVO_BF16 work split: each segment's (head, 256-query) units are laid end
- * to end over their 128-key tiles and cut into equal pieces, one per CTA, so
- * that the segment's pieces fill the GPU's SMs once; units cut in two are
- * merged by a second kernel.  The cut depends on the segment's length only, so
- * a segment's output is bit for bit the same alone and among other segments.
- * flags bit 1 (REVO_ATTN_WHOLE_UNITS): one CTA per unit instead, one launch
- * (results equal within rounding, not bit for bit).  The step-level entry
- * point keeps its partial-result buffer per device (grown on demand).
+ * REVO_BF16 work split: one CTA per (head, 256-query) unit of a segment for
+ * its whole waves of units (the GPU's SM count each); the units of a last,
+ * partly filled wave are cut into up to 8 key ranges so that wave fills the
+ * SMs, and a second kernel merges their parts.  The cut depends on the
+ * segment's length only, so a segment's output is bit for bit the same alone
+ * and among other segments.  flags bit 1 (REVO_ATTN_WHOLE_UNITS): no cut, one
+ * launch (results equal within rounding, not bit for bit).  The step-level
+ * entry point keeps its partial-result buffer per device (grown on demand).
  */
 #define REVO_ATTN_WHOLE_UNITS 2
 REVO_API revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D,

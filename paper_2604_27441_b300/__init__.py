@@ -72,7 +72,8 @@ class Pose(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("device_bytes", C.c_size_t), ("batches", C.c_uint64), ("graph_replays", C.c_uint64),
                 ("graphs_captured", C.c_int), ("tuned_shapes", C.c_int), ("tuned_wide", C.c_int),
-                ("pending", C.c_int), ("in_flight", C.c_int), ("tuned_pair", C.c_int)]
+                ("pending", C.c_int), ("in_flight", C.c_int), ("tuned_pair", C.c_int),
+                ("tuned_timed", C.c_int)]
 
 
 class Result(C.Structure):

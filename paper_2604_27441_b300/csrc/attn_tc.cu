@@ -4,16 +4,18 @@
 // no token dropping), computed flash-style with an online softmax.
 //
 // Work decomposition.  A unit is (head, 256-query item) of one segment; its
-// work is nkv steps, one per 128-key K/V tile.  Each segment's units are laid
-// end to end (head-major) and cut into pieces of equal length, chosen from
-// the segment's length alone so that the segment's pieces fill the SMs once
-// (at least kMinPieceSteps steps each).  One CTA runs one piece: a run of
-// sub-units, the first and last possibly covering only part of a unit's key
-// range.  A whole unit's rows are written as bf16; a part writes its
-// unnormalised O, reference maximum and sum to a partial slot, and
-// attn_combine_kernel merges a split unit's parts in piece order.  The cut
-// depends on the segment's length only, so a segment gives bit for bit the
-// same result alone and inside a batch of other segments.
+// work is nkv steps, one per 128-key K/V tile.  One CTA runs one piece.  Of a
+// segment's U units (head-major), the whole waves -- floor(U / SMs) * SMs
+// units -- run as one piece each; the rest, which would leave SMs idle in a
+// last, partly filled wave, are each cut into c key ranges (c = SMs / rest,
+// at most 8), and attn_combine_kernel merges each such unit's parts in order.
+// A whole unit's rows are written as bf16; a part writes its unnormalised O,
+// reference maximum and sum to a partial slot.  The cut depends on the
+// segment's length only, so a segment gives bit for bit the same result alone
+// and inside a batch of other segments; in a batch the whole units dominate
+// and the few parts add little traffic.  (Pieces that cross unit boundaries
+// balance one segment alone slightly better, but cost 40% more SM-time with
+// other kernels in flight: every unit boundary then writes and merges parts.)
 //
 // One CTA owns two 128-row query tiles (256 queries) of the current unit; both
 // share every K/V tile it streams in (128 keys each).  TMA reads the head's
@@ -69,28 +71,46 @@ constexpr uint32_t kSCol = 0;
 constexpr uint32_t kPCol = 128;
 constexpr uint32_t kOCol = 192;
 constexpr float kRescaleLog2 = 8.0f;  // rescale once a row max grows by more than 2^8
-constexpr int kMinPieceSteps = 4;     // K/V tiles of the shortest piece
+constexpr int kMaxChunks = 8;         // key ranges a unit of the last wave is cut into, at most
 constexpr int kPartRows = kTiles * kQ;  // 256 rows per partial slot
 constexpr int kCombineRows = 16;        // rows per combine block (x 16 column groups = 256 threads)
 
 // The pieces of one launch.  Segments with tokens, in grid order (longest
-// pieces first); slot k covers pieces [piece_prefix[k], piece_prefix[k+1]) of
-// the grid and the interior piece boundaries [bnd_prefix[k], bnd_prefix[k+1])
-// of the combine.
+// units first); slot k covers pieces [piece_prefix[k], piece_prefix[k+1]) of
+// the grid: whole[k] whole units, then (units - whole[k]) * chunks[k] parts of
+// clen[k] K/V tiles (the last part of a unit shorter), whose partial slots are
+// part_prefix[k] + their index among the slot's parts; the combine's blocks
+// [split_prefix[k], split_prefix[k+1]) * 16 merge the slot's cut units.
 struct TcAttnParams {
-  int D, heads, n_slots, pieces;
+  int D, heads, n_slots, pieces, parts;
   float scale_log2;
   int s0[kMaxSegments], s1[kMaxSegments];     // key rows
   int qs0[kMaxSegments], qs1[kMaxSegments];   // query rows (within the key rows)
   int items[kMaxSegments], nkv[kMaxSegments]; // 256-query items, 128-key tiles
-  int plen[kMaxSegments];                     // steps per piece
+  int whole[kMaxSegments], chunks[kMaxSegments], clen[kMaxSegments];
   int piece_prefix[kMaxSegments + 1];
-  int bnd_prefix[kMaxSegments + 1];
-  // Partial slots: 2 per piece (its first and its last sub-unit); O
-  // [2 * pieces][256][64], then (m, l) [2 * pieces][256][2].  Null: every
-  // piece is one whole unit.
+  int part_prefix[kMaxSegments + 1];
+  int split_prefix[kMaxSegments + 1];
+  // Partial slots: O [parts][256][64], then (m, l) [parts][256][2].  Null:
+  // every piece is one whole unit.
   float* part;
 };
+
+// Piece p (grid order within slot k) as a range of steps [step0, step1) in
+// the slot's unit-major step order.
+REVO_DEVI void piece_steps(const TcAttnParams& P, int k, int p, int* step0, int* step1) {
+  const int nkv = P.nkv[k], whole = P.whole[k];
+  if (p < whole) {
+    *step0 = p * nkv;
+    *step1 = *step0 + nkv;
+  } else {
+    const int q = p - whole;
+    const int u = whole + q / P.chunks[k];
+    const int kb = (q % P.chunks[k]) * P.clen[k];
+    *step0 = u * nkv + kb;
+    *step1 = u * nkv + min(kb + P.clen[k], nkv);
+  }
+}
 
 // One sub-unit of a piece: unit u of the segment, K/V tiles [kb, ke).
 struct SubUnit {
@@ -225,9 +245,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int s0 = P.s0[k];
   const int s1 = P.s1[k];
   const int nkv = P.nkv[k];
-  const int work = P.heads * P.items[k] * nkv;
-  const int step0 = (b - P.piece_prefix[k]) * P.plen[k];
-  const int step1 = min(work, step0 + P.plen[k]);
+  const int piece = b - P.piece_prefix[k];
+  int step0 = 0, step1 = 0;
+  piece_steps(P, k, piece, &step0, &step1);
   const int u0 = step0 / nkv;
   const int n_sub = (step1 - 1) / nkv - u0 + 1;
   const int D = P.D;
@@ -526,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (su.partial) {
         // Partial: unnormalised O, the reference maximum m (log2 units) and
         // the sum l of this sub-unit's K/V range.
-        const int slot = 2 * b + (i == 0 ? 0 : 1);
+        const int slot = P.part_prefix[k] + (piece - P.whole[k]);
         const size_t slot_row = static_cast<size_t>(slot) * kPartRows + t * kQ + r;
         float4* po = reinterpret_cast<float4*>(P.part + slot_row * kHD);
 #pragma unroll
@@ -536,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           po[8 + x] = make_float4(__uint_as_float(o1[4 * x]), __uint_as_float(o1[4 * x + 1]),
                                   __uint_as_float(o1[4 * x + 2]), __uint_as_float(o1[4 * x + 3]));
         }
-        float* pml = P.part + static_cast<size_t>(2 * P.pieces) * kPartRows * kHD + slot_row * 2;
+        float* pml = P.part + static_cast<size_t>(P.parts) * kPartRows * kHD + slot_row * 2;
         *reinterpret_cast<float2*>(pml) = make_float2(m, l);
       } else {
         const int row = su.q0 + t * kQ + r;
@@ -568,42 +588,33 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Merges the parts of each split unit: per query row O = sum_c 2^(m_c - M) O_c,
-// l = sum_c 2^(m_c - M) l_c with M = max_c m_c over the unit's pieces in piece
+// Merges the parts of each cut unit: per query row O = sum_c 2^(m_c - M) O_c,
+// l = sum_c 2^(m_c - M) l_c with M = max_c m_c over the unit's parts in key
 // order, and writes O / l as bf16.  A block covers 16 rows x 16 groups of 4
-// columns of the unit whose first interior piece boundary is the block's
-// boundary (other boundaries inside the same unit exit at once).
+// columns of one cut unit.
 __global__ void __launch_bounds__(256) attn_combine_kernel(const __grid_constant__ TcAttnParams P,
                                                            __nv_bfloat16* __restrict__ out) {
   constexpr int kBlocksPerUnit = kPartRows / kCombineRows;
-  const int bnd = static_cast<int>(blockIdx.x) / kBlocksPerUnit;
+  const int cut = static_cast<int>(blockIdx.x) / kBlocksPerUnit;
   const int rblk = static_cast<int>(blockIdx.x) % kBlocksPerUnit;
   int k = 0;
-  while (k + 1 < P.n_slots && P.bnd_prefix[k + 1] <= bnd) ++k;
-  const int nkv = P.nkv[k], plen = P.plen[k], items = P.items[k];
-  const int p = bnd - P.bnd_prefix[k] + 1;  // boundary between pieces p-1 and p of the segment
-  const int at = p * plen;
-  const int u = at / nkv;
-  if (at % nkv == 0) return;                               // on a unit edge: nothing split here
-  if (p >= 2 && (p - 1) * plen > u * nkv) return;          // an earlier boundary of u merges it
+  while (k + 1 < P.n_slots && P.split_prefix[k + 1] <= cut) ++k;
+  const int local = cut - P.split_prefix[k];  // cut unit of slot k
+  const int u = P.whole[k] + local;
   const int row = rblk * kCombineRows + static_cast<int>(threadIdx.x) / 16;
   const int c4 = static_cast<int>(threadIdx.x) % 16;
-  const int h = u / items;
-  const int q = P.qs0[k] + (u % items) * kPartRows + row;
+  const int h = u / P.items[k];
+  const int q = P.qs0[k] + (u % P.items[k]) * kPartRows + row;
   if (q >= P.qs1[k]) return;
-  const int pf = (u * nkv) / plen;
-  const int pl = ((u + 1) * nkv - 1) / plen;
-  const float* ml = P.part + static_cast<size_t>(2 * P.pieces) * kPartRows * kHD;
+  const int first = P.part_prefix[k] + local * P.chunks[k];
+  const int nparts = (P.nkv[k] + P.clen[k] - 1) / P.clen[k];
+  const float* ml = P.part + static_cast<size_t>(P.parts) * kPartRows * kHD;
   float M = -INFINITY;
-  for (int pp = pf; pp <= pl; ++pp) {
-    const int slot = 2 * (P.piece_prefix[k] + pp) + ((pp * plen) / nkv == u ? 0 : 1);
-    M = fmaxf(M, ml[(static_cast<size_t>(slot) * kPartRows + row) * 2]);
-  }
+  for (int c = 0; c < nparts; ++c) M = fmaxf(M, ml[(static_cast<size_t>(first + c) * kPartRows + row) * 2]);
   float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
   float L = 0.f;
-  for (int pp = pf; pp <= pl; ++pp) {
-    const int slot = 2 * (P.piece_prefix[k] + pp) + ((pp * plen) / nkv == u ? 0 : 1);
-    const size_t sr = static_cast<size_t>(slot) * kPartRows + row;
+  for (int c = 0; c < nparts; ++c) {
+    const size_t sr = static_cast<size_t>(first + c) * kPartRows + row;
     const float w = ex2_approx(ml[sr * 2] - M);
     const float4 oc = reinterpret_cast<const float4*>(P.part + sr * kHD)[c4];
     o.x = fmaf(w, oc.x, o.x);
@@ -619,12 +630,12 @@ __global__ void __launch_bounds__(256) attn_combine_kernel(const __grid_constant
 
 int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
 
-// Fills the piece table of P (segments with tokens, longest pieces first).
-// whole_units: one unit per piece (no partial slots).
+// Fills the piece table of P (segments with tokens, longest units first).
+// whole_units: one piece per unit, nothing cut.
 bool plan_pieces(TcAttnParams* P, int M, int heads, const Segments& seg, int num_sms, bool whole_units) {
   const int G = num_sms > 0 ? num_sms : 148;
   struct S {
-    int g, q0, q1, items, nkv, plen, pieces;
+    int g, q0, q1, items, nkv, whole, chunks, clen, pieces, parts, cut;
   };
   std::vector<S> v;
   for (int g = 0; g < seg.n; ++g) {
@@ -638,15 +649,22 @@ bool plan_pieces(TcAttnParams* P, int M, int heads, const Segments& seg, int num
     if (s.q1 == s.q0) continue;
     s.items = ceil_div(s.q1 - s.q0, kPartRows);
     s.nkv = ceil_div(len, kKV);
-    const long long work = static_cast<long long>(heads) * s.items * s.nkv;
-    if (work > (1LL << 30)) return false;
-    s.plen = whole_units ? s.nkv : std::max(ceil_div(work, G), kMinPieceSteps);
-    s.pieces = ceil_div(work, s.plen);
+    const long long units = static_cast<long long>(heads) * s.items;
+    if (units * s.nkv > (1LL << 30)) return false;
+    const int U = static_cast<int>(units);
+    const int rest = U % G;
+    int c = rest > 0 && !whole_units ? std::min(std::min(G / rest, kMaxChunks), s.nkv) : 1;
+    s.whole = c >= 2 ? U - rest : U;
+    s.clen = c >= 2 ? ceil_div(s.nkv, c) : s.nkv;
+    s.chunks = c >= 2 ? ceil_div(s.nkv, s.clen) : 1;  // parts per cut unit (none empty)
+    s.cut = U - s.whole;
+    s.parts = s.cut * s.chunks;
+    s.pieces = s.whole + s.parts;
     v.push_back(s);
   }
-  std::stable_sort(v.begin(), v.end(), [](const S& a, const S& b) { return a.plen > b.plen; });
+  std::stable_sort(v.begin(), v.end(), [](const S& a, const S& b) { return a.nkv > b.nkv; });
   P->n_slots = static_cast<int>(v.size());
-  int pieces = 0, bnds = 0;
+  int pieces = 0, parts = 0, cuts = 0;
   for (int i = 0; i < P->n_slots; ++i) {
     const S& s = v[i];
     P->s0[i] = seg.start[s.g];
@@ -655,15 +673,21 @@ bool plan_pieces(TcAttnParams* P, int M, int heads, const Segments& seg, int num
     P->qs1[i] = s.q1;
     P->items[i] = s.items;
     P->nkv[i] = s.nkv;
-    P->plen[i] = s.plen;
+    P->whole[i] = s.whole;
+    P->chunks[i] = s.chunks;
+    P->clen[i] = s.clen;
     P->piece_prefix[i] = pieces;
-    P->bnd_prefix[i] = bnds;
+    P->part_prefix[i] = parts;
+    P->split_prefix[i] = cuts;
     pieces += s.pieces;
-    bnds += s.pieces - 1;
+    parts += s.parts;
+    cuts += s.cut;
   }
   P->piece_prefix[P->n_slots] = pieces;
-  P->bnd_prefix[P->n_slots] = bnds;
+  P->part_prefix[P->n_slots] = parts;
+  P->split_prefix[P->n_slots] = cuts;
   P->pieces = pieces;
+  P->parts = parts;
   return true;
 }
 
@@ -672,19 +696,15 @@ bool plan_pieces(TcAttnParams* P, int M, int heads, const Segments& seg, int num
 size_t attention_partial_bytes(int M, int heads, const Segments& seg, int num_sms) {
   TcAttnParams P{};
   if (!plan_pieces(&P, M, heads, seg, num_sms, false)) return 0;
-  return static_cast<size_t>(2 * P.pieces) * kPartRows * (kHD + 2) * sizeof(float);
+  return static_cast<size_t>(P.parts) * kPartRows * (kHD + 2) * sizeof(float);
 }
 
 size_t attention_partial_bytes_bound(int n_seg, int seg_len, int heads, int num_sms) {
-  // A segment of work W has at most min(SMs, ceil(W / kMinPieceSteps)) pieces
-  // (its piece length is at least W / SMs and at least kMinPieceSteps); W
-  // grows with the length.  The piece count itself is not monotone in the
-  // length, so the bound uses the cap, not the longest segment's count.
+  // A segment's parts: its cut units (fewer than the SMs) times the parts per
+  // unit (at most SMs / cut units), so at most one part per SM.
   if (n_seg <= 0 || n_seg > kMaxSegments || seg_len <= 0 || heads <= 0) return 0;
   const int G = num_sms > 0 ? num_sms : 148;
-  const long long work = static_cast<long long>(heads) * ceil_div(seg_len, kPartRows) * ceil_div(seg_len, kKV);
-  const long long pieces = std::min<long long>(G, (work + kMinPieceSteps - 1) / kMinPieceSteps);
-  return static_cast<size_t>(2 * pieces * n_seg) * kPartRows * (kHD + 2) * sizeof(float);
+  return static_cast<size_t>(G) * n_seg * kPartRows * (kHD + 2) * sizeof(float);
 }
 
 bool encode_attention_tmap(CUtensorMap* map, const void* qkv, int M, int D) {
@@ -707,9 +727,9 @@ cudaError_t launch_attention_tc(const CUtensorMap& qkv_map, void* out, int M, in
   if (e != cudaSuccess) return e;
   attn_tc_kernel<<<P.pieces, kThreads, kSmemBytes, st>>>(qkv_map, static_cast<__nv_bfloat16*>(out), P, err);
   int n = 1;
-  const int bnds = P.bnd_prefix[P.n_slots];
-  if (part && bnds > 0) {
-    attn_combine_kernel<<<bnds * (kPartRows / kCombineRows), 256, 0, st>>>(P, static_cast<__nv_bfloat16*>(out));
+  const int cuts = P.split_prefix[P.n_slots];
+  if (part && cuts > 0) {
+    attn_combine_kernel<<<cuts * (kPartRows / kCombineRows), 256, 0, st>>>(P, static_cast<__nv_bfloat16*>(out));
     ++n;
   }
   if (launched) *launched = n;

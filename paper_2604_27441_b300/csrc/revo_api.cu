@@ -883,6 +883,7 @@ revo_status revo_recover_stats(revo_ctx* c, revo_stats* out) {
       out->tuned_shapes += static_cast<int>(c->net[m]->tuned_bn.size());
       out->tuned_wide += c->net[m]->tuned_shapes_256;
       out->tuned_pair += c->net[m]->tuned_shapes_pair;
+      out->tuned_timed += c->net[m]->tuned_shapes_128 + c->net[m]->tuned_shapes_256;
     }
   out->pending = static_cast<int>(c->pending.size());
   for (const auto& kv : c->batches) out->in_flight += kv.second.lane >= 0 && !kv.second.done;

@@ -317,12 +317,13 @@ def check_attention_bf16(got, qkv64, heads, seg, cache_key=None):
 @pytest.mark.parametrize("seg,heads", ATT_CASES + [((0, 900), 12), ((0, 10800), 2), ((0, 129, 385, 3600), 12),
                                                    ((0, 4320, 5600, 5856), 4)])
 def test_attention_bf16_tcgen05(seg, heads, whole_units):
-    """By default each segment's units are cut into pieces that fill the SMs
-    (units cut in two are merged by a second kernel); whole_units runs one
-    CTA per (head, 256 queries) unit.  The cases cover pieces shorter than a
-    unit (N = 900), pieces spanning several units with split units at both
-    ends (N = 3600, 10800), units whose second query tile is empty (lengths
-    129, 256 + 16, ...) and segments of mixed lengths in one launch."""
+    """By default the units of a segment's last, partly filled wave are cut
+    into key ranges merged by a second kernel; whole_units runs one CTA per
+    (head, 256 queries) unit.  The cases cover every unit cut (N = 900, 48
+    units), whole waves plus a cut tail (N = 3600: 148 whole + 32 cut in 4),
+    nothing cut (N = 10800 with 2 heads), units whose second query tile is
+    empty (lengths 129, 256 + 16, ...) and segments of mixed lengths in one
+    launch."""
     M, D = seg[-1], 64 * heads
     qkv = bf16(synth.normal(M + heads, (M, 3 * D)))
     out = torch.zeros((M, D), dtype=torch.bfloat16, device="cuda")
@@ -356,8 +357,8 @@ def test_attention_bf16_query_rows(seg, queries, heads):
 
 
 def test_attention_segment_alone_equals_in_a_batch():
-    """The pieces of a segment depend on its length only: its output inside a
-    launch with other segments is bit for bit its output alone."""
+    """A segment's cut depends on its length only: its output inside a launch
+    with other segments is bit for bit its output alone."""
     heads, D = 12, 768
     lens = (3600, 900, 10800, 4320)
     seg = np.concatenate([[0], np.cumsum(lens)]).tolist()

@@ -419,3 +419,52 @@ def test_error_statuses():
         t = ctx.submit(o.request(0, rgb, dep))
         assert ctx.poll(t).status == R.REVO_OK
         del keep, small
+
+
+def test_weights_from_seed_and_file_equal_the_arrays(tmp_path):
+    """A context whose models come from a seed (revo_init_weights' random
+    initialisation) or from flat float32 files computes exactly what the same
+    weights passed as arrays give."""
+    rgb, dep = synth.make_tiny_plane(31, "rgb", 64, 96, 5), synth.make_tiny_plane(32, "depth", 64, 96, 5)
+    with make_ctx(SMALL, R.BF16, (64, 96)) as ctx:
+        want = run(ctx, 0, rgb, dep)
+    cfg = R.config(**SMALL, precision=R.BF16, max_height=64, max_width=96, max_streams=4, seed=0, random_init=3)
+    with R.Context(cfg) as ctx:
+        got_seed = run(ctx, 0, rgb, dep)
+    paths = []
+    for C, seed in ((3, 0), (1, 1)):
+        p = tmp_path / f"w{C}.bin"
+        synth.flatten(weights(SMALL, C)).tofile(p)
+        paths.append(str(p))
+    cfg = R.config(**SMALL, precision=R.BF16, max_height=64, max_width=96, max_streams=4,
+                   rgb_weights_path=paths[0], depth_weights_path=paths[1])
+    with R.Context(cfg) as ctx:
+        got_file = run(ctx, 0, rgb, dep)
+    for a, b, c in zip(want, got_seed, got_file):
+        np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(a, c)
+
+
+def test_autotune_cache_file_round_trip(tmp_path):
+    """With autotune on, create times every GEMM shape and writes the cache
+    file; a second context reads it and times nothing; both give the same
+    outputs as a context without tuning (a tile choice never changes results)."""
+    cache = str(tmp_path / "tiles.txt")
+    rgb, dep = synth.make_request(1020, "320x240")
+    outs, tuned = [], []
+    for tune, path in ((0, None), (1, cache), (1, cache)):
+        kw = dict(autotune_cache=path) if path else {}
+        cfg = R.config(**VITB, precision=R.BF16, max_height=240, max_width=320, max_streams=2, autotune=tune, **kw)
+        with R.Context(cfg, synth.flatten(weights(VITB, 3)), synth.flatten(weights(VITB, 1))) as ctx:
+            outs.append(run(ctx, 0, rgb, dep))
+            st = ctx.stats()
+            tuned.append((st["tuned_shapes"], st["tuned_timed"]))
+        if tune:
+            lines = open(cache).read().splitlines()
+            assert lines[0].startswith("revo-autotune 1 sm_10")
+            assert len(lines) - 1 == st["tuned_shapes"] > 0
+    assert tuned[0][0] == 0 and tuned[1][0] == tuned[2][0]
+    assert tuned[1][1] == tuned[1][0] and tuned[2][1] == 0   # the second context timed nothing
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            np.testing.assert_array_equal(x, y)
