@@ -61,6 +61,9 @@ MIX16 = ["320x240", "640x480", "1280x720+640x576", "320x240", "640x480", "1280x7
          "320x240", "640x480"]
 TICK_WORKLOAD = ("mixed16: 16 participant streams (6 x 320x240, 6 x 640x480, 4 x 1280x720 RGB + 640x576 depth), "
                  "independent Gilbert-Elliott slice loss, one batch per modality per step")
+# Tile choices are shared by the benchmark's contexts through one cache file
+# (each context times only the GEMM shapes the file lacks).
+TILE_CACHE = os.path.join(tempfile.gettempdir(), f"revo_tiles_{os.getpid()}.txt")
 # DRAM bytes (read + write) of one attn_tc_kernel launch of the tick's batched
 # RGB encoder attention, from an ncu capture of the current kernel version
 # (None once the kernel changes).
@@ -347,9 +350,10 @@ def tick_segments(wl_rgb: bool = True) -> list:
 def attention_roofline(R, torch, stream) -> dict:
     """The dominant kernel of the tick, timed alone on the same stream with CUDA
     events: the batched tcgen05 attention of one RGB encoder block over the 16
-    requests' token segments (N = 900 x 6, 3600 x 6, 10800 x 4; 12 heads x 64).
-    Achieved = 4 N^2 D summed over the segments / launch time.  Beside it the
-    same kernel on one 640x480 request (N = 3600) and its one-CTA-per-unit form."""
+    requests' token segments (N = 900 x 6, 3600 x 6, 10800 x 4; 12 heads x 64),
+    in the form the forward runs (one CTA per unit).  Achieved = 4 N^2 D summed
+    over the segments / launch time.  Beside it the same kernel on one 640x480
+    request (N = 3600) and its tail-cut form (REVO_ATTN_SPLIT_TAIL)."""
     D, heads = 768, 12
     lens = tick_segments(True)
     seg = np.concatenate([[0], np.cumsum(lens)]).astype(int).tolist()
@@ -375,7 +379,7 @@ def attention_roofline(R, torch, stream) -> dict:
     f1 = 4 * N1 * N1 * D
     q1, o1 = qkv[:N1].contiguous(), out[:N1]
     sec1 = timed(lambda: R.op_attention(R.BF16, q1, o1, N1, D, heads, [0, N1], stream=stream), 50)
-    sec1w = timed(lambda: R.op_attention(R.BF16, q1, o1, N1, D, heads, [0, N1], stream=stream, whole_units=True), 50)
+    sec1s = timed(lambda: R.op_attention(R.BF16, q1, o1, N1, D, heads, [0, N1], stream=stream, split_tail=True), 50)
     assert R.take_device_error() == 0
     peak = peaks().get("bf16_tflops")
     tf = lambda f, s: f / s / 1e12  # noqa: E731
@@ -388,8 +392,8 @@ def attention_roofline(R, torch, stream) -> dict:
             "flops_per_launch": flops, "us_per_launch": sec * 1e6,
             "n3600_alone": {"us_per_launch": sec1 * 1e6, "achieved": tf(f1, sec1),
                             "frac": tf(f1, sec1) / peak if peak else None},
-            "n3600_whole_units": {"us_per_launch": sec1w * 1e6, "achieved": tf(f1, sec1w),
-                                  "frac": tf(f1, sec1w) / peak if peak else None}}
+            "n3600_split_tail": {"us_per_launch": sec1s * 1e6, "achieved": tf(f1, sec1s),
+                                 "frac": tf(f1, sec1s) / peak if peak else None}}
 
 
 class StreamIO:
@@ -472,7 +476,7 @@ def _with_flag(R, req, extra):
 def tick_context(R, precision, stream, graphs=True, lanes=1):
     import synth
     cfg = R.config(**VITB, precision=precision, max_height=720, max_width=1280, max_streams=16, max_batch=16,
-                   lanes=lanes, use_graphs=1 if graphs else 0, autotune=1)
+                   lanes=lanes, use_graphs=1 if graphs else 0, autotune=1, autotune_cache=TILE_CACHE)
     return R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
                      synth.flatten(synth.weights(synth.DEPTH, seed=1)), stream=stream)
 
@@ -500,10 +504,15 @@ def measure_tick(R, torch, ctx, streams, stream, steps, warmup, clock_gpu=None):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lat, launches = [], 0
     clk = ClockSampler(clock_gpu) if clock_gpu is not None else None
+    # REVO_PROFILE_RANGE=1 marks the timed ticks for a profiler started with
+    # --profile-from-start off (it changes nothing else).
+    mark = os.environ.get("REVO_PROFILE_RANGE") == "1"
     if clk:
         clk.__enter__()
     try:
         torch.cuda.synchronize()
+        if mark:
+            torch.cuda.profiler.start()
         e0.record(stream)
         for _ in range(steps):
             res = tick_once(R, ctx, streams)
@@ -511,6 +520,8 @@ def measure_tick(R, torch, ctx, streams, stream, steps, warmup, clock_gpu=None):
             launches += res[0].kernel_launches  # every request of the batch reports the batch's launches
         e1.record(stream)
         torch.cuda.synchronize()
+        if mark:
+            torch.cuda.profiler.stop()
     finally:
         if clk:
             clk.__exit__()
@@ -569,6 +580,7 @@ def measure_serving(R, torch, precision, n_streams, seconds, serve_warmup, max_b
     rng = np.random.default_rng(5000 + n_streams)
     cfg = R.config(**VITB, precision=precision, max_height=720, max_width=1280, max_streams=n_streams,
                    max_batch=max_batch, lanes=lanes, use_graphs=1 if graphs else 0, autotune=1,
+                   autotune_cache=TILE_CACHE,
                    hbm_budget_bytes=40 << 30)
     ctx = R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
                     synth.flatten(synth.weights(synth.DEPTH, seed=1)))
@@ -652,7 +664,7 @@ def measure_batch1(R, torch, precision, stream, steps, warmup, in_flight=2, grap
     writes the de-normalised float outputs for the quality check."""
     import synth
     cfg = R.config(**VITB, precision=precision, device=local, max_height=H, max_width=W, max_streams=8,
-                   max_batch=1, lanes=in_flight, use_graphs=1 if graphs else 0, autotune=1)
+                   max_batch=1, lanes=in_flight, use_graphs=1 if graphs else 0, autotune=1, autotune_cache=TILE_CACHE)
     ctx = R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
                     synth.flatten(synth.weights(synth.DEPTH, seed=1)), stream=stream)
     streams = [StreamIO(R, torch, ctx, sid, "640x480", 2000 + 100 * rank + sid, r, 1, True, values=sid == 2)
@@ -856,7 +868,7 @@ def run_kt(args) -> None:
         shape = dict(VITB, k=k, tubelet=T)
         cfgs = [synth.ModelConfig(channels=C, k=k, tubelet=T) for C in (3, 1)]
         ctx = R.Context(R.config(**shape, precision=precision, max_height=H, max_width=W, max_streams=2,
-                                 max_batch=1, lanes=1, use_graphs=1, autotune=1),
+                                 max_batch=1, lanes=1, use_graphs=1, autotune=1, autotune_cache=TILE_CACHE),
                         synth.flatten(synth.weights(cfgs[0], seed=0)), synth.flatten(synth.weights(cfgs[1], seed=1)),
                         stream=stream)
         io = StreamIO(R, torch, ctx, 0, "640x480", 7000 + 10 * k + T, 0.2, 1, True, k=k)
@@ -890,12 +902,12 @@ def run_profile_kernel(args) -> None:
     fl = flops_per_model(3, H, W)
     N, D = fl["N"], 768
     stream = torch.cuda.Stream()
-    if args.profile_kernel in ("attention", "attention_whole"):
+    if args.profile_kernel in ("attention", "attention_split"):
         qkv = torch.randn((N, 3 * D), device="cuda").to(torch.bfloat16)
         out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
-        whole = args.profile_kernel == "attention_whole"
+        split = args.profile_kernel == "attention_split"
         launch = lambda: R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream,  # noqa: E731
-                                        whole_units=whole)
+                                        split_tail=split)
         flops = fl["attn_enc_per_block"]
     elif args.profile_kernel == "attention_tick":  # the tick's batched RGB encoder attention
         lens = tick_segments(True)
@@ -966,7 +978,7 @@ def run_profile_kernel(args) -> None:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-kernel", choices=["attention", "attention_whole", "attention_tick", "fc1", "fc1_pair",
+    ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "attention_tick", "fc1", "fc1_pair",
                                                  "fc1_fp8", "fc1_fp8_pair", "fc2", "fc2_pair", "assemble", "blend"],
                     default=None, help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)

@@ -474,16 +474,19 @@ REVO_API revo_status revo_op_frame_metrics(const void* a, size_t pitch_a, const 
  * the whole segment -- and, at REVO_BF16, only those output rows are written
  * (REVO_FP32 writes every row).  The recovery network uses it for its last
  * decoder block, whose only consumer is the pixel head on the final slot.
- * REVO_BF16 work split: one CTA per (head, 256-query) unit of a segment for
- * its whole waves of units (the GPU's SM count each); the units of a last,
+ * REVO_BF16 work split: one CTA per (head, 256-query) unit, one launch.
+ * flags bit 0 (REVO_ATTN_SPLIT_TAIL): a segment's whole waves of units (the
+ * GPU's SM count each) stay one CTA per unit, and the units of its last,
  * partly filled wave are cut into up to 8 key ranges so that wave fills the
- * SMs, and a second kernel merges their parts.  The cut depends on the
- * segment's length only, so a segment's output is bit for bit the same alone
- * and among other segments.  flags bit 1 (REVO_ATTN_WHOLE_UNITS): no cut, one
- * launch (results equal within rounding, not bit for bit).  The step-level
- * entry point keeps its partial-result buffer per device (grown on demand).
+ * SMs; a second kernel merges their parts.  It pays when the launch has the
+ * GPU to itself (N = 3600, 12 heads: 84 -> 68 us) and costs SM-time when
+ * other kernels run beside it.  The cut depends on the segment's length only,
+ * so a segment's output is bit for bit the same alone and among other
+ * segments; against the uncut form it is equal within rounding.  The
+ * step-level entry point keeps its partial-result buffer per device (grown on
+ * demand).
  */
-#define REVO_ATTN_WHOLE_UNITS 2
+#define REVO_ATTN_SPLIT_TAIL 1
 REVO_API revo_status revo_op_attention(revo_precision precision, const void* qkv, void* out, int M, int D,
                               int heads, const int* seg_start, const int* q_begin, const int* q_end, int n_seg,
                               int flags, void* stream);

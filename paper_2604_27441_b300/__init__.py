@@ -277,10 +277,10 @@ def op_frame_metrics(a, b, height, width, channels, sample_bytes, data_range, sc
                                               _stream(stream)), "revo_op_frame_metrics")
 
 
-ATTN_WHOLE_UNITS = 2
+ATTN_SPLIT_TAIL = 1
 
 
-def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None, whole_units=False, queries=None):
+def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None, split_tail=False, queries=None):
     """queries: optional list of (begin, end) query rows per segment."""
     n = len(seg_start) - 1
     arr = (C.c_int * len(seg_start))(*[int(v) for v in seg_start])
@@ -288,7 +288,7 @@ def op_attention(precision, qkv, out, M, D, heads, seg_start, stream=None, whole
     if queries is not None:
         qb = (C.c_int * n)(*[int(a) for a, _ in queries])
         qe = (C.c_int * n)(*[int(b) for _, b in queries])
-    flags = ATTN_WHOLE_UNITS if whole_units else 0
+    flags = ATTN_SPLIT_TAIL if split_tail else 0
     return _check(lib().revo_op_attention(precision, ptr(qkv), ptr(out), M, D, heads, arr, qb, qe, n, flags,
                                           _stream(stream)),
                   "revo_op_attention")

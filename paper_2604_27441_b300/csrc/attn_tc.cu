@@ -4,33 +4,30 @@
 // no token dropping), computed flash-style with an online softmax.
 //
 // Work decomposition.  A unit is (head, 256-query item) of one segment; its
-// work is nkv steps, one per 128-key K/V tile.  One CTA runs one piece.  Of a
-// segment's U units (head-major), the whole waves -- floor(U / SMs) * SMs
-// units -- run as one piece each; the rest, which would leave SMs idle in a
-// last, partly filled wave, are each cut into c key ranges (c = SMs / rest,
-// at most 8), and attn_combine_kernel merges each such unit's parts in order.
-// A whole unit's rows are written as bf16; a part writes its unnormalised O,
-// reference maximum and sum to a partial slot.  The cut depends on the
-// segment's length only, so a segment gives bit for bit the same result alone
-// and inside a batch of other segments; in a batch the whole units dominate
-// and the few parts add little traffic.  (Pieces that cross unit boundaries
-// balance one segment alone slightly better, but cost 40% more SM-time with
-// other kernels in flight: every unit boundary then writes and merges parts.)
+// work is nkv steps, one per 128-key K/V tile; one CTA runs one piece, a unit
+// or a key range of one.  By default every unit is one piece.  With the tail
+// cut (an option for a segment that has the GPU to itself), of a segment's U
+// units (head-major) the whole waves -- floor(U / SMs) * SMs units -- run as
+// one piece each and the rest, which would leave SMs idle in a last, partly
+// filled wave, are each cut into c key ranges (c = SMs / rest, at most 8);
+// a part writes its unnormalised O, reference maximum and sum to a partial
+// slot and attn_combine_kernel merges each cut unit's parts in key order.  The
+// cut depends on the segment's length only, so a segment gives bit for bit the
+// same result alone and inside a batch of other segments.
 //
 // One CTA owns two 128-row query tiles (256 queries) of the current unit; both
 // share every K/V tile it streams in (128 keys each).  TMA reads the head's
 // 64-column slices of Q, K and V straight out of the qkv matrix [M][3D]
-// (128-byte swizzle), so no head-split pass is needed.  Q is double-buffered
-// so the next sub-unit's queries load while the current one runs.  Per K/V
-// tile j and query tile t:
+// (128-byte swizzle), so no head-split pass is needed.
+// Per K/V tile j and query tile t:
 //   S_t(j) = Q_t K_j^T         tcgen05.mma M=128 N=128 K=64 -> the S columns
 //   P_t(j) = exp2(S c - m_t)   softmax warpgroup t, bf16, into the P columns
 //   O_t  += P_t(j) V_j         tcgen05.mma M=128 N=64 K=128, A = P from TMEM,
 //                              V read N-major from shared memory
 // Each query tile has S (128 columns), P (64: bf16 pairs) and O (64): 256 of
-// TMEM's 512 columns.  S and P live apart, so S_t(j+1) -- also the first S of
-// the next sub-unit -- is issued as soon as the softmax has loaded S_t(j) into
-// registers, and PV_t(j) during the next block's exponentials; the softmax
+// TMEM's 512 columns.  S and P live apart, so S_t(j+1) is issued as soon as
+// the softmax has loaded S_t(j) into registers, and PV_t(j) during the next
+// block's exponentials; the softmax
 // only waits for PV_t(j-1) before it writes P_t(j).  A rescale of O happens
 // only when a row's maximum grows by more than 2^8 (P stays below 256; the
 // result is the same softmax).
@@ -38,11 +35,10 @@
 // Warp roles (352 threads): warp 0 TMA, warp 1 TMEM allocator + MMA issuer
 // of tile 0, warps 2..5 softmax of tile 0, warps 6..9 softmax of tile 1 (warp
 // w owns rows 32*(w%4) .. +31 of its tile, the TMEM lanes it may access),
-// warp 10 MMA issuer of tile 1.  Handoffs: Q and K/V tiles, S ready, PV done
-// and Q free are mbarriers (TMA transaction counts, tcgen05.commit); S free
-// and P ready are named barriers on which the MMA warp waits suspended.  A
-// unit whose second tile lies past the segment end runs on tile 0 alone (tile
-// 1's MMA thread then only passes its Q buffer and K/V stages on).
+// warp 10 MMA issuer of tile 1.  Handoffs: Q and K/V tiles, S ready and PV
+// done are mbarriers (TMA transaction counts, tcgen05.commit); S free and P
+// ready are named barriers on which the MMA warp waits suspended.  A unit
+// whose second tile lies past its query rows runs on tile 0 alone.
 #include <algorithm>
 #include <vector>
 
@@ -63,7 +59,7 @@ constexpr int kThreads = 64 + kTiles * 128 + 32;  // + the second tile's MMA war
 constexpr int kQBytes = kQ * kHD * 2;    // 16 KB: 128 rows x 128 B
 constexpr int kKVBytes = kKV * kHD * 2;  // 16 KB
 constexpr int kBoxBytes = kBoxRows * kHD * 2;
-constexpr int kSmemBytes = 1024 + 2 * kQBytes * kTiles + 2 * kKVBytes * kKvStages + 1024;
+constexpr int kSmemBytes = 1024 + kQBytes * kTiles + 2 * kKVBytes * kKvStages + 1024;
 static_assert(kSmemBytes <= 232448, "shared memory per CTA");
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kTileCols = 256;   // per tile: S at 0 (128 columns), P at 128 (64), O at 192 (64)
@@ -95,40 +91,6 @@ struct TcAttnParams {
   // every piece is one whole unit.
   float* part;
 };
-
-// Piece p (grid order within slot k) as a range of steps [step0, step1) in
-// the slot's unit-major step order.
-REVO_DEVI void piece_steps(const TcAttnParams& P, int k, int p, int* step0, int* step1) {
-  const int nkv = P.nkv[k], whole = P.whole[k];
-  if (p < whole) {
-    *step0 = p * nkv;
-    *step1 = *step0 + nkv;
-  } else {
-    const int q = p - whole;
-    const int u = whole + q / P.chunks[k];
-    const int kb = (q % P.chunks[k]) * P.clen[k];
-    *step0 = u * nkv + kb;
-    *step1 = u * nkv + min(kb + P.clen[k], nkv);
-  }
-}
-
-// One sub-unit of a piece: unit u of the segment, K/V tiles [kb, ke).
-struct SubUnit {
-  int h, q0, ntiles, kb, ke;
-  bool partial;
-};
-
-REVO_DEVI SubUnit sub_unit(const TcAttnParams& P, int k, int u, int step0, int step1) {
-  const int nkv = P.nkv[k], items = P.items[k];
-  SubUnit su;
-  su.h = u / items;
-  su.q0 = P.qs0[k] + (u % items) * kPartRows;
-  su.ntiles = (P.qs1[k] - su.q0) > kQ ? 2 : 1;
-  su.kb = max(step0 - u * nkv, 0);
-  su.ke = min(step1 - u * nkv, nkv);
-  su.partial = su.kb > 0 || su.ke < nkv;
-  return su;
-}
 
 // Keys at or beyond `nvalid` in columns [col0, col0 + 32) get a score of -inf.
 REVO_DEVI void mask_chunk(uint32_t (&v)[32], int col0, int nvalid) {
@@ -224,13 +186,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const __grid_constant__ TcAttnParams P, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sQ = smem;                          // 2 buffers x kTiles x 16 KB
-  uint8_t* sK = sQ + 2 * kTiles * kQBytes;     // kKvStages x 16 KB
-  uint8_t* sV = sK + kKvStages * kKVBytes;     // kKvStages x 16 KB
+  uint8_t* sQ = smem;                        // kTiles x 16 KB
+  uint8_t* sK = sQ + kTiles * kQBytes;       // kKvStages x 16 KB
+  uint8_t* sV = sK + kKvStages * kKVBytes;   // kKvStages x 16 KB
   uint64_t* bars = reinterpret_cast<uint64_t*>(sV + kKvStages * kKVBytes);
-  uint64_t* q_full = bars;                  // [2] Q buffer loaded
-  uint64_t* q_empty = q_full + 2;           // [2] every S MMA of the buffer's sub-unit done
-  uint64_t* kv_full = q_empty + 2;
+  uint64_t* q_full = bars;
+  uint64_t* kv_full = q_full + 1;
   uint64_t* kv_empty = kv_full + kKvStages;
   uint64_t* s_full = kv_empty + kKvStages;  // [kTiles] S_t(j) in the S columns
   uint64_t* pv_done = s_full + kTiles;      // [kTiles] PV_t(j) accumulated: P columns free, O stable
@@ -239,28 +200,32 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int b = static_cast<int>(blockIdx.x);
   int k = 0;
-  while (k + 1 < P.n_slots && P.piece_prefix[k + 1] <= b) ++k;
-  const int s0 = P.s0[k];
+  while (k + 1 < P.n_slots && P.piece_prefix[k + 1] <= static_cast<int>(blockIdx.x)) ++k;
+  const int piece = static_cast<int>(blockIdx.x) - P.piece_prefix[k];
+  int unit = piece, kv0 = 0, kv1 = P.nkv[k];  // this CTA: unit `unit`, K/V tiles [kv0, kv1)
+  if (piece >= P.whole[k]) {
+    const int q = piece - P.whole[k];
+    unit = P.whole[k] + q / P.chunks[k];
+    kv0 = (q % P.chunks[k]) * P.clen[k];
+    kv1 = min(kv0 + P.clen[k], P.nkv[k]);
+  }
+  const bool partial = kv0 > 0 || kv1 < P.nkv[k];
+  const int nkv = kv1 - kv0;
+  const int h = unit / P.items[k];
+  const int s0 = P.s0[k];                // key rows
   const int s1 = P.s1[k];
-  const int nkv = P.nkv[k];
-  const int piece = b - P.piece_prefix[k];
-  int step0 = 0, step1 = 0;
-  piece_steps(P, k, piece, &step0, &step1);
-  const int u0 = step0 / nkv;
-  const int n_sub = (step1 - 1) / nkv - u0 + 1;
+  const int q0 = P.qs0[k] + (unit % P.items[k]) * (kTiles * kQ);
+  const int q1 = P.qs1[k];               // query rows end
+  const int ntiles = (q1 - q0) > kQ ? kTiles : 1;  // the second tile may lie past the query rows
   const int D = P.D;
 
   if (threadIdx.x == 0) {
     tma_prefetch_desc(&tm);
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&q_full[i], 1);
-      mbar_init(&q_empty[i], kTiles);  // one commit per query tile's MMA thread
-    }
+    mbar_init(q_full, 1);
     for (int s = 0; s < kKvStages; ++s) {
       mbar_init(&kv_full[s], 1);
-      mbar_init(&kv_empty[s], kTiles);  // one release per query tile's MMA thread
+      mbar_init(&kv_empty[s], ntiles);  // one release per query tile's MMA thread
     }
     for (int t = 0; t < kTiles; ++t) {
       mbar_init(&s_full[t], 1);
@@ -280,170 +245,108 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int g = 0;                // K/V tiles issued
-      int q_loads = 0;          // Q buffers issued
-      bool ok = true;
-      for (int i = 0; i < n_sub && ok; ++i) {
-        const SubUnit su = sub_unit(P, k, u0 + i, step0, step1);
-        const int buf = i & 1;
-        if (i >= 2 && !mbar_wait_sleepy(&q_empty[buf], ((i - 2) >> 1) & 1, err, kDevTimeoutProducer)) {
-          ok = false;
-          break;
+      mbar_arrive_expect_tx(q_full, ntiles * kQBytes);
+      for (int t = 0; t < ntiles; ++t)
+        for (int b = 0; b < kQ / kBoxRows; ++b)
+          tma_load_2d(sQ + t * kQBytes + b * kBoxBytes, &tm, h * kHD, q0 + t * kQ + b * kBoxRows, q_full);
+      int issued = 0;
+      for (int j = 0; j < nkv; ++j) {
+        const int st = j % kKvStages;
+        if (!mbar_wait_sleepy(&kv_empty[st], ((j / kKvStages) & 1) ^ 1u, err, kDevTimeoutProducer)) break;
+        mbar_arrive_expect_tx(&kv_full[st], 2 * kKVBytes);
+        for (int b = 0; b < kKV / kBoxRows; ++b) {
+          const int row = s0 + (kv0 + j) * kKV + b * kBoxRows;
+          tma_load_2d(sK + st * kKVBytes + b * kBoxBytes, &tm, D + h * kHD, row, &kv_full[st]);
+          tma_load_2d(sV + st * kKVBytes + b * kBoxBytes, &tm, 2 * D + h * kHD, row, &kv_full[st]);
         }
-        mbar_arrive_expect_tx(&q_full[buf], su.ntiles * kQBytes);
-        for (int t = 0; t < su.ntiles; ++t)
-          for (int bx = 0; bx < kQ / kBoxRows; ++bx)
-            tma_load_2d(sQ + (buf * kTiles + t) * kQBytes + bx * kBoxBytes, &tm, su.h * kHD,
-                        su.q0 + t * kQ + bx * kBoxRows, &q_full[buf]);
-        q_loads = i + 1;
-        for (int j = su.kb; j < su.ke; ++j, ++g) {
-          const int st = g % kKvStages;
-          if (!mbar_wait_sleepy(&kv_empty[st], ((g / kKvStages) & 1) ^ 1u, err, kDevTimeoutProducer)) {
-            ok = false;
-            break;
-          }
-          mbar_arrive_expect_tx(&kv_full[st], 2 * kKVBytes);
-          for (int bx = 0; bx < kKV / kBoxRows; ++bx) {
-            const int row = s0 + j * kKV + bx * kBoxRows;
-            tma_load_2d(sK + st * kKVBytes + bx * kBoxBytes, &tm, D + su.h * kHD, row, &kv_full[st]);
-            tma_load_2d(sV + st * kKVBytes + bx * kBoxBytes, &tm, 2 * D + su.h * kHD, row, &kv_full[st]);
-          }
-        }
+        issued = j + 1;
       }
       // No copy may still write into shared memory when the CTA exits: wait
-      // (bounded) for the last load issued into every stage and Q buffer.
-      for (int gg = max(0, g - kKvStages); gg < g; ++gg) mbar_drain(&kv_full[gg % kKvStages], (gg / kKvStages) & 1);
-      for (int i = max(0, q_loads - 2); i < q_loads; ++i) mbar_drain(&q_full[i & 1], (i >> 1) & 1);
+      // (bounded) for the queries and the last load issued into every stage.
+      mbar_drain(q_full, 0);
+      for (int j = max(0, issued - kKvStages); j < issued; ++j) mbar_drain(&kv_full[j % kKvStages], (j / kKvStages) & 1);
     }
   } else if (warp == 1 || warp == kThreads / 32 - 1) {
     // One MMA warp per query tile (warp 1: tile 0, the last warp: tile 1);
-    // lane 0 issues, in a fixed order per K/V tile: the next S once the
-    // softmax has read the current S out of the S columns (S-free barrier),
-    // PV once it has written P (P-ready barrier).  The whole warp takes part
-    // in both named barriers for every K/V tile of the tile's sub-units, also
-    // after a failed wait.  Every Q and K/V phase is waited for in order, also
-    // for a sub-unit this tile has no rows in (it then releases the Q buffer
-    // and the stages at once): so no wait can meet a barrier a phase behind or
-    // ahead of the one it means.
+    // lane 0 issues, in a fixed order per K/V tile j: S(j+1) once the softmax
+    // has read S(j) out of the S columns (S-free barrier), PV(j) once it has
+    // written P(j) (P-ready barrier).  The whole warp takes part in both named
+    // barriers for every j, also after a failed wait.
     const int t = warp == 1 ? 0 : 1;
-    constexpr uint32_t kIdS = idesc_bf16(kQ, kKV);
-    constexpr uint32_t kIdPV = idesc_bf16(kQ, kHD, /*b_mn_major=*/true);
-    const uint32_t tbase = tmem + t * kTileCols;
-    bool ok = true;
-    bool issued = false;
-    auto issue_s = [&](int i, int g) {
-      const uint32_t q_lo = sw128_lo(smem_u32(sQ + ((i & 1) * kTiles + t) * kQBytes));
-      const uint32_t k_lo = sw128_lo(smem_u32(sK + (g % kKvStages) * kKVBytes));
+    if (t < ntiles) {
+      constexpr uint32_t kIdS = idesc_bf16(kQ, kKV);
+      constexpr uint32_t kIdPV = idesc_bf16(kQ, kHD, /*b_mn_major=*/true);
+      const uint32_t tbase = tmem + t * kTileCols;
+      const uint32_t q_lo = sw128_lo(smem_u32(sQ + t * kQBytes));
+      auto issue_s = [&](int j) {
+        const uint32_t k_lo = sw128_lo(smem_u32(sK + (j % kKvStages) * kKVBytes));
 #pragma unroll
-      for (int kk = 0; kk < kHD / 16; ++kk)  // 16 dims: 32 B of the swizzled rows
-        mma_f16_hl(tbase + kSCol, q_lo + kk * 2, kSw128Hi, k_lo + kk * 2, kSw128Hi, kIdS, kk > 0 ? 1u : 0u);
-      mma_commit(&s_full[t]);
-      issued = true;
-    };
-    // Waits for sub-unit i's queries and K/V tile g, then issues S (lane 0).
-    auto start_s = [&](int i, int g) {
-      if (lane != 0 || !ok) return;
-      ok = mbar_wait(&q_full[i & 1], (i >> 1) & 1, err, kDevTimeoutMma) &&
-           mbar_wait(&kv_full[g % kKvStages], (g / kKvStages) & 1, err, kDevTimeoutMma);
-      if (ok) {
-        tc_fence_after();
-        issue_s(i, g);
-      }
-    };
-    int g = 0;               // K/V tiles before sub-unit i
-    bool s_issued = false;   // the first S of sub-unit i was issued ahead
-    for (int i = 0; i < n_sub; ++i) {
-      const SubUnit su = sub_unit(P, k, u0 + i, step0, step1);
-      const int n = su.ke - su.kb;
-      if (su.ntiles <= t) {
-        if (lane == 0 && ok) {
-          ok = mbar_wait(&q_full[i & 1], (i >> 1) & 1, err, kDevTimeoutMma);
-          if (ok) mbar_arrive(&q_empty[i & 1]);
-          for (int jj = 0; jj < n && ok; ++jj) {
-            ok = mbar_wait(&kv_full[(g + jj) % kKvStages], ((g + jj) / kKvStages) & 1, err, kDevTimeoutMma);
-            if (ok) mbar_arrive(&kv_empty[(g + jj) % kKvStages]);
-          }
+        for (int kk = 0; kk < kHD / 16; ++kk)  // 16 dims: 32 B of the swizzled rows
+          mma_f16_hl(tbase + kSCol, q_lo + kk * 2, kSw128Hi, k_lo + kk * 2, kSw128Hi, kIdS, kk > 0 ? 1u : 0u);
+        mma_commit(&s_full[t]);
+      };
+      bool ok = true;
+      if (lane == 0) {
+        ok = mbar_wait(q_full, 0, err, kDevTimeoutMma) && (nkv == 0 || mbar_wait(&kv_full[0], 0, err, kDevTimeoutMma));
+        if (ok && nkv > 0) {
+          tc_fence_after();
+          issue_s(0);
         }
-        g += n;
-        s_issued = false;
-        continue;
       }
-      if (!s_issued) start_s(i, g);
-      const bool next_here = i + 1 < n_sub && sub_unit(P, k, u0 + i + 1, step0, step1).ntiles > t;
-      for (int jj = 0; jj < n; ++jj) {
-        const int gc = g + jj;
+      for (int j = 0; j < nkv; ++j) {
         __syncwarp();
         bar_sync_named(s_free_id(t), kSoftmaxPlusMma);
-        if (jj + 1 < n) {
-          if (lane == 0 && ok) {
-            ok = mbar_wait(&kv_full[(gc + 1) % kKvStages], ((gc + 1) / kKvStages) & 1, err, kDevTimeoutMma);
-            if (ok) {
-              tc_fence_after();
-              issue_s(i, gc + 1);
-            }
+        if (lane == 0 && ok && j + 1 < nkv) {
+          const int jn = j + 1;
+          ok = mbar_wait(&kv_full[jn % kKvStages], (jn / kKvStages) & 1, err, kDevTimeoutMma);
+          if (ok) {
+            tc_fence_after();
+            issue_s(jn);
           }
-        } else {
-          // Every S of this sub-unit is issued: its Q buffer frees once they complete.
-          if (lane == 0 && ok) mma_commit(&q_empty[i & 1]);
-          if (next_here) start_s(i + 1, g + n);
         }
         __syncwarp();
         bar_sync_named(p_ready_id(t), kSoftmaxPlusMma);
         if (lane == 0 && ok) {
           tc_fence_after();
-          const uint32_t v_lo = sw128_lo(smem_u32(sV + (gc % kKvStages) * kKVBytes));
+          const uint32_t v_lo = sw128_lo(smem_u32(sV + (j % kKvStages) * kKVBytes));
 #pragma unroll
           for (int kk = 0; kk < kKV / 16; ++kk)  // 16 keys: 8 TMEM columns of P, 2048 B of V
             mma_f16_tmem_a_hl(tbase + kOCol, tbase + kPCol + kk * 8, v_lo + kk * 128, kSw128Hi, kIdPV,
-                              (jj > 0 || kk > 0) ? 1u : 0u);
+                              (j > 0 || kk > 0) ? 1u : 0u);
           mma_commit(&pv_done[t]);
-          mma_commit(&kv_empty[gc % kKvStages]);  // this tile is done with K_j, V_j
+          mma_commit(&kv_empty[j % kKvStages]);  // this tile is done with K_j, V_j
         }
       }
-      g += n;
-      s_issued = next_here;
+      __syncwarp();
+      if (lane == 0) {
+        // Nothing this thread issued may still run when TMEM is freed.
+        mma_commit(&drained[t]);
+        mbar_drain(&drained[t], 0);
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    if (lane == 0 && issued) {
-      // Nothing this thread issued may still run when TMEM is freed.
-      mma_commit(&drained[t]);
-      mbar_drain(&drained[t], 0);
-    }
-    __syncwarp();
   } else {
     const int t = (warp - 2) >> 2;  // query tile of this warpgroup
     const int q = warp & 3;
     const int r = q * 32 + lane;    // row within the tile
-    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-    const uint32_t tbase = tmem + t * kTileCols + lane_off;
-    const uint32_t s_addr = tbase + kSCol;
-    const uint32_t p_addr = tbase + kPCol;
-    const uint32_t o_addr = tbase + kOCol;
-    const uint64_t c2 = pk2(P.scale_log2, P.scale_log2);
-    const float c = P.scale_log2;
-    bool ok = true;
-    int jt = 0;  // K/V tiles this tile has processed (s_full / pv_done phases)
-    for (int i = 0; i < n_sub; ++i) {
-      const SubUnit su = sub_unit(P, k, u0 + i, step0, step1);
-      if (su.ntiles <= t) continue;
-      const int n = su.ke - su.kb;
+    if (t < ntiles) {
+      const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+      const uint32_t tbase = tmem + t * kTileCols + lane_off;
+      const uint32_t s_addr = tbase + kSCol;
+      const uint32_t p_addr = tbase + kPCol;
+      const uint32_t o_addr = tbase + kOCol;
+      const uint64_t c2 = pk2(P.scale_log2, P.scale_log2);
+      const float c = P.scale_log2;
       float m = -INFINITY;  // the maximum P is taken relative to (log2 units)
       float l = 0.f;
-      for (int jj = 0; jj < n; ++jj, ++jt) {
-        if (!ok) {
-          // After a failed wait: take part in this tile's named barriers in
-          // order, waiting on each (arriving ahead could complete a later phase).
-          __syncwarp();
-          bar_sync_named(s_free_id(t), kSoftmaxPlusMma);
-          __syncwarp();
-          bar_sync_named(p_ready_id(t), kSoftmaxPlusMma);
-          continue;
-        }
-        if (!mbar_wait_warp(&s_full[t], jt & 1, err, kDevTimeoutSoftmax, lane)) {
+      bool ok = true;
+      int j = 0;
+      int passed = 0;  // named barriers of tile j already arrived at (0, 1: S-free)
+      for (; j < nkv; ++j) {
+        passed = 0;
+        if (!mbar_wait_warp(&s_full[t], j & 1, err, kDevTimeoutSoftmax, lane)) {
           ok = false;
-          --jj;  // this tile's two barriers are still ahead
-          --jt;
-          continue;
+          break;
         }
         tc_fence_after();
         uint32_t v0[32], v1[32], v2[32], v3[32];
@@ -456,7 +359,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         __syncwarp();
         bar_arrive_named(s_free_id(t), kSoftmaxPlusMma);
-        const int nvalid = min(kKV, s1 - (s0 + (su.kb + jj) * kKV));
+        passed = 1;
+        const int nvalid = min(kKV, s1 - (s0 + (kv0 + j) * kKV));
         if (nvalid < kKV) {
           mask_chunk(v0, 0, nvalid);
           mask_chunk(v1, 32, nvalid);
@@ -465,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         float mx8[8];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) mx8[x] = -INFINITY;
+        for (int i = 0; i < 8; ++i) mx8[i] = -INFINITY;
         max_chunk(v0, mx8);
         max_chunk(v1, mx8);
         max_chunk(v2, mx8);
@@ -475,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float alpha = ex2_approx(m - m_new);  // 1 when m is kept, 0 on the first tile
         uint64_t sum2[4];
 #pragma unroll
-        for (int x = 0; x < 4; ++x) sum2[x] = 0ull;  // +0.0f pairs
+        for (int i = 0; i < 4; ++i) sum2[i] = 0ull;  // +0.0f pairs
         const uint64_t negm2 = pk2(-m_new, -m_new);
         // Keys 0..63 first, so that their registers are free before the
         // second half is computed; each half is stored as soon as the P
@@ -483,97 +387,98 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t pk0[32], pk1[32];
         exp_chunk(v0, c2, negm2, pk0, 0, sum2);
         exp_chunk(v1, c2, negm2, pk0, 16, sum2);
-        bool wait_ok = true;
-        if (jj > 0) {
+        if (j > 0) {
           // PV(j-1) must have read P(j-1) before P(j) replaces it, and O must
-          // hold it before a rescale.  pv_done has jt-1 or jt completions here
-          // (PV(jt) needs this block's P), so the parity is unambiguous.  (At
-          // jj == 0 the previous sub-unit's last PV was waited for already.)
-          wait_ok = mbar_wait_warp(&pv_done[t], (jt - 1) & 1, err, kDevTimeoutSoftmax, lane);
-          if (wait_ok) {
-            tc_fence_after();
-            if (__any_sync(0xffffffffu, alpha != 1.f)) {
-              // Rare: O *= alpha, 16 columns at a time (few live registers).
+          // hold it before a rescale.  pv_done has j-1 or j completions here
+          // (PV(j) needs this block's P), so the parity is unambiguous.
+          if (!mbar_wait_warp(&pv_done[t], (j - 1) & 1, err, kDevTimeoutSoftmax, lane)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (__any_sync(0xffffffffu, alpha != 1.f)) {
+            // Rare: O *= alpha, 16 columns at a time (few live registers).
 #pragma unroll 1
-              for (int c16 = 0; c16 < kHD; c16 += 16) {
-                uint32_t o16[16];
-                tmem_ld16(o_addr + c16, o16);
-                tmem_wait_ld();
+            for (int c16 = 0; c16 < kHD; c16 += 16) {
+              uint32_t o16[16];
+              tmem_ld16(o_addr + c16, o16);
+              tmem_wait_ld();
 #pragma unroll
-                for (int x = 0; x < 16; ++x) o16[x] = __float_as_uint(__uint_as_float(o16[x]) * alpha);
-                tmem_st16(o_addr + c16, o16);
-                tmem_wait_st();
-              }
+              for (int i = 0; i < 16; ++i) o16[i] = __float_as_uint(__uint_as_float(o16[i]) * alpha);
+              tmem_st16(o_addr + c16, o16);
+              tmem_wait_st();
             }
           }
         }
-        if (wait_ok) {
-          tmem_st32(p_addr, pk0);
-          exp_chunk(v2, c2, negm2, pk1, 0, sum2);
-          exp_chunk(v3, c2, negm2, pk1, 16, sum2);
-          tmem_st32(p_addr + 32, pk1);
-          float sum8[8];
+        tmem_st32(p_addr, pk0);
+        exp_chunk(v2, c2, negm2, pk1, 0, sum2);
+        exp_chunk(v3, c2, negm2, pk1, 16, sum2);
+        tmem_st32(p_addr + 32, pk1);
+        float sum8[8];
 #pragma unroll
-          for (int x = 0; x < 4; ++x) unpk2(sum2[x], sum8[2 * x], sum8[2 * x + 1]);
-          const float sum = reduce8_sum(sum8);
-          tmem_wait_st();
-          l = l * alpha + sum;
-          m = m_new;
-          tc_fence_before();
-          __syncwarp();
-          bar_arrive_named(p_ready_id(t), kSoftmaxPlusMma);
-        } else {
-          ok = false;
-          __syncwarp();
-          bar_sync_named(p_ready_id(t), kSoftmaxPlusMma);
-        }
+        for (int i = 0; i < 4; ++i) unpk2(sum2[i], sum8[2 * i], sum8[2 * i + 1]);
+        const float sum = reduce8_sum(sum8);
+        tmem_wait_st();
+        l = l * alpha + sum;
+        m = m_new;
+        tc_fence_before();
+        __syncwarp();
+        bar_arrive_named(p_ready_id(t), kSoftmaxPlusMma);
       }
-      if (!ok || n == 0) continue;
-      // The sub-unit's last PV: completion jt-1 of pv_done (the next PV needs
-      // a P this warpgroup has not written yet).
-      if (!mbar_wait_warp(&pv_done[t], (jt - 1) & 1, err, kDevTimeoutSoftmax, lane)) {
-        ok = false;
-        continue;
+      // After a failed wait: take part in the remaining named barriers in
+      // order, waiting on each (arriving ahead could complete a later phase).
+      for (; j < nkv; ++j) {
+        __syncwarp();
+        if (passed == 0) bar_sync_named(s_free_id(t), kSoftmaxPlusMma);
+        passed = 0;
+        __syncwarp();
+        bar_sync_named(p_ready_id(t), kSoftmaxPlusMma);
       }
-      tc_fence_after();
+      // The last PV: completion nkv-1 of pv_done (nothing later is issued).
+      const int last = nkv - 1;
       uint32_t o0[32], o1[32];
-      tmem_ld32(o_addr, o0);
-      tmem_ld32(o_addr + 32, o1);
-      tmem_wait_ld();
-      // O is in registers: the next sub-unit's first PV may overwrite it
-      // (it is issued after this warpgroup's next P-ready arrival).
-      tc_fence_before();
-      if (su.partial) {
+      bool have_o = false;
+      if (ok && nkv > 0 && mbar_wait_warp(&pv_done[t], last & 1, err, kDevTimeoutSoftmax, lane)) {
+        tc_fence_after();
+        tmem_ld32(o_addr, o0);
+        tmem_ld32(o_addr + 32, o1);
+        tmem_wait_ld();
+        have_o = true;
+      }
+      if (partial) {
         // Partial: unnormalised O, the reference maximum m (log2 units) and
-        // the sum l of this sub-unit's K/V range.
+        // the sum l of this CTA's K/V range.
         const int slot = P.part_prefix[k] + (piece - P.whole[k]);
         const size_t slot_row = static_cast<size_t>(slot) * kPartRows + t * kQ + r;
         float4* po = reinterpret_cast<float4*>(P.part + slot_row * kHD);
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          po[x] = make_float4(__uint_as_float(o0[4 * x]), __uint_as_float(o0[4 * x + 1]),
-                              __uint_as_float(o0[4 * x + 2]), __uint_as_float(o0[4 * x + 3]));
-          po[8 + x] = make_float4(__uint_as_float(o1[4 * x]), __uint_as_float(o1[4 * x + 1]),
-                                  __uint_as_float(o1[4 * x + 2]), __uint_as_float(o1[4 * x + 3]));
+        for (int u = 0; u < 8; ++u) {
+          po[u] = have_o ? make_float4(__uint_as_float(o0[4 * u]), __uint_as_float(o0[4 * u + 1]),
+                                       __uint_as_float(o0[4 * u + 2]), __uint_as_float(o0[4 * u + 3]))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+          po[8 + u] = have_o ? make_float4(__uint_as_float(o1[4 * u]), __uint_as_float(o1[4 * u + 1]),
+                                           __uint_as_float(o1[4 * u + 2]), __uint_as_float(o1[4 * u + 3]))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float* pml = P.part + static_cast<size_t>(P.parts) * kPartRows * kHD + slot_row * 2;
-        *reinterpret_cast<float2*>(pml) = make_float2(m, l);
-      } else {
-        const int row = su.q0 + t * kQ + r;
-        if (row < P.qs1[k]) {
+        pml[0] = have_o ? m : -INFINITY;
+        pml[1] = have_o ? l : 0.f;
+      } else if (have_o) {
+        const int row = q0 + t * kQ + r;
+        if (row < q1) {
           const float inv = 1.f / l;
-          uint4* dst = reinterpret_cast<uint4*>(out + static_cast<size_t>(row) * D + su.h * kHD);
+          uint4* dst = reinterpret_cast<uint4*>(out + static_cast<size_t>(row) * D + h * kHD);
 #pragma unroll
-          for (int x = 0; x < 4; ++x) {
-            dst[x] = make_uint4(pack_bf16x2(__uint_as_float(o0[8 * x]) * inv, __uint_as_float(o0[8 * x + 1]) * inv),
-                                pack_bf16x2(__uint_as_float(o0[8 * x + 2]) * inv, __uint_as_float(o0[8 * x + 3]) * inv),
-                                pack_bf16x2(__uint_as_float(o0[8 * x + 4]) * inv, __uint_as_float(o0[8 * x + 5]) * inv),
-                                pack_bf16x2(__uint_as_float(o0[8 * x + 6]) * inv, __uint_as_float(o0[8 * x + 7]) * inv));
-            dst[4 + x] =
-                make_uint4(pack_bf16x2(__uint_as_float(o1[8 * x]) * inv, __uint_as_float(o1[8 * x + 1]) * inv),
-                           pack_bf16x2(__uint_as_float(o1[8 * x + 2]) * inv, __uint_as_float(o1[8 * x + 3]) * inv),
-                           pack_bf16x2(__uint_as_float(o1[8 * x + 4]) * inv, __uint_as_float(o1[8 * x + 5]) * inv),
-                           pack_bf16x2(__uint_as_float(o1[8 * x + 6]) * inv, __uint_as_float(o1[8 * x + 7]) * inv));
+          for (int u = 0; u < 4; ++u) {
+            dst[u] = make_uint4(pack_bf16x2(__uint_as_float(o0[8 * u]) * inv, __uint_as_float(o0[8 * u + 1]) * inv),
+                                pack_bf16x2(__uint_as_float(o0[8 * u + 2]) * inv, __uint_as_float(o0[8 * u + 3]) * inv),
+                                pack_bf16x2(__uint_as_float(o0[8 * u + 4]) * inv, __uint_as_float(o0[8 * u + 5]) * inv),
+                                pack_bf16x2(__uint_as_float(o0[8 * u + 6]) * inv, __uint_as_float(o0[8 * u + 7]) * inv));
+            dst[4 + u] =
+                make_uint4(pack_bf16x2(__uint_as_float(o1[8 * u]) * inv, __uint_as_float(o1[8 * u + 1]) * inv),
+                           pack_bf16x2(__uint_as_float(o1[8 * u + 2]) * inv, __uint_as_float(o1[8 * u + 3]) * inv),
+                           pack_bf16x2(__uint_as_float(o1[8 * u + 4]) * inv, __uint_as_float(o1[8 * u + 5]) * inv),
+                           pack_bf16x2(__uint_as_float(o1[8 * u + 6]) * inv, __uint_as_float(o1[8 * u + 7]) * inv));
           }
         }
       }
@@ -728,7 +633,7 @@ cudaError_t launch_attention_tc(const CUtensorMap& qkv_map, void* out, int M, in
   attn_tc_kernel<<<P.pieces, kThreads, kSmemBytes, st>>>(qkv_map, static_cast<__nv_bfloat16*>(out), P, err);
   int n = 1;
   const int cuts = P.split_prefix[P.n_slots];
-  if (part && cuts > 0) {
+  if (cuts > 0) {
     attn_combine_kernel<<<cuts * (kPartRows / kCombineRows), 256, 0, st>>>(P, static_cast<__nv_bfloat16*>(out));
     ++n;
   }

@@ -7,6 +7,8 @@
 // keeps each request's tokens to themselves (one segment per request).
 #include <string.h>
 
+#include <algorithm>
+
 #include "model.h"
 
 namespace revo {
@@ -22,13 +24,19 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
-// GEMM row counts share a tile choice within power-of-two buckets (at least
-// 128 rows): a launch of M rows uses the choice timed at the bucket's top.
+// GEMM row counts share a tile choice within buckets: multiples of 128 rows
+// up to 8192 (where the number of 128-row tiles against the SM count decides
+// the choice), powers of two above; a launch of M rows uses the choice timed
+// at its bucket's top.
 int tune_bucket(int M) {
-  int b = 128;
+  if (M <= 8192) return ((std::max(M, 1) + 127) / 128) * 128;
+  int b = 16384;
   while (b < M && b < (1 << 30)) b *= 2;
   return b;
 }
+
+// The next bucket after b (the autotuner's ladder of row counts).
+int next_tune_bucket(int b) { return b < 8192 ? b + 128 : b * 2; }
 
 uint64_t tune_key(int M, int N, int K, bool f8, int epi) {
   return (static_cast<uint64_t>(tune_bucket(M)) << 36) | (static_cast<uint64_t>(N) << 22) |
@@ -253,13 +261,6 @@ WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_
   l.xc = put(static_cast<size_t>(capp) * s.Dd * 4);
   l.attc = put(static_cast<size_t>(capp) * s.Dd * e);
   l.err = put(256);
-  if (precision != REVO_FP32) {
-    // Up to max_seg requests of up to cap / max_seg tokens, at either width.
-    const int seg_len = max_seg > 0 ? (cap + max_seg - 1) / max_seg : cap;
-    const int sms = device_sm_count();
-    l.part = put(std::max(attention_partial_bytes_bound(max_seg, seg_len, s.H, sms),
-                          attention_partial_bytes_bound(max_seg, seg_len, s.Hd, sms)));
-  }
   if (precision == REVO_FP8) {
     l.h8 = put(static_cast<size_t>(cap) * D);
     l.h8s = put(static_cast<size_t>(cap) * 4);
@@ -301,7 +302,6 @@ Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, in
   w->attc = base + l.attc;
   w->err = reinterpret_cast<int*>(base + l.err);
   w->sms = device_sm_count();
-  if (precision != REVO_FP32) w->attn_part = reinterpret_cast<float*>(base + l.part);
   if (precision == REVO_FP8) {
     w->h8 = base + l.h8;
     w->h8_scale = reinterpret_cast<float*>(base + l.h8s);
@@ -325,7 +325,7 @@ struct Fwd {
   int sms;
   bool tc;
   size_t e;  // activation element size
-  int extra_launches = 0;  // kernels beyond one per attention (the combine of split units)
+  int extra_launches = 0;  // kernels beyond one per attention (none: the forward cuts no unit)
 
   // `amap` / `cmap`: the A operand and output tensor maps (tensor-core path).
   cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M,
@@ -450,7 +450,7 @@ struct Fwd {
     if (tc)
     {
       int nl = 1;
-      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st, ws->attn_part, ws->sms, &nl);
+      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st, nullptr, ws->sms, &nl);
       extra_launches += nl - 1;
     }
     else
@@ -484,7 +484,7 @@ struct Fwd {
     }
     if (tc) {
       int nl = 1;
-      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, q, ws->err, st, ws->attn_part, ws->sms, &nl);
+      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, q, ws->err, st, nullptr, ws->sms, &nl);
       extra_launches += nl - 1;
     } else {
       e = launch_attention_simt(static_cast<const float*>(ws->qkv), static_cast<float*>(ws->att), M, d, heads, seg,
@@ -701,7 +701,7 @@ cudaError_t net_autotune(Net* net, Workspace* ws, int max_tokens, int max_patche
   const bool f8f_d = net->precision == REVO_FP8 && (net->fp8_mask & 8);
   // Rows of every token: the tubelet embedding, the blocks (all alike within
   // the encoder and within the decoder) and the encoder->decoder Linear.
-  for (int b = 128; e == cudaSuccess; b *= 2) {
+  for (int b = 128; e == cudaSuccess; b = next_tune_bucket(b)) {
     const int M = std::min(b, max_tokens);
     if (!encode_maps(s, ws, M)) return cudaErrorInvalidValue;
     tune(&ws->m_tok, net->patch, kEpiF32, M, &ws->o_x_enc, false);
@@ -722,7 +722,7 @@ cudaError_t net_autotune(Net* net, Workspace* ws, int max_tokens, int max_patche
   }
   // The final slot's rows: the pixel head (the last block's other shapes are
   // the decoder's, timed above for these row counts).
-  for (int b = 128; e == cudaSuccess; b *= 2) {
+  for (int b = 128; e == cudaSuccess; b = next_tune_bucket(b)) {
     const int M = std::min(b, max_patches);
     if (!encode_compact_maps(s, ws, M)) return cudaErrorInvalidValue;
     tune(&ws->c_h, net->head, kEpiF32, M, &ws->c_o_head, false);

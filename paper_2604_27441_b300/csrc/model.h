@@ -97,7 +97,6 @@ struct Workspace {
   void* attc = nullptr;   // [cap_patches][D'] attention output
   uint8_t* h8 = nullptr;  // [cap][max width] E4M3 LayerNorm output (FP8 precision)
   float* h8_scale = nullptr;  // [cap] its per-token scales
-  float* attn_part = nullptr;  // partial results of the tensor-core attention's split units
   int sms = 0;
   int* err = nullptr;    // device error word of the tensor-core kernels
   size_t bytes = 0;
@@ -117,7 +116,7 @@ Net* net_create(const NetShape& s, int precision, const float* host_weights, std
 void net_destroy(Net* n);
 size_t net_bytes(const NetShape& s, int precision);
 
-// max_segments: requests per batch (sizes the attention's partial results).
+// max_segments: requests per batch.
 size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments);
 Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments,
                             std::string* err);
@@ -149,11 +148,10 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
                         int* launches, const JobArgs* dev_args = nullptr);
 
 // GEMM tile autotuning (tensor-core path), done once at create: every GEMM
-// shape of the network is timed for row counts 128, 256, ... up to max_tokens
-// (the head up to max_patches) on `ws` and `st`, skipping shapes that already
-// have a choice (from an autotune cache file).  A forward then only looks the
-// choices up (tune_bucket: a launch of M rows uses the choice of the smallest
-// power of two >= M, at least 128).
+// shape of the network is timed for the row counts of tune_bucket's ladder up
+// to max_tokens (the head up to max_patches) on `ws` and `st`, skipping shapes
+// that already have a choice (from an autotune cache file).  A forward then
+// only looks the choices up.
 cudaError_t net_autotune(Net* net, Workspace* ws, int max_tokens, int max_patches, cudaStream_t st, int num_sms);
 int tune_bucket(int M);
 uint64_t tune_key(int M, int N, int K, bool f8, int epi);

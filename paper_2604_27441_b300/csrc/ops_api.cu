@@ -436,7 +436,7 @@ revo_status revo_op_attention(revo_precision precision, const void* qkv, void* o
   int* err = op_error_word();
   if (!err) return REVO_ECUDA;
   float* part = nullptr;
-  if (!(flags & REVO_ATTN_WHOLE_UNITS)) {
+  if (flags & REVO_ATTN_SPLIT_TAIL) {
     const size_t need = attention_partial_bytes(M, heads, seg, device_sm_count());
     if (!(part = op_attention_partial(need))) {
       set_last_error("revo_op_attention: partial-result buffer allocation failed");

@@ -313,13 +313,13 @@ def check_attention_bf16(got, qkv64, heads, seg, cache_key=None):
             assert rel_rms(got[a:b], ref[a:b]) < 4e-3, (a, b, rel_rms(got[a:b], ref[a:b]))
 
 
-@pytest.mark.parametrize("whole_units", [False, True])
+@pytest.mark.parametrize("split_tail", [False, True])
 @pytest.mark.parametrize("seg,heads", ATT_CASES + [((0, 900), 12), ((0, 10800), 2), ((0, 129, 385, 3600), 12),
                                                    ((0, 4320, 5600, 5856), 4)])
-def test_attention_bf16_tcgen05(seg, heads, whole_units):
-    """By default the units of a segment's last, partly filled wave are cut
-    into key ranges merged by a second kernel; whole_units runs one CTA per
-    (head, 256 queries) unit.  The cases cover every unit cut (N = 900, 48
+def test_attention_bf16_tcgen05(seg, heads, split_tail):
+    """One CTA per (head, 256 queries) unit; with split_tail the units of a
+    segment's last, partly filled wave are cut into key ranges merged by a
+    second kernel.  The cases cover every unit cut (N = 900, 48
     units), whole waves plus a cut tail (N = 3600: 148 whole + 32 cut in 4),
     nothing cut (N = 10800 with 2 heads), units whose second query tile is
     empty (lengths 129, 256 + 16, ...) and segments of mixed lengths in one
@@ -327,7 +327,7 @@ def test_attention_bf16_tcgen05(seg, heads, whole_units):
     M, D = seg[-1], 64 * heads
     qkv = bf16(synth.normal(M + heads, (M, 3 * D)))
     out = torch.zeros((M, D), dtype=torch.bfloat16, device="cuda")
-    R.op_attention(R.BF16, qkv.cuda(), out, M, D, heads, seg, whole_units=whole_units)
+    R.op_attention(R.BF16, qkv.cuda(), out, M, D, heads, seg, split_tail=split_tail)
     torch.cuda.synchronize()
     check_attention_bf16(f64(out), f64(qkv), heads, seg, cache_key=(tuple(seg), heads))
     assert R.take_device_error() == 0
@@ -356,19 +356,21 @@ def test_attention_bf16_query_rows(seg, queries, heads):
     assert R.take_device_error() == 0
 
 
-def test_attention_segment_alone_equals_in_a_batch():
-    """A segment's cut depends on its length only: its output inside a launch
-    with other segments is bit for bit its output alone."""
+@pytest.mark.parametrize("split_tail", [False, True])
+def test_attention_segment_alone_equals_in_a_batch(split_tail):
+    """A segment's work split depends on its length only: its output inside a
+    launch with other segments is bit for bit its output alone (with and
+    without the tail cut)."""
     heads, D = 12, 768
     lens = (3600, 900, 10800, 4320)
     seg = np.concatenate([[0], np.cumsum(lens)]).tolist()
     M = seg[-1]
     qkv = bf16(synth.normal(77, (M, 3 * D))).cuda()
     out = torch.zeros((M, D), dtype=torch.bfloat16, device="cuda")
-    R.op_attention(R.BF16, qkv, out, M, D, heads, seg)
+    R.op_attention(R.BF16, qkv, out, M, D, heads, seg, split_tail=split_tail)
     for a, b in zip(seg[:-1], seg[1:]):
         alone = torch.zeros((b - a, D), dtype=torch.bfloat16, device="cuda")
-        R.op_attention(R.BF16, qkv[a:b].contiguous(), alone, b - a, D, heads, [0, b - a])
+        R.op_attention(R.BF16, qkv[a:b].contiguous(), alone, b - a, D, heads, [0, b - a], split_tail=split_tail)
         torch.cuda.synchronize()
         assert torch.equal(alone, out[a:b]), (a, b)
     assert R.take_device_error() == 0
