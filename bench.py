@@ -945,6 +945,23 @@ def run_profile_kernel(args) -> None:
         tile = 256 | (R.TILE_PAIR if args.profile_kernel == "fc1_fp8_pair" else 0)
         launch = lambda: R.op_linear_fp8(2, a, sa, w, sw, b, out, N, 4 * D, D, tile, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
+    elif args.profile_kernel in ("fc1_tick", "fc2_tick"):  # the tick's RGB rows (M = 70200), CTA-pair 256 tiles
+        Mt = sum(tick_segments(True))
+        if args.profile_kernel == "fc1_tick":
+            a = torch.randn((Mt, D), device="cuda").to(torch.bfloat16)
+            w = (torch.randn((4 * D, D), device="cuda") / 28).to(torch.bfloat16)
+            b = torch.zeros(4 * D, device="cuda")
+            out = torch.empty((Mt, 4 * D), dtype=torch.bfloat16, device="cuda")
+            launch = lambda: R.op_linear(R.BF16, 2, a, w, b, out, Mt, 4 * D, D, 256 | R.TILE_PAIR,  # noqa: E731
+                                         stream=stream)
+        else:
+            a = torch.randn((Mt, 4 * D), device="cuda").to(torch.bfloat16)
+            w = (torch.randn((D, 4 * D), device="cuda") / 56).to(torch.bfloat16)
+            b = torch.zeros(D, device="cuda")
+            out = torch.zeros((Mt, D), device="cuda")
+            launch = lambda: R.op_linear(R.BF16, 3, a, w, b, out, Mt, D, 4 * D, 256 | R.TILE_PAIR,  # noqa: E731
+                                         stream=stream)
+        flops = 2 * Mt * D * 4 * D
     elif args.profile_kernel in ("fc2", "fc2_pair"):  # fc2 of an encoder block: residual f32 += [N, 3072] x [768, 3072]^T
         a = torch.randn((N, 4 * D), device="cuda").to(torch.bfloat16)
         w = (torch.randn((D, 4 * D), device="cuda") / 56).to(torch.bfloat16)
@@ -979,7 +996,8 @@ def run_profile_kernel(args) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "attention_tick", "fc1", "fc1_pair",
-                                                 "fc1_fp8", "fc1_fp8_pair", "fc2", "fc2_pair", "assemble", "blend"],
+                                                 "fc1_fp8", "fc1_fp8_pair", "fc2", "fc2_pair", "fc1_tick", "fc2_tick",
+                                                 "assemble", "blend"],
                     default=None, help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
