@@ -495,7 +495,8 @@ REVO_API revo_status revo_op_attention(revo_precision precision, const void* qkv
  * x[(s*Hp + r)*Wp + c][:] += the sinusoidal embedding of (taus[s], r, c), each
  * part D/3 wide, half sines half cosines at frequencies 10000^(-2i/(D/3))
  * (Section 3.4.1: the embedding encodes the temporal distance between the
- * references and the target).  x float32 device; taus host, `slots` <= 8.
+ * references and the target).  x float32 device; taus host, `slots` <= 8;
+ * D a multiple of 192, at most 1024.
  */
 REVO_API revo_status revo_op_add_position(float* x, int slots, int grid_h, int grid_w, int D, const int* taus,
                                  void* stream);

@@ -5,6 +5,8 @@
 #include <cuda_fp8.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "revo_internal.h"
 
@@ -192,33 +194,80 @@ struct PeArgs {
   int Hp, Wp, D, part;
 };
 
-// One thread per (token, part, i < part / 2): sin(pos w_i) goes to column
-// part * which + i and cos(pos w_i) to column part * which + part / 2 + i, both
-// from one sincosf.  The frequencies are staged in shared memory (indexing the
-// parameter array per lane would serialise the warp's constant loads).
-__global__ void add_pe_kernel(float* __restrict__ x, int rows, const __grid_constant__ PeArgs a) {
+// The embedding values of one part at integer position `pos`: column i <
+// part / 2 holds sin(pos w_i), column part / 2 + i holds cos(pos w_i), both from
+// one sincosf of the float32 product pos * w_i.
+REVO_DEVI void pe_part(float pos, const float* om, int half, float* out, int tid, int nthreads) {
+  for (int i = tid; i < half; i += nthreads) {
+    float sv, cv;
+    sincosf(pos * om[i], &sv, &cv);
+    out[i] = sv;
+    out[half + i] = cv;
+  }
+}
+
+// Table of the column part for positions 0 .. rows-1: tab[c][0 .. part).
+__global__ void pe_table_kernel(float* __restrict__ tab, int rows, const __grid_constant__ PeArgs a) {
   __shared__ float om[128];
   const int half = a.part / 2;
   for (int i = threadIdx.x; i < half; i += blockDim.x) om[i] = a.omega[i];
   __syncthreads();
-  const int per_row = 3 * half;
-  const int idx = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
-  if (idx >= rows * per_row) return;
-  const int n = idx / per_row;
-  const int r = idx - n * per_row;
-  const int which = r / half;
-  const int i = r - which * half;
-  const int hw = a.Hp * a.Wp;
-  const int s = n / hw;
-  const int rem = n - s * hw;
+  pe_part(static_cast<float>(blockIdx.x), om, half, tab + static_cast<size_t>(blockIdx.x) * a.part, threadIdx.x,
+          blockDim.x);
+}
+
+// One CTA per (slot s, patch row r): the temporal part of slot s and the row
+// part of r are computed once into shared memory, the column part comes from
+// `ctab` (pe_table_kernel's table, or computed per element without one); then
+// each of the row's Wp token rows of x gets the three parts added with 16-byte
+// accesses.  Every value is the same float32 sincosf of pos * w_i as a per
+// element evaluation, so the result does not depend on the table.
+__global__ void add_pe_kernel(float* __restrict__ x, const __grid_constant__ PeArgs a,
+                              const float* __restrict__ ctab) {
+  __shared__ float om[128];
+  __shared__ __align__(16) float tp[1024 / 3 + 4];
+  __shared__ __align__(16) float rp[1024 / 3 + 4];
+  const int half = a.part / 2;
+  for (int i = threadIdx.x; i < half; i += blockDim.x) om[i] = a.omega[i];
+  __syncthreads();
+  const int s = static_cast<int>(blockIdx.x) / a.Hp;
+  const int r = static_cast<int>(blockIdx.x) % a.Hp;
   const int tau = a.taus_dev ? __ldg(a.taus_dev + s) : a.taus[s];
-  const float pos = which == 0 ? static_cast<float>(tau) : which == 1 ? static_cast<float>(rem / a.Wp)
-                                                                       : static_cast<float>(rem % a.Wp);
-  float sv, cv;
-  sincosf(pos * om[i], &sv, &cv);
-  float* row = x + static_cast<size_t>(n) * a.D + which * a.part;
-  row[i] += sv;
-  row[half + i] += cv;
+  pe_part(static_cast<float>(tau), om, half, tp, threadIdx.x, blockDim.x);
+  pe_part(static_cast<float>(r), om, half, rp, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int nv = a.D / 4;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    const int col = 4 * j;
+    const int which = col / a.part;  // a part is a multiple of 64 columns: a vector stays in one part
+    const int q = col - which * a.part;
+    for (int c = 0; c < a.Wp; ++c) {
+      float4 v;
+      if (which == 0) {
+        v = *reinterpret_cast<const float4*>(tp + q);
+      } else if (which == 1) {
+        v = *reinterpret_cast<const float4*>(rp + q);
+      } else if (ctab) {
+        v = __ldg(reinterpret_cast<const float4*>(ctab + static_cast<size_t>(c) * a.part + q));
+      } else {
+        float e[4];
+        for (int u = 0; u < 4; ++u) {
+          const int i = (q + u) % half;
+          float sv, cv;
+          sincosf(static_cast<float>(c) * om[i], &sv, &cv);
+          e[u] = q + u < half ? sv : cv;
+        }
+        v = make_float4(e[0], e[1], e[2], e[3]);
+      }
+      float4* p = reinterpret_cast<float4*>(x + (static_cast<size_t>(s * a.Hp + r) * a.Wp + c) * a.D) + j;
+      float4 y = *p;
+      y.x += v.x;
+      y.y += v.y;
+      y.z += v.z;
+      y.w += v.w;
+      *p = y;
+    }
+  }
 }
 
 // ------------------------------------------------------------ LayerNorm --
@@ -639,23 +688,39 @@ cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st, const Assemb
   return cudaGetLastError();
 }
 
+namespace {
+bool pe_args(PeArgs* a, int D) {
+  a->D = D;
+  a->part = D / 3;
+  if (D % 192 != 0 || a->part / 2 > 128) return false;
+  for (int i = 0; i < a->part / 2; ++i) a->omega[i] = static_cast<float>(pow(10000.0, -2.0 * i / a->part));
+  return true;
+}
+}  // namespace
+
+cudaError_t launch_pe_table(float* tab, int rows, int D, cudaStream_t st) {
+  PeArgs a{};
+  if (!pe_args(&a, D) || rows < 0) return cudaErrorInvalidValue;
+  if (rows == 0) return cudaSuccess;
+  pe_table_kernel<<<rows, 128, 0, st>>>(tab, rows, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, int D, cudaStream_t st,
-                          const int* taus_dev) {
+                          const int* taus_dev, const float* ctab, int ctab_rows) {
   PeArgs a{};
   a.taus_dev = taus_dev;
   a.Hp = Hp;
   a.Wp = Wp;
-  a.D = D;
-  a.part = D / 3;
-  if (D % 6 != 0 || a.part / 2 > 128 || slots > 8 || slots < 0) return cudaErrorInvalidValue;
-  for (int i = 0; i < a.part / 2; ++i) a.omega[i] = static_cast<float>(pow(10000.0, -2.0 * i / a.part));
+  if (!pe_args(&a, D) || slots > 8 || slots < 0 || Hp < 0 || Wp < 0) return cudaErrorInvalidValue;
   if (!taus_dev)
     for (int s = 0; s < slots; ++s) a.taus[s] = taus[s];
-  const long long rows = static_cast<long long>(slots) * Hp * Wp;
-  const long long threads = rows * (D / 2);
-  if (threads == 0) return cudaSuccess;
-  if (threads > 0x7FFFFFFFll) return cudaErrorInvalidValue;
-  add_pe_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(x, static_cast<int>(rows), a);
+  if (ctab && Wp > ctab_rows) ctab = nullptr;
+  const long long blocks = static_cast<long long>(slots) * Hp;
+  if (blocks == 0 || Wp == 0) return cudaSuccess;
+  if (blocks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+  const int threads = std::min(256, ((D / 4 + 31) / 32) * 32);
+  add_pe_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(x, a, ctab);
   return cudaGetLastError();
 }
 

@@ -239,9 +239,9 @@ void net_destroy(Net* n) {
 
 namespace {
 struct WsLayout {
-  size_t tok, x, h, qkv, att, mlp, head, xc, attc, err, h8, h8s, part, total;
+  size_t tok, x, h, qkv, att, mlp, head, xc, attc, pe_enc, pe_dec, err, h8, h8s, part, total;
 };
-WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_seg) {
+WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_seg, int max_wp) {
   const size_t e = precision != REVO_FP32 ? 2 : 4;
   const size_t D = s.D > s.Dd ? s.D : s.Dd;
   WsLayout l{};
@@ -260,6 +260,8 @@ WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_
   l.head = put(static_cast<size_t>(capp) * s.head_dim_out() * 4);
   l.xc = put(static_cast<size_t>(capp) * s.Dd * 4);
   l.attc = put(static_cast<size_t>(capp) * s.Dd * e);
+  l.pe_enc = put(static_cast<size_t>(max_wp) * (s.D / 3) * 4);
+  l.pe_dec = put(static_cast<size_t>(max_wp) * (s.Dd / 3) * 4);
   l.err = put(256);
   if (precision == REVO_FP8) {
     l.h8 = put(static_cast<size_t>(cap) * D);
@@ -270,13 +272,14 @@ WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_
 }
 }  // namespace
 
-size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments) {
-  return ws_layout(s, precision, cap_tokens, cap_patches, max_segments).total;
+size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments,
+                       int max_wp) {
+  return ws_layout(s, precision, cap_tokens, cap_patches, max_segments, max_wp).total;
 }
 
 Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments,
-                            std::string* err) {
-  const WsLayout l = ws_layout(s, precision, cap_tokens, cap_patches, max_segments);
+                            int max_wp, std::string* err) {
+  const WsLayout l = ws_layout(s, precision, cap_tokens, cap_patches, max_segments, max_wp);
   uint8_t* base = nullptr;
   if (cudaMalloc(&base, l.total) != cudaSuccess) {
     *err = "workspace allocation failed";
@@ -300,6 +303,16 @@ Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, in
   w->head = reinterpret_cast<float*>(base + l.head);
   w->xc = reinterpret_cast<float*>(base + l.xc);
   w->attc = base + l.attc;
+  w->pe_enc = reinterpret_cast<float*>(base + l.pe_enc);
+  w->pe_dec = reinterpret_cast<float*>(base + l.pe_dec);
+  w->pe_rows = max_wp;
+  if (launch_pe_table(w->pe_enc, max_wp, s.D, 0) != cudaSuccess ||
+      launch_pe_table(w->pe_dec, max_wp, s.Dd, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(base);
+    delete w;
+    *err = "position embedding tables failed";
+    return nullptr;
+  }
   w->err = reinterpret_cast<int*>(base + l.err);
   w->sms = device_sm_count();
   if (precision == REVO_FP8) {
@@ -634,7 +647,8 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
   if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32, ws->x, s.D, M, &ws->o_x_enc)) != cudaSuccess) return e;
   for (int i = 0; i < n; ++i)
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.D, jobs[i].H / s.p, jobs[i].W / s.p,
-                           s.slots(), args[i].taus, s.D, st, dev_args ? dev_args[i].taus : nullptr)) != cudaSuccess)
+                           s.slots(), args[i].taus, s.D, st, dev_args ? dev_args[i].taus : nullptr, ws->pe_enc,
+                           ws->pe_rows)) != cudaSuccess)
       return e;
 
   const Fwd::Maps enc_maps{&ws->m_h_enc, &ws->m_att_enc, &ws->m_mlp_enc, &ws->m_qkv_enc,
@@ -648,7 +662,8 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
     return e;
   for (int i = 0; i < n; ++i)
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.Dd, jobs[i].H / s.p, jobs[i].W / s.p,
-                           s.slots(), args[i].taus, s.Dd, st, dev_args ? dev_args[i].taus : nullptr)) != cudaSuccess)
+                           s.slots(), args[i].taus, s.Dd, st, dev_args ? dev_args[i].taus : nullptr, ws->pe_dec,
+                           ws->pe_rows)) != cudaSuccess)
       return e;
   // The final slot's rows of each request, stacked in request order: the rows
   // the last decoder block, the final LN and the pixel head work on (the head

@@ -74,6 +74,26 @@ float* op_attention_partial(size_t bytes) {
   return bufs[dev];
 }
 
+// The position embedding's column-part table of the step-level entry point,
+// one per device and width (built on first use).
+float* op_pe_table(int D, int rows) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || D % 192 || D > 1024) return nullptr;
+  static float* tabs[64][6] = {};
+  const int w = D / 192 - 1;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!tabs[dev][w]) {
+    float* p = nullptr;
+    if (cudaMalloc(&p, static_cast<size_t>(rows) * (D / 3) * sizeof(float)) != cudaSuccess) return nullptr;
+    if (launch_pe_table(p, rows, D, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+      cudaFree(p);
+      return nullptr;
+    }
+    tabs[dev][w] = p;
+  }
+  return tabs[dev][w];
+}
+
 }  // namespace revo
 
 using namespace revo;
@@ -448,11 +468,24 @@ revo_status revo_op_attention(revo_precision precision, const void* qkv, void* o
 }
 
 revo_status revo_op_add_position(float* x, int slots, int grid_h, int grid_w, int D, const int* taus, void* stream) {
-  if (!x || !taus || slots < 0 || slots > 8 || grid_h < 0 || grid_w < 0 || D % 6) {
+  if (!x || !taus || slots < 0 || slots > 8 || grid_h < 0 || grid_w < 0 || D % 192 || D > 1024) {
     set_last_error("revo_op_add_position: bad argument");
     return REVO_EINVAL;
   }
-  return cuda_status(launch_add_pe(x, grid_h, grid_w, slots, taus, D, static_cast<cudaStream_t>(stream)),
+  // Up to 256 patch columns the column part comes from a table (as in the
+  // recovery forward); wider grids compute it per element (the same values).
+  constexpr int kTabRows = 256;
+  const float* tab = nullptr;
+  if (grid_w <= kTabRows) {
+    float* t = op_pe_table(D, kTabRows);
+    if (!t) {
+      set_last_error("revo_op_add_position: table allocation failed");
+      return REVO_ENOMEM;
+    }
+    tab = t;
+  }
+  return cuda_status(launch_add_pe(x, grid_h, grid_w, slots, taus, D, static_cast<cudaStream_t>(stream), nullptr, tab,
+                                   kTabRows),
                      "revo_op_add_position");
 }
 

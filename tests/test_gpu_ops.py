@@ -508,8 +508,11 @@ def test_depth_stats(case):
         np.testing.assert_allclose(got, [mu, sg], rtol=2e-6, atol=0)
 
 
-@pytest.mark.parametrize("D,hp,wp,taus", [(768, 15, 20, (5, 3, 1)), (384, 45, 80, (7, 5, 3)), (192, 2, 3, (1,))])
+@pytest.mark.parametrize("D,hp,wp,taus", [(768, 15, 20, (5, 3, 1)), (384, 45, 80, (7, 5, 3)), (192, 2, 3, (1,)),
+                                         (192, 2, 300, (4, 2))])
 def test_position_embedding(D, hp, wp, taus):
+    """Up to 256 patch columns the column part comes from a table, wider grids
+    compute it per element; both against the oracle."""
     S = len(taus)
     x = torch.zeros((S * hp * wp, D), dtype=torch.float32, device="cuda")
     R.op_add_position(x, S, hp, wp, D, list(taus))
