@@ -473,10 +473,11 @@ def _with_flag(R, req, extra):
     return c
 
 
-def tick_context(R, precision, stream, graphs=True, lanes=1):
+def tick_context(R, precision, stream, graphs=True, lanes=1, serial=0):
     import synth
     cfg = R.config(**VITB, precision=precision, max_height=720, max_width=1280, max_streams=16, max_batch=16,
-                   lanes=lanes, use_graphs=1 if graphs else 0, autotune=1, autotune_cache=TILE_CACHE)
+                   lanes=lanes, use_graphs=1 if graphs else 0, autotune=1, autotune_cache=TILE_CACHE,
+                   serial_models=serial)
     return R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
                      synth.flatten(synth.weights(synth.DEPTH, seed=1)), stream=stream)
 
@@ -732,7 +733,7 @@ def run_ours(args) -> None:
 
     stream = torch.cuda.Stream()
     precision = PRECISIONS[args.precision](R)
-    ctx = tick_context(R, precision, stream, graphs=not args.no_graphs)
+    ctx = tick_context(R, precision, stream, graphs=not args.no_graphs, serial=int(args.serial_models))
     streams = tick_streams(R, torch, ctx, True, base_seed=4000 + 100 * rank)
     for _ in range(2):  # autotuning and graph capture of the batch's size pattern
         tick_once(R, ctx, streams)
@@ -1007,6 +1008,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the FP64 oracle (quality and cpu_baseline)")
     ap.add_argument("--no-graphs", action="store_true", help="plain kernel launches instead of graph replay")
     ap.add_argument("--quick", action="store_true", help="the tick and its e2e only")
+    ap.add_argument("--serial-models", action="store_true",
+                    help="the tick's RGB and depth forwards one after the other instead of side by side")
     ap.add_argument("--workload", choices=["mixed16", "640x480", "serving", "kt"], default="mixed16",
                     help="mixed16: the headline line; 640x480: batch-1 frames only; serving: the real-time loop "
                          "only; kt: the k/T latency sweep")

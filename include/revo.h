@@ -124,6 +124,11 @@ typedef struct {
    * shape it lacks, and writes the file back; NULL = time them all at create.
    * Requests never wait for tuning. */
   const char* autotune_cache;
+  /* 1 = a batch's RGB forward runs before its depth forward instead of beside
+   * it on a second CUDA stream (the results are the same).  Two large
+   * forwards side by side split the SMs between persistent GEMM kernels and
+   * their caches; one after the other each has the GPU to itself. */
+  int serial_models;
 } revo_config;
 
 typedef struct revo_ctx revo_ctx;

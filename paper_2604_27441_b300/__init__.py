@@ -43,7 +43,8 @@ class Config(C.Structure):
                 ("rgb_weights", C.c_void_p), ("rgb_weights_count", C.c_size_t),
                 ("depth_weights", C.c_void_p), ("depth_weights_count", C.c_size_t),
                 ("rgb_weights_path", C.c_char_p), ("depth_weights_path", C.c_char_p),
-                ("seed", C.c_uint64), ("random_init", C.c_int), ("autotune_cache", C.c_char_p)]
+                ("seed", C.c_uint64), ("random_init", C.c_int), ("autotune_cache", C.c_char_p),
+                ("serial_models", C.c_int)]
 
 
 class Plane(C.Structure):

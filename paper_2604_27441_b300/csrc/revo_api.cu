@@ -357,6 +357,11 @@ revo_status launch_batch(revo_ctx* c, int count) {
     b.launches += nl;
     if (e != cudaSuccess) st = cuda_status(e, "forward launch");
     cudaMemcpyAsync(b.err_host + m, L.ws[m]->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (m == 0 && c->cfg.serial_models && !jobs[1].empty()) {
+      // The depth forward starts once the RGB forward has finished.
+      cudaEventRecord(L.fork, main);
+      cudaStreamWaitEvent(L.st[1], L.fork, 0);
+    }
   }
   cudaEventRecord(L.join, L.st[1]);
   cudaStreamWaitEvent(main, L.join, 0);

@@ -468,3 +468,27 @@ def test_autotune_cache_file_round_trip(tmp_path):
     for o in outs[1:]:
         for x, y in zip(outs[0], o):
             np.testing.assert_array_equal(x, y)
+
+
+def test_serial_models_equal_concurrent_models():
+    """serial_models runs a batch's RGB forward before its depth forward
+    instead of beside it: the outputs are the same bit for bit."""
+    reqs = [synth.make_request(1030 + i, "320x240") for i in range(3)]
+    got = {}
+    for serial in (0, 1):
+        cfg = R.config(**VITB, precision=R.BF16, max_height=240, max_width=320, max_streams=3, max_batch=3,
+                       serial_models=serial)
+        with R.Context(cfg, synth.flatten(weights(VITB, 3)), synth.flatten(weights(VITB, 1))) as ctx:
+            keep = [push_refs(ctx, sid, rgb, dep) for sid, (rgb, dep) in enumerate(reqs)]
+            outs = [Outputs(rgb, dep) for rgb, dep in reqs]
+            tickets = []
+            for sid, o in enumerate(outs):
+                r = o.request(sid, *reqs[sid])
+                r.flags |= R.HOLD if sid < 2 else 0
+                tickets.append(ctx.submit(r))
+            assert all(ctx.poll(t).batch_size == 3 for t in tickets)
+            got[serial] = [o.numpy() for o in outs]
+            del keep
+    for a, b in zip(got[0], got[1]):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
