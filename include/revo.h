@@ -514,6 +514,37 @@ REVO_API revo_status revo_op_add_position(float* x, int slots, int grid_h, int g
  * 0, 65535).  out = lost ? code : decoded, bit for bit for received pixels;
  * values (optional, dense float32 [H][W][C]) gets v at every pixel.
  */
+/*
+ * Batched forms (p = 16): every job of the batch in one launch, as the
+ * recovery forward runs them.  The jobs are copied (on `stream`) into a
+ * per-device argument table unless it already holds the same jobs; calls on
+ * one device must run in stream order.  Results are bit for bit those of the
+ * single-job calls.  n <= 64.
+ */
+typedef struct {
+  int height, width;
+  const void* frames[8];   /* device: the k references oldest first, then the current frame */
+  size_t pitch_bytes;
+  const float* mu_sigma;   /* depth: device (mu, sigma); RGB: NULL */
+  void* out;               /* device: [S*Hp*Wp][T*C*p*p] */
+} revo_assemble_job;
+REVO_API revo_status revo_op_assemble_batch(int channels, int k, int T, int n, const revo_assemble_job* jobs,
+                                            int out_bf16, void* stream);
+
+typedef struct {
+  int height, width;
+  const float* head;       /* device [Hp*Wp][C*p*p] */
+  const void* decoded;     /* device frame */
+  size_t pitch_bytes;
+  const uint32_t* mask;    /* device */
+  size_t mask_pitch_words;
+  const float* mu_sigma;   /* depth: device (mu, sigma) */
+  void* out;               /* device frame */
+  size_t out_pitch;
+  float* values;           /* optional */
+} revo_blend_job;
+REVO_API revo_status revo_op_blend_batch(int channels, int n, const revo_blend_job* jobs, void* stream);
+
 REVO_API revo_status revo_op_blend(int channels, int p, int height, int width, const float* head,
                           const void* decoded, size_t pitch_bytes, const uint32_t* mask,
                           size_t mask_pitch_words, const float* mu_sigma, void* out,

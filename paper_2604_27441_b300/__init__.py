@@ -62,6 +62,17 @@ class Request(C.Structure):
                 ("rgb_values", C.c_void_p), ("depth_values", C.c_void_p)]
 
 
+class AssembleJob(C.Structure):
+    _fields_ = [("height", C.c_int), ("width", C.c_int), ("frames", C.c_void_p * 8), ("pitch_bytes", C.c_size_t),
+                ("mu_sigma", C.c_void_p), ("out", C.c_void_p)]
+
+
+class BlendJob(C.Structure):
+    _fields_ = [("height", C.c_int), ("width", C.c_int), ("head", C.c_void_p), ("decoded", C.c_void_p),
+                ("pitch_bytes", C.c_size_t), ("mask", C.c_void_p), ("mask_pitch_words", C.c_size_t),
+                ("mu_sigma", C.c_void_p), ("out", C.c_void_p), ("out_pitch", C.c_size_t), ("values", C.c_void_p)]
+
+
 class Intrinsics(C.Structure):
     _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float)]
 
@@ -111,6 +122,8 @@ _SIGS = {
                                 C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
                                 C.c_void_p]),
     "revo_op_take_device_error": (C.c_int, []),
+    "revo_op_assemble_batch": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    "revo_op_blend_batch": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "revo_init_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_void_p, C.c_size_t]),
     "revo_op_wait_selftest": (C.c_int, [C.c_longlong, C.c_void_p]),
     "revo_op_quantize_rows_e4m3": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -306,6 +319,32 @@ def op_blend(channels, p, height, width, head, decoded, pitch_bytes, mask, mask_
     return _check(lib().revo_op_blend(channels, p, height, width, ptr(head), ptr(decoded), pitch_bytes, ptr(mask),
                                       mask_pitch_words, ptr(mu_sigma), ptr(out), out_pitch, ptr(values),
                                       _stream(stream)), "revo_op_blend")
+
+
+def op_assemble_batch(channels, k, T, jobs, out_bf16, stream=None):
+    """jobs: list of dicts with height, width, frames (k refs + current), pitch_bytes, mu_sigma, out."""
+    arr = (AssembleJob * len(jobs))()
+    for a, j in zip(arr, jobs):
+        a.height, a.width, a.pitch_bytes = j["height"], j["width"], j["pitch_bytes"]
+        for f, fr in enumerate(j["frames"]):
+            a.frames[f] = ptr(fr)
+        a.mu_sigma = ptr(j.get("mu_sigma"))
+        a.out = ptr(j["out"])
+    return _check(lib().revo_op_assemble_batch(channels, k, T, len(jobs), C.cast(arr, C.c_void_p), out_bf16,
+                                               _stream(stream)), "revo_op_assemble_batch")
+
+
+def op_blend_batch(channels, jobs, stream=None):
+    """jobs: list of dicts with height, width, head, decoded, pitch_bytes, mask, mask_pitch_words,
+    mu_sigma, out, out_pitch, values."""
+    arr = (BlendJob * len(jobs))()
+    for a, j in zip(arr, jobs):
+        a.height, a.width, a.pitch_bytes = j["height"], j["width"], j["pitch_bytes"]
+        a.head, a.decoded, a.mask = ptr(j["head"]), ptr(j["decoded"]), ptr(j["mask"])
+        a.mask_pitch_words, a.mu_sigma = j["mask_pitch_words"], ptr(j.get("mu_sigma"))
+        a.out, a.out_pitch, a.values = ptr(j["out"]), j["out_pitch"], ptr(j.get("values"))
+    return _check(lib().revo_op_blend_batch(channels, len(jobs), C.cast(arr, C.c_void_p), _stream(stream)),
+                  "revo_op_blend_batch")
 
 
 def take_device_error() -> int:

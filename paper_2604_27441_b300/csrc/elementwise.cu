@@ -185,6 +185,11 @@ __global__ void __launch_bounds__(kAsmThreads) assemble16_kernel(const __grid_co
 __global__ void __launch_bounds__(kAsmThreads) assemble16_kernel_dev(const AssembleArgs* __restrict__ a) {
   assemble16_body(*a);
 }
+// One launch for a batch: blockIdx.y picks the request (blocks past its size return).
+__global__ void __launch_bounds__(kAsmThreads) assemble16_kernel_batch(const uint8_t* __restrict__ args,
+                                                                       size_t stride) {
+  assemble16_body(*reinterpret_cast<const AssembleArgs*>(args + blockIdx.y * stride));
+}
 
 // ------------------------------------------------------------------- PE --
 struct PeArgs {
@@ -656,6 +661,9 @@ __global__ void __launch_bounds__(kBlendThreads) blend16_kernel(const __grid_con
 __global__ void __launch_bounds__(kBlendThreads) blend16_kernel_dev(const BlendArgs* __restrict__ a) {
   blend16_body(*a);
 }
+__global__ void __launch_bounds__(kBlendThreads) blend16_kernel_batch(const uint8_t* __restrict__ args, size_t stride) {
+  blend16_body(*reinterpret_cast<const BlendArgs*>(args + blockIdx.y * stride));
+}
 
 __global__ void f32_to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {
   const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
@@ -685,6 +693,39 @@ cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st, const Assemb
     assemble_kernel_dev<<<grid, 256, 0, st>>>(dev);
   else
     assemble_kernel<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_batch(const AssembleArgs* host, int n, const AssembleArgs* dev, size_t stride,
+                                  cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > 65535 || !dev) return cudaErrorInvalidValue;
+  long long threads = 0;
+  for (int i = 0; i < n; ++i) {
+    const AssembleArgs& a = host[i];
+    if (a.T <= 0 || a.F % a.T != 0 || a.p != 16 || a.H % 16 || a.W % 16 || a.F > kMaxRefs + 1 ||
+        (a.C != 1 && a.C != 3))
+      return cudaErrorInvalidValue;
+    threads = std::max(threads, static_cast<long long>(a.F) * (a.H / 16) * (a.W / 16) * 32);
+  }
+  if (threads == 0) return cudaSuccess;
+  const dim3 grid(static_cast<unsigned>((threads + kAsmThreads - 1) / kAsmThreads), static_cast<unsigned>(n));
+  assemble16_kernel_batch<<<grid, kAsmThreads, 0, st>>>(reinterpret_cast<const uint8_t*>(dev), stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend_batch(const BlendArgs* host, int n, const BlendArgs* dev, size_t stride, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > 65535 || !dev) return cudaErrorInvalidValue;
+  long long threads = 0;
+  for (int i = 0; i < n; ++i) {
+    const BlendArgs& a = host[i];
+    if (a.p != 16 || a.H % 16 || a.W % 16 || (a.C != 1 && a.C != 3)) return cudaErrorInvalidValue;
+    threads = std::max(threads, static_cast<long long>(a.H) * (a.W / 8));
+  }
+  if (threads == 0) return cudaSuccess;
+  const dim3 grid(static_cast<unsigned>((threads + kBlendThreads - 1) / kBlendThreads), static_cast<unsigned>(n));
+  blend16_kernel_batch<<<grid, kBlendThreads, 0, st>>>(reinterpret_cast<const uint8_t*>(dev), stride);
   return cudaGetLastError();
 }
 

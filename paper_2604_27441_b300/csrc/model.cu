@@ -641,9 +641,15 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
   if (e != cudaSuccess) return e;
 
   // Tubelet assembly + normalisation, tubelet embedding, embeddings.
-  for (int i = 0; i < n; ++i)
-    if ((e = launch_assemble(args[i].assemble, st, dev_args ? &dev_args[i].assemble : nullptr)) != cudaSuccess)
-      return e;
+  if (dev_args) {
+    // One launch for the batch, each request's arguments from the device table.
+    std::vector<AssembleArgs> aa(n);
+    for (int i = 0; i < n; ++i) aa[i] = args[i].assemble;
+    if ((e = launch_assemble_batch(aa.data(), n, &dev_args[0].assemble, sizeof(JobArgs), st)) != cudaSuccess) return e;
+  } else {
+    for (int i = 0; i < n; ++i)
+      if ((e = launch_assemble(args[i].assemble, st)) != cudaSuccess) return e;
+  }
   if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32, ws->x, s.D, M, &ws->o_x_enc)) != cudaSuccess) return e;
   for (int i = 0; i < n; ++i)
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.D, jobs[i].H / s.p, jobs[i].W / s.p,
@@ -691,12 +697,19 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
   if ((e = f.linear(&ws->c_h, ws->h, net->head, kEpiF32, ws->head, s.head_dim_out(), patches, &ws->c_o_head)) !=
       cudaSuccess)
     return e;
-  for (int i = 0; i < n; ++i)
-    if ((e = launch_blend(args[i].blend, st, dev_args ? &dev_args[i].blend : nullptr)) != cudaSuccess) return e;
-  // One kernel per step: per request assemble, 2 embeddings, blend; tubelet
-  // embedding, encoder LN, encoder->decoder, final LN, head; 7 per transformer
-  // block, 8 for the last (the row gather).
-  if (launches) *launches = 5 + 7 * (s.L + s.Ld) + 1 + 4 * n + f.extra_launches;
+  if (dev_args) {
+    std::vector<BlendArgs> bb(n);
+    for (int i = 0; i < n; ++i) bb[i] = args[i].blend;
+    if ((e = launch_blend_batch(bb.data(), n, &dev_args[0].blend, sizeof(JobArgs), st)) != cudaSuccess) return e;
+  } else {
+    for (int i = 0; i < n; ++i)
+      if ((e = launch_blend(args[i].blend, st)) != cudaSuccess) return e;
+  }
+  // One kernel per step: per request 2 embeddings, and assemble and blend
+  // (one launch each for the whole batch with the device argument table);
+  // tubelet embedding, encoder LN, encoder->decoder, final LN, head; 7 per
+  // transformer block, 8 for the last (the row gather).
+  if (launches) *launches = 5 + 7 * (s.L + s.Ld) + 1 + 2 * n + (dev_args ? 2 : 2 * n) + f.extra_launches;
   return cudaSuccess;
 }
 

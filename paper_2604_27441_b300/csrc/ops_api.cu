@@ -1,6 +1,7 @@
 // Step-level entry points of the C ABI: each runs one stage of the recovery
 // forward on caller-owned device buffers.
 #include <stdarg.h>
+#include <string.h>
 #include <stdio.h>
 
 #include <mutex>
@@ -92,6 +93,36 @@ float* op_pe_table(int D, int rows) {
     tabs[dev][w] = p;
   }
   return tabs[dev][w];
+}
+
+// The argument table of the step-level batched launches (one per device,
+// grown on demand; calls on one device run in stream order).  The host bytes
+// are uploaded on `st` unless the table already holds exactly them (a repeated
+// call with the same jobs launches without a copy).  Returns the device table.
+void* op_arg_table(const void* host, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  static void* bufs[64] = {};
+  static size_t sizes[64] = {};
+  static std::vector<uint8_t> held[64];
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!bufs[dev] || sizes[dev] < bytes) {
+    if (bufs[dev]) {
+      if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
+      cudaFree(bufs[dev]);
+      bufs[dev] = nullptr;
+    }
+    held[dev].clear();
+    if (cudaMalloc(&bufs[dev], bytes) != cudaSuccess) return nullptr;
+    sizes[dev] = bytes;
+  }
+  const uint8_t* h = static_cast<const uint8_t*>(host);
+  if (held[dev].size() != bytes || memcmp(held[dev].data(), h, bytes) != 0) {
+    // From pageable memory: the call returns once the bytes are staged.
+    if (cudaMemcpyAsync(bufs[dev], h, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return nullptr;
+    held[dev].assign(h, h + bytes);
+  }
+  return bufs[dev];
 }
 
 }  // namespace revo
@@ -515,3 +546,71 @@ revo_status revo_op_blend(int channels, int p, int height, int width, const floa
 }
 
 }  // extern "C"
+
+revo_status revo_op_assemble_batch(int channels, int k, int T, int n, const revo_assemble_job* jobs, int out_bf16,
+                                   void* stream) {
+  if (!jobs || n <= 0 || n > kMaxSegments || k < 1 || k > kMaxRefs || (channels != 1 && channels != 3)) {
+    set_last_error("revo_op_assemble_batch: bad argument");
+    return REVO_EINVAL;
+  }
+  std::vector<AssembleArgs> a(n);
+  for (int i = 0; i < n; ++i) {
+    const revo_assemble_job& j = jobs[i];
+    if (!j.out || (channels == 1 && !j.mu_sigma)) {
+      set_last_error("revo_op_assemble_batch: bad job %d", i);
+      return REVO_EINVAL;
+    }
+    a[i] = AssembleArgs{};
+    for (int f = 0; f <= k; ++f) {
+      if (!j.frames[f]) {
+        set_last_error("revo_op_assemble_batch: job %d lacks frame %d", i, f);
+        return REVO_EINVAL;
+      }
+      a[i].frames[f] = j.frames[f];
+      a[i].pitch[f] = j.pitch_bytes;
+    }
+    a[i].mu_sigma = j.mu_sigma;
+    a[i].out = j.out;
+    a[i].C = channels;
+    a[i].F = k + 1;
+    a[i].T = T;
+    a[i].p = 16;
+    a[i].H = j.height;
+    a[i].W = j.width;
+    a[i].out_bf16 = out_bf16;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* dev = op_arg_table(a.data(), n * sizeof(AssembleArgs), st);
+  if (!dev) {
+    set_last_error("revo_op_assemble_batch: argument table allocation or upload failed");
+    return REVO_ENOMEM;
+  }
+  return cuda_status(launch_assemble_batch(a.data(), n, static_cast<const AssembleArgs*>(dev), sizeof(AssembleArgs), st),
+                     "revo_op_assemble_batch");
+}
+
+revo_status revo_op_blend_batch(int channels, int n, const revo_blend_job* jobs, void* stream) {
+  if (!jobs || n <= 0 || n > kMaxSegments || (channels != 1 && channels != 3)) {
+    set_last_error("revo_op_blend_batch: bad argument");
+    return REVO_EINVAL;
+  }
+  std::vector<BlendArgs> a(n);
+  for (int i = 0; i < n; ++i) {
+    const revo_blend_job& j = jobs[i];
+    if (!j.head || !j.decoded || !j.mask || !j.out || (channels == 1 && !j.mu_sigma) ||
+        j.mask_pitch_words < static_cast<size_t>((j.width + 31) / 32)) {
+      set_last_error("revo_op_blend_batch: bad job %d", i);
+      return REVO_EINVAL;
+    }
+    a[i] = BlendArgs{channels, 16, j.height, j.width, j.head, j.decoded, j.pitch_bytes, j.mask, j.mask_pitch_words,
+                     j.mu_sigma, j.out, j.out_pitch, j.values};
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* dev = op_arg_table(a.data(), n * sizeof(BlendArgs), st);
+  if (!dev) {
+    set_last_error("revo_op_blend_batch: argument table allocation or upload failed");
+    return REVO_ENOMEM;
+  }
+  return cuda_status(launch_blend_batch(a.data(), n, static_cast<const BlendArgs*>(dev), sizeof(BlendArgs), st),
+                     "revo_op_blend_batch");
+}

@@ -101,6 +101,11 @@ struct AssembleArgs {
 // `dev` (optional): a device copy of `a` that the kernel reads instead of its
 // by-value arguments (the launch shape still comes from `a`).
 cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st, const AssembleArgs* dev = nullptr);
+// All n requests of a batch in one launch (p = 16): request i's arguments are
+// read from the device at (const char*)dev + i * stride; `host` holds the same
+// n argument sets (the launch shape: the largest request).
+cudaError_t launch_assemble_batch(const AssembleArgs* host, int n, const AssembleArgs* dev, size_t stride,
+                                  cudaStream_t st);
 
 // x[(s*Hp + r)*Wp + c][:] += sincos(tau_s) | sincos(r) | sincos(c), each D/3 wide
 // (D a multiple of 192).  `taus_dev` (optional): device copy of the temporal
@@ -139,6 +144,7 @@ struct BlendArgs {
   float* values;  // optional dense [H][W][C]
 };
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t st, const BlendArgs* dev = nullptr);
+cudaError_t launch_blend_batch(const BlendArgs* host, int n, const BlendArgs* dev, size_t stride, cudaStream_t st);
 
 cudaError_t launch_f32_to_bf16(const float* in, void* out, size_t n, cudaStream_t st);
 

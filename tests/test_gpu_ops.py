@@ -522,6 +522,45 @@ def test_position_embedding(D, hp, wp, taus):
 
 # -------------------------------------------------------------------- blend
 
+@pytest.mark.parametrize("modality", ["rgb", "depth"])
+def test_batched_assemble_and_blend_equal_single_launches(modality):
+    """One launch for several requests of different sizes (the forward's form)
+    gives bit for bit what one launch per request gives."""
+    C, k, T, p = (3, 5, 2, 16) if modality == "rgb" else (1, 5, 2, 16)
+    sizes = [(48, 80), (32, 128), (64, 64)]
+    assemble_jobs, blend_jobs, singles = [], [], []
+    for i, (H, W) in enumerate(sizes):
+        pl = synth.make_tiny_plane(500 + i, modality, H, W, k)
+        pitch = W * (3 if C == 3 else 2)
+        refs = [dev(f) for f in pl.refs]
+        cur = dev(pl.decoded)
+        ms = dev(np.array([1800.0 + i, 600.0], np.float32)) if C == 1 else None
+        S, Hp, Wp = (k + 1) // T, H // p, W // p
+        tok_b = torch.zeros((S * Hp * Wp, T * C * p * p), dtype=torch.bfloat16, device="cuda")
+        tok_s = torch.zeros_like(tok_b)
+        R.op_assemble(C, k, T, p, H, W, refs, cur, pitch, ms, tok_s, 1)
+        assemble_jobs.append(dict(height=H, width=W, frames=refs + [cur], pitch_bytes=pitch, mu_sigma=ms, out=tok_b))
+        head = dev(synth.normal(900 + i, (Hp * Wp, C * p * p)))
+        mask = dev(pl.mask)
+        shape = pl.decoded.shape
+        odt = torch.uint8 if C == 3 else torch.int16
+        out_b, out_s = torch.zeros(shape, dtype=odt, device="cuda"), torch.zeros(shape, dtype=odt, device="cuda")
+        val_b = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        val_s = torch.zeros_like(val_b)
+        R.op_blend(C, p, H, W, head, cur, pitch, mask, pl.mask.shape[1], ms, out_s, pitch, val_s)
+        blend_jobs.append(dict(height=H, width=W, head=head, decoded=cur, pitch_bytes=pitch, mask=mask,
+                               mask_pitch_words=pl.mask.shape[1], mu_sigma=ms, out=out_b, out_pitch=pitch,
+                               values=val_b))
+        singles.append((tok_b, tok_s, out_b, out_s, val_b, val_s, refs, cur, head, mask, ms))
+    R.op_assemble_batch(C, k, T, assemble_jobs, 1)
+    R.op_blend_batch(C, blend_jobs)
+    torch.cuda.synchronize()
+    for tok_b, tok_s, out_b, out_s, val_b, val_s, *_ in singles:
+        assert torch.equal(tok_b, tok_s)
+        assert torch.equal(out_b, out_s)
+        assert torch.equal(val_b, val_s)
+
+
 @pytest.mark.parametrize("modality,H,W", [("rgb", 48, 80), ("depth", 64, 48), ("rgb", 240, 320)])
 def test_blend_codes_bit_exact(modality, H, W):
     """Received pixels are copied bit for bit; lost pixels carry the float32
