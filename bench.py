@@ -946,6 +946,11 @@ def run_profile_kernel(args) -> None:
         out = torch.empty((M, D), dtype=torch.bfloat16, device="cuda")
         launch = lambda: R.op_attention(R.BF16, qkv, out, M, D, 12, seg, stream=stream)  # noqa: E731
         flops = sum(4 * n * n * D for n in lens)
+    elif args.profile_kernel == "pe":  # the position embedding of one 1280x720 request at the encoder width
+        S, hp, wp = 3, 45, 80
+        x = torch.zeros((S * hp * wp, D), device="cuda")
+        launch = lambda: R.op_add_position(x, S, hp, wp, D, [5, 3, 1], stream=stream)  # noqa: E731
+        flops, nbytes = None, 2 * x.numel() * 4
     elif args.profile_kernel in ("assemble", "blend"):  # the HBM-bound stages at 1280x720 RGB, k = 5, T = 2
         Hh, Ww, k, T, p = 720, 1280, 5, 2, 16
         frames = [torch.randint(0, 256, (Hh, Ww, 3), dtype=torch.uint8, device="cuda") for _ in range(k + 1)]
@@ -1026,7 +1031,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "attention_tick", "fc1", "fc1_pair",
                                                  "fc1_fp8", "fc1_fp8_pair", "fc2", "fc2_pair", "fc1_tick", "fc2_tick",
-                                                 "assemble", "blend"],
+                                                 "assemble", "blend", "pe"],
                     default=None, help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)

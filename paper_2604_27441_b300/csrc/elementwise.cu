@@ -221,56 +221,68 @@ __global__ void pe_table_kernel(float* __restrict__ tab, int rows, const __grid_
           blockDim.x);
 }
 
-// One CTA per (slot s, patch row r): the temporal part of slot s and the row
-// part of r are computed once into shared memory, the column part comes from
-// `ctab` (pe_table_kernel's table, or computed per element without one); then
-// each of the row's Wp token rows of x gets the three parts added with 16-byte
-// accesses.  Every value is the same float32 sincosf of pos * w_i as a per
-// element evaluation, so the result does not depend on the table.
+// One CTA per (slot s, run of 8 tokens of the slot): the temporal part of
+// slot s is computed once into shared memory; the row and column parts come
+// from `ptab` (pe_table_kernel's table: the part's values at integer position
+// q, the same for rows and columns), or are computed per element without one.
+// Each thread owns a 16-byte column group and adds it to the run's 8 token
+// rows (8 independent read-modify-writes in flight).  Every value is the same
+// float32 sincosf of pos * w_i as a per-element evaluation, so the result does
+// not depend on the table.
+constexpr int kPeRun = 8;
 __global__ void add_pe_kernel(float* __restrict__ x, const __grid_constant__ PeArgs a,
-                              const float* __restrict__ ctab) {
+                              const float* __restrict__ ptab) {
   __shared__ float om[128];
   __shared__ __align__(16) float tp[1024 / 3 + 4];
-  __shared__ __align__(16) float rp[1024 / 3 + 4];
   const int half = a.part / 2;
   for (int i = threadIdx.x; i < half; i += blockDim.x) om[i] = a.omega[i];
   __syncthreads();
-  const int s = static_cast<int>(blockIdx.x) / a.Hp;
-  const int r = static_cast<int>(blockIdx.x) % a.Hp;
+  const int hw = a.Hp * a.Wp;
+  const int runs = (hw + kPeRun - 1) / kPeRun;
+  const int s = static_cast<int>(blockIdx.x) / runs;
+  const int t0 = (static_cast<int>(blockIdx.x) % runs) * kPeRun;
   const int tau = a.taus_dev ? __ldg(a.taus_dev + s) : a.taus[s];
   pe_part(static_cast<float>(tau), om, half, tp, threadIdx.x, blockDim.x);
-  pe_part(static_cast<float>(r), om, half, rp, threadIdx.x, blockDim.x);
   __syncthreads();
   const int nv = a.D / 4;
   for (int j = threadIdx.x; j < nv; j += blockDim.x) {
     const int col = 4 * j;
     const int which = col / a.part;  // a part is a multiple of 64 columns: a vector stays in one part
     const int q = col - which * a.part;
-    for (int c = 0; c < a.Wp; ++c) {
-      float4 v;
+    float4 v[kPeRun];
+#pragma unroll
+    for (int u = 0; u < kPeRun; ++u) {
+      const int t = t0 + u;
+      if (t >= hw) break;
+      const int pos = which == 1 ? t / a.Wp : t % a.Wp;
       if (which == 0) {
-        v = *reinterpret_cast<const float4*>(tp + q);
-      } else if (which == 1) {
-        v = *reinterpret_cast<const float4*>(rp + q);
-      } else if (ctab) {
-        v = __ldg(reinterpret_cast<const float4*>(ctab + static_cast<size_t>(c) * a.part + q));
+        v[u] = *reinterpret_cast<const float4*>(tp + q);
+      } else if (ptab) {
+        v[u] = __ldg(reinterpret_cast<const float4*>(ptab + static_cast<size_t>(pos) * a.part + q));
       } else {
-        float e[4];
-        for (int u = 0; u < 4; ++u) {
-          const int i = (q + u) % half;
+        float e4[4];
+        for (int w = 0; w < 4; ++w) {
+          const int i = (q + w) % half;
           float sv, cv;
-          sincosf(static_cast<float>(c) * om[i], &sv, &cv);
-          e[u] = q + u < half ? sv : cv;
+          sincosf(static_cast<float>(pos) * om[i], &sv, &cv);
+          e4[w] = q + w < half ? sv : cv;
         }
-        v = make_float4(e[0], e[1], e[2], e[3]);
+        v[u] = make_float4(e4[0], e4[1], e4[2], e4[3]);
       }
-      float4* p = reinterpret_cast<float4*>(x + (static_cast<size_t>(s * a.Hp + r) * a.Wp + c) * a.D) + j;
-      float4 y = *p;
-      y.x += v.x;
-      y.y += v.y;
-      y.z += v.z;
-      y.w += v.w;
-      *p = y;
+    }
+    float4* p = reinterpret_cast<float4*>(x + (static_cast<size_t>(s) * hw + t0) * a.D) + j;
+    float4 y[kPeRun];
+#pragma unroll
+    for (int u = 0; u < kPeRun; ++u)
+      if (t0 + u < hw) y[u] = p[static_cast<size_t>(u) * nv];
+#pragma unroll
+    for (int u = 0; u < kPeRun; ++u) {
+      if (t0 + u >= hw) break;
+      y[u].x += v[u].x;
+      y[u].y += v[u].y;
+      y[u].z += v[u].z;
+      y[u].w += v[u].w;
+      p[static_cast<size_t>(u) * nv] = y[u];
     }
   }
 }
@@ -748,7 +760,7 @@ cudaError_t launch_pe_table(float* tab, int rows, int D, cudaStream_t st) {
 }
 
 cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, int D, cudaStream_t st,
-                          const int* taus_dev, const float* ctab, int ctab_rows) {
+                          const int* taus_dev, const float* ptab, int ptab_rows) {
   PeArgs a{};
   a.taus_dev = taus_dev;
   a.Hp = Hp;
@@ -756,12 +768,13 @@ cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, 
   if (!pe_args(&a, D) || slots > 8 || slots < 0 || Hp < 0 || Wp < 0) return cudaErrorInvalidValue;
   if (!taus_dev)
     for (int s = 0; s < slots; ++s) a.taus[s] = taus[s];
-  if (ctab && Wp > ctab_rows) ctab = nullptr;
-  const long long blocks = static_cast<long long>(slots) * Hp;
-  if (blocks == 0 || Wp == 0) return cudaSuccess;
-  if (blocks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+  if (ptab && (Wp > ptab_rows || Hp > ptab_rows)) ptab = nullptr;
+  const long long hw = static_cast<long long>(Hp) * Wp;
+  const long long blocks = static_cast<long long>(slots) * ((hw + kPeRun - 1) / kPeRun);
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > 0x7FFFFFFFll || hw > 0x7FFFFFFFll) return cudaErrorInvalidValue;
   const int threads = std::min(256, ((D / 4 + 31) / 32) * 32);
-  add_pe_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(x, a, ctab);
+  add_pe_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(x, a, ptab);
   return cudaGetLastError();
 }
 

@@ -95,8 +95,8 @@ struct Workspace {
   // The last decoder block's rows (the final slot of each request, stacked):
   float* xc = nullptr;    // [cap_patches][D'] residual stream
   void* attc = nullptr;   // [cap_patches][D'] attention output
-  // The position embedding's column part for patch columns 0 .. pe_rows-1,
-  // at the encoder and the decoder width (launch_pe_table).
+  // The position embedding's row / column part at patch positions
+  // 0 .. pe_rows-1, at the encoder and the decoder width (launch_pe_table).
   float* pe_enc = nullptr;
   float* pe_dec = nullptr;
   int pe_rows = 0;
@@ -121,7 +121,7 @@ Net* net_create(const NetShape& s, int precision, const float* host_weights, std
 void net_destroy(Net* n);
 size_t net_bytes(const NetShape& s, int precision);
 
-// max_segments: requests per batch; max_wp: patch columns of the widest frame.
+// max_segments: requests per batch; max_wp: patch rows or columns of the largest frame.
 size_t workspace_bytes(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments,
                        int max_wp);
 Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, int cap_patches, int max_segments,

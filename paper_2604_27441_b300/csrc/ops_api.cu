@@ -503,11 +503,12 @@ revo_status revo_op_add_position(float* x, int slots, int grid_h, int grid_w, in
     set_last_error("revo_op_add_position: bad argument");
     return REVO_EINVAL;
   }
-  // Up to 256 patch columns the column part comes from a table (as in the
-  // recovery forward); wider grids compute it per element (the same values).
+  // Up to 256 patch rows and columns the row and column parts come from a
+  // table (as in the recovery forward); larger grids compute them per element
+  // (the same values).
   constexpr int kTabRows = 256;
   const float* tab = nullptr;
-  if (grid_w <= kTabRows) {
+  if (grid_w <= kTabRows && grid_h <= kTabRows) {
     float* t = op_pe_table(D, kTabRows);
     if (!t) {
       set_last_error("revo_op_add_position: table allocation failed");

@@ -632,7 +632,8 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
     if (wn[m] != param_count(s)) return fail(REVO_EINVAL, "weight count does not match the network shape%s");
     cap_p[m] = cfg->max_batch * request_patches(s, cfg->max_height, cfg->max_width);
     cap_tok[m] = cfg->max_batch * request_tokens(s, cfg->max_height, cfg->max_width);
-    need += net_bytes(s, cfg->precision) + cfg->lanes * workspace_bytes(s, cfg->precision, cap_tok[m], cap_p[m], cfg->max_batch, cfg->max_width / cfg->patch);
+    need += net_bytes(s, cfg->precision) + cfg->lanes * workspace_bytes(s, cfg->precision, cap_tok[m], cap_p[m], cfg->max_batch,
+                                                  std::max(cfg->max_width, cfg->max_height) / cfg->patch);
     need += static_cast<size_t>(cfg->max_streams) * cfg->k * frame_bytes(m, cfg->max_height, cfg->max_width);
     need += static_cast<size_t>(2 * cfg->max_batch * cfg->lanes) *
             (frame_bytes(m, cfg->max_height, cfg->max_width) * 2 + mask_words(cfg->max_height, cfg->max_width) * 4 +
@@ -666,7 +667,7 @@ revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out) {
     for (int m = 0; m < 2; ++m) {
       if (!c->net[m]) continue;
       L.ws[m] = workspace_create(c->shape[m], cfg->precision, cap_tok[m], cap_p[m], cfg->max_batch,
-                                 cfg->max_width / cfg->patch, &err);
+                                 std::max(cfg->max_width, cfg->max_height) / cfg->patch, &err);
       if (!L.ws[m]) return fail(REVO_ENOMEM, "workspace: %s", err.c_str());
       c->bytes += L.ws[m]->bytes;
       if (!cfg->use_graphs) continue;

@@ -109,11 +109,12 @@ cudaError_t launch_assemble_batch(const AssembleArgs* host, int n, const Assembl
 
 // x[(s*Hp + r)*Wp + c][:] += sincos(tau_s) | sincos(r) | sincos(c), each D/3 wide
 // (D a multiple of 192).  `taus_dev` (optional): device copy of the temporal
-// distances, read instead of `taus`.  `ctab` (optional): launch_pe_table's
-// table of the column part for positions 0 .. ctab_rows-1 (the same values).
+// distances, read instead of `taus`.  `ptab` (optional): launch_pe_table's
+// table of a part at integer positions 0 .. ptab_rows-1, used for the row and
+// the column parts (the same values as computing them).
 cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, int D, cudaStream_t st,
-                          const int* taus_dev = nullptr, const float* ctab = nullptr, int ctab_rows = 0);
-// tab[c][0 .. D/3) = the embedding's part at position c, for c < rows.
+                          const int* taus_dev = nullptr, const float* ptab = nullptr, int ptab_rows = 0);
+// tab[q][0 .. D/3) = the embedding's part at position q, for q < rows.
 cudaError_t launch_pe_table(float* tab, int rows, int D, cudaStream_t st);
 
 cudaError_t launch_layernorm(const float* x, const float* g, const float* b, void* out, int M, int D, int out_bf16,

@@ -509,10 +509,12 @@ def test_depth_stats(case):
 
 
 @pytest.mark.parametrize("D,hp,wp,taus", [(768, 15, 20, (5, 3, 1)), (384, 45, 80, (7, 5, 3)), (192, 2, 3, (1,)),
-                                         (192, 2, 300, (4, 2))])
+                                         (192, 2, 300, (4, 2)), (192, 260, 3, (1,))])
 def test_position_embedding(D, hp, wp, taus):
-    """Up to 256 patch columns the column part comes from a table, wider grids
-    compute it per element; both against the oracle."""
+    """Up to 256 patch rows and columns the row and column parts come from a
+    table, larger grids compute them per element; both against the oracle
+    (grids whose slot size is not a multiple of the kernel's 8-token runs
+    included)."""
     S = len(taus)
     x = torch.zeros((S * hp * wp, D), dtype=torch.float32, device="cuda")
     R.op_add_position(x, S, hp, wp, D, list(taus))
