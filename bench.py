@@ -67,7 +67,7 @@ TILE_CACHE = os.path.join(tempfile.gettempdir(), f"revo_tiles_{os.getpid()}.txt"
 # DRAM bytes (read + write) of one attn_tc_kernel launch of the tick's batched
 # RGB encoder attention, from an ncu capture of the current kernel version
 # (None once the kernel changes).
-ATTN_DRAM_BYTES_PER_LAUNCH = None
+ATTN_DRAM_BYTES_PER_LAUNCH = 329552640 + 89673984
 
 
 def run_pipelined(R, ctx, req_list, n: int, depth: int, start: int = 0):
