@@ -351,6 +351,29 @@ REVO_API revo_status revo_op_depth_stats_noalloc(const uint16_t* depth, int heig
 REVO_API revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A, const void* W,
                            const float* bias, void* out, int M, int N, int K, int tile_n, void* stream);
 
+/*
+ * A residual Linear with the LayerNorm that follows it, in one launch (the
+ * transformer block's "x = x + proj(att); h = LN2(x)" and
+ * "x = x + fc2(mlp); h = LN1'(x)" steps, Section 3.4.1):
+ *   x[m][n] += sum_k A[m][k] W[n][k] + bias[n]        (float32, in place)
+ *   ln_out[m] = LayerNorm(x[m]; gamma, beta), eps 1e-6
+ * A [M][K] and W [N][K] bf16 (tensor cores, float32 accumulation), x float32
+ * [M][N], gamma / beta float32 [N], all device.  ln_fp8 == 0: ln_out bf16
+ * [M][N]; ln_fp8 != 0: ln_out E4M3 codes [M][N] with ln_row_scale [M], the
+ * per-row rule of revo_op_layernorm_e4m3.  The LayerNorm of a block of 128
+ * rows runs in the GEMM epilogue of the CTA that adds the block's last column
+ * tile; its values equal revo_op_layernorm (revo_op_layernorm_e4m3) applied
+ * to the updated x, bit for bit.  K % 64 == 0, N % 32 == 0, N <= 1024; tile_n
+ * 128 or 256, | REVO_TILE_PAIR.  Uses a per-device scratch of row-block
+ * counters (one call at a time per device).  Errors: REVO_EINVAL, REVO_ECUDA.
+ * Speed: one SM normalises each 128-row block with a few rows in flight, so
+ * at the model's widths (768, 384) this is slower than revo_op_linear then
+ * revo_op_layernorm, and the recovery forward uses those two.
+ */
+REVO_API revo_status revo_op_linear_resid_ln(const void* A, const void* W, const float* bias, float* x, int M, int N,
+                                             int K, const float* gamma, const float* beta, void* ln_out,
+                                             float* ln_row_scale, int ln_fp8, int tile_n, void* stream);
+
 /* Row-wise LayerNorm, eps 1e-6: x float32 [M][D] -> out (bf16 if out_bf16, else float32). */
 REVO_API revo_status revo_op_layernorm(const float* x, const float* gamma, const float* beta, void* out,
                               int M, int D, int out_bf16, void* stream);

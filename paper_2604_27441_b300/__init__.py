@@ -113,6 +113,8 @@ _SIGS = {
     "revo_op_linear": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                  C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "revo_op_layernorm": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "revo_op_linear_resid_ln": (C.c_int, [C.c_void_p] * 4 + [C.c_int] * 3 + [C.c_void_p] * 4 + [C.c_int, C.c_int,
+                                                                                               C.c_void_p]),
     "revo_op_attention": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
                                     C.c_int, C.c_void_p]),
@@ -222,6 +224,15 @@ def op_depth_stats_noalloc(depth, height, width, pitch_bytes, mu_sigma, stream=N
 def op_linear(precision, epilogue, A, W, bias, out, M, N, K, tile_n=0, stream=None):
     return _check(lib().revo_op_linear(precision, epilogue, ptr(A), ptr(W), ptr(bias), ptr(out), M, N, K, tile_n,
                                        _stream(stream)), "revo_op_linear")
+
+
+def op_linear_resid_ln(A, W, bias, x, M, N, K, gamma, beta, ln_out, ln_row_scale=None, ln_fp8=False, tile_n=0,
+                       stream=None):
+    """x += A W^T + bias, then ln_out = LayerNorm(x) (bf16, or E4M3 codes with
+    per-row scales when ln_fp8), in one tensor-core launch."""
+    return _check(lib().revo_op_linear_resid_ln(ptr(A), ptr(W), ptr(bias), ptr(x), M, N, K, ptr(gamma), ptr(beta),
+                                                ptr(ln_out), ptr(ln_row_scale), int(bool(ln_fp8)), tile_n,
+                                                _stream(stream)), "revo_op_linear_resid_ln")
 
 
 def op_layernorm(x, gamma, beta, out, M, D, out_bf16, stream=None):

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "layernorm_row.cuh"
 #include "revo_internal.h"
 
 namespace revo {
@@ -288,29 +289,8 @@ __global__ void add_pe_kernel(float* __restrict__ x, const __grid_constant__ PeA
 }
 
 // ------------------------------------------------------------ LayerNorm --
-// One warp per row, two passes over registers, eps 1e-6, biased variance.
-constexpr int kLnMaxVec = 8;  // D <= 1024
-
-// Four floats -> four E4M3 codes (round to nearest even, saturating to +-448),
-// the first value in the lowest byte.
-REVO_DEVI uint32_t pack_e4m3x4(float a, float b, float c, float d) {
-  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-  return lo | (hi << 16);
-}
-
-// Per-row E4M3 scale rule: s = amax / 448, inverse 448 / amax; an all-zero row
-// keeps s = 1.
-REVO_DEVI void e4m3_row_scale(float amax, float* s, float* inv) {
-  if (amax > 0.f) {
-    *s = amax / 448.0f;
-    *inv = 448.0f / amax;
-  } else {
-    *s = 1.0f;
-    *inv = 1.0f;
-  }
-}
-
+// One warp per row (ln_row in layernorm_row.cuh, shared with the GEMM
+// epilogue that fuses the LayerNorm after a residual add).
 // OUT: 0 float32, 1 bf16, 2 E4M3 codes + a per-row scale.
 template <int OUT>
 __global__ void layernorm_kernel(const float* __restrict__ x, const float* __restrict__ g,
@@ -319,70 +299,7 @@ __global__ void layernorm_kernel(const float* __restrict__ x, const float* __res
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= M) return;
-  const float4* xr = reinterpret_cast<const float4*>(x + static_cast<size_t>(warp) * D);
-  const int nv = D / 4;
-  float4 v[kLnMaxVec];
-  float sum = 0.f;
-#pragma unroll
-  for (int i = 0; i < kLnMaxVec; ++i) {
-    const int c = lane + 32 * i;
-    if (c < nv) {
-      v[i] = __ldg(xr + c);
-      sum += (v[i].x + v[i].y) + (v[i].z + v[i].w);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  const float mean = sum / D;
-  float sq = 0.f;
-#pragma unroll
-  for (int i = 0; i < kLnMaxVec; ++i) {
-    const int c = lane + 32 * i;
-    if (c < nv) {
-      const float a0 = v[i].x - mean, a1 = v[i].y - mean, a2 = v[i].z - mean, a3 = v[i].w - mean;
-      sq += (a0 * a0 + a1 * a1) + (a2 * a2 + a3 * a3);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  const float rstd = 1.0f / sqrtf(sq / D + 1e-6f);
-  const float4* g4 = reinterpret_cast<const float4*>(g);
-  const float4* b4 = reinterpret_cast<const float4*>(b);
-  float amax = 0.f;
-#pragma unroll
-  for (int i = 0; i < kLnMaxVec; ++i) {
-    const int c = lane + 32 * i;
-    if (c < nv) {
-      const float4 gg = __ldg(g4 + c), bb = __ldg(b4 + c);
-      const float y0 = (v[i].x - mean) * rstd * gg.x + bb.x;
-      const float y1 = (v[i].y - mean) * rstd * gg.y + bb.y;
-      const float y2 = (v[i].z - mean) * rstd * gg.z + bb.z;
-      const float y3 = (v[i].w - mean) * rstd * gg.w + bb.w;
-      if (OUT == 2) {
-        v[i] = make_float4(y0, y1, y2, y3);
-        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(y0), fabsf(y1)), fmaxf(fabsf(y2), fabsf(y3))));
-      } else if (OUT == 1) {
-        uint2* o = reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out) + static_cast<size_t>(warp) * D) + c;
-        *o = make_uint2(pack_bf16x2(y0, y1), pack_bf16x2(y2, y3));
-      } else {
-        float4* o = reinterpret_cast<float4*>(static_cast<float*>(out) + static_cast<size_t>(warp) * D) + c;
-        *o = make_float4(y0, y1, y2, y3);
-      }
-    }
-  }
-  if (OUT == 2) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    float sc, inv;
-    e4m3_row_scale(amax, &sc, &inv);
-    uint32_t* orow = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(out) + static_cast<size_t>(warp) * D);
-#pragma unroll
-    for (int i = 0; i < kLnMaxVec; ++i) {
-      const int c = lane + 32 * i;
-      if (c < nv) orow[c] = pack_e4m3x4(v[i].x * inv, v[i].y * inv, v[i].z * inv, v[i].w * inv);
-    }
-    if (lane == 0) row_scale[warp] = sc;
-  }
+  ln_row<OUT, false>(x, g, b, out, row_scale, warp, D, lane);
 }
 
 // One warp per row: amax pass, then the codes.

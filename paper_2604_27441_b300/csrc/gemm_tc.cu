@@ -39,6 +39,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "layernorm_row.cuh"
 #include "revo_internal.h"
 
 namespace revo {
@@ -125,13 +126,19 @@ REVO_DEVI uint32_t pack_bf16_pair(uint64_t v) {
   return pack_bf16x2(lo, hi);
 }
 
+// kEpiResidLn with LnFuse mode 2 (E4M3 LayerNorm output): a kernel template
+// argument only, chosen by launch_gemm_tc from the mode.
+constexpr int kEpiResidLn8 = 5;
+__host__ __device__ constexpr bool epi_resid(int epi) { return epi == kEpiResidF32 || epi == kEpiResidLn || epi == kEpiResidLn8; }
+__host__ __device__ constexpr bool epi_ln(int epi) { return epi == kEpiResidLn || epi == kEpiResidLn8; }
+
 // One epilogue chunk: 32 rows (this warp's lanes) x 128 bytes of output
 // (32 f32 columns or 64 bf16 columns) starting at tile column `c0`.
 template <int EPI, bool F8>
 REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, int n0, int c0, uint8_t* chunk,
                               const CUtensorMap* map, int row0, int lane, float rs, const float* __restrict__ cs) {
   uint4 pieces[8];
-  if (EPI == kEpiF32 || EPI == kEpiResidF32) {
+  if (EPI == kEpiF32 || epi_resid(EPI)) {
     uint32_t r[32];
     tmem_ld32(taddr + c0, r);
     tmem_wait_ld();
@@ -176,11 +183,64 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
   fence_proxy_async_smem();
   __syncwarp();
   if (lane == 0) {
-    if (EPI == kEpiResidF32)
+    if (epi_resid(EPI))
       tma_reduce_add_2d(map, chunk, n0 + c0, row0);
     else
       tma_store_2d(map, chunk, n0 + c0, row0);
     bulk_commit();
+  }
+}
+
+// The rows of one completed row block, R at a time per epilogue warp (warp e
+// takes rows e, e + 8, ...), NV float4 of a row per lane.
+template <int OUT, int NV, int R>
+REVO_DEVI void ln_block_rows(const LnFuse& ln, int m0, int rows, int N, int e, int lane) {
+  for (int r = e; r < rows; r += R * kEpiWarps)
+    ln_rows<OUT, true, NV, R>(ln.x, ln.g, ln.b, ln.out, ln.row_scale, m0 + r, kEpiWarps, m0 + rows, N, lane);
+}
+
+// kEpiResidLn, after the epilogue warps have added a tile into rows
+// [m0, m0 + 128) of x: each warp waits for its reduce-adds to complete, fences
+// (a proxy fence -- the adds came through the async proxy -- then a gpu-scope
+// fence) and arrives on ln_in; warp 0 then counts the tile for the row block
+// (after a gpu-scope fence: the count publishes every warp's adds) and
+// publishes on ln_out whether this CTA completed it (all n_tiles column tiles
+// added); that CTA normalises the rows, reading x through L2.  Every wait is
+// bounded (a failed wait leaves the rows alone; the error word reports it).
+// `phase`: the parity of this CTA's counted tiles, flipped here.
+template <int OUT>
+REVO_DEVI void ln_after_tile(const LnFuse& ln, int m0, int M, int N, int n_tiles, int e, int lane, int* flag,
+                             uint64_t* ln_in, uint64_t* ln_out, uint32_t& phase, int* err) {
+  if (m0 >= M) return;  // a pair tile's rows past the end: no block, no count (same in every warp)
+  if (lane == 0) {
+    bulk_wait_all();
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __threadfence();
+    mbar_arrive(ln_in);
+  }
+  int ok = 1;
+  if (e == 0 && lane == 0) {
+    int last = 0;
+    if (mbar_wait(ln_in, phase, err, kDevTimeoutEpilogue)) {
+      const int rb = m0 / kBM;
+      __threadfence();
+      last = atomicAdd(&ln.counters[rb], 1) == n_tiles - 1;
+      if (last) ln.counters[rb] = 0;
+    }
+    *flag = last;
+    mbar_arrive(ln_out);
+  }
+  if (lane == 0) ok = mbar_wait(ln_out, phase, err, kDevTimeoutEpilogue) ? 1 : 0;
+  phase ^= 1u;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  if (ok && *reinterpret_cast<volatile int*>(flag)) {
+    __threadfence();
+    const int rows = min(kBM, M - m0);
+    if (N <= 512)
+      ln_block_rows<OUT, 4, 2>(ln, m0, rows, N, e, lane);
+    else
+      ln_block_rows<OUT, kLnMaxVec, 1>(ln, m0, rows, N, e, lane);
   }
 }
 
@@ -189,12 +249,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const float* __restrict__ bias,
                    const float* __restrict__ row_scale, const float* __restrict__ col_scale, int M, int N, int K,
-                   int* err) {
+                   int* err, const __grid_constant__ LnFuse ln) {
   using Cfg = TcGemmCfg<BN>;
   constexpr int S = Cfg::kStages;
   constexpr uint32_t kIdesc = F8 ? idesc_e4m3(kBM, BN) : idesc_bf16(kBM, BN);
   constexpr int kKe = F8 ? kBK8 : kBK;  // K elements per stage
-  constexpr int kChunkCols = (EPI == kEpiF32 || EPI == kEpiResidF32) ? 32 : 64;
+  constexpr int kChunkCols = (EPI == kEpiF32 || epi_resid(EPI)) ? 32 : 64;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -206,6 +266,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  int* ln_flag = reinterpret_cast<int*>(tmem_slot + 1);  // kEpiResidLn: this CTA completed the row block
+  uint64_t* ln_in = reinterpret_cast<uint64_t*>(tmem_slot + 2);  // 8-byte aligned: tmem_slot follows 8-byte barriers
+  uint64_t* ln_out = ln_in + 1;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -226,6 +289,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], kEpiWarps);
     }
+    mbar_init(ln_in, kEpiWarps);
+    mbar_init(ln_out, 1);
     fence_mbarrier_init();
   }
   if (warp == 1) {
@@ -302,6 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int half = e >> 2;
     uint8_t* chunk = sOut + e * kOutChunkBytes;
     int t_local = 0;
+    uint32_t ln_phase = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++t_local) {
       const int acc = t_local & 1;
       const uint32_t acc_phase = (t_local >> 1) & 1;
@@ -320,6 +386,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
+      if constexpr (epi_ln(EPI))
+        ln_after_tile<EPI == kEpiResidLn8 ? 2 : 1>(ln, m0, M, N, n_tiles, e, lane, ln_flag, ln_in, ln_out, ln_phase,
+                                                   err);
     }
     if (lane == 0) bulk_wait_all();
   }
@@ -356,12 +425,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmC, const float* __restrict__ bias,
                         const float* __restrict__ row_scale, const float* __restrict__ col_scale, int M, int N, int K,
-                        int* err) {
+                        int* err, const __grid_constant__ LnFuse ln) {
   using Cfg = TcGemmPairCfg<BN>;
   constexpr int S = Cfg::kStages;
   constexpr uint32_t kIdesc = F8 ? idesc_e4m3(2 * kBM, BN) : idesc_bf16(2 * kBM, BN);
   constexpr int kKe = F8 ? kBK8 : kBK;
-  constexpr int kChunkCols = (EPI == kEpiF32 || EPI == kEpiResidF32) ? 32 : 64;
+  constexpr int kChunkCols = (EPI == kEpiF32 || epi_resid(EPI)) ? 32 : 64;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -373,6 +442,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  int* ln_flag = reinterpret_cast<int*>(tmem_slot + 1);  // kEpiResidLn: this CTA completed the row block
+  uint64_t* ln_in = reinterpret_cast<uint64_t*>(tmem_slot + 2);  // 8-byte aligned: tmem_slot follows 8-byte barriers
+  uint64_t* ln_out = ln_in + 1;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -396,6 +468,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], 2 * kEpiWarps);  // rank 0's: the epilogue warps of both CTAs
     }
+    mbar_init(ln_in, kEpiWarps);  // this CTA's own epilogue warps
+    mbar_init(ln_out, 1);
     fence_mbarrier_init();
   }
   if (warp == 1) {
@@ -476,6 +550,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int half = e >> 2;
     uint8_t* chunk = sOut + e * kOutChunkBytes;
     int t_local = 0;
+    uint32_t ln_phase = 0;
     for (int tile = pair; tile < num_tiles; tile += npairs, ++t_local) {
       const int acc = t_local & 1;
       const uint32_t acc_phase = (t_local >> 1) & 1;
@@ -494,6 +569,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[acc]), 0));
+      if constexpr (epi_ln(EPI))
+        ln_after_tile<EPI == kEpiResidLn8 ? 2 : 1>(ln, m0, M, N, n_tiles, e, lane, ln_flag, ln_in, ln_out, ln_phase,
+                                                   err);
     }
     if (lane == 0) bulk_wait_all();
   }
@@ -514,7 +592,7 @@ namespace {
 template <int BN, int EPI, bool F8 = false>
 cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const float* bias, int M,
                           int N, int K, int* err, int num_sms, cudaStream_t st, const float* row_scale = nullptr,
-                          const float* col_scale = nullptr) {
+                          const float* col_scale = nullptr, const LnFuse& ln = LnFuse{}) {
   using Cfg = TcGemmCfg<BN>;
   auto kern = gemm_tc_kernel<BN, EPI, F8>;
   static std::atomic<unsigned long long> attr_done{0};  // one per template instance
@@ -522,14 +600,14 @@ cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const CUte
   if (e != cudaSuccess) return e;
   const int tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
   const int grid = tiles < num_sms ? tiles : num_sms;
-  kern<<<grid, kThreads, Cfg::kSmemBytes, st>>>(a, b, c, bias, row_scale, col_scale, M, N, K, err);
+  kern<<<grid, kThreads, Cfg::kSmemBytes, st>>>(a, b, c, bias, row_scale, col_scale, M, N, K, err, ln);
   return cudaGetLastError();
 }
 
 template <int BN, int EPI, bool F8 = false>
 cudaError_t launch_pair_epi(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const float* bias, int M,
                             int N, int K, int* err, int num_sms, cudaStream_t st, const float* row_scale = nullptr,
-                            const float* col_scale = nullptr) {
+                            const float* col_scale = nullptr, const LnFuse& ln = LnFuse{}) {
   using Cfg = TcGemmPairCfg<BN>;
   auto kern = gemm_tc_pair_kernel<BN, EPI, F8>;
   static std::atomic<unsigned long long> attr_done{0};  // one per template instance
@@ -538,20 +616,20 @@ cudaError_t launch_pair_epi(const CUtensorMap& a, const CUtensorMap& b, const CU
   const int tiles = ((M + 2 * kBM - 1) / (2 * kBM)) * ((N + BN - 1) / BN);
   const int pairs = std::min(tiles, num_sms / 2);
   if (pairs < 1) return cudaErrorInvalidValue;
-  kern<<<2 * pairs, kThreads, Cfg::kSmemBytes, st>>>(a, b, c, bias, row_scale, col_scale, M, N, K, err);
+  kern<<<2 * pairs, kThreads, Cfg::kSmemBytes, st>>>(a, b, c, bias, row_scale, col_scale, M, N, K, err, ln);
   return cudaGetLastError();
 }
 
 template <bool F8>
 cudaError_t launch_any(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
                        const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st,
-                       const float* row_scale, const float* col_scale) {
+                       const float* row_scale, const float* col_scale, const LnFuse& ln = LnFuse{}) {
 #define REVO_GEMM_CASE(W, E)                                                                                 \
   if (bn == (W) && epi == (E)) return launch_bn_epi<W, E, F8>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, \
-                                                             col_scale);                                          \
+                                                             col_scale, ln);                                      \
   if (bn == ((W) | kTilePair) && epi == (E))                                                                 \
-    return launch_pair_epi<W, E, F8>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, col_scale);
-  if (!F8) {
+    return launch_pair_epi<W, E, F8>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, col_scale, ln);
+  if constexpr (!F8) {
     if (bn == 192 && epi == kEpiF32)
       return launch_bn_epi<192, kEpiF32, false>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, col_scale);
     if (bn == 192 && epi == kEpiResidF32)
@@ -560,6 +638,10 @@ cudaError_t launch_any(const CUtensorMap& a, const CUtensorMap& b, const CUtenso
     REVO_GEMM_CASE(256, kEpiF32)
     REVO_GEMM_CASE(128, kEpiResidF32)
     REVO_GEMM_CASE(256, kEpiResidF32)
+    REVO_GEMM_CASE(128, kEpiResidLn)
+    REVO_GEMM_CASE(256, kEpiResidLn)
+    REVO_GEMM_CASE(128, kEpiResidLn8)
+    REVO_GEMM_CASE(256, kEpiResidLn8)
   }
   REVO_GEMM_CASE(128, kEpiBf16)
   REVO_GEMM_CASE(256, kEpiBf16)
@@ -572,10 +654,19 @@ cudaError_t launch_any(const CUtensorMap& a, const CUtensorMap& b, const CUtenso
 }  // namespace
 
 cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
-                           const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st) {
+                           const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st,
+                           const LnFuse* ln) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   const bool bf16_out = epi == kEpiBf16 || epi == kEpiGeluBf16;
   if (K % kBK != 0 || N % (bf16_out ? 64 : 32) != 0) return cudaErrorInvalidValue;
+  if (epi == kEpiResidLn) {
+    // The fused LayerNorm: a whole row of x in one warp's registers (N <= 1024).
+    if (!ln || !ln->x || !ln->g || !ln->b || !ln->out || !ln->counters || (ln->mode == 2 && !ln->row_scale) ||
+        (ln->mode != 1 && ln->mode != 2) || N % 4 != 0 || N > 4 * 32 * kLnMaxVec || (bn & ~kTilePair) == 192)
+      return cudaErrorInvalidValue;
+    return launch_any<false>(a, b, c, bn, ln->mode == 2 ? kEpiResidLn8 : kEpiResidLn, bias, M, N, K, err, num_sms,
+                             st, nullptr, nullptr, *ln);
+  }
   return launch_any<false>(a, b, c, bn, epi, bias, M, N, K, err, num_sms, st, nullptr, nullptr);
 }
 

@@ -338,11 +338,12 @@ struct Fwd {
   int sms;
   bool tc;
   size_t e;  // activation element size
-  int extra_launches = 0;  // kernels beyond one per attention (none: the forward cuts no unit)
+  int launched = 0;  // kernels enqueued so far
 
   // `amap` / `cmap`: the A operand and output tensor maps (tensor-core path).
   cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M,
                      const CUtensorMap* cmap) {
+    ++launched;
     if (!tc) return launch_gemm_simt(epi, static_cast<const float*>(A), w.w32, w.b, out, ldo, M, w.out, w.in, st);
     int bn = pick_bn(M, w.out, sms);
     if (net->autotune && M > 0) {
@@ -354,6 +355,7 @@ struct Fwd {
 
   // FP8 Linear: A = the E4M3 LayerNorm output with its per-token scales.
   cudaError_t linear8(const CUtensorMap* amap, const LinearW& w, int epi, int M, const CUtensorMap* cmap) {
+    ++launched;
     int bn = pick_bn(M, w.out, sms);
     if (net->autotune && M > 0) {
       cudaError_t e = tuned_width(amap, w, epi, M, cmap, true, &bn);
@@ -441,78 +443,97 @@ struct Fwd {
     const CUtensorMap* h8;                   // E4M3 LayerNorm output (FP8 precision)
   };
 
-  // LayerNorm then a LayerNorm-fed Linear (qkv, fc1): in E4M3 with per-token
-  // and per-channel scales at FP8 precision, else from the bf16 / f32 LN output.
-  cudaError_t ln_linear(const float* x, const float* g, const float* bb, int d, int M, const LinearW& w, int epi,
-                        void* out, int ldo, const Maps& mp, const CUtensorMap* cmap, int fp8_bit) {
-    cudaError_t e;
-    if (net->precision == REVO_FP8 && (net->fp8_mask >> fp8_bit) & 1) {
-      if ((e = launch_layernorm_e4m3(x, g, bb, ws->h8, ws->h8_scale, M, d, st)) != cudaSuccess) return e;
-      return linear8(mp.h8, w, epi, M, cmap);
-    }
-    if ((e = launch_layernorm(x, g, bb, ws->h, M, d, tc, st)) != cudaSuccess) return e;
+  // FP8 precision: is the layer of bit `bit` (see Net::fp8_mask) an E4M3 layer?
+  bool fp8_layer(int bit) const { return net->precision == REVO_FP8 && ((net->fp8_mask >> bit) & 1); }
+
+  // The LayerNorm of x's first M rows in the format of the Linear that reads it
+  // (fp8 bit `bit`): E4M3 codes and per-token scales into h8 for an E4M3 layer,
+  // else bf16 (float32 on the SIMT path) into h.
+  cudaError_t layernorm(const float* x, const float* g, const float* bb, int d, int M, int bit) {
+    ++launched;
+    if (fp8_layer(bit)) return launch_layernorm_e4m3(x, g, bb, ws->h8, ws->h8_scale, M, d, st);
+    return launch_layernorm(x, g, bb, ws->h, M, d, tc, st);
+  }
+
+  // The Linear that reads the LayerNorm output (qkv, fc1, enc2dec, head).
+  cudaError_t from_ln(const LinearW& w, int epi, void* out, int ldo, int M, const Maps& mp, const CUtensorMap* cmap,
+                      int bit) {
+    if (fp8_layer(bit)) return linear8(mp.h8, w, epi, M, cmap);
     return linear(mp.h, ws->h, w, epi, out, ldo, M, cmap);
   }
 
-  cudaError_t block(const BlockW& b, int d, int heads, int M, const Segments& seg, const Maps& mp, bool dec) {
+  // A residual Linear x += A W^T + b (proj, fc2) followed by the LayerNorm
+  // (g, bb) of x for the Linear of fp8 bit `bit`, as two launches.  (The
+  // GEMM can also normalise each completed 128-row block in its epilogue,
+  // kEpiResidLn; at these widths that LayerNorm runs on one SM per row block
+  // with a few rows in flight and stalls the GEMM longer than the separate,
+  // HBM-bound LayerNorm launch takes, so the forward does not use it.)
+  cudaError_t resid_ln(const CUtensorMap* amap, const void* A, const LinearW& w, float* x, int d, int M,
+                       const CUtensorMap* cmap, const float* g, const float* bb, int bit) {
+    cudaError_t e = linear(amap, A, w, kEpiResidF32, x, d, M, cmap);
+    return e != cudaSuccess ? e : layernorm(x, g, bb, d, M, bit);
+  }
+
+  // What follows a block's fc2: the next block's LN1 (fp8 bit of its qkv) or
+  // the stack's final LayerNorm (bf16, read by a plain Linear).
+  struct NextLn {
+    const float *g, *b;
+    int bit;
+  };
+  static constexpr int kNoFp8 = 30;  // an fp8 bit no layer has
+
+  // One transformer block on rows [0, M) of x whose LN1 output is already in
+  // h / h8; leaves `next`'s LayerNorm of the block's output there.
+  cudaError_t block(const BlockW& b, int d, int heads, int M, const Segments& seg, const Maps& mp, bool dec,
+                    const NextLn& next) {
     cudaError_t e;
     const int bit = dec ? 2 : 0;
-    if ((e = ln_linear(ws->x, b.ln1g, b.ln1b, d, M, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, mp, mp.o_qkv,
-                       bit)) != cudaSuccess)
-      return e;
-    if (tc)
-    {
-      int nl = 1;
-      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st, nullptr, ws->sms, &nl);
-      extra_launches += nl - 1;
-    }
-    else
-      e = launch_attention_simt(static_cast<const float*>(ws->qkv), static_cast<float*>(ws->att), M, d, heads, seg,
-                                st);
-    if (e != cudaSuccess) return e;
-    if ((e = linear(mp.att, ws->att, b.proj, kEpiResidF32, ws->x, d, M, mp.o_x)) != cudaSuccess) return e;
-    if ((e = ln_linear(ws->x, b.ln2g, b.ln2b, d, M, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, mp, mp.o_mlp,
-                       bit + 1)) != cudaSuccess)
-      return e;
-    return linear(mp.mlp, ws->mlp, b.fc2, kEpiResidF32, ws->x, d, M, mp.o_x);
+    if ((e = from_ln(b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, M, mp, mp.o_qkv, bit)) != cudaSuccess) return e;
+    if ((e = attention(d, heads, M, seg, mp)) != cudaSuccess) return e;
+    if ((e = resid_ln(mp.att, ws->att, b.proj, ws->x, d, M, mp.o_x, b.ln2g, b.ln2b, bit + 1)) != cudaSuccess) return e;
+    if ((e = from_ln(b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, M, mp, mp.o_mlp, bit + 1)) != cudaSuccess) return e;
+    return resid_ln(mp.mlp, ws->mlp, b.fc2, ws->x, d, M, mp.o_x, next.g, next.b, next.bit);
+  }
+
+  cudaError_t attention(int d, int heads, int M, const Segments& seg, const Maps& mp) {
+    ++launched;
+    if (!tc)
+      return launch_attention_simt(static_cast<const float*>(ws->qkv), static_cast<float*>(ws->att), M, d, heads, seg,
+                                   st);
+    int nl = 1;
+    cudaError_t e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, seg, ws->err, st, nullptr, ws->sms, &nl);
+    launched += nl - 1;
+    return e;
   }
 
   // The last decoder block on the rows that reach the pixel head (Section
   // 3.4.1: the output is the target frame, the last frame of the final
-  // tubelet slot): LN1 and qkv on every token (keys and values of the whole
-  // request), attention with the final slot's queries only, then those rows
-  // are stacked (runs.dst: their row in the head output) and proj, LN2, fc1,
-  // fc2 run on them alone.  An exact saving: no other row reaches the head.
+  // tubelet slot): qkv on every token (keys and values of the whole request;
+  // LN1 is already in h / h8), attention with the final slot's queries only,
+  // then those rows are stacked (runs.dst: their row in the head output) and
+  // proj, LN2, fc1, fc2 run on them alone, leaving the final LayerNorm of the
+  // stacked rows in h.  An exact saving: no other row reaches the head.
   cudaError_t last_block(const BlockW& b, int d, int heads, int M, const Segments& seg, const Maps& mp,
                          const RowRuns& runs, const Maps& cm) {
     cudaError_t e;
-    if ((e = ln_linear(ws->x, b.ln1g, b.ln1b, d, M, b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, mp, mp.o_qkv,
-                       2)) != cudaSuccess)
-      return e;
+    if ((e = from_ln(b.qkv, tc ? kEpiBf16 : kEpiF32, ws->qkv, 3 * d, M, mp, mp.o_qkv, 2)) != cudaSuccess) return e;
     Segments q = seg;
-    q.queries = true;
-    for (int i = 0; i < seg.n; ++i) {
-      q.q_begin[i] = runs.src[i];
-      q.q_end[i] = runs.src[i] + (runs.dst[i + 1] - runs.dst[i]);
-    }
     if (tc) {
-      int nl = 1;
-      e = launch_attention_tc(*mp.qkv, ws->att, M, d, heads, q, ws->err, st, nullptr, ws->sms, &nl);
-      extra_launches += nl - 1;
-    } else {
-      e = launch_attention_simt(static_cast<const float*>(ws->qkv), static_cast<float*>(ws->att), M, d, heads, seg,
-                                st);
+      q.queries = true;
+      for (int i = 0; i < seg.n; ++i) {
+        q.q_begin[i] = runs.src[i];
+        q.q_end[i] = runs.src[i] + (runs.dst[i + 1] - runs.dst[i]);
+      }
     }
-    if (e != cudaSuccess) return e;
+    if ((e = attention(d, heads, M, q, mp)) != cudaSuccess) return e;
+    ++launched;
     if ((e = launch_gather_rows(ws->x, ws->att, static_cast<int>(this->e), d, runs, ws->xc, ws->attc, st)) !=
         cudaSuccess)
       return e;
     const int P = runs.dst[runs.n];
-    if ((e = linear(cm.att, ws->attc, b.proj, kEpiResidF32, ws->xc, d, P, cm.o_x)) != cudaSuccess) return e;
-    if ((e = ln_linear(ws->xc, b.ln2g, b.ln2b, d, P, b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, cm, cm.o_mlp, 3)) !=
-        cudaSuccess)
-      return e;
-    return linear(cm.mlp, ws->mlp, b.fc2, kEpiResidF32, ws->xc, d, P, cm.o_x);
+    if ((e = resid_ln(cm.att, ws->attc, b.proj, ws->xc, d, P, cm.o_x, b.ln2g, b.ln2b, 3)) != cudaSuccess) return e;
+    if ((e = from_ln(b.fc1, kEpiGeluBf16, ws->mlp, net->s.r * d, P, cm, cm.o_mlp, 3)) != cudaSuccess) return e;
+    return resid_ln(cm.mlp, ws->mlp, b.fc2, ws->xc, d, P, cm.o_x, net->dec_norm_g, net->dec_norm_b, kNoFp8);
   }
 };
 
@@ -645,13 +666,14 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
     // One launch for the batch, each request's arguments from the device table.
     std::vector<AssembleArgs> aa(n);
     for (int i = 0; i < n; ++i) aa[i] = args[i].assemble;
+    ++f.launched;
     if ((e = launch_assemble_batch(aa.data(), n, &dev_args[0].assemble, sizeof(JobArgs), st)) != cudaSuccess) return e;
   } else {
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i, ++f.launched)
       if ((e = launch_assemble(args[i].assemble, st)) != cudaSuccess) return e;
   }
   if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32, ws->x, s.D, M, &ws->o_x_enc)) != cudaSuccess) return e;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i, ++f.launched)
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.D, jobs[i].H / s.p, jobs[i].W / s.p,
                            s.slots(), args[i].taus, s.D, st, dev_args ? dev_args[i].taus : nullptr, ws->pe_enc,
                            ws->pe_rows)) != cudaSuccess)
@@ -661,12 +683,22 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
                            &ws->o_x_enc, &ws->o_qkv_enc, &ws->o_mlp_enc, &ws->m_h8_enc};
   const Fwd::Maps dec_maps{&ws->m_h_dec, &ws->m_att_dec, &ws->m_mlp_dec, &ws->m_qkv_dec,
                            &ws->o_x_dec, &ws->o_qkv_dec, &ws->o_mlp_dec, &ws->m_h8_dec};
-  for (const BlockW& b : net->enc)
-    if ((e = f.block(b, s.D, s.H, M, seg, enc_maps, false)) != cudaSuccess) return e;
-  if ((e = launch_layernorm(ws->x, net->enc_norm_g, net->enc_norm_b, ws->h, M, s.D, f.tc, st)) != cudaSuccess) return e;
+  // Encoder: LN1 of the first block; every later LayerNorm (each block's LN2,
+  // the next block's LN1, the encoder's final LN) follows the residual Linear
+  // before it.
+  if (s.L > 0) {
+    if ((e = f.layernorm(ws->x, net->enc[0].ln1g, net->enc[0].ln1b, s.D, M, 0)) != cudaSuccess) return e;
+  } else if ((e = f.layernorm(ws->x, net->enc_norm_g, net->enc_norm_b, s.D, M, Fwd::kNoFp8)) != cudaSuccess) {
+    return e;
+  }
+  for (int i = 0; i < s.L; ++i) {
+    const Fwd::NextLn next = i + 1 < s.L ? Fwd::NextLn{net->enc[i + 1].ln1g, net->enc[i + 1].ln1b, 0}
+                                         : Fwd::NextLn{net->enc_norm_g, net->enc_norm_b, Fwd::kNoFp8};
+    if ((e = f.block(net->enc[i], s.D, s.H, M, seg, enc_maps, false, next)) != cudaSuccess) return e;
+  }
   if ((e = f.linear(&ws->m_h_enc, ws->h, net->enc2dec, kEpiF32, ws->x, s.Dd, M, &ws->o_x_dec)) != cudaSuccess)
     return e;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i, ++f.launched)
     if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.Dd, jobs[i].H / s.p, jobs[i].W / s.p,
                            s.slots(), args[i].taus, s.Dd, st, dev_args ? dev_args[i].taus : nullptr, ws->pe_dec,
                            ws->pe_rows)) != cudaSuccess)
@@ -684,32 +716,29 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
   }
   if (f.tc && !encode_compact_maps(s, ws, patches)) return cudaErrorInvalidValue;
   const Fwd::Maps last_maps{&ws->c_h, &ws->c_att, &ws->c_mlp, nullptr, &ws->c_o_x, nullptr, &ws->c_o_mlp, &ws->c_h8};
-  for (int i = 0; i < s.Ld; ++i) {
-    const BlockW& b = net->dec[i];
-    if ((e = i + 1 < s.Ld ? f.block(b, s.Dd, s.Hd, M, seg, dec_maps, true)
-                          : f.last_block(b, s.Dd, s.Hd, M, seg, dec_maps, runs, last_maps)) != cudaSuccess)
-      return e;
+  // Decoder (check_shape: Ld >= 1), the same chaining; the last block leaves
+  // the final LayerNorm of the stacked rows in h.
+  if ((e = f.layernorm(ws->x, net->dec[0].ln1g, net->dec[0].ln1b, s.Dd, M, 2)) != cudaSuccess) return e;
+  for (int i = 0; i + 1 < s.Ld; ++i) {
+    const Fwd::NextLn next{net->dec[i + 1].ln1g, net->dec[i + 1].ln1b, 2};
+    if ((e = f.block(net->dec[i], s.Dd, s.Hd, M, seg, dec_maps, true, next)) != cudaSuccess) return e;
   }
+  if ((e = f.last_block(net->dec[s.Ld - 1], s.Dd, s.Hd, M, seg, dec_maps, runs, last_maps)) != cudaSuccess) return e;
 
-  // Final LN and pixel head on the stacked rows, then the blend per request.
-  if ((e = launch_layernorm(ws->xc, net->dec_norm_g, net->dec_norm_b, ws->h, patches, s.Dd, f.tc, st)) != cudaSuccess)
-    return e;
+  // Pixel head on the stacked rows, then the blend per request.
   if ((e = f.linear(&ws->c_h, ws->h, net->head, kEpiF32, ws->head, s.head_dim_out(), patches, &ws->c_o_head)) !=
       cudaSuccess)
     return e;
   if (dev_args) {
     std::vector<BlendArgs> bb(n);
     for (int i = 0; i < n; ++i) bb[i] = args[i].blend;
+    ++f.launched;
     if ((e = launch_blend_batch(bb.data(), n, &dev_args[0].blend, sizeof(JobArgs), st)) != cudaSuccess) return e;
   } else {
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i, ++f.launched)
       if ((e = launch_blend(args[i].blend, st)) != cudaSuccess) return e;
   }
-  // One kernel per step: per request 2 embeddings, and assemble and blend
-  // (one launch each for the whole batch with the device argument table);
-  // tubelet embedding, encoder LN, encoder->decoder, final LN, head; 7 per
-  // transformer block, 8 for the last (the row gather).
-  if (launches) *launches = 5 + 7 * (s.L + s.Ld) + 1 + 2 * n + (dev_args ? 2 : 2 * n) + f.extra_launches;
+  if (launches) *launches = f.launched;
   return cudaSuccess;
 }
 

@@ -75,6 +75,29 @@ float* op_attention_partial(size_t bytes) {
   return bufs[dev];
 }
 
+// The row-block counters of the step-level fused LayerNorm (one per device,
+// grown on demand, zeroed by every call on its stream).
+int* op_ln_counters(size_t count) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  static int* bufs[64] = {};
+  static size_t sizes[64] = {};
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!bufs[dev] || sizes[dev] < count) {
+    if (bufs[dev]) {
+      if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
+      cudaFree(bufs[dev]);
+      bufs[dev] = nullptr;
+      sizes[dev] = 0;
+    }
+    int* p = nullptr;
+    if (cudaMalloc(&p, count * sizeof(int)) != cudaSuccess) return nullptr;
+    bufs[dev] = p;
+    sizes[dev] = count;
+  }
+  return bufs[dev];
+}
+
 // The position embedding's column-part table of the step-level entry point,
 // one per device and width (built on first use).
 float* op_pe_table(int D, int rows) {
@@ -272,6 +295,50 @@ revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A
   }
   return cuda_status(launch_gemm_tc(ma, mb, mc, bn, epilogue, bias, M, N, K, err, device_sm_count(), st),
                      "revo_op_linear");
+}
+
+revo_status revo_op_linear_resid_ln(const void* A, const void* W, const float* bias, float* x, int M, int N, int K,
+                                    const float* gamma, const float* beta, void* ln_out, float* ln_row_scale,
+                                    int ln_fp8, int tile_n, void* stream) {
+  if (!A || !W || !x || !gamma || !beta || !ln_out || (ln_fp8 && !ln_row_scale) || M < 0 || N <= 0 || K <= 0) {
+    set_last_error("revo_op_linear_resid_ln: bad argument");
+    return REVO_EINVAL;
+  }
+  if (K % 64 || N % 32 || N > 1024 || (tile_n & ~REVO_TILE_PAIR) == 192) {
+    set_last_error("revo_op_linear_resid_ln: needs K %% 64 == 0, N %% 32 == 0, N <= 1024 and a 128 or 256 tile");
+    return REVO_EINVAL;
+  }
+  if (M == 0) return REVO_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool pair = (tile_n & REVO_TILE_PAIR) != 0;
+  const int width = (tile_n & ~REVO_TILE_PAIR) == 256 ? 256 : 128;
+  const int bn = pair ? (width | kTilePair) : width;
+  CUtensorMap ma, mb, mc;
+  if (!encode_tmap_bf16_2d(&ma, A, M, K, K, 128, 64) ||
+      !encode_tmap_bf16_2d(&mb, W, N, K, K, pair ? width / 2 : width, 64) ||
+      !encode_tmap_out_2d(&mc, x, true, M, N, N)) {
+    set_last_error("revo_op_linear_resid_ln: tensor map encoding failed (alignment?)");
+    return REVO_EINVAL;
+  }
+  int* err = op_error_word();
+  const size_t blocks = static_cast<size_t>(M + 127) / 128;
+  int* counters = op_ln_counters(blocks);
+  if (!err || !counters) {
+    set_last_error("revo_op_linear_resid_ln: no device scratch");
+    return REVO_ECUDA;
+  }
+  cudaError_t e = cudaMemsetAsync(counters, 0, blocks * sizeof(int), st);
+  if (e != cudaSuccess) return cuda_status(e, "revo_op_linear_resid_ln");
+  LnFuse ln{};
+  ln.x = x;
+  ln.g = gamma;
+  ln.b = beta;
+  ln.out = ln_out;
+  ln.row_scale = ln_row_scale;
+  ln.counters = counters;
+  ln.mode = ln_fp8 ? 2 : 1;
+  return cuda_status(launch_gemm_tc(ma, mb, mc, bn, kEpiResidLn, bias, M, N, K, err, device_sm_count(), st, &ln),
+                     "revo_op_linear_resid_ln");
 }
 
 revo_status revo_op_layernorm(const float* x, const float* gamma, const float* beta, void* out, int M, int D,

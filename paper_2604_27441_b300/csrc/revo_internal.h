@@ -18,6 +18,7 @@ enum Epilogue : int {
   kEpiBf16 = 1,      // store bf16
   kEpiGeluBf16 = 2,  // store bf16(gelu(.))
   kEpiResidF32 = 3,  // float32 out += .
+  kEpiResidLn = 4,   // float32 out += ., then the LayerNorm of every completed row block (LnFuse)
 };
 
 // GEMM tile widths: 128 or 256 output columns per tile of 128 rows (one CTA);
@@ -55,8 +56,22 @@ bool encode_tmap_u8_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64
 // kEpiResidF32 (the residual epilogue adds into it), bf16 otherwise.  `bn` is a
 // tile width (see kTilePair); `a` has 128-row boxes, `b` bn-row boxes, or
 // bn/2-row boxes for a pair width.
+// A LayerNorm fused after a residual GEMM (kEpiResidLn: x += A W^T + b): each
+// CTA counts the column tiles it has added into a 128-row block of x; the one
+// that completes the block normalises those rows (the standalone LayerNorm's
+// arithmetic, bit for bit) into `out`.
+struct LnFuse {
+  const float* x;     // the residual stream the GEMM adds into, [M][N] float32
+  const float* g;     // gain [N]
+  const float* b;     // shift [N]
+  void* out;          // bf16 [M][N] (mode 1) or E4M3 codes [M][N] (mode 2)
+  float* row_scale;   // mode 2: per-row scales [M]
+  int* counters;      // [ceil(M / 128)] zero between launches (the last CTA resets its own)
+  int mode;           // 1 bf16, 2 E4M3 with per-row scales
+};
 cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
-                           const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st);
+                           const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st,
+                           const LnFuse* ln = nullptr);
 // FP8 (E4M3) operands with per-row scales of A (`row_scale`, M entries: one per
 // token) and per-output-channel scales of W (`col_scale`, N entries):
 // Y = epilogue(row_scale[m] * col_scale[n] * (A8 W8^T)[m][n] + b[n]).  `a` and

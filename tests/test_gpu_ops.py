@@ -216,6 +216,67 @@ def test_layernorm_e4m3(M, D):
     assert (np.abs(deq - ref) <= bound).all()
 
 
+# ------------------------------------------- residual Linear + LayerNorm
+
+@pytest.mark.parametrize("M,N,K", [(1, 384, 384), (127, 768, 768), (300, 384, 1536), (1000, 768, 3072),
+                                   (4100, 768, 768), (1300, 320, 256)])
+@pytest.mark.parametrize("tile", [128, 256, 128 | 0x1000, 256 | 0x1000])
+@pytest.mark.parametrize("fp8", [False, True])
+def test_linear_resid_ln_equals_separate_launches(M, N, K, tile, fp8):
+    """The LayerNorm fused into the residual GEMM's epilogue (the CTA that adds
+    a row block's last column tile normalises the block) gives exactly what
+    the residual Linear then the standalone LayerNorm give: the same x, bit for
+    bit, and the same bf16 values or E4M3 codes and scales; and x and the
+    LayerNorm agree with the oracle (x + A W^T + b, then LN; eps 1e-6)."""
+    if (tile & 0xFFF) == 256 and N < 256:
+        tile = (tile & 0x1000) | 128
+    A = bf16(synth.normal(M + N, (M, K), 1.0))
+    W = bf16(synth.normal(M + N + 1, (N, K), 1.0 / np.sqrt(K)))
+    b = synth.normal(M + N + 2, (N,), 0.1)
+    x0 = synth.normal(M + N + 3, (M, N), 2.0) + 0.25
+    g = 1 + synth.normal(M + N + 4, (N,), 0.1)
+    beta = synth.normal(M + N + 5, (N,), 0.1)
+    Ad, Wd, bd, gd, betad = A.cuda(), W.cuda(), dev(b), dev(g), dev(beta)
+    x_sep, x_fused = dev(x0), dev(x0)
+    if fp8:
+        h_sep = torch.zeros((M, N), dtype=torch.uint8, device="cuda")
+        h_fused = torch.full((M, N), 0x7F, dtype=torch.uint8, device="cuda")
+        s_sep = torch.zeros(M, dtype=torch.float32, device="cuda")
+        s_fused = torch.full((M,), -1.0, dtype=torch.float32, device="cuda")
+    else:
+        h_sep = torch.zeros((M, N), dtype=torch.bfloat16, device="cuda")
+        h_fused = torch.full((M, N), float("nan"), dtype=torch.bfloat16, device="cuda")
+        s_sep = s_fused = None
+    R.op_linear(R.BF16, 3, Ad, Wd, bd, x_sep, M, N, K, tile)
+    if fp8:
+        R.op_layernorm_e4m3(x_sep, gd, betad, h_sep, s_sep, M, N)
+    else:
+        R.op_layernorm(x_sep, gd, betad, h_sep, M, N, 1)
+    R.op_linear_resid_ln(Ad, Wd, bd, x_fused, M, N, K, gd, betad, h_fused, s_fused, fp8, tile)
+    # A second call on the same buffers: the row-block counters start from zero again.
+    x_again, h_again = dev(x0), torch.empty_like(h_fused)
+    s_again = torch.empty_like(s_fused) if fp8 else None
+    R.op_linear_resid_ln(Ad, Wd, bd, x_again, M, N, K, gd, betad, h_again, s_again, fp8, tile)
+    torch.cuda.synchronize()
+    assert torch.equal(x_fused, x_sep) and torch.equal(x_again, x_sep)
+    assert torch.equal(h_fused.view(torch.uint8) if not fp8 else h_fused,
+                       h_sep.view(torch.uint8) if not fp8 else h_sep)
+    assert torch.equal(h_again.view(torch.uint8) if not fp8 else h_again,
+                       h_sep.view(torch.uint8) if not fp8 else h_sep)
+    if fp8:
+        assert torch.equal(s_fused, s_sep) and torch.equal(s_again, s_sep)
+    x_ref = x0.astype(np.float64) + O.linear(f64(A), f64(W), b.astype(np.float64))
+    np.testing.assert_allclose(f64(x_fused), x_ref, rtol=1e-5, atol=2e-4)
+    ln_ref = O.layer_norm(x_ref, g.astype(np.float64), beta.astype(np.float64))
+    if fp8:
+        s = s_fused.cpu().numpy().astype(np.float64)
+        deq = F8.dequantise_rows(h_fused.cpu().numpy(), s)
+        bound = np.maximum(np.abs(ln_ref) * 2.0 ** -4, s[:, None] * 2.0 ** -10) * (1 + 1e-3) + 2e-4
+        assert (np.abs(deq - ln_ref) <= bound).all()
+    else:
+        np.testing.assert_allclose(f64(h_fused), ln_ref, rtol=8e-3, atol=8e-3)
+
+
 @pytest.mark.parametrize("M,N,K,bn", [(300, 256, 768, 128), (1000, 2304, 768, 256), (517, 1536, 384, 256),
                                       (3600, 3072, 768, 0), (1, 64, 128, 128), (129, 384, 384, 128)])
 @pytest.mark.parametrize("epi", [1, 2])
