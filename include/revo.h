@@ -352,6 +352,25 @@ REVO_API revo_status revo_op_linear(revo_precision precision, int epilogue, cons
                            const float* bias, void* out, int M, int N, int K, int tile_n, void* stream);
 
 /*
+ * The tubelet (or encoder -> decoder) Linear with the position embedding
+ * added in its epilogue, in one launch (Section 3.4.1: token embedding plus
+ * the sinusoidal embedding of temporal distance, patch row and patch column):
+ *   out[m][n] = (sum_k A[m][k] W[n][k] + bias[n]) + pe(m)[n]
+ * for the M = slots * grid_h * grid_w tokens of one request (token m is slot
+ * m / (grid_h grid_w), patch row and column from m % (grid_h grid_w), as in
+ * revo_op_add_position, whose values pe(m) are; the result equals
+ * revo_op_linear(REVO_BF16, epilogue 0) followed by revo_op_add_position, bit
+ * for bit).  A [M][K], W [N][K] bf16, bias [N] (may be NULL), out float32
+ * [M][N], device; taus host [slots].  N a multiple of 192 up to 1024, K % 64
+ * == 0, slots <= 8; tile_n as for revo_op_linear (192 on single tiles).  Uses
+ * a per-device scratch of token positions (one call at a time per device).
+ * Errors: REVO_EINVAL, REVO_ECUDA.
+ */
+REVO_API revo_status revo_op_linear_pe(const void* A, const void* W, const float* bias, float* out, int slots,
+                                       int grid_h, int grid_w, int N, int K, const int* taus, int tile_n,
+                                       void* stream);
+
+/*
  * A residual Linear with the LayerNorm that follows it, in one launch (the
  * transformer block's "x = x + proj(att); h = LN2(x)" and
  * "x = x + fc2(mlp); h = LN1'(x)" steps, Section 3.4.1):

@@ -113,6 +113,7 @@ _SIGS = {
     "revo_op_linear": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                  C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "revo_op_layernorm": (C.c_int, [C.c_void_p] * 4 + [C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "revo_op_linear_pe": (C.c_int, [C.c_void_p] * 4 + [C.c_int] * 5 + [C.POINTER(C.c_int), C.c_int, C.c_void_p]),
     "revo_op_linear_resid_ln": (C.c_int, [C.c_void_p] * 4 + [C.c_int] * 3 + [C.c_void_p] * 4 + [C.c_int, C.c_int,
                                                                                                C.c_void_p]),
     "revo_op_attention": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
@@ -224,6 +225,14 @@ def op_depth_stats_noalloc(depth, height, width, pitch_bytes, mu_sigma, stream=N
 def op_linear(precision, epilogue, A, W, bias, out, M, N, K, tile_n=0, stream=None):
     return _check(lib().revo_op_linear(precision, epilogue, ptr(A), ptr(W), ptr(bias), ptr(out), M, N, K, tile_n,
                                        _stream(stream)), "revo_op_linear")
+
+
+def op_linear_pe(A, W, bias, out, slots, grid_h, grid_w, N, K, taus, tile_n=0, stream=None):
+    """out = A W^T + bias + the position embedding of one request's tokens, in
+    one tensor-core launch (the same floats as op_linear then op_add_position)."""
+    t = (C.c_int * max(1, len(taus)))(*[int(v) for v in taus])
+    return _check(lib().revo_op_linear_pe(ptr(A), ptr(W), ptr(bias), ptr(out), slots, grid_h, grid_w, N, K, t,
+                                          tile_n, _stream(stream)), "revo_op_linear_pe")
 
 
 def op_linear_resid_ln(A, W, bias, x, M, N, K, gamma, beta, ln_out, ln_row_scale=None, ln_fp8=False, tile_n=0,

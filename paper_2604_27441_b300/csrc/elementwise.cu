@@ -123,6 +123,7 @@ REVO_DEVI void assemble16_body(const AssembleArgs& a) {
   const int f = static_cast<int>(ft / Hp);
   const int s = f / T, t = f % T;
   const size_t n = static_cast<size_t>(s * Hp + ty) * Wp + tx;
+  if (a.pe_pos && t == 0 && lane == 0) a.pe_pos[n] = make_int2(a.taus[s], (ty << 16) | tx);
   const size_t K = static_cast<size_t>(T) * C * 256;
   const uint8_t* src = static_cast<const uint8_t*>(a.frames[f]) + static_cast<size_t>(ty * 16 + y) * a.pitch[f];
   float v[3][8];
@@ -603,7 +604,7 @@ __global__ void f32_to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16* 
 
 cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st, const AssembleArgs* dev) {
   if (a.T <= 0 || a.F % a.T != 0 || a.p <= 0 || a.p > 16 || a.H % a.p || a.W % a.p || a.F > kMaxRefs + 1 ||
-      (a.C != 1 && a.C != 3))
+      (a.C != 1 && a.C != 3) || (a.pe_pos && a.p != 16))
     return cudaErrorInvalidValue;
   if (a.p == 16) {
     const long long threads = static_cast<long long>(a.F) * (a.H / 16) * (a.W / 16) * 32;  // a warp per token-frame
@@ -658,15 +659,40 @@ cudaError_t launch_blend_batch(const BlendArgs* host, int n, const BlendArgs* de
   return cudaGetLastError();
 }
 
+bool pe_omega(int D, float* omega) {
+  const int part = D / 3;
+  if (D <= 0 || D % 192 != 0 || part / 2 > 128) return false;
+  for (int i = 0; i < part / 2; ++i) omega[i] = static_cast<float>(pow(10000.0, -2.0 * i / part));
+  return true;
+}
+
 namespace {
 bool pe_args(PeArgs* a, int D) {
   a->D = D;
   a->part = D / 3;
-  if (D % 192 != 0 || a->part / 2 > 128) return false;
-  for (int i = 0; i < a->part / 2; ++i) a->omega[i] = static_cast<float>(pow(10000.0, -2.0 * i / a->part));
-  return true;
+  return pe_omega(D, a->omega);
+}
+
+// One thread per token of one request.
+__global__ void pe_positions_kernel(int2* __restrict__ pe_pos, int Hp, int Wp, int n, const __grid_constant__ PeArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int hw = Hp * Wp;
+  const int t = i % hw;
+  pe_pos[i] = make_int2(a.taus[i / hw], ((t / Wp) << 16) | (t % Wp));
 }
 }  // namespace
+
+cudaError_t launch_pe_positions(int2* pe_pos, int Hp, int Wp, int slots, const int* taus, cudaStream_t st) {
+  if (Hp < 0 || Wp < 0 || Hp > 0xFFFF || Wp > 0xFFFF || slots < 0 || slots > 8) return cudaErrorInvalidValue;
+  const long long n = static_cast<long long>(slots) * Hp * Wp;
+  if (n == 0) return cudaSuccess;
+  if (n > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+  PeArgs a{};
+  for (int s = 0; s < slots; ++s) a.taus[s] = taus[s];
+  pe_positions_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(pe_pos, Hp, Wp, static_cast<int>(n), a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pe_table(float* tab, int rows, int D, cudaStream_t st) {
   PeArgs a{};

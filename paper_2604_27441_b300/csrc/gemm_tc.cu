@@ -126,7 +126,7 @@ REVO_DEVI uint32_t pack_bf16_pair(uint64_t v) {
   return pack_bf16x2(lo, hi);
 }
 
-// kEpiResidLn with LnFuse mode 2 (E4M3 LayerNorm output): a kernel template
+// kEpiResidLn with EpiAux mode 2 (E4M3 LayerNorm output): a kernel template
 // argument only, chosen by launch_gemm_tc from the mode.
 constexpr int kEpiResidLn8 = 5;
 __host__ __device__ constexpr bool epi_resid(int epi) { return epi == kEpiResidF32 || epi == kEpiResidLn || epi == kEpiResidLn8; }
@@ -134,11 +134,48 @@ __host__ __device__ constexpr bool epi_ln(int epi) { return epi == kEpiResidLn |
 
 // One epilogue chunk: 32 rows (this warp's lanes) x 128 bytes of output
 // (32 f32 columns or 64 bf16 columns) starting at tile column `c0`.
+// The position embedding's values at columns q .. q + 31 of a part for an
+// integer position beyond the table (a large temporal distance): the same
+// float32 sincosf of pos * w_i the table holds.  Out of line: rarely taken.
+__device__ __noinline__ void pe_chunk_computed(const EpiAux& aux, int pos, int q, float* e) {
+  const int half = aux.pe_part / 2;
+  for (int w = 0; w < 32; ++w) {
+    const int i = (q + w) % half;
+    float sv, cv;
+    sincosf(static_cast<float>(pos) * __ldg(aux.pe_omega + i), &sv, &cv);
+    e[w] = q + w < half ? sv : cv;
+  }
+}
+
+// kEpiF32Pe: adds the position embedding of row `row` at columns col ..
+// col + 31 (one part of it) to the 16 packed pairs v.
+REVO_DEVI void add_pe_chunk(uint64_t (&v)[16], const EpiAux& aux, int row, int M, int col) {
+  const int2 d = row < M ? __ldg(aux.pe_pos + row) : make_int2(0, 0);
+  const int which = col / aux.pe_part;
+  const int q = col - which * aux.pe_part;
+  const int pos = which == 0 ? d.x : which == 1 ? (d.y >> 16) : (d.y & 0xFFFF);
+  if (pos >= 0 && pos < aux.pe_rows) {
+    const float4* src = reinterpret_cast<const float4*>(aux.pe_tab + static_cast<size_t>(pos) * aux.pe_part + q);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float4 t = __ldg(src + k);
+      v[2 * k] = add2(v[2 * k], pk2(t.x, t.y));
+      v[2 * k + 1] = add2(v[2 * k + 1], pk2(t.z, t.w));
+    }
+  } else {
+    float e[32];
+    pe_chunk_computed(aux, pos, q, e);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = add2(v[i], pk2(e[2 * i], e[2 * i + 1]));
+  }
+}
+
 template <int EPI, bool F8>
 REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, int n0, int c0, uint8_t* chunk,
-                              const CUtensorMap* map, int row0, int lane, float rs, const float* __restrict__ cs) {
+                              const CUtensorMap* map, int row0, int lane, float rs, const float* __restrict__ cs,
+                              const EpiAux& aux, int M) {
   uint4 pieces[8];
-  if (EPI == kEpiF32 || epi_resid(EPI)) {
+  if (EPI == kEpiF32 || EPI == kEpiF32Pe || epi_resid(EPI)) {
     uint32_t r[32];
     tmem_ld32(taddr + c0, r);
     tmem_wait_ld();
@@ -147,6 +184,7 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
     for (int i = 0; i < 16; ++i) v[i] = pk2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
     if (F8) apply_scales(v, rs, cs, n0 + c0);
     add_bias(v, bias, n0 + c0);
+    if (EPI == kEpiF32Pe) add_pe_chunk(v, aux, row0 + lane, M, n0 + c0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       float a, b, c, d;
@@ -194,7 +232,7 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
 // The rows of one completed row block, R at a time per epilogue warp (warp e
 // takes rows e, e + 8, ...), NV float4 of a row per lane.
 template <int OUT, int NV, int R>
-REVO_DEVI void ln_block_rows(const LnFuse& ln, int m0, int rows, int N, int e, int lane) {
+REVO_DEVI void ln_block_rows(const EpiAux& ln, int m0, int rows, int N, int e, int lane) {
   for (int r = e; r < rows; r += R * kEpiWarps)
     ln_rows<OUT, true, NV, R>(ln.x, ln.g, ln.b, ln.out, ln.row_scale, m0 + r, kEpiWarps, m0 + rows, N, lane);
 }
@@ -209,7 +247,7 @@ REVO_DEVI void ln_block_rows(const LnFuse& ln, int m0, int rows, int N, int e, i
 // bounded (a failed wait leaves the rows alone; the error word reports it).
 // `phase`: the parity of this CTA's counted tiles, flipped here.
 template <int OUT>
-REVO_DEVI void ln_after_tile(const LnFuse& ln, int m0, int M, int N, int n_tiles, int e, int lane, int* flag,
+REVO_DEVI void ln_after_tile(const EpiAux& ln, int m0, int M, int N, int n_tiles, int e, int lane, int* flag,
                              uint64_t* ln_in, uint64_t* ln_out, uint32_t& phase, int* err) {
   if (m0 >= M) return;  // a pair tile's rows past the end: no block, no count (same in every warp)
   if (lane == 0) {
@@ -249,12 +287,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const float* __restrict__ bias,
                    const float* __restrict__ row_scale, const float* __restrict__ col_scale, int M, int N, int K,
-                   int* err, const __grid_constant__ LnFuse ln) {
+                   int* err, const __grid_constant__ EpiAux ln) {
   using Cfg = TcGemmCfg<BN>;
   constexpr int S = Cfg::kStages;
   constexpr uint32_t kIdesc = F8 ? idesc_e4m3(kBM, BN) : idesc_bf16(kBM, BN);
   constexpr int kKe = F8 ? kBK8 : kBK;  // K elements per stage
-  constexpr int kChunkCols = (EPI == kEpiF32 || epi_resid(EPI)) ? 32 : 64;
+  constexpr int kChunkCols = (EPI == kEpiF32 || EPI == kEpiF32Pe || epi_resid(EPI)) ? 32 : 64;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -381,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
       for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += kChunkCols) {
         if (n0 + c0 >= N) break;
-        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale);
+        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale, ln, M);
       }
       tc_fence_before();
       __syncwarp();
@@ -425,12 +463,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmC, const float* __restrict__ bias,
                         const float* __restrict__ row_scale, const float* __restrict__ col_scale, int M, int N, int K,
-                        int* err, const __grid_constant__ LnFuse ln) {
+                        int* err, const __grid_constant__ EpiAux ln) {
   using Cfg = TcGemmPairCfg<BN>;
   constexpr int S = Cfg::kStages;
   constexpr uint32_t kIdesc = F8 ? idesc_e4m3(2 * kBM, BN) : idesc_bf16(2 * kBM, BN);
   constexpr int kKe = F8 ? kBK8 : kBK;
-  constexpr int kChunkCols = (EPI == kEpiF32 || epi_resid(EPI)) ? 32 : 64;
+  constexpr int kChunkCols = (EPI == kEpiF32 || EPI == kEpiF32Pe || epi_resid(EPI)) ? 32 : 64;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -564,7 +602,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll 1
       for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2) && m0 + q * 32 < M; c0 += kChunkCols) {
         if (n0 + c0 >= N) break;
-        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale);
+        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale, ln, M);
       }
       tc_fence_before();
       __syncwarp();
@@ -592,7 +630,7 @@ namespace {
 template <int BN, int EPI, bool F8 = false>
 cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const float* bias, int M,
                           int N, int K, int* err, int num_sms, cudaStream_t st, const float* row_scale = nullptr,
-                          const float* col_scale = nullptr, const LnFuse& ln = LnFuse{}) {
+                          const float* col_scale = nullptr, const EpiAux& ln = EpiAux{}) {
   using Cfg = TcGemmCfg<BN>;
   auto kern = gemm_tc_kernel<BN, EPI, F8>;
   static std::atomic<unsigned long long> attr_done{0};  // one per template instance
@@ -607,7 +645,7 @@ cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const CUte
 template <int BN, int EPI, bool F8 = false>
 cudaError_t launch_pair_epi(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const float* bias, int M,
                             int N, int K, int* err, int num_sms, cudaStream_t st, const float* row_scale = nullptr,
-                            const float* col_scale = nullptr, const LnFuse& ln = LnFuse{}) {
+                            const float* col_scale = nullptr, const EpiAux& ln = EpiAux{}) {
   using Cfg = TcGemmPairCfg<BN>;
   auto kern = gemm_tc_pair_kernel<BN, EPI, F8>;
   static std::atomic<unsigned long long> attr_done{0};  // one per template instance
@@ -623,7 +661,7 @@ cudaError_t launch_pair_epi(const CUtensorMap& a, const CUtensorMap& b, const CU
 template <bool F8>
 cudaError_t launch_any(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
                        const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st,
-                       const float* row_scale, const float* col_scale, const LnFuse& ln = LnFuse{}) {
+                       const float* row_scale, const float* col_scale, const EpiAux& ln = EpiAux{}) {
 #define REVO_GEMM_CASE(W, E)                                                                                 \
   if (bn == (W) && epi == (E)) return launch_bn_epi<W, E, F8>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, \
                                                              col_scale, ln);                                      \
@@ -642,6 +680,10 @@ cudaError_t launch_any(const CUtensorMap& a, const CUtensorMap& b, const CUtenso
     REVO_GEMM_CASE(256, kEpiResidLn)
     REVO_GEMM_CASE(128, kEpiResidLn8)
     REVO_GEMM_CASE(256, kEpiResidLn8)
+    if (bn == 192 && epi == kEpiF32Pe)
+      return launch_bn_epi<192, kEpiF32Pe, false>(a, b, c, bias, M, N, K, err, num_sms, st, row_scale, col_scale, ln);
+    REVO_GEMM_CASE(128, kEpiF32Pe)
+    REVO_GEMM_CASE(256, kEpiF32Pe)
   }
   REVO_GEMM_CASE(128, kEpiBf16)
   REVO_GEMM_CASE(256, kEpiBf16)
@@ -655,7 +697,7 @@ cudaError_t launch_any(const CUtensorMap& a, const CUtensorMap& b, const CUtenso
 
 cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
                            const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st,
-                           const LnFuse* ln) {
+                           const EpiAux* ln) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   const bool bf16_out = epi == kEpiBf16 || epi == kEpiGeluBf16;
   if (K % kBK != 0 || N % (bf16_out ? 64 : 32) != 0) return cudaErrorInvalidValue;
@@ -667,6 +709,13 @@ cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUt
     return launch_any<false>(a, b, c, bn, ln->mode == 2 ? kEpiResidLn8 : kEpiResidLn, bias, M, N, K, err, num_sms,
                              st, nullptr, nullptr, *ln);
   }
+  if (epi == kEpiF32Pe) {
+    if (!ln || !ln->pe_pos || !ln->pe_tab || !ln->pe_omega || ln->pe_part <= 0 || ln->pe_part % 64 != 0 ||
+        N != 3 * ln->pe_part || ln->pe_rows < 0)
+      return cudaErrorInvalidValue;
+    return launch_any<false>(a, b, c, bn, epi, bias, M, N, K, err, num_sms, st, nullptr, nullptr, *ln);
+  }
+  if (epi != kEpiF32 && epi != kEpiBf16 && epi != kEpiGeluBf16 && epi != kEpiResidF32) return cudaErrorInvalidValue;
   return launch_any<false>(a, b, c, bn, epi, bias, M, N, K, err, num_sms, st, nullptr, nullptr);
 }
 

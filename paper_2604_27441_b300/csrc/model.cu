@@ -238,8 +238,12 @@ void net_destroy(Net* n) {
 }
 
 namespace {
+// Rows of the position-embedding tables: every patch row and column of the
+// largest frame, and temporal distances up to 63 (larger ones are computed).
+int pe_table_rows(int max_wp) { return max_wp > 64 ? max_wp : 64; }
+
 struct WsLayout {
-  size_t tok, x, h, qkv, att, mlp, head, xc, attc, pe_enc, pe_dec, err, h8, h8s, part, total;
+  size_t tok, x, h, qkv, att, mlp, head, xc, attc, pe_enc, pe_dec, pe_om, pe_pos, err, h8, h8s, part, total;
 };
 WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_seg, int max_wp) {
   const size_t e = precision != REVO_FP32 ? 2 : 4;
@@ -260,8 +264,11 @@ WsLayout ws_layout(const NetShape& s, int precision, int cap, int capp, int max_
   l.head = put(static_cast<size_t>(capp) * s.head_dim_out() * 4);
   l.xc = put(static_cast<size_t>(capp) * s.Dd * 4);
   l.attc = put(static_cast<size_t>(capp) * s.Dd * e);
-  l.pe_enc = put(static_cast<size_t>(max_wp) * (s.D / 3) * 4);
-  l.pe_dec = put(static_cast<size_t>(max_wp) * (s.Dd / 3) * 4);
+  const int pe_rows = pe_table_rows(max_wp);
+  l.pe_enc = put(static_cast<size_t>(pe_rows) * (s.D / 3) * 4);
+  l.pe_dec = put(static_cast<size_t>(pe_rows) * (s.Dd / 3) * 4);
+  l.pe_om = put(2 * 128 * 4);
+  l.pe_pos = put(static_cast<size_t>(cap) * sizeof(int2));
   l.err = put(256);
   if (precision == REVO_FP8) {
     l.h8 = put(static_cast<size_t>(cap) * D);
@@ -305,9 +312,15 @@ Workspace* workspace_create(const NetShape& s, int precision, int cap_tokens, in
   w->attc = base + l.attc;
   w->pe_enc = reinterpret_cast<float*>(base + l.pe_enc);
   w->pe_dec = reinterpret_cast<float*>(base + l.pe_dec);
-  w->pe_rows = max_wp;
-  if (launch_pe_table(w->pe_enc, max_wp, s.D, 0) != cudaSuccess ||
-      launch_pe_table(w->pe_dec, max_wp, s.Dd, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  w->pe_rows = pe_table_rows(max_wp);
+  w->pe_om_enc = reinterpret_cast<float*>(base + l.pe_om);
+  w->pe_om_dec = w->pe_om_enc + 128;
+  w->pe_pos = reinterpret_cast<int2*>(base + l.pe_pos);
+  float om[2][128] = {};
+  if (!pe_omega(s.D, om[0]) || !pe_omega(s.Dd, om[1]) ||
+      cudaMemcpy(w->pe_om_enc, om, sizeof(om), cudaMemcpyHostToDevice) != cudaSuccess ||
+      launch_pe_table(w->pe_enc, w->pe_rows, s.D, 0) != cudaSuccess ||
+      launch_pe_table(w->pe_dec, w->pe_rows, s.Dd, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
     cudaFree(base);
     delete w;
     *err = "position embedding tables failed";
@@ -341,16 +354,17 @@ struct Fwd {
   int launched = 0;  // kernels enqueued so far
 
   // `amap` / `cmap`: the A operand and output tensor maps (tensor-core path).
+  // `aux`: the operands of a fused epilogue (kEpiF32Pe; tile choice as kEpiF32).
   cudaError_t linear(const CUtensorMap* amap, const void* A, const LinearW& w, int epi, void* out, int ldo, int M,
-                     const CUtensorMap* cmap) {
+                     const CUtensorMap* cmap, const EpiAux* aux = nullptr) {
     ++launched;
     if (!tc) return launch_gemm_simt(epi, static_cast<const float*>(A), w.w32, w.b, out, ldo, M, w.out, w.in, st);
     int bn = pick_bn(M, w.out, sms);
     if (net->autotune && M > 0) {
-      cudaError_t e = tuned_width(amap, w, epi, M, cmap, false, &bn);
+      cudaError_t e = tuned_width(amap, w, epi == kEpiF32Pe ? kEpiF32 : epi, M, cmap, false, &bn);
       if (e != cudaSuccess) return e;
     }
-    return launch(amap, w, epi, M, false, bn, cmap);
+    return launch(amap, w, epi, M, false, bn, cmap, aux);
   }
 
   // FP8 Linear: A = the E4M3 LayerNorm output with its per-token scales.
@@ -366,13 +380,13 @@ struct Fwd {
 
   // One launch of tile width bn (see kTilePair) writing through `dst`.
   cudaError_t launch(const CUtensorMap* amap, const LinearW& w, int epi, int M, bool f8, int bn,
-                     const CUtensorMap* dst) {
+                     const CUtensorMap* dst, const EpiAux* aux = nullptr) {
     const int rows = (bn & kTilePair) ? (bn & ~kTilePair) / 2 : bn;  // W rows per CTA and tile
     if (f8)
       return launch_gemm_tc_fp8(*amap, rows == 256 ? w.map8_256 : rows == 128 ? w.map8_128 : w.map8_64, *dst, bn,
                                 epi, w.b, ws->h8_scale, w.w8_scale, M, w.out, w.in, ws->err, sms, st);
     return launch_gemm_tc(*amap, rows == 256 ? w.map256 : rows == 128 ? w.map128 : w.map64, *dst, bn, epi, w.b, M,
-                          w.out, w.in, ws->err, sms, st);
+                          w.out, w.in, ws->err, sms, st, aux);
   }
 
   // The autotuner's choice for this shape.  While serving (tuning == false)
@@ -581,6 +595,17 @@ bool encode_compact_maps(const NetShape& s, Workspace* ws, int P) {
 
 namespace {
 
+// The position-embedding operands of the embedding GEMMs at width D.
+EpiAux pe_aux(const Workspace* ws, const float* tab, const float* omega, int D) {
+  EpiAux a{};
+  a.pe_pos = ws->pe_pos;
+  a.pe_tab = tab;
+  a.pe_omega = omega;
+  a.pe_rows = ws->pe_rows;
+  a.pe_part = D / 3;
+  return a;
+}
+
 // Token segments (one per request) and the patch total; false if a size is invalid.
 bool batch_segments(const NetShape& s, const PlaneJob* jobs, int n, Segments* seg, int* patches) {
   seg->n = n;
@@ -624,6 +649,11 @@ cudaError_t prepare_job_args(const Net* net, const Workspace* ws, const PlaneJob
     a.H = jobs[i].H;
     a.W = jobs[i].W;
     a.out_bf16 = tc;
+    if (tc) {
+      // Token positions for the position embedding in the embedding GEMMs.
+      a.pe_pos = ws->pe_pos + seg.start[i];
+      for (int t = 0; t < 8; ++t) a.taus[t] = jobs[i].taus[t];
+    }
     BlendArgs& bl = j.blend;
     bl.C = s.C;
     bl.p = s.p;
@@ -672,12 +702,21 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
     for (int i = 0; i < n; ++i, ++f.launched)
       if ((e = launch_assemble(args[i].assemble, st)) != cudaSuccess) return e;
   }
-  if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32, ws->x, s.D, M, &ws->o_x_enc)) != cudaSuccess) return e;
-  for (int i = 0; i < n; ++i, ++f.launched)
-    if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.D, jobs[i].H / s.p, jobs[i].W / s.p,
-                           s.slots(), args[i].taus, s.D, st, dev_args ? dev_args[i].taus : nullptr, ws->pe_enc,
-                           ws->pe_rows)) != cudaSuccess)
+  // Tubelet embedding + position embedding: on the tensor-core path the
+  // embedding is added in the GEMM's epilogue (token positions from the
+  // assemble kernel), else by a pass per request.
+  if (f.tc) {
+    const EpiAux pe = pe_aux(ws, ws->pe_enc, ws->pe_om_enc, s.D);
+    if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32Pe, ws->x, s.D, M, &ws->o_x_enc, &pe)) != cudaSuccess)
       return e;
+  } else {
+    if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32, ws->x, s.D, M, &ws->o_x_enc)) != cudaSuccess) return e;
+    for (int i = 0; i < n; ++i, ++f.launched)
+      if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.D, jobs[i].H / s.p, jobs[i].W / s.p,
+                             s.slots(), args[i].taus, s.D, st, dev_args ? dev_args[i].taus : nullptr, ws->pe_enc,
+                             ws->pe_rows)) != cudaSuccess)
+        return e;
+  }
 
   const Fwd::Maps enc_maps{&ws->m_h_enc, &ws->m_att_enc, &ws->m_mlp_enc, &ws->m_qkv_enc,
                            &ws->o_x_enc, &ws->o_qkv_enc, &ws->o_mlp_enc, &ws->m_h8_enc};
@@ -696,13 +735,21 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
                                          : Fwd::NextLn{net->enc_norm_g, net->enc_norm_b, Fwd::kNoFp8};
     if ((e = f.block(net->enc[i], s.D, s.H, M, seg, enc_maps, false, next)) != cudaSuccess) return e;
   }
-  if ((e = f.linear(&ws->m_h_enc, ws->h, net->enc2dec, kEpiF32, ws->x, s.Dd, M, &ws->o_x_dec)) != cudaSuccess)
-    return e;
-  for (int i = 0; i < n; ++i, ++f.launched)
-    if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.Dd, jobs[i].H / s.p, jobs[i].W / s.p,
-                           s.slots(), args[i].taus, s.Dd, st, dev_args ? dev_args[i].taus : nullptr, ws->pe_dec,
-                           ws->pe_rows)) != cudaSuccess)
+  // Encoder -> decoder Linear + the decoder's position embedding (the same way).
+  if (f.tc) {
+    const EpiAux pe = pe_aux(ws, ws->pe_dec, ws->pe_om_dec, s.Dd);
+    if ((e = f.linear(&ws->m_h_enc, ws->h, net->enc2dec, kEpiF32Pe, ws->x, s.Dd, M, &ws->o_x_dec, &pe)) !=
+        cudaSuccess)
       return e;
+  } else {
+    if ((e = f.linear(&ws->m_h_enc, ws->h, net->enc2dec, kEpiF32, ws->x, s.Dd, M, &ws->o_x_dec)) != cudaSuccess)
+      return e;
+    for (int i = 0; i < n; ++i, ++f.launched)
+      if ((e = launch_add_pe(ws->x + static_cast<size_t>(seg.start[i]) * s.Dd, jobs[i].H / s.p, jobs[i].W / s.p,
+                             s.slots(), args[i].taus, s.Dd, st, dev_args ? dev_args[i].taus : nullptr, ws->pe_dec,
+                             ws->pe_rows)) != cudaSuccess)
+        return e;
+  }
   // The final slot's rows of each request, stacked in request order: the rows
   // the last decoder block, the final LN and the pixel head work on (the head
   // output is then in the order the blend reads it).

@@ -95,11 +95,14 @@ struct Workspace {
   // The last decoder block's rows (the final slot of each request, stacked):
   float* xc = nullptr;    // [cap_patches][D'] residual stream
   void* attc = nullptr;   // [cap_patches][D'] attention output
-  // The position embedding's row / column part at patch positions
-  // 0 .. pe_rows-1, at the encoder and the decoder width (launch_pe_table).
+  // The position embedding's part at integer positions 0 .. pe_rows-1, at
+  // the encoder and the decoder width (launch_pe_table).
   float* pe_enc = nullptr;
   float* pe_dec = nullptr;
   int pe_rows = 0;
+  float* pe_om_enc = nullptr;  // the parts' frequencies at the two widths
+  float* pe_om_dec = nullptr;
+  int2* pe_pos = nullptr;      // [cap] each token's temporal distance and patch position (assemble writes it)
   uint8_t* h8 = nullptr;  // [cap][max width] E4M3 LayerNorm output (FP8 precision)
   float* h8_scale = nullptr;  // [cap] its per-token scales
   int sms = 0;

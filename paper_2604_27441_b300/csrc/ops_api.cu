@@ -51,51 +51,52 @@ int* op_error_word() {
   return g_err_word[dev];
 }
 
-// The partial-result scratch of the step-level attention (one per device,
-// grown on demand; calls on one device run in stream order).
-float* op_attention_partial(size_t bytes) {
+// Device scratch of the step-level entry points, one buffer per kind and
+// device, grown on demand (a grown buffer replaces the old one after the
+// device is idle: earlier launches may still use it); calls on one device run
+// in stream order.
+enum OpScratch { kScratchAttnPartial = 0, kScratchLnCounters = 1, kScratchPePositions = 2, kScratchKinds = 3 };
+void* op_scratch(int kind, size_t bytes) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  static float* bufs[64] = {};
-  static size_t sizes[64] = {};
+  static void* bufs[kScratchKinds][64] = {};
+  static size_t sizes[kScratchKinds][64] = {};
   std::lock_guard<std::mutex> lk(g_err_mu);
-  if (!bufs[dev] || sizes[dev] < bytes) {
-    if (bufs[dev]) {
-      // Earlier launches may still read the old buffer.
+  void*& buf = bufs[kind][dev];
+  if (!buf || sizes[kind][dev] < bytes) {
+    if (buf) {
       if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
-      cudaFree(bufs[dev]);
-      bufs[dev] = nullptr;
-      sizes[dev] = 0;
+      cudaFree(buf);
+      buf = nullptr;
+      sizes[kind][dev] = 0;
     }
-    float* p = nullptr;
+    void* p = nullptr;
     if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) return nullptr;
-    bufs[dev] = p;
-    sizes[dev] = bytes;
+    buf = p;
+    sizes[kind][dev] = bytes;
   }
-  return bufs[dev];
+  return buf;
 }
 
-// The row-block counters of the step-level fused LayerNorm (one per device,
-// grown on demand, zeroed by every call on its stream).
-int* op_ln_counters(size_t count) {
+// The frequencies of the position embedding's parts at width D, one copy per
+// device and width (built on first use).
+const float* op_pe_omega(int D) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  static int* bufs[64] = {};
-  static size_t sizes[64] = {};
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || D % 192 || D > 1024) return nullptr;
+  static float* oms[64][6] = {};
+  const int w = D / 192 - 1;
   std::lock_guard<std::mutex> lk(g_err_mu);
-  if (!bufs[dev] || sizes[dev] < count) {
-    if (bufs[dev]) {
-      if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
-      cudaFree(bufs[dev]);
-      bufs[dev] = nullptr;
-      sizes[dev] = 0;
+  if (!oms[dev][w]) {
+    float host[128] = {};
+    float* p = nullptr;
+    if (!pe_omega(D, host) || cudaMalloc(&p, sizeof(host)) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(p, host, sizeof(host), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(p);
+      return nullptr;
     }
-    int* p = nullptr;
-    if (cudaMalloc(&p, count * sizeof(int)) != cudaSuccess) return nullptr;
-    bufs[dev] = p;
-    sizes[dev] = count;
+    oms[dev][w] = p;
   }
-  return bufs[dev];
+  return oms[dev][w];
 }
 
 // The position embedding's column-part table of the step-level entry point,
@@ -297,6 +298,57 @@ revo_status revo_op_linear(revo_precision precision, int epilogue, const void* A
                      "revo_op_linear");
 }
 
+revo_status revo_op_linear_pe(const void* A, const void* W, const float* bias, float* out, int slots, int grid_h,
+                              int grid_w, int N, int K, const int* taus, int tile_n, void* stream) {
+  if (!A || !W || !out || !taus || slots < 0 || slots > 8 || grid_h < 0 || grid_w < 0 || grid_h > 0xFFFF ||
+      grid_w > 0xFFFF || N % 192 || N <= 0 || N > 1024 || K <= 0) {
+    set_last_error("revo_op_linear_pe: bad argument");
+    return REVO_EINVAL;
+  }
+  if (K % 64) {
+    set_last_error("revo_op_linear_pe: needs K %% 64 == 0");
+    return REVO_EINVAL;
+  }
+  const long long Mll = static_cast<long long>(slots) * grid_h * grid_w;
+  if (Mll > (1LL << 30)) {
+    set_last_error("revo_op_linear_pe: too many tokens");
+    return REVO_EINVAL;
+  }
+  const int M = static_cast<int>(Mll);
+  if (M == 0) return REVO_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool pair = (tile_n & REVO_TILE_PAIR) != 0;
+  const int req = tile_n & ~REVO_TILE_PAIR;
+  const int width = req == 256 ? 256 : (req == 192 && !pair) ? 192 : 128;
+  const int bn = pair ? (width | kTilePair) : width;
+  CUtensorMap ma, mb, mc;
+  if (!encode_tmap_bf16_2d(&ma, A, M, K, K, 128, 64) ||
+      !encode_tmap_bf16_2d(&mb, W, N, K, K, pair ? width / 2 : width, 64) ||
+      !encode_tmap_out_2d(&mc, out, true, M, N, N)) {
+    set_last_error("revo_op_linear_pe: tensor map encoding failed (alignment?)");
+    return REVO_EINVAL;
+  }
+  constexpr int kTabRows = 256;  // the table of revo_op_add_position
+  int* err = op_error_word();
+  auto* pos = static_cast<int2*>(op_scratch(kScratchPePositions, static_cast<size_t>(M) * sizeof(int2)));
+  const float* tab = op_pe_table(N, kTabRows);
+  const float* om = op_pe_omega(N);
+  if (!err || !pos || !tab || !om) {
+    set_last_error("revo_op_linear_pe: no device scratch");
+    return REVO_ECUDA;
+  }
+  cudaError_t e = launch_pe_positions(pos, grid_h, grid_w, slots, taus, st);
+  if (e != cudaSuccess) return cuda_status(e, "revo_op_linear_pe");
+  EpiAux aux{};
+  aux.pe_pos = pos;
+  aux.pe_tab = tab;
+  aux.pe_omega = om;
+  aux.pe_rows = kTabRows;
+  aux.pe_part = N / 3;
+  return cuda_status(launch_gemm_tc(ma, mb, mc, bn, kEpiF32Pe, bias, M, N, K, err, device_sm_count(), st, &aux),
+                     "revo_op_linear_pe");
+}
+
 revo_status revo_op_linear_resid_ln(const void* A, const void* W, const float* bias, float* x, int M, int N, int K,
                                     const float* gamma, const float* beta, void* ln_out, float* ln_row_scale,
                                     int ln_fp8, int tile_n, void* stream) {
@@ -322,14 +374,14 @@ revo_status revo_op_linear_resid_ln(const void* A, const void* W, const float* b
   }
   int* err = op_error_word();
   const size_t blocks = static_cast<size_t>(M + 127) / 128;
-  int* counters = op_ln_counters(blocks);
+  int* counters = static_cast<int*>(op_scratch(kScratchLnCounters, blocks * sizeof(int)));
   if (!err || !counters) {
     set_last_error("revo_op_linear_resid_ln: no device scratch");
     return REVO_ECUDA;
   }
   cudaError_t e = cudaMemsetAsync(counters, 0, blocks * sizeof(int), st);
   if (e != cudaSuccess) return cuda_status(e, "revo_op_linear_resid_ln");
-  LnFuse ln{};
+  EpiAux ln{};
   ln.x = x;
   ln.g = gamma;
   ln.b = beta;
@@ -556,7 +608,7 @@ revo_status revo_op_attention(revo_precision precision, const void* qkv, void* o
   float* part = nullptr;
   if (flags & REVO_ATTN_SPLIT_TAIL) {
     const size_t need = attention_partial_bytes(M, heads, seg, device_sm_count());
-    if (!(part = op_attention_partial(need))) {
+    if (!(part = static_cast<float*>(op_scratch(kScratchAttnPartial, need)))) {
       set_last_error("revo_op_attention: partial-result buffer allocation failed");
       return REVO_ENOMEM;
     }

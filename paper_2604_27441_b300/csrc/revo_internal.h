@@ -18,7 +18,8 @@ enum Epilogue : int {
   kEpiBf16 = 1,      // store bf16
   kEpiGeluBf16 = 2,  // store bf16(gelu(.))
   kEpiResidF32 = 3,  // float32 out += .
-  kEpiResidLn = 4,   // float32 out += ., then the LayerNorm of every completed row block (LnFuse)
+  kEpiResidLn = 4,   // float32 out += ., then the LayerNorm of every completed row block (EpiAux)
+  kEpiF32Pe = 6,     // store float32 (. + the position embedding of the row's token, EpiAux)
 };
 
 // GEMM tile widths: 128 or 256 output columns per tile of 128 rows (one CTA);
@@ -56,11 +57,19 @@ bool encode_tmap_u8_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64
 // kEpiResidF32 (the residual epilogue adds into it), bf16 otherwise.  `bn` is a
 // tile width (see kTilePair); `a` has 128-row boxes, `b` bn-row boxes, or
 // bn/2-row boxes for a pair width.
-// A LayerNorm fused after a residual GEMM (kEpiResidLn: x += A W^T + b): each
+// Operands of the fused epilogues.
+// kEpiResidLn, a LayerNorm fused after a residual GEMM (x += A W^T + b): each
 // CTA counts the column tiles it has added into a 128-row block of x; the one
 // that completes the block normalises those rows (the standalone LayerNorm's
 // arithmetic, bit for bit) into `out`.
-struct LnFuse {
+// kEpiF32Pe, the position embedding added in the embedding GEMMs' epilogue:
+// out[m][n] = (acc + b[n]) + pe(m, n) with the values launch_add_pe adds (the
+// same float32 sums, bit for bit).  Row m's token has the temporal distance
+// pe_pos[m].x and the patch position (row, column) = (pe_pos[m].y >> 16,
+// pe_pos[m].y & 0xFFFF); column n lies in part n / pe_part (0 temporal, 1 row,
+// 2 column), whose value at an integer position below pe_rows comes from
+// pe_tab (launch_pe_table), else from sincosf with the frequencies pe_omega.
+struct EpiAux {
   const float* x;     // the residual stream the GEMM adds into, [M][N] float32
   const float* g;     // gain [N]
   const float* b;     // shift [N]
@@ -68,10 +77,14 @@ struct LnFuse {
   float* row_scale;   // mode 2: per-row scales [M]
   int* counters;      // [ceil(M / 128)] zero between launches (the last CTA resets its own)
   int mode;           // 1 bf16, 2 E4M3 with per-row scales
+  const int2* pe_pos;      // [M] token positions
+  const float* pe_tab;     // [pe_rows][pe_part]
+  const float* pe_omega;   // [pe_part / 2]
+  int pe_rows, pe_part;    // N == 3 * pe_part, pe_part % 64 == 0
 };
 cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
                            const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st,
-                           const LnFuse* ln = nullptr);
+                           const EpiAux* ln = nullptr);
 // FP8 (E4M3) operands with per-row scales of A (`row_scale`, M entries: one per
 // token) and per-output-channel scales of W (`col_scale`, N entries):
 // Y = epilogue(row_scale[m] * col_scale[n] * (A8 W8^T)[m][n] + b[n]).  `a` and
@@ -112,6 +125,10 @@ struct AssembleArgs {
   void* out;                         // [S*Hp*Wp][T*C*p*p]
   int C, F, T, p, H, W;
   int out_bf16;
+  // Optional (p = 16 kernels): each token's position for kEpiF32Pe,
+  // pe_pos[(s*Hp + r)*Wp + c] = {taus[s], r << 16 | c}.
+  int2* pe_pos;
+  int taus[8];
 };
 // `dev` (optional): a device copy of `a` that the kernel reads instead of its
 // by-value arguments (the launch shape still comes from `a`).
@@ -131,6 +148,11 @@ cudaError_t launch_add_pe(float* x, int Hp, int Wp, int slots, const int* taus, 
                           const int* taus_dev = nullptr, const float* ptab = nullptr, int ptab_rows = 0);
 // tab[q][0 .. D/3) = the embedding's part at position q, for q < rows.
 cudaError_t launch_pe_table(float* tab, int rows, int D, cudaStream_t st);
+// The frequencies of a part at width D (D / 6 floats, host): false if D is not
+// a multiple of 192 or above 1536.
+bool pe_omega(int D, float* omega);
+// pe_pos of one request's S*Hp*Wp tokens (see AssembleArgs::pe_pos).
+cudaError_t launch_pe_positions(int2* pe_pos, int Hp, int Wp, int slots, const int* taus, cudaStream_t st);
 
 cudaError_t launch_layernorm(const float* x, const float* g, const float* b, void* out, int M, int D, int out_bf16,
                              cudaStream_t st);

@@ -583,6 +583,34 @@ def test_position_embedding(D, hp, wp, taus):
     np.testing.assert_allclose(x.cpu().numpy(), O.position_embedding(list(taus), hp, wp, D), rtol=0, atol=2e-5)
 
 
+@pytest.mark.parametrize("D,K,hp,wp,taus", [(768, 1536, 15, 20, (5, 3, 1)), (384, 768, 45, 80, (7, 5, 3)),
+                                           (192, 64, 2, 3, (0,)), (192, 128, 2, 300, (4, 2)),
+                                           (384, 256, 3, 5, (1000, 64, 63)), (768, 768, 1, 129, (70000,))])
+@pytest.mark.parametrize("tile", [128, 192, 256, 128 | 0x1000, 256 | 0x1000])
+def test_linear_with_position_embedding_equals_separate_launches(D, K, hp, wp, taus, tile):
+    """The position embedding added in the embedding GEMM's epilogue (table
+    values below 256, per-element sincosf beyond: a 300-column grid, temporal
+    distances 1000 and 70000) gives the same floats as the Linear then
+    op_add_position, bit for bit, and the sum agrees with the oracle."""
+    S = len(taus)
+    M = S * hp * wp
+    A = bf16(synth.normal(M + D, (M, K), 1.0))
+    W = bf16(synth.normal(M + D + 1, (D, K), 1.0 / np.sqrt(K)))
+    b = synth.normal(M + D + 2, (D,), 0.1)
+    Ad, Wd, bd = A.cuda(), W.cuda(), dev(b)
+    sep = torch.empty((M, D), dtype=torch.float32, device="cuda")
+    fused = torch.full((M, D), float("nan"), dtype=torch.float32, device="cuda")
+    R.op_linear(R.BF16, 0, Ad, Wd, bd, sep, M, D, K, tile)
+    R.op_add_position(sep, S, hp, wp, D, list(taus))
+    R.op_linear_pe(Ad, Wd, bd, fused, S, hp, wp, D, K, list(taus), tile)
+    torch.cuda.synchronize()
+    assert torch.equal(fused.view(torch.int32), sep.view(torch.int32))
+    ref = O.linear(f64(A), f64(W), b.astype(np.float64)) + O.position_embedding(list(taus), hp, wp, D)
+    # float32 pos * w_i is off by up to pos * 2^-24 (relative), and sin / cos
+    # have slope <= 1: the embedding's own error grows with the position.
+    np.testing.assert_allclose(f64(fused), ref, rtol=1e-5, atol=1e-4 + max(max(taus), hp, wp) * 2.0 ** -23)
+
+
 # -------------------------------------------------------------------- blend
 
 @pytest.mark.parametrize("modality", ["rgb", "depth"])
