@@ -437,6 +437,49 @@ def test_attention_segment_alone_equals_in_a_batch(split_tail):
     assert R.take_device_error() == 0
 
 
+def _reference_ladder_qkv(M, heads, seed):
+    """q, k, v (bf16 values) whose scores climb in steps the kernel's softmax
+    must follow by moving its reference.  Head 0: query rows r % 3 == 0 have
+    q[0] = 16, rows r % 3 == 1 have q[0] = 8 (lanes of one warp differ), the
+    others 0; key dimension 0 is 0 except at a few keys, so with the scale
+    log2(e)/8 a row with q[0] = 16 sees scores (log2 units) of about 69 at key
+    50 (block 0, keys 32..63 of the block: above the first 32 keys' maximum by
+    far more than 57), 138.5 at key 140 (block 1, keys 0..31), 207.7 at key 300
+    (block 2, keys 32..63), 271.2 at key 420 (block 3, keys 32..63: 63 above,
+    kept as is), then 277 and 268 at keys 460 and 455 (block 3, keys 64..127:
+    the reference moves while keys 32..63's P is already in TMEM, and key 420
+    keeps a 2^-6 share).  Values of the ladder keys are distinct."""
+    D = 64 * heads
+    a = synth.normal(seed, (M, 3 * D)).astype(np.float32)
+    a[:, 0] = np.where(np.arange(M) % 3 == 0, 16.0, np.where(np.arange(M) % 3 == 1, 8.0, 0.0))
+    a[:, D] = 0.0
+    for key, b, vv in ((50, 24.0, 3.0), (140, 48.0, -2.0), (300, 72.0, 1.5), (420, 94.0, -3.0), (455, 93.0, 2.5),
+                       (460, 96.0, 4.0)):
+        if key < M:
+            a[key, D] = b
+            a[key, 2 * D:2 * D + 64] = vv
+    return bf16(a)
+
+
+@pytest.mark.parametrize("split_tail", [False, True])
+@pytest.mark.parametrize("seg,heads", [((0, 1000), 2), ((0, 600, 1600), 2), ((0, 3600), 12)])
+def test_attention_bf16_reference_moves(seg, heads, split_tail):
+    """Scores that climb by more than 57 (log2 units) past a row's reference,
+    in each group of keys of a block and in the first block: the kernel moves
+    the reference, scales what it holds by an exact power of two, and the
+    output stays within the bf16-derived bound of the FP64 oracle (also with
+    the tail cut, whose parts start mid-segment)."""
+    M, D = seg[-1], 64 * heads
+    qkv = _reference_ladder_qkv(M, heads, 91 + M)
+    out = torch.zeros((M, D), dtype=torch.bfloat16, device="cuda")
+    R.op_attention(R.BF16, qkv.cuda(), out, M, D, heads, seg, split_tail=split_tail)
+    torch.cuda.synchronize()
+    got = f64(out)
+    assert np.isfinite(got).all()
+    check_attention_bf16(got, f64(qkv), heads, seg)
+    assert R.take_device_error() == 0
+
+
 @pytest.mark.parametrize("seg,heads", ATT_CASES[:2] + [((0, 700), 4)])
 def test_attention_fp32_simt(seg, heads):
     M, D = seg[-1], 64 * heads
