@@ -457,6 +457,21 @@ REVO_DEVI float tanh_approx(float x) {
   return y;
 }
 
+// Input normalisation of RGB codes (Section 3.4.1; the ImageNet mean and
+// standard deviation per channel): x * (1 / (255 std_c)) + (-mean_c / std_c)
+// in one FMA, constants rounded once from their exact values.  Shared by the
+// assemble kernels and the implicit-GEMM embedding's producer, so both give the
+// same bf16 operand bit for bit.
+constexpr float kRgbScaleR = 0.0171247534f, kRgbScaleG = 0.0175070036f, kRgbScaleB = 0.0174291935f;
+constexpr float kRgbShiftR = -2.11790395f, kRgbShiftG = -2.03571439f, kRgbShiftB = -1.80444443f;
+
+// Byte `byte` of `word` as a float: 2^23 + b as a float, minus 2^23 (exact).
+REVO_DEVI float byte_to_float(uint32_t word, int byte) {
+  uint32_t bits;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(bits) : "r"(word), "r"(0x4B000000u), "r"(0x7650u | static_cast<uint32_t>(byte)));
+  return __uint_as_float(bits) - 8388608.f;
+}
+
 // GELU in the tanh form of Hendrycks & Gimpel (2016),
 // 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))): within 4.8e-4 of the erf form
 // everywhere (largest near x = 2.7, 2e-4 relative), below the bf16 rounding of

@@ -99,16 +99,9 @@ __global__ void assemble_kernel_dev(const AssembleArgs* __restrict__ a) { assemb
 // once from their exact values; within 2 ulp of (x / 255 - mean_c) / std_c),
 // depth as (d - mu) * (1 / sigma).  A row that is not 8-byte aligned falls
 // back to byte loads.
-__constant__ float kRgbScale[3] = {0.0171247534f, 0.0175070036f, 0.0174291935f};
-__constant__ float kRgbShift[3] = {-2.11790395f, -2.03571439f, -1.80444443f};
+__constant__ float kRgbScale[3] = {kRgbScaleR, kRgbScaleG, kRgbScaleB};
+__constant__ float kRgbShift[3] = {kRgbShiftR, kRgbShiftG, kRgbShiftB};
 constexpr int kAsmThreads = 256;
-
-REVO_DEVI float byte_to_float(uint32_t word, int byte) {
-  // 2^23 + b as a float, minus 2^23: exact for a byte.
-  uint32_t bits;
-  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(bits) : "r"(word), "r"(0x4B000000u), "r"(0x7650u | static_cast<uint32_t>(byte)));
-  return __uint_as_float(bits) - 8388608.f;
-}
 
 REVO_DEVI void assemble16_body(const AssembleArgs& a) {
   const int C = a.C, T = a.T, H = a.H;

@@ -147,10 +147,10 @@ __device__ __noinline__ void pe_chunk_computed(const EpiAux& aux, int pos, int q
   }
 }
 
-// kEpiF32Pe: adds the position embedding of row `row` at columns col ..
-// col + 31 (one part of it) to the 16 packed pairs v.
-REVO_DEVI void add_pe_chunk(uint64_t (&v)[16], const EpiAux& aux, int row, int M, int col) {
-  const int2 d = row < M ? __ldg(aux.pe_pos + row) : make_int2(0, 0);
+// kEpiF32Pe: adds the position embedding of a row at position d = {tau,
+// patch row << 16 | patch column} at columns col .. col + 31 (one part of it)
+// to the 16 packed pairs v.
+REVO_DEVI void add_pe_chunk(uint64_t (&v)[16], const EpiAux& aux, int2 d, int col) {
   const int which = col / aux.pe_part;
   const int q = col - which * aux.pe_part;
   const int pos = which == 0 ? d.x : which == 1 ? (d.y >> 16) : (d.y & 0xFFFF);
@@ -170,10 +170,11 @@ REVO_DEVI void add_pe_chunk(uint64_t (&v)[16], const EpiAux& aux, int row, int M
   }
 }
 
+// `pe_d`: the row's position (kEpiF32Pe only).
 template <int EPI, bool F8>
 REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, int n0, int c0, uint8_t* chunk,
                               const CUtensorMap* map, int row0, int lane, float rs, const float* __restrict__ cs,
-                              const EpiAux& aux, int M) {
+                              const EpiAux& aux, int2 pe_d) {
   uint4 pieces[8];
   if (EPI == kEpiF32 || EPI == kEpiF32Pe || epi_resid(EPI)) {
     uint32_t r[32];
@@ -184,7 +185,7 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
     for (int i = 0; i < 16; ++i) v[i] = pk2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
     if (F8) apply_scales(v, rs, cs, n0 + c0);
     add_bias(v, bias, n0 + c0);
-    if (EPI == kEpiF32Pe) add_pe_chunk(v, aux, row0 + lane, M, n0 + c0);
+    if (EPI == kEpiF32Pe) add_pe_chunk(v, aux, pe_d, n0 + c0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       float a, b, c, d;
@@ -416,10 +417,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BN;
       const int my_row = m0 + q * 32 + lane;
       const float rs = (F8 && my_row < M) ? __ldg(row_scale + my_row) : 0.f;
+      const int2 pe_d = (EPI == kEpiF32Pe && my_row < M) ? __ldg(ln.pe_pos + my_row) : make_int2(0, 0);
 #pragma unroll 1
       for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += kChunkCols) {
         if (n0 + c0 >= N) break;
-        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale, ln, M);
+        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale, ln, pe_d);
       }
       tc_fence_before();
       __syncwarp();
@@ -599,10 +601,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BN;
       const int my_row = m0 + q * 32 + lane;
       const float rs = (F8 && my_row < M) ? __ldg(row_scale + my_row) : 0.f;
+      const int2 pe_d = (EPI == kEpiF32Pe && my_row < M) ? __ldg(ln.pe_pos + my_row) : make_int2(0, 0);
 #pragma unroll 1
       for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2) && m0 + q * 32 < M; c0 += kChunkCols) {
         if (n0 + c0 >= N) break;
-        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale, ln, M);
+        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale, ln, pe_d);
       }
       tc_fence_before();
       __syncwarp();
@@ -626,6 +629,340 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 }  // namespace
 
 namespace {
+
+// ---- The tubelet embedding as an implicit GEMM (the Conv3d of Section 3.4.1
+// with kernel = stride = (T, 16, 16), bias, plus the (tau, row, column)
+// embedding in the epilogue).  No token matrix is stored: four producer warps
+// build each 128-row A stage in shared memory from the frames themselves --
+// thread r of them owns tile row r, i.e. one token, and writes its 64 K
+// elements (slot frame t, channel c, patch rows 4 yq .. 4 yq + 3) as bf16 in
+// the 128-byte-swizzled layout, normalised exactly as the assemble kernel
+// does -- then fence the writes into the async proxy and arrive on the
+// stage's barrier; TMA streams the W tile onto the same barrier; one thread
+// issues tcgen05.mma; four epilogue warps add bias and position embedding and
+// store the float32 rows by TMA.  Each token's position is also written out
+// for the encoder->decoder Linear.  K keeps the (t, c, y, x) order of the
+// weights, so the result is bit for bit the assemble + GEMM pair's.
+//
+// Warp roles (320 threads): warp 0 TMA (W), warp 1 TMEM allocator + MMA
+// issuer, warps 2..5 epilogue (TMEM lanes 32 (w % 4) .. +31, every column),
+// warps 6..9 operand producers.
+constexpr int kEmbEpiWarps = 4;
+constexpr int kEmbCvtWarps = 4;
+constexpr int kEmbThreads = 64 + 32 * (kEmbEpiWarps + kEmbCvtWarps);
+
+template <int BN>
+struct EmbedCfg {
+  static constexpr int kStages = (BN == 128) ? 6 : 4;
+  static constexpr int kABytes = kBM * kBK * 2;
+  static constexpr int kBBytes = BN * kBK * 2;
+  static constexpr int kTmemCols = tmem_cols_for(BN);
+  static constexpr int kSmemBytes =
+      1024 /*align slack*/ + kStages * (kABytes + kBBytes) + kEmbEpiWarps * kOutChunkBytes + 256 /*barriers*/;
+};
+
+// The request, slot and patch of batch row `row` (false past the last row).
+REVO_DEVI bool embed_token(const EmbedParams& ep, int row, int& req, int& s, int& ty, int& tx) {
+  if (row < 0 || row >= ep.seg_start[ep.n]) return false;
+  int lo = 0, hi = ep.n - 1;  // the last request whose rows start at or before `row`
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ep.seg_start[mid] <= row) lo = mid; else hi = mid - 1;
+  }
+  const int wp = ep.wp[lo], hw = ep.hp[lo] * wp;
+  const int local = row - ep.seg_start[lo];
+  req = lo;
+  s = local / hw;
+  const int rem = local - s * hw;
+  ty = rem / wp;
+  tx = rem - ty * wp;
+  return true;
+}
+
+REVO_DEVI const AssembleArgs* embed_job(const EmbedParams& ep, int req) {
+  return reinterpret_cast<const AssembleArgs*>(ep.jobs + static_cast<size_t>(req) * ep.stride);
+}
+
+// One token's source: its patch origin in each of its slot's T (<= 2) frames.
+struct EmbedRow {
+  const uint8_t* base[2];
+  size_t pitch[2];
+  float mu, inv;  // depth statistics (C == 1)
+  bool valid, aligned;
+};
+
+REVO_DEVI EmbedRow embed_row(const EmbedParams& ep, int row) {
+  EmbedRow r{};
+  int req, s, ty, tx;
+  if (!embed_token(ep, row, req, s, ty, tx)) return r;
+  const AssembleArgs* a = embed_job(ep, req);
+  const int colb = tx * (ep.C == 3 ? 48 : 32);
+  uintptr_t bits = 0;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    if (t >= ep.T) break;
+    const int f = s * ep.T + t;
+    const size_t pitch = a->pitch[f];
+    r.pitch[t] = pitch;
+    r.base[t] = static_cast<const uint8_t*>(a->frames[f]) + static_cast<size_t>(ty) * 16 * pitch + colb;
+    bits |= reinterpret_cast<uintptr_t>(r.base[t]) | pitch;
+  }
+  if (ep.C == 1) {
+    r.mu = a->mu_sigma[0];
+    r.inv = 1.f / a->mu_sigma[1];
+  }
+  r.aligned = (bits & (ep.C == 3 ? 7u : 15u)) == 0;
+  r.valid = true;
+  return r;
+}
+
+// Channel CH of 8 pieces of 8 RGB pixels (24 bytes each) as bf16, normalised
+// (the channel is a template argument so that every byte index is fixed).
+template <int CH>
+REVO_DEVI void rgb_pieces(const uint32_t (&b)[8][6], float sc, float sh, uint4 (&pieces)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float v[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const int byte = 3 * x + CH;
+      v[x] = fmaf(byte_to_float(b[j][byte >> 2], byte & 3), sc, sh);
+    }
+    pieces[j] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                           pack_bf16x2(v[6], v[7]));
+  }
+}
+
+// This thread's row r of an A stage for K block kb: K elements kb*64 .. +63 =
+// frame t of the slot, channel c, patch rows 4*yq .. 4*yq + 3 (16 pixels
+// each); piece j (8 elements) is row 4*yq + j/2, pixels 8*(j%2) .. +7.  All
+// loads are issued before any conversion.  Rows past the batch are zero.
+REVO_DEVI void embed_fill_row(uint8_t* stage, int r, const EmbedRow& er, int kb, int C) {
+  uint4 pieces[8];
+  if (!er.valid) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pieces[j] = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    const int tc = kb >> 2, yq = kb & 3;
+    const int t = C == 3 ? tc / 3 : tc;
+    const int c = tc - t * C;
+    const size_t pitch = t == 0 ? er.pitch[0] : er.pitch[1];  // no dynamic index: er stays in registers
+    const uint8_t* rowp = (t == 0 ? er.base[0] : er.base[1]) + static_cast<size_t>(4 * yq) * pitch;
+    if (C == 3) {
+      uint32_t b[8][6];  // piece j: 24 bytes = 8 pixels x 3 channels
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint8_t* p = rowp + static_cast<size_t>(j >> 1) * pitch + (j & 1) * 24;
+        if (er.aligned) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2*>(p) + i);
+            b[j][2 * i] = w.x;
+            b[j][2 * i + 1] = w.y;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 6; ++i)
+            b[j][i] = p[4 * i] | (p[4 * i + 1] << 8) | (p[4 * i + 2] << 16) | (static_cast<uint32_t>(p[4 * i + 3]) << 24);
+        }
+      }
+      if (c == 0)
+        rgb_pieces<0>(b, kRgbScaleR, kRgbShiftR, pieces);
+      else if (c == 1)
+        rgb_pieces<1>(b, kRgbScaleG, kRgbShiftG, pieces);
+      else
+        rgb_pieces<2>(b, kRgbScaleB, kRgbShiftB, pieces);
+    } else {
+      uint32_t w16[8][4];  // piece j: 8 depth samples
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint8_t* p = rowp + static_cast<size_t>(j >> 1) * pitch + (j & 1) * 16;
+        if (er.aligned) {
+          const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
+          w16[j][0] = w.x, w16[j][1] = w.y, w16[j][2] = w.z, w16[j][3] = w.w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            w16[j][i] = p[4 * i] | (p[4 * i + 1] << 8) | (p[4 * i + 2] << 16) | (static_cast<uint32_t>(p[4 * i + 3]) << 24);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float v[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+          v[x] = (static_cast<float>((w16[j][x >> 1] >> (16 * (x & 1))) & 0xFFFFu) - er.mu) * er.inv;
+        pieces[j] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                               pack_bf16x2(v[6], v[7]));
+      }
+    }
+  }
+  stage_row(stage, r, pieces);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kEmbThreads, 1)
+    embed_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmC,
+                    const float* __restrict__ bias, int M, int N, int K, int* err, const __grid_constant__ EpiAux pe,
+                    const __grid_constant__ EmbedParams ep) {
+  using Cfg = EmbedCfg<BN>;
+  constexpr int S = Cfg::kStages;
+  constexpr uint32_t kIdesc = idesc_bf16(kBM, BN);
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + S * Cfg::kABytes;
+  uint8_t* sOut = sB + S * Cfg::kBBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sOut + kEmbEpiWarps * kOutChunkBytes);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int m_tiles = (M + kBM - 1) / kBM;
+  const int n_tiles = (N + BN - 1) / BN;
+  const int num_tiles = m_tiles * n_tiles;
+  const int num_kb = K / kBK;
+
+  if (threadIdx.x == 0) {
+    tma_prefetch_desc(&tmB);
+    tma_prefetch_desc(&tmC);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1 + kEmbCvtWarps);  // the W copy's arrival + one per producer warp
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], kEmbEpiWarps);
+    }
+    fence_mbarrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, Cfg::kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+        const int n0 = (tile % n_tiles) * BN;
+        for (int kb = 0; kb < num_kb; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, err, kDevTimeoutProducer)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[stage], Cfg::kBBytes);
+          tma_load_2d(sB + stage * Cfg::kBBytes, &tmB, kb * kBK, n0, &full[stage]);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int t_local = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++t_local) {
+        const int acc = t_local & 1;
+        const uint32_t acc_phase = (t_local >> 1) & 1;
+        if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, err, kDevTimeoutMma)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * BN;
+        for (int kb = 0; kb < num_kb; ++kb) {
+          if (!mbar_wait(&full[stage], phase, err, kDevTimeoutMma)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_lo = sw128_lo(smem_u32(sA + stage * Cfg::kABytes));
+          const uint32_t b_lo = sw128_lo(smem_u32(sB + stage * Cfg::kBBytes));
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)  // 4 x 32 bytes of K per stage
+            mma_f16_hl(d_tmem, a_lo + kk * 2, kSw128Hi, b_lo + kk * 2, kSw128Hi, kIdesc, (kb | kk) != 0 ? 1u : 0u);
+          mma_commit(&empty[stage]);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (ok) mma_commit(&tfull[acc]);
+      }
+    }
+  } else if (warp < 2 + kEmbEpiWarps) {
+    const int e = warp - 2;
+    const int q = warp & 3;
+    uint8_t* chunk = sOut + e * kOutChunkBytes;
+    int t_local = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++t_local) {
+      const int acc = t_local & 1;
+      const uint32_t acc_phase = (t_local >> 1) & 1;
+      const int m0 = (tile / n_tiles) * kBM;
+      const int n0 = (tile % n_tiles) * BN;
+      const int my_row = m0 + q * 32 + lane;
+      int2 pe_d = make_int2(0, 0);
+      int req, s, ty, tx;
+      if (embed_token(ep, my_row, req, s, ty, tx)) {
+        pe_d = make_int2(embed_job(ep, req)->taus[s], (ty << 16) | tx);
+        if (n0 == 0) ep.pe_pos[my_row] = pe_d;
+      }
+      if (!mbar_wait(&tfull[acc], acc_phase, err, kDevTimeoutEpilogue)) break;
+      tc_fence_after();
+      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BN;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN && m0 + q * 32 < M; c0 += 32) {
+        if (n0 + c0 >= N) break;
+        epilogue_chunk<kEpiF32Pe, false>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, 0.f, nullptr, pe,
+                                         pe_d);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+    if (lane == 0) bulk_wait_all();
+  } else {
+    const int r = static_cast<int>(threadIdx.x) - 32 * (2 + kEmbEpiWarps);  // the A row this thread fills
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      const EmbedRow er = embed_row(ep, (tile / n_tiles) * kBM + r);
+      for (int kb = 0; kb < num_kb; ++kb) {
+        if (!mbar_wait_warp(&empty[stage], phase ^ 1u, err, kDevTimeoutProducer, lane)) {
+          ok = false;
+          break;
+        }
+        embed_fill_row(sA + stage * Cfg::kABytes, r, er, kb, ep.C);
+        fence_proxy_async_smem();  // the generic-proxy writes, visible to tcgen05.mma
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[stage]);
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, Cfg::kTmemCols);
+  }
+}
 
 template <int BN, int EPI, bool F8 = false>
 cudaError_t launch_bn_epi(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const float* bias, int M,
@@ -725,6 +1062,33 @@ cudaError_t launch_gemm_tc_fp8(const CUtensorMap& a, const CUtensorMap& b, const
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (K % kBK8 != 0 || N % 64 != 0 || !row_scale || !col_scale) return cudaErrorInvalidValue;
   return launch_any<true>(a, b, c, bn, epi, bias, M, N, K, err, num_sms, st, row_scale, col_scale);
+}
+
+cudaError_t launch_embed_tc(const CUtensorMap& w, const CUtensorMap& c, int bn, const float* bias, int M, int N,
+                            int K, int* err, int num_sms, cudaStream_t st, const EpiAux& pe, const EmbedParams& ep) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (ep.n <= 0 || ep.n > kMaxSegments || ep.seg_start[0] != 0 || ep.seg_start[ep.n] != M || !ep.jobs ||
+      !ep.pe_pos || (ep.C != 1 && ep.C != 3) || ep.T < 1 || ep.T > 2 || K != ep.T * ep.C * 256 || K % kBK != 0 ||
+      N % 32 != 0 || !pe.pe_tab || !pe.pe_omega || pe.pe_part <= 0 || pe.pe_part % 64 != 0 ||
+      N != 3 * pe.pe_part || pe.pe_rows < 0)
+    return cudaErrorInvalidValue;
+  for (int i = 0; i < ep.n; ++i)
+    if (ep.seg_start[i + 1] < ep.seg_start[i] || ep.hp[i] <= 0 || ep.wp[i] <= 0 || ep.hp[i] > 0xFFFF ||
+        ep.wp[i] > 0xFFFF || (ep.seg_start[i + 1] - ep.seg_start[i]) % (ep.hp[i] * ep.wp[i]) != 0)
+      return cudaErrorInvalidValue;
+  const int tiles_m = (M + kBM - 1) / kBM;
+  auto go = [&](auto kern, int smem, int tn, std::atomic<unsigned long long>& done) -> cudaError_t {
+    cudaError_t e = ensure_smem_attr(kern, smem, done);
+    if (e != cudaSuccess) return e;
+    const int tiles = tiles_m * ((N + tn - 1) / tn);
+    const int grid = tiles < num_sms ? tiles : num_sms;
+    kern<<<grid, kEmbThreads, smem, st>>>(w, c, bias, M, N, K, err, pe, ep);
+    return cudaGetLastError();
+  };
+  static std::atomic<unsigned long long> done128{0}, done256{0};
+  if (bn == 256) return go(embed_tc_kernel<256>, EmbedCfg<256>::kSmemBytes, 256, done256);
+  if (bn == 128) return go(embed_tc_kernel<128>, EmbedCfg<128>::kSmemBytes, 128, done128);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace revo

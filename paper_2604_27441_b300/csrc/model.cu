@@ -691,8 +691,32 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
   cudaError_t e = prepare_job_args(net, ws, jobs, n, args.data());
   if (e != cudaSuccess) return e;
 
-  // Tubelet assembly + normalisation, tubelet embedding, embeddings.
-  if (dev_args) {
+  // Tubelet assembly + normalisation, tubelet embedding, embeddings.  With
+  // a device argument table (graph replay) on the tensor-core path, p = 16,
+  // T <= 2: one implicit-GEMM launch reads the frames directly (no token
+  // matrix); otherwise the assemble kernel writes the tokens for the GEMM.
+  const bool implicit_embed = f.tc && dev_args && s.p == 16 && s.T <= 2;
+  if (implicit_embed) {
+    EmbedParams ep{};
+    ep.n = n;
+    ep.C = s.C;
+    ep.T = s.T;
+    for (int i = 0; i <= n; ++i) ep.seg_start[i] = seg.start[i];
+    for (int i = 0; i < n; ++i) {
+      ep.hp[i] = jobs[i].H / s.p;
+      ep.wp[i] = jobs[i].W / s.p;
+    }
+    ep.jobs = reinterpret_cast<const uint8_t*>(&dev_args[0].assemble);
+    ep.stride = sizeof(JobArgs);
+    ep.pe_pos = ws->pe_pos;
+    const EpiAux pe = pe_aux(ws, ws->pe_enc, ws->pe_om_enc, s.D);
+    const LinearW& w = net->patch;
+    const int bn = w.out % 256 == 0 ? 256 : 128;
+    ++f.launched;
+    if ((e = launch_embed_tc(bn == 256 ? w.map256 : w.map128, ws->o_x_enc, bn, w.b, M, w.out, w.in, ws->err,
+                             f.sms, st, pe, ep)) != cudaSuccess)
+      return e;
+  } else if (dev_args) {
     // One launch for the batch, each request's arguments from the device table.
     std::vector<AssembleArgs> aa(n);
     for (int i = 0; i < n; ++i) aa[i] = args[i].assemble;
@@ -705,7 +729,9 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
   // Tubelet embedding + position embedding: on the tensor-core path the
   // embedding is added in the GEMM's epilogue (token positions from the
   // assemble kernel), else by a pass per request.
-  if (f.tc) {
+  if (implicit_embed) {
+    // Done: the implicit GEMM above includes both.
+  } else if (f.tc) {
     const EpiAux pe = pe_aux(ws, ws->pe_enc, ws->pe_om_enc, s.D);
     if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32Pe, ws->x, s.D, M, &ws->o_x_enc, &pe)) != cudaSuccess)
       return e;

@@ -139,6 +139,31 @@ cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st, const Assemb
 cudaError_t launch_assemble_batch(const AssembleArgs* host, int n, const AssembleArgs* dev, size_t stride,
                                   cudaStream_t st);
 
+// The tubelet embedding as an implicit GEMM (p = 16): x[M][N] = tokens W^T + b
+// + the position embedding, where the token rows are never stored: producer
+// warps read each token's pixels straight from the frames of its request
+// (the same normalisation as the assemble kernel, bit for bit) into the
+// swizzled shared-memory operand, TMA streams W, tcgen05.mma accumulates in
+// TMEM.  The batch's rows are the requests' tokens stacked in order: request
+// i owns rows [seg_start[i], seg_start[i+1]) of Hp[i] x Wp[i] patches per
+// slot; its frames, pitches, depth statistics and temporal distances are read
+// from the device table at jobs + i * stride (AssembleArgs; the runtime writes
+// it before each graph replay).  Each token's position {tau, r << 16 | c} is
+// also written to pe_pos[row] for the encoder->decoder Linear's epilogue.
+struct EmbedParams {
+  int n, C, T;
+  int seg_start[kMaxSegments + 1];
+  int hp[kMaxSegments], wp[kMaxSegments];
+  const uint8_t* jobs;
+  size_t stride;
+  int2* pe_pos;
+};
+// `w`: the embedding weight map (bn-row boxes, K-major bf16 [N][K] with K =
+// T*C*256 in (t, c, y, x) order); `c`: the float32 output map (32-column boxes).
+// bn 128 or 256; M = seg_start[n]; `pe` holds the embedding table operands.
+cudaError_t launch_embed_tc(const CUtensorMap& w, const CUtensorMap& c, int bn, const float* bias, int M, int N,
+                            int K, int* err, int num_sms, cudaStream_t st, const EpiAux& pe, const EmbedParams& ep);
+
 // x[(s*Hp + r)*Wp + c][:] += sincos(tau_s) | sincos(r) | sincos(c), each D/3 wide
 // (D a multiple of 192).  `taus_dev` (optional): device copy of the temporal
 // distances, read instead of `taus`.  `ptab` (optional): launch_pe_table's

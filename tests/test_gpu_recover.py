@@ -249,12 +249,15 @@ def test_batch_result_equals_alone():
             np.testing.assert_array_equal(x, y)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_graph_replay_equals_plain_launches(precision):
     """With graph replay on, a size pattern runs eagerly, is then captured, then
     replayed; every run reads its own requests' frames, masks and temporal
     distances (new content each time, same sizes) and gives exactly what plain
-    launches give."""
+    launches give.  At BF16 and FP8 the graph path embeds the tubelets with the
+    implicit GEMM (frames read in the GEMM's producer) and the plain path with
+    the assemble kernel + GEMM: the same operands and K order, so the same
+    bits."""
     shape = SMALL if precision == 0 else VITB
     rounds = [[synth.make_request(3000 + 10 * it + j, wl, index=40 + it, delta=1 + (it + j) % 3)
                for j, wl in enumerate(("320x240", "640x480", "320x240"))] for it in range(4)]
@@ -322,12 +325,49 @@ def test_hold_batches_mixed_sizes_with_autotuned_tiles():
 def test_k_and_tubelet_variants(k, T):
     """Other reference counts and tubelet sizes (the paper's ablation over k
     and T, Section 4 / Appendix B.3) through the same kernels, BF16 against
-    the FP64 oracle at 320x240."""
+    the FP64 oracle at 320x240; the graph path (implicit-GEMM embedding over
+    k + 1 frames in slots of T) gives the plain path's bits."""
     shape = dict(VITB, k=k, tubelet=T)
     rgb, dep = synth.make_request(1200 + 10 * k + T, "320x240", k=k)
-    with make_ctx(shape, R.BF16, (240, 320)) as ctx:
-        got = run(ctx, 0, rgb, dep)
-    check(R.BF16, got, oracle(shape, rgb, dep, f"kt{k}{T}"), rgb, dep)
+    got = {}
+    for graphs in (0, 1):
+        with make_ctx(shape, R.BF16, (240, 320), use_graphs=graphs) as ctx:
+            got[graphs] = run(ctx, 0, rgb, dep)
+    for x, y in zip(got[0], got[1]):
+        np.testing.assert_array_equal(x, y)
+    check(R.BF16, got[1], oracle(shape, rgb, dep, f"kt{k}{T}"), rgb, dep)
+
+
+def test_unaligned_current_frame():
+    """The current frame read straight from the caller's device buffers at
+    addresses that are only 4-byte (RGB) and 2-byte (depth) aligned: the
+    implicit-GEMM embedding, the assemble kernel and the blend take their
+    narrow-load paths, and the graph path still gives the plain path's bits
+    (twice: the eager run and the captured replay)."""
+    rgb, dep = synth.make_request(3500, "320x240", loss_rate=0.2)
+    got = {}
+    for graphs in (0, 1):
+        with make_ctx(VITB, R.BF16, (240, 320), use_graphs=graphs) as ctx:
+            keep = push_refs(ctx, 0, rgb, dep)
+            rbuf = torch.zeros(rgb.decoded.size + 16, dtype=torch.uint8, device="cuda")
+            rbuf[4:4 + rgb.decoded.size] = torch.from_numpy(rgb.decoded.reshape(-1)).cuda()
+            dbuf = torch.zeros(dep.decoded.size + 8, dtype=torch.int16, device="cuda")
+            dbuf[1:1 + dep.decoded.size] = torch.from_numpy(dep.decoded.reshape(-1).view(np.int16)).cuda()
+            for rep in range(2):
+                o = Outputs(rgb, dep)
+                req = o.request(0, rgb, dep)
+                req.rgb.data = rbuf.data_ptr() + 4
+                req.depth.data = dbuf.data_ptr() + 2
+                assert ctx.poll(ctx.submit(req)).status == R.REVO_OK
+                got[graphs, rep] = o.numpy()
+            del keep
+    for rep in range(2):
+        for x, y in zip(got[0, rep], got[1, rep]):
+            np.testing.assert_array_equal(x, y)
+    with make_ctx(VITB, R.BF16, (240, 320)) as ctx:
+        aligned = run(ctx, 0, rgb, dep)
+    for x, y in zip(aligned, got[1, 1]):
+        np.testing.assert_array_equal(x, y)
 
 
 def test_two_lanes_interleaved_streams():
