@@ -976,7 +976,51 @@ def run_profile_kernel(args) -> None:
     fl = flops_per_model(3, H, W)
     N, D = fl["N"], 768
     stream = torch.cuda.Stream()
-    if args.profile_kernel in ("attention", "attention_split"):
+    if args.profile_kernel == "embed":  # the implicit-GEMM tubelet embedding inside one 640x480 RGB-D request
+        import synth
+        cfg = R.config(**VITB, precision=R.BF16, max_height=480, max_width=640, max_streams=1, max_batch=1,
+                       use_graphs=1, autotune=0)
+        ctx = R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
+                        synth.flatten(synth.weights(synth.DEPTH, seed=1)), stream=stream)
+        sio = StreamIO(R, torch, ctx, 0, "640x480", 4100, 0.2, 1, True)
+        for _ in range(args.warmup):
+            ctx.poll(ctx.submit(sio.reqs[0]))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.poll(ctx.submit(sio.reqs[0]))
+        print(json.dumps({"kernel": "embed (whole requests)", "us_per_request": (time.perf_counter() - t0) * 1e6 /
+                          args.steps, "device_error": R.take_device_error()}))
+        ctx.close()
+        return
+    if args.profile_kernel in ("embed_tick", "embed_tick_separate"):
+        # The tick's RGB tubelet embedding (16 requests, 70200 tokens, K = 1536):
+        # the implicit GEMM, or the assemble kernel + the GEMM over the stored tokens.
+        jobs, taus = [], []
+        for wl in MIX16:
+            import synth
+            h, w = synth.WORKLOADS[wl]["rgb"]
+            fr = [torch.randint(0, 256, (h, w, 3), dtype=torch.uint8, device="cuda") for _ in range(6)]
+            jobs.append(dict(height=h, width=w, frames=fr, pitch_bytes=w * 3, mu_sigma=None))
+            taus.append([5, 3, 1])
+        Mt = sum(tick_segments(True))
+        Wt = (torch.randn((D, 1536), device="cuda") / 40).to(torch.bfloat16)
+        b = torch.zeros(D, device="cuda")
+        out = torch.empty((Mt, D), device="cuda")
+        if args.profile_kernel == "embed_tick":
+            launch = lambda: R.op_embed_batch(3, 5, 2, jobs, taus, Wt, b, out, D, stream=stream)  # noqa: E731
+        else:
+            tok = torch.empty((Mt, 1536), dtype=torch.bfloat16, device="cuda")
+            row, ajobs = 0, []
+            for j in jobs:
+                n = 3 * (j["height"] // 16) * (j["width"] // 16)
+                ajobs.append(dict(j, out=tok[row:row + n]))
+                row += n
+
+            def launch():
+                R.op_assemble_batch(3, 5, 2, ajobs, 1, stream=stream)
+                R.op_linear(R.BF16, 0, tok, Wt, b, out, Mt, D, 1536, 256 | R.TILE_PAIR, stream=stream)
+        flops = 2 * Mt * D * 1536
+    elif args.profile_kernel in ("attention", "attention_split"):
         qkv = torch.randn((N, 3 * D), device="cuda").to(torch.bfloat16)
         out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
         split = args.profile_kernel == "attention_split"
@@ -1074,7 +1118,8 @@ def run_profile_kernel(args) -> None:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-kernel", choices=["attention", "attention_split", "attention_tick", "fc1", "fc1_pair",
+    ap.add_argument("--profile-kernel", choices=["embed", "embed_tick", "embed_tick_separate", "attention",
+                                                 "attention_split", "attention_tick", "fc1", "fc1_pair",
                                                  "fc1_fp8", "fc1_fp8_pair", "fc2", "fc2_pair", "fc1_tick", "fc2_tick",
                                                  "assemble", "blend", "pe"],
                     default=None, help="only launch one kernel of the step (for profiler captures)")

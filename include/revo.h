@@ -573,6 +573,31 @@ typedef struct {
 REVO_API revo_status revo_op_assemble_batch(int channels, int k, int T, int n, const revo_assemble_job* jobs,
                                             int out_bf16, void* stream);
 
+/*
+ * The tubelet embedding of a batch as one implicit GEMM (Section 3.4.1: the
+ * tubelet Conv3d with kernel = stride = (T, 16, 16), plus the sinusoidal
+ * embedding of temporal distance, patch row and patch column).  The token
+ * matrix is never stored: the kernel reads each token's pixels from the
+ * jobs' frames, normalises them (as revo_op_assemble_batch does) into the
+ * tensor-core operand, and adds bias and position embedding in its epilogue.
+ * jobs as for revo_op_assemble_batch (frames and pitch device; `out` is not
+ * used); taus host [n][8]: job i's temporal distance per slot at taus[i*8 +
+ * s]; W bf16 [N][K] device with K = T * channels * 256 in (t, c, y, x) order;
+ * bias float32 [N] (may be NULL); out float32 [M][N] device, M = the jobs'
+ * token counts ((k + 1) / T * H/16 * W/16 each) summed, rows in job order.
+ * T 1 or 2, (k + 1) % T == 0, at most 8 slots, H and W multiples of 16; N a
+ * multiple of 192 up to 1024.  The K blocks (64 wide) are accumulated with the
+ * channel blocks of each (frame, patch-row quad) together, so that each pixel
+ * is read once: depth bit for bit revo_op_assemble_batch (bf16) then
+ * revo_op_linear_pe per job, RGB the same sums in another order (equal within
+ * float32 rounding).  Uses the per-device position scratch and
+ * argument table (calls on one device in stream order).
+ * Errors: REVO_EINVAL, REVO_ENOMEM, REVO_ECUDA.
+ */
+REVO_API revo_status revo_op_embed_batch(int channels, int k, int T, int n, const revo_assemble_job* jobs,
+                                         const int* taus, const void* W, const float* bias, float* out, int N,
+                                         void* stream);
+
 typedef struct {
   int height, width;
   const float* head;       /* device [Hp*Wp][C*p*p] */

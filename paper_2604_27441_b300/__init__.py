@@ -126,6 +126,8 @@ _SIGS = {
                                 C.c_void_p]),
     "revo_op_take_device_error": (C.c_int, []),
     "revo_op_assemble_batch": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    "revo_op_embed_batch": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_int), C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "revo_op_blend_batch": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "revo_init_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_void_p, C.c_size_t]),
     "revo_op_wait_selftest": (C.c_int, [C.c_longlong, C.c_void_p]),
@@ -352,6 +354,22 @@ def op_assemble_batch(channels, k, T, jobs, out_bf16, stream=None):
         a.out = ptr(j["out"])
     return _check(lib().revo_op_assemble_batch(channels, k, T, len(jobs), C.cast(arr, C.c_void_p), out_bf16,
                                                _stream(stream)), "revo_op_assemble_batch")
+
+
+def op_embed_batch(channels, k, T, jobs, taus, W, bias, out, N, stream=None):
+    """jobs as for op_assemble_batch (no "out"); taus: per job a list of its slots' temporal distances."""
+    arr = (AssembleJob * len(jobs))()
+    for a, j in zip(arr, jobs):
+        a.height, a.width, a.pitch_bytes = j["height"], j["width"], j["pitch_bytes"]
+        for f, fr in enumerate(j["frames"]):
+            a.frames[f] = ptr(fr)
+        a.mu_sigma = ptr(j.get("mu_sigma"))
+    t8 = (C.c_int * (8 * len(jobs)))()
+    for i, ts in enumerate(taus):
+        for s_, t in enumerate(ts):
+            t8[8 * i + s_] = int(t)
+    return _check(lib().revo_op_embed_batch(channels, k, T, len(jobs), C.cast(arr, C.c_void_p), t8, ptr(W), ptr(bias),
+                                            ptr(out), N, _stream(stream)), "revo_op_embed_batch")
 
 
 def op_blend_batch(channels, jobs, stream=None):

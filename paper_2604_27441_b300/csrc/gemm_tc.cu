@@ -355,8 +355,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
-          tma_load_2d(sA + stage * Cfg::kABytes, &tmA, kb * kKe, m0, &full[stage]);
-          tma_load_2d(sB + stage * Cfg::kBBytes, &tmB, kb * kKe, n0, &full[stage]);
+          const int kx = (ln.kperm ? embed_kblock(kb) : kb) * kKe;
+          tma_load_2d(sA + stage * Cfg::kABytes, &tmA, kx, m0, &full[stage]);
+          tma_load_2d(sB + stage * Cfg::kBBytes, &tmB, kx, n0, &full[stage]);
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -538,8 +539,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           }
           if (rank == 0) mbar_arrive_expect_tx(&full[stage], 2 * Cfg::kStageBytes);
           const uint32_t bar = full0 + stage * static_cast<uint32_t>(sizeof(uint64_t));
-          tma_load_2d_pair(sA + stage * Cfg::kABytes, &tmA, kb * kKe, m0, bar);
-          tma_load_2d_pair(sB + stage * Cfg::kBBytes, &tmB, kb * kKe, n0, bar);
+          const int kx = (ln.kperm ? embed_kblock(kb) : kb) * kKe;
+          tma_load_2d_pair(sA + stage * Cfg::kABytes, &tmA, kx, m0, bar);
+          tma_load_2d_pair(sB + stage * Cfg::kBBytes, &tmB, kx, n0, bar);
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -632,23 +634,25 @@ namespace {
 
 // ---- The tubelet embedding as an implicit GEMM (the Conv3d of Section 3.4.1
 // with kernel = stride = (T, 16, 16), bias, plus the (tau, row, column)
-// embedding in the epilogue).  No token matrix is stored: four producer warps
+// embedding in the epilogue).  No token matrix is stored: eight producer warps
 // build each 128-row A stage in shared memory from the frames themselves --
-// thread r of them owns tile row r, i.e. one token, and writes its 64 K
-// elements (slot frame t, channel c, patch rows 4 yq .. 4 yq + 3) as bf16 in
-// the 128-byte-swizzled layout, normalised exactly as the assemble kernel
-// does -- then fence the writes into the async proxy and arrive on the
-// stage's barrier; TMA streams the W tile onto the same barrier; one thread
+// two threads per tile row, i.e. per token, write its 64 K elements (slot
+// frame t, channel c, patch rows 4 yq .. 4 yq + 3) as bf16 in the
+// 128-byte-swizzled layout, normalised exactly as the assemble kernel does,
+// with the next K block's loads already in flight -- then fence the writes
+// into the async proxy and arrive on the stage's barrier; TMA streams the W tile onto the same barrier; one thread
 // issues tcgen05.mma; four epilogue warps add bias and position embedding and
 // store the float32 rows by TMA.  Each token's position is also written out
-// for the encoder->decoder Linear.  K keeps the (t, c, y, x) order of the
-// weights, so the result is bit for bit the assemble + GEMM pair's.
+// for the encoder->decoder Linear.  The K blocks of the weights' (t, c, y, x)
+// order are taken channel blocks of a pixel group together (embed_kblock), so
+// each pixel is read once for its three channels; the assemble + GEMM path
+// takes the same order (EpiAux::kperm) and gives the same bits.
 //
-// Warp roles (320 threads): warp 0 TMA (W), warp 1 TMEM allocator + MMA
+// Warp roles (448 threads): warp 0 TMA (W), warp 1 TMEM allocator + MMA
 // issuer, warps 2..5 epilogue (TMEM lanes 32 (w % 4) .. +31, every column),
-// warps 6..9 operand producers.
+// warps 6..13 operand producers (two threads per tile row).
 constexpr int kEmbEpiWarps = 4;
-constexpr int kEmbCvtWarps = 4;
+constexpr int kEmbCvtWarps = 8;  // two per row: 256 threads
 constexpr int kEmbThreads = 64 + 32 * (kEmbEpiWarps + kEmbCvtWarps);
 
 template <int BN>
@@ -711,93 +715,164 @@ REVO_DEVI EmbedRow embed_row(const EmbedParams& ep, int row) {
     r.mu = a->mu_sigma[0];
     r.inv = 1.f / a->mu_sigma[1];
   }
-  r.aligned = (bits & (ep.C == 3 ? 7u : 15u)) == 0;
+  r.aligned = (bits & 15u) == 0;
   r.valid = true;
   return r;
 }
 
-// Channel CH of 8 pieces of 8 RGB pixels (24 bytes each) as bf16, normalised
-// (the channel is a template argument so that every byte index is fixed).
-template <int CH>
-REVO_DEVI void rgb_pieces(const uint32_t (&b)[8][6], float sc, float sh, uint4 (&pieces)[8]) {
+// Producer work is split into two threads per row (pieces 4h .. 4h + 3 of
+// the row's 8) and into a load step and a convert step, so that the loads of
+// the next K block are in flight while this one is converted.
+constexpr int kEmbPieces = 4;
+
+// The raw bytes of this thread's 4 pieces for pixel group g = (frame t of the
+// slot, patch-row quad yq) = 4 t + yq: 24 bytes (8 RGB pixels, all three
+// channels) or 16 bytes (8 depth samples) each, as 6 or 4 words.  The K block
+// of channel c of the group holds elements ((t C + c) 4 + yq) * 64 .. +63:
+// patch rows 4*yq .. 4*yq + 3, 16 pixels each; piece j (8 elements) is patch
+// row 4*yq + j/2, pixels 8*(j%2) .. +7.  Byte loads when a row is not 16-byte aligned.
+struct EmbedRaw {
+  uint32_t w[kEmbPieces][6];
+};
+
+REVO_DEVI void embed_load(const EmbedRow& er, int g, int C, int h, EmbedRaw& raw) {
+  if (!er.valid) return;
+  const int t = g >> 2, yq = g & 3;
+  const size_t pitch = t == 0 ? er.pitch[0] : er.pitch[1];  // no dynamic index: er stays in registers
+  const uint8_t* rowp = (t == 0 ? er.base[0] : er.base[1]) + static_cast<size_t>(4 * yq) * pitch;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    float v[8];
+  for (int jj = 0; jj < kEmbPieces; ++jj) {
+    const int j = kEmbPieces * h + jj;
+    const uint8_t* p = rowp + static_cast<size_t>(j >> 1) * pitch + (j & 1) * (C == 3 ? 24 : 16);
+    if (C == 3) {
+      if (er.aligned) {
+        // 24 bytes at offset 0 or 8 (mod 16) of a 16-byte aligned row: one
+        // 16-byte and one 8-byte load.
+        if ((j & 1) == 0) {
+          const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+          const uint2 b = __ldg(reinterpret_cast<const uint2*>(p + 16));
+          raw.w[jj][0] = a.x, raw.w[jj][1] = a.y, raw.w[jj][2] = a.z, raw.w[jj][3] = a.w;
+          raw.w[jj][4] = b.x, raw.w[jj][5] = b.y;
+        } else {
+          const uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+          const uint4 b = __ldg(reinterpret_cast<const uint4*>(p + 8));
+          raw.w[jj][0] = a.x, raw.w[jj][1] = a.y;
+          raw.w[jj][2] = b.x, raw.w[jj][3] = b.y, raw.w[jj][4] = b.z, raw.w[jj][5] = b.w;
+        }
+      } else {
 #pragma unroll
-    for (int x = 0; x < 8; ++x) {
-      const int byte = 3 * x + CH;
-      v[x] = fmaf(byte_to_float(b[j][byte >> 2], byte & 3), sc, sh);
+        for (int i = 0; i < 6; ++i)
+          raw.w[jj][i] = p[4 * i] | (p[4 * i + 1] << 8) | (p[4 * i + 2] << 16) | (static_cast<uint32_t>(p[4 * i + 3]) << 24);
+      }
+    } else {
+      if (er.aligned) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
+        raw.w[jj][0] = w.x, raw.w[jj][1] = w.y, raw.w[jj][2] = w.z, raw.w[jj][3] = w.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          raw.w[jj][i] = p[4 * i] | (p[4 * i + 1] << 8) | (p[4 * i + 2] << 16) | (static_cast<uint32_t>(p[4 * i + 3]) << 24);
+      }
     }
-    pieces[j] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                           pack_bf16x2(v[6], v[7]));
   }
 }
 
-// This thread's row r of an A stage for K block kb: K elements kb*64 .. +63 =
-// frame t of the slot, channel c, patch rows 4*yq .. 4*yq + 3 (16 pixels
-// each); piece j (8 elements) is row 4*yq + j/2, pixels 8*(j%2) .. +7.  All
-// loads are issued before any conversion.  Rows past the batch are zero.
-REVO_DEVI void embed_fill_row(uint8_t* stage, int r, const EmbedRow& er, int kb, int C) {
-  uint4 pieces[8];
+// Channel CH of the pieces as normalised bf16 (the channel is a template
+// argument so that every byte index is fixed).
+// The float bits of 2^23 + (byte `b` of `word`) (exact).
+REVO_DEVI uint32_t magic_byte(uint32_t word, int b) {
+  uint32_t bits;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(bits) : "r"(word), "r"(0x4B000000u), "r"(0x7650u | static_cast<uint32_t>(b)));
+  return bits;
+}
+
+// The float bits of 2^23 + (16-bit half `hf` of `word`) (exact).
+REVO_DEVI uint32_t magic_half(uint32_t word, int hf) {
+  uint32_t bits;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(bits) : "r"(word), "r"(0x4B000000u), "r"(hf ? 0x7432u : 0x7410u));
+  return bits;
+}
+
+// Channel CH of the pieces as normalised bf16 (the channel is a template
+// argument so that every byte index is fixed): per pair of pixels, the two
+// codes as floats (2^23 + b - 2^23, exact) and one packed FMA, each lane
+// rounded as the assemble kernel's scalar fmaf.
+template <int CH>
+REVO_DEVI void rgb_pieces(const EmbedRaw& raw, float sc, float sh, uint4 (&pieces)[kEmbPieces]) {
+  const uint64_t m2 = pk2(-8388608.f, -8388608.f), sc2 = pk2(sc, sc), sh2 = pk2(sh, sh);
+#pragma unroll
+  for (int j = 0; j < kEmbPieces; ++j) {
+    uint32_t pw[4];
+#pragma unroll
+    for (int x = 0; x < 8; x += 2) {
+      const int b0 = 3 * x + CH, b1 = 3 * (x + 1) + CH;
+      const uint64_t f = add2(pk2(__uint_as_float(magic_byte(raw.w[j][b0 >> 2], b0 & 3)),
+                                  __uint_as_float(magic_byte(raw.w[j][b1 >> 2], b1 & 3))), m2);
+      pw[x >> 1] = pack_bf16_pair(fma2(f, sc2, sh2));
+    }
+    pieces[j] = make_uint4(pw[0], pw[1], pw[2], pw[3]);
+  }
+}
+
+// Depth pieces: (d - mu) * (1 / sigma) per sample, as the assemble kernel's
+// scalar operations, two samples per packed instruction.
+REVO_DEVI void depth_pieces(const EmbedRaw& raw, float mu, float inv, uint4 (&pieces)[kEmbPieces]) {
+  const uint64_t m2 = pk2(-8388608.f, -8388608.f), mu2 = pk2(-mu, -mu), inv2 = pk2(inv, inv);
+#pragma unroll
+  for (int j = 0; j < kEmbPieces; ++j) {
+    uint32_t pw[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint64_t d = add2(pk2(__uint_as_float(magic_half(raw.w[j][i], 0)),
+                                  __uint_as_float(magic_half(raw.w[j][i], 1))), m2);
+      pw[i] = pack_bf16_pair(mul2(add2(d, mu2), inv2));
+    }
+    pieces[j] = make_uint4(pw[0], pw[1], pw[2], pw[3]);
+  }
+}
+
+// Converts channel c of the raw pieces exactly as the assemble kernel does
+// and writes them into row r of the A stage (128-byte swizzle: piece j of row
+// r at 16-byte slot j ^ (r % 8)).  Rows past the batch are zero.
+REVO_DEVI void embed_store(uint8_t* stage, int r, int h, const EmbedRow& er, const EmbedRaw& raw, int c, int C) {
+  uint4 pieces[kEmbPieces];
   if (!er.valid) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) pieces[j] = make_uint4(0u, 0u, 0u, 0u);
+    for (int j = 0; j < kEmbPieces; ++j) pieces[j] = make_uint4(0u, 0u, 0u, 0u);
+  } else if (C == 3) {
+    if (c == 0)
+      rgb_pieces<0>(raw, kRgbScaleR, kRgbShiftR, pieces);
+    else if (c == 1)
+      rgb_pieces<1>(raw, kRgbScaleG, kRgbShiftG, pieces);
+    else
+      rgb_pieces<2>(raw, kRgbScaleB, kRgbShiftB, pieces);
   } else {
-    const int tc = kb >> 2, yq = kb & 3;
-    const int t = C == 3 ? tc / 3 : tc;
-    const int c = tc - t * C;
-    const size_t pitch = t == 0 ? er.pitch[0] : er.pitch[1];  // no dynamic index: er stays in registers
-    const uint8_t* rowp = (t == 0 ? er.base[0] : er.base[1]) + static_cast<size_t>(4 * yq) * pitch;
-    if (C == 3) {
-      uint32_t b[8][6];  // piece j: 24 bytes = 8 pixels x 3 channels
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint8_t* p = rowp + static_cast<size_t>(j >> 1) * pitch + (j & 1) * 24;
-        if (er.aligned) {
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const uint2 w = __ldg(reinterpret_cast<const uint2*>(p) + i);
-            b[j][2 * i] = w.x;
-            b[j][2 * i + 1] = w.y;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 6; ++i)
-            b[j][i] = p[4 * i] | (p[4 * i + 1] << 8) | (p[4 * i + 2] << 16) | (static_cast<uint32_t>(p[4 * i + 3]) << 24);
-        }
-      }
-      if (c == 0)
-        rgb_pieces<0>(b, kRgbScaleR, kRgbShiftR, pieces);
-      else if (c == 1)
-        rgb_pieces<1>(b, kRgbScaleG, kRgbShiftG, pieces);
-      else
-        rgb_pieces<2>(b, kRgbScaleB, kRgbShiftB, pieces);
-    } else {
-      uint32_t w16[8][4];  // piece j: 8 depth samples
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint8_t* p = rowp + static_cast<size_t>(j >> 1) * pitch + (j & 1) * 16;
-        if (er.aligned) {
-          const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
-          w16[j][0] = w.x, w16[j][1] = w.y, w16[j][2] = w.z, w16[j][3] = w.w;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            w16[j][i] = p[4 * i] | (p[4 * i + 1] << 8) | (p[4 * i + 2] << 16) | (static_cast<uint32_t>(p[4 * i + 3]) << 24);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float v[8];
-#pragma unroll
-        for (int x = 0; x < 8; ++x)
-          v[x] = (static_cast<float>((w16[j][x >> 1] >> (16 * (x & 1))) & 0xFFFFu) - er.mu) * er.inv;
-        pieces[j] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                               pack_bf16x2(v[6], v[7]));
-      }
-    }
+    depth_pieces(raw, er.mu, er.inv, pieces);
   }
-  stage_row(stage, r, pieces);
+  uint8_t* base = stage + r * 128;
+#pragma unroll
+  for (int jj = 0; jj < kEmbPieces; ++jj) {
+    const int j = kEmbPieces * h + jj;
+    *reinterpret_cast<uint4*>(base + ((j ^ (r & 7)) << 4)) = pieces[jj];
+  }
+}
+
+// One producer step: waits for the stage to be free, converts and stores this
+// thread's pieces of channel c of its raw pixel group, fences them into the
+// async proxy and arrives (once per warp) on the stage's barrier.
+template <int S>
+REVO_DEVI bool embed_step(const EmbedRow& er, const EmbedRaw& raw, int c, int r, int h, int C, uint8_t* sA,
+                          uint64_t* full, uint64_t* empty, int& stage, uint32_t& phase, int* err, int lane) {
+  if (!mbar_wait_warp(&empty[stage], phase ^ 1u, err, kDevTimeoutProducer, lane)) return false;
+  embed_store(sA + stage * (kBM * kBK * 2), r, h, er, raw, c, C);
+  fence_proxy_async_smem();  // the generic-proxy writes, visible to tcgen05.mma
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&full[stage]);
+  if (++stage == S) {
+    stage = 0;
+    phase ^= 1u;
+  }
+  return true;
 }
 
 template <int BN>
@@ -862,7 +937,7 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
             break;
           }
           mbar_arrive_expect_tx(&full[stage], Cfg::kBBytes);
-          tma_load_2d(sB + stage * Cfg::kBBytes, &tmB, kb * kBK, n0, &full[stage]);
+          tma_load_2d(sB + stage * Cfg::kBBytes, &tmB, (ep.C == 3 ? embed_kblock(kb) : kb) * kBK, n0, &full[stage]);
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -934,25 +1009,29 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
     }
     if (lane == 0) bulk_wait_all();
   } else {
-    const int r = static_cast<int>(threadIdx.x) - 32 * (2 + kEmbEpiWarps);  // the A row this thread fills
+    // Producer thread i fills pieces 4h .. 4h + 3 of A row r (one token).
+    const int i = static_cast<int>(threadIdx.x) - 32 * (2 + kEmbEpiWarps);
+    const int r = i % kBM, h = i / kBM;
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       const EmbedRow er = embed_row(ep, (tile / n_tiles) * kBM + r);
-      for (int kb = 0; kb < num_kb; ++kb) {
-        if (!mbar_wait_warp(&empty[stage], phase ^ 1u, err, kDevTimeoutProducer, lane)) {
-          ok = false;
-          break;
-        }
-        embed_fill_row(sA + stage * Cfg::kABytes, r, er, kb, ep.C);
-        fence_proxy_async_smem();  // the generic-proxy writes, visible to tcgen05.mma
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[stage]);
-        if (++stage == S) {
-          stage = 0;
-          phase ^= 1u;
-        }
+      // K steps in pixel groups g = 4 t + yq, the C channel blocks of a group
+      // in a row (the W copies follow the same order), so each pixel is loaded
+      // once for all channels.  Two raw buffers taken in turn: group g + 1's
+      // loads are issued before group g is converted (4 T groups, an even
+      // number).
+      const int groups = num_kb / ep.C;
+      EmbedRaw ra, rb;
+      embed_load(er, 0, ep.C, h, ra);
+      for (int g = 0; g < groups && ok; g += 2) {
+        embed_load(er, g + 1, ep.C, h, rb);
+        for (int c = 0; c < ep.C && ok; ++c)
+          ok = embed_step<S>(er, ra, c, r, h, ep.C, sA, full, empty, stage, phase, err, lane);
+        if (g + 2 < groups) embed_load(er, g + 2, ep.C, h, ra);
+        for (int c = 0; c < ep.C && ok; ++c)
+          ok = embed_step<S>(er, rb, c, r, h, ep.C, sA, full, empty, stage, phase, err, lane);
       }
     }
   }

@@ -709,6 +709,89 @@ revo_status revo_op_assemble_batch(int channels, int k, int T, int n, const revo
                      "revo_op_assemble_batch");
 }
 
+revo_status revo_op_embed_batch(int channels, int k, int T, int n, const revo_assemble_job* jobs, const int* taus,
+                                const void* W, const float* bias, float* out, int N, void* stream) {
+  if (!jobs || !taus || !W || !out || n <= 0 || n > kMaxSegments || k < 1 || k > kMaxRefs ||
+      (channels != 1 && channels != 3) || T < 1 || T > 2 || (k + 1) % T != 0 || N <= 0 || N % 192 || N > 1024) {
+    set_last_error("revo_op_embed_batch: bad argument");
+    return REVO_EINVAL;
+  }
+  const int slots = (k + 1) / T;
+  if (slots > 8) {
+    set_last_error("revo_op_embed_batch: more than 8 slots");
+    return REVO_EINVAL;
+  }
+  std::vector<AssembleArgs> a(n);
+  EmbedParams ep{};
+  ep.n = n;
+  ep.C = channels;
+  ep.T = T;
+  long long M = 0;
+  for (int i = 0; i < n; ++i) {
+    const revo_assemble_job& j = jobs[i];
+    if (j.height <= 0 || j.width <= 0 || j.height % 16 || j.width % 16 || j.height / 16 > 0xFFFF ||
+        j.width / 16 > 0xFFFF || (channels == 1 && !j.mu_sigma)) {
+      set_last_error("revo_op_embed_batch: bad job %d", i);
+      return REVO_EINVAL;
+    }
+    a[i] = AssembleArgs{};
+    for (int f = 0; f <= k; ++f) {
+      if (!j.frames[f]) {
+        set_last_error("revo_op_embed_batch: job %d lacks frame %d", i, f);
+        return REVO_EINVAL;
+      }
+      a[i].frames[f] = j.frames[f];
+      a[i].pitch[f] = j.pitch_bytes;
+    }
+    a[i].mu_sigma = j.mu_sigma;
+    a[i].C = channels;
+    a[i].F = k + 1;
+    a[i].T = T;
+    a[i].p = 16;
+    a[i].H = j.height;
+    a[i].W = j.width;
+    a[i].out_bf16 = 1;
+    for (int s = 0; s < slots; ++s) a[i].taus[s] = taus[i * 8 + s];
+    ep.seg_start[i] = static_cast<int>(M);
+    ep.hp[i] = j.height / 16;
+    ep.wp[i] = j.width / 16;
+    M += static_cast<long long>(slots) * ep.hp[i] * ep.wp[i];
+    if (M > (1LL << 30)) {
+      set_last_error("revo_op_embed_batch: too many tokens");
+      return REVO_EINVAL;
+    }
+  }
+  ep.seg_start[n] = static_cast<int>(M);
+  const int K = T * channels * 256;
+  const int bn = N % 256 == 0 ? 256 : 128;
+  CUtensorMap mb, mc;
+  if (!encode_tmap_bf16_2d(&mb, W, N, K, K, bn, 64) || !encode_tmap_out_2d(&mc, out, true, M, N, N)) {
+    set_last_error("revo_op_embed_batch: tensor map encoding failed (alignment?)");
+    return REVO_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  constexpr int kTabRows = 256;  // the table of revo_op_add_position
+  int* err = op_error_word();
+  auto* pos = static_cast<int2*>(op_scratch(kScratchPePositions, static_cast<size_t>(M) * sizeof(int2)));
+  const float* tab = op_pe_table(N, kTabRows);
+  const float* om = op_pe_omega(N);
+  void* dev = op_arg_table(a.data(), n * sizeof(AssembleArgs), st);
+  if (!err || !pos || !tab || !om || !dev) {
+    set_last_error("revo_op_embed_batch: no device scratch");
+    return REVO_ECUDA;
+  }
+  ep.jobs = static_cast<const uint8_t*>(dev);
+  ep.stride = sizeof(AssembleArgs);
+  ep.pe_pos = pos;
+  EpiAux aux{};
+  aux.pe_tab = tab;
+  aux.pe_omega = om;
+  aux.pe_rows = kTabRows;
+  aux.pe_part = N / 3;
+  return cuda_status(launch_embed_tc(mb, mc, bn, bias, static_cast<int>(M), N, K, err, device_sm_count(), st, aux, ep),
+                     "revo_op_embed_batch");
+}
+
 revo_status revo_op_blend_batch(int channels, int n, const revo_blend_job* jobs, void* stream) {
   if (!jobs || n <= 0 || n > kMaxSegments || (channels != 1 && channels != 3)) {
     set_last_error("revo_op_blend_batch: bad argument");

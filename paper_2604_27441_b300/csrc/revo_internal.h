@@ -81,6 +81,12 @@ struct EpiAux {
   const float* pe_tab;     // [pe_rows][pe_part]
   const float* pe_omega;   // [pe_part / 2]
   int pe_rows, pe_part;    // N == 3 * pe_part, pe_part % 64 == 0
+  // Order of the K blocks (64 wide) for the RGB tubelet embedding (K = T * 3 *
+  // 256 in (t, c, y, x) order): 0 natural; 1 the three channel blocks of each
+  // (frame t, patch-row quad) consecutive -- step i takes block
+  // embed_kblock(i), so the implicit GEMM reads each pixel quad once for all
+  // three channels.
+  int kperm;
 };
 cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
                            const float* bias, int M, int N, int K, int* err, int num_sms, cudaStream_t st,
@@ -150,6 +156,12 @@ cudaError_t launch_assemble_batch(const AssembleArgs* host, int n, const Assembl
 // from the device table at jobs + i * stride (AssembleArgs; the runtime writes
 // it before each graph replay).  Each token's position {tau, r << 16 | c} is
 // also written to pe_pos[row] for the encoder->decoder Linear's epilogue.
+// K block taken at step i of the channel-grouped order (kperm 1).
+__host__ __device__ inline int embed_kblock(int i) {
+  const int t = i / 12, rem = i - 12 * t, yq = rem / 3, c = rem - 3 * yq;
+  return (3 * t + c) * 4 + yq;
+}
+
 struct EmbedParams {
   int n, C, T;
   int seg_start[kMaxSegments + 1];

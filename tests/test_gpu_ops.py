@@ -695,6 +695,61 @@ def test_batched_assemble_and_blend_equal_single_launches(modality):
         assert torch.equal(val_b, val_s)
 
 
+@pytest.mark.parametrize("unaligned", [False, True])
+@pytest.mark.parametrize("k,T", [(5, 2), (3, 1)])
+@pytest.mark.parametrize("modality", ["rgb", "depth"])
+def test_embed_batch_equals_assemble_and_linear_pe(modality, k, T, unaligned):
+    """The implicit-GEMM tubelet embedding of a batch of requests of different
+    sizes (no token matrix: the GEMM's producer warps read the frames) against
+    the assemble kernel's bf16 tokens through revo_op_linear_pe per request:
+    the same operands and epilogue, so depth is equal bit for bit; RGB takes its
+    K blocks with the three channel blocks of a pixel group together, the same
+    float32 sums in another order (24 block sums re-associated: within 1e-5).  The batch spans
+    several 128-row tiles with a ragged last one; one request's temporal
+    distance lies beyond the embedding table; with `unaligned` every frame row
+    starts off the 8/16-byte grid (the narrow-load path)."""
+    C = 3 if modality == "rgb" else 1
+    N, p = 768, 16
+    K = T * C * p * p
+    S = (k + 1) // T
+    sizes = [(48, 80), (160, 224), (32, 128), (64, 64)]
+    rng = np.random.default_rng(17 + k + T + C)
+    W = bf16(synth.normal(4242 + K, (N, K), 1.0 / np.sqrt(K))).cuda()
+    b = dev(synth.normal(4243, (N,), 0.1))
+    jobs, taus, refs_out = [], [], []
+    for i, (H, Wd) in enumerate(sizes):
+        pl = synth.make_tiny_plane(610 + 7 * i + k, modality, H, Wd, k)
+        frames = list(pl.refs) + [pl.decoded]
+        if unaligned:
+            pf = [pitched(f, 4 if C == 3 else 6, 4 if C == 3 else 2) for f in frames]
+            fr, pitch = [x[0] for x in pf], pf[0][1]
+        else:
+            fr, pitch = [dev(f) for f in frames], Wd * (3 if C == 3 else 2)
+        ms = dev(np.array([1500.0 + 50 * i, 700.0 - 30 * i], np.float32)) if C == 1 else None
+        ts = [int(x) for x in rng.integers(1, 9, S)]
+        if i == 1:
+            ts[0] = 300  # beyond the 256-row embedding table
+        Hp, Wp = H // p, Wd // p
+        tok = torch.zeros((S * Hp * Wp, K), dtype=torch.bfloat16, device="cuda")
+        R.op_assemble(C, k, T, p, H, Wd, fr[:k], fr[k], pitch, ms, tok, 1)
+        want = torch.zeros((S * Hp * Wp, N), dtype=torch.float32, device="cuda")
+        R.op_linear_pe(tok, W, b, want, S, Hp, Wp, N, K, ts, 256)
+        jobs.append(dict(height=H, width=Wd, frames=fr, pitch_bytes=pitch, mu_sigma=ms))
+        taus.append(ts)
+        refs_out.append(want)
+    M = sum(t.shape[0] for t in refs_out)
+    assert M > 3 * 128 and M % 128
+    out = torch.full((M, N), 7.0, dtype=torch.float32, device="cuda")
+    R.op_embed_batch(C, k, T, jobs, taus, W, b, out, N)
+    torch.cuda.synchronize()
+    want = torch.cat(refs_out)
+    if C == 1:
+        assert torch.equal(out, want)
+    else:
+        np.testing.assert_allclose(f64(out), f64(want), rtol=1e-5, atol=2e-5)
+    assert R.take_device_error() == 0
+
+
 @pytest.mark.parametrize("modality,H,W", [("rgb", 48, 80), ("depth", 64, 48), ("rgb", 240, 320)])
 def test_blend_codes_bit_exact(modality, H, W):
     """Received pixels are copied bit for bit; lost pixels carry the float32
