@@ -107,12 +107,13 @@ REVO_DEVI float max3(float a, float b, float c) {
 }
 
 // Independent chains of the row maximum and of the packed partial sums.  Two
-// of each measured fastest on the B300 (the tick's batched RGB encoder
-// attention: 1597 us; 1658 with 8 and 4, 1601 with 3 and 2, 1682 with 2 and
-// 3, 1786 with one sum chain): fewer live registers and a shorter final
+// maximum and three sum chains measured fastest on the B300 (the tick's
+// batched RGB encoder attention: 1580 us; 1588 with 2 and 2, 1586 with 4 and
+// 2, 1627 with 2 and 4, 1658 with 8 and 4 before S was loaded 64 columns at a
+// time, 1786 with one sum chain): few live registers and a short final
 // reduction, while the other query tile's warp covers the latencies.
 constexpr int kMaxChains = 2;
-constexpr int kSumChains = 2;
+constexpr int kSumChains = 3;
 
 // Running maxima in kMaxChains independent chains, two new values per
 // instruction.
@@ -137,6 +138,7 @@ REVO_DEVI void exp_chunk(const uint32_t (&v)[32], uint64_t c2, uint64_t negm2, u
     pk[off + i / 2] = pack_bf16x2(p0, p1);
   }
 }
+
 
 // Handoffs from the softmax warpgroup of tile t to its MMA warp, on named
 // barriers (128 softmax threads arrive, the 32 threads of the MMA warp wait
@@ -370,10 +372,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         uint32_t v0[32], v1[32], v2[32], v3[32];
-        tmem_ld32(s_addr, v0);
-        tmem_ld32(s_addr + 32, v1);
-        tmem_ld32(s_addr + 64, v2);
-        tmem_ld32(s_addr + 96, v3);
+        tmem_ld64(s_addr, v0, v1);
+        tmem_ld64(s_addr + 64, v2, v3);
         tmem_wait_ld();
         // S(j) is in registers: the S columns may take S(j+1).
         tc_fence_before();
