@@ -68,7 +68,7 @@ TILE_CACHE = os.path.join(tempfile.gettempdir(), f"revo_tiles_{os.getpid()}.txt"
 # DRAM bytes (read + write) of one attn_tc_kernel launch of the tick's batched
 # RGB encoder attention, from an ncu capture of the current kernel version
 # (None once the kernel changes).
-ATTN_DRAM_BYTES_PER_LAUNCH = None  # re-captured below once the kernel is profiled again
+ATTN_DRAM_BYTES_PER_LAUNCH = None
 
 
 def run_pipelined(R, ctx, req_list, n: int, depth: int, start: int = 0):

@@ -132,6 +132,16 @@ REVO_DEVI void tma_reduce_add_2d(const CUtensorMap* map, const void* smem_src, i
                : "memory");
 }
 
+// Plain (untiled) bulk copy of `bytes` contiguous bytes global -> shared,
+// completing on `bar` with that many transaction bytes.  Both addresses and
+// the size must be multiples of 16 bytes.
+REVO_DEVI void bulk_load_1d(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(smem_dst)),
+               "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 REVO_DEVI void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Waits until no committed bulk group is still reading its shared-memory source.
 REVO_DEVI void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }

@@ -653,17 +653,21 @@ namespace {
 // warps 6..13 operand producers (two threads per tile row).
 constexpr int kEmbEpiWarps = 4;
 constexpr int kEmbCvtWarps = 8;  // two per row: 256 threads
-constexpr int kEmbThreads = 64 + 32 * (kEmbEpiWarps + kEmbCvtWarps);
+constexpr int kEmbRawWarp = 2 + kEmbEpiWarps + kEmbCvtWarps;  // the raw-pixel loader
+constexpr int kEmbThreads = 32 * (kEmbRawWarp + 1);
+constexpr int kEmbRawStages = 2;
+constexpr int kEmbRawBytes = kBM * 4 * 48;  // one pixel group of a tile: 4 patch rows x 128 tokens x 48 B (RGB)
 
 template <int BN>
 struct EmbedCfg {
-  static constexpr int kStages = (BN == 128) ? 6 : 4;
+  static constexpr int kStages = (BN == 128) ? 4 : 3;
   static constexpr int kABytes = kBM * kBK * 2;
   static constexpr int kBBytes = BN * kBK * 2;
   static constexpr int kTmemCols = tmem_cols_for(BN);
-  static constexpr int kSmemBytes =
-      1024 /*align slack*/ + kStages * (kABytes + kBBytes) + kEmbEpiWarps * kOutChunkBytes + 256 /*barriers*/;
+  static constexpr int kSmemBytes = 1024 /*align slack*/ + kStages * (kABytes + kBBytes) +
+                                    kEmbEpiWarps * kOutChunkBytes + kEmbRawStages * kEmbRawBytes + 256 /*barriers*/;
 };
+static_assert(EmbedCfg<256>::kSmemBytes <= 232448 && EmbedCfg<128>::kSmemBytes <= 232448, "shared memory per CTA");
 
 // The request, slot and patch of batch row `row` (false past the last row).
 REVO_DEVI bool embed_token(const EmbedParams& ep, int row, int& req, int& s, int& ty, int& tx) {
@@ -857,6 +861,43 @@ REVO_DEVI void embed_store(uint8_t* stage, int r, int h, const EmbedRow& er, con
   }
 }
 
+// This thread's 4 pieces of a pixel group from a raw stage ([4][128][bpt]):
+// piece j is patch row j / 2 of the quad, pixels 8 (j % 2) .. + 7 (24 or 16
+// bytes at a 16- or 8-byte aligned offset).
+REVO_DEVI void embed_load_raw(const uint8_t* raw_stage, int r, int h, int bpt, bool valid, EmbedRaw& raw) {
+  if (!valid) return;
+#pragma unroll
+  for (int jj = 0; jj < kEmbPieces; ++jj) {
+    const int j = kEmbPieces * h + jj;
+    const uint8_t* p = raw_stage + ((j >> 1) * kBM + r) * bpt + (j & 1) * (bpt / 2);
+    if (bpt == 48) {
+      if ((j & 1) == 0) {
+        const uint4 a = *reinterpret_cast<const uint4*>(p);
+        const uint2 b = *reinterpret_cast<const uint2*>(p + 16);
+        raw.w[jj][0] = a.x, raw.w[jj][1] = a.y, raw.w[jj][2] = a.z, raw.w[jj][3] = a.w;
+        raw.w[jj][4] = b.x, raw.w[jj][5] = b.y;
+      } else {
+        const uint2 a = *reinterpret_cast<const uint2*>(p);
+        const uint4 b = *reinterpret_cast<const uint4*>(p + 8);
+        raw.w[jj][0] = a.x, raw.w[jj][1] = a.y;
+        raw.w[jj][2] = b.x, raw.w[jj][3] = b.y, raw.w[jj][4] = b.z, raw.w[jj][5] = b.w;
+      }
+    } else {
+      const uint4 a = *reinterpret_cast<const uint4*>(p);
+      raw.w[jj][0] = a.x, raw.w[jj][1] = a.y, raw.w[jj][2] = a.z, raw.w[jj][3] = a.w;
+    }
+  }
+}
+
+// Bounded wait for the phase of the given parity while unwinding (copies still
+// in flight when the CTA is about to exit); records nothing.
+REVO_DEVI void mbar_drain_gemm(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  while (!mbar_try_wait(a, parity))
+    if (clock64() - t0 > 20000000LL) return;
+}
+
 // One producer step: waits for the stage to be free, converts and stores this
 // thread's pieces of channel c of its raw pixel group, fences them into the
 // async proxy and arrives (once per warp) on the stage's barrier.
@@ -889,11 +930,15 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
   uint8_t* sA = smem;
   uint8_t* sB = smem + S * Cfg::kABytes;
   uint8_t* sOut = sB + S * Cfg::kBBytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sOut + kEmbEpiWarps * kOutChunkBytes);
+  uint8_t* sRaw = sOut + kEmbEpiWarps * kOutChunkBytes;  // kEmbRawStages pixel groups
+  uint64_t* full = reinterpret_cast<uint64_t*>(sRaw + kEmbRawStages * kEmbRawBytes);
   uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* raw_full = tempty + 2;                  // [kEmbRawStages] a pixel group landed
+  uint64_t* raw_empty = raw_full + kEmbRawStages;   // [kEmbRawStages] the producers hold it in registers
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(raw_empty + kEmbRawStages);
+  int* raw_bulk = reinterpret_cast<int*>(tmem_slot + 1);  // [kEmbRawStages] 1: copied; 0: read the frames directly
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -912,6 +957,10 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], kEmbEpiWarps);
+    }
+    for (int a = 0; a < kEmbRawStages; ++a) {
+      mbar_init(&raw_full[a], 1);
+      mbar_init(&raw_empty[a], kEmbCvtWarps);
     }
     fence_mbarrier_init();
   }
@@ -1008,30 +1057,121 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
       if (lane == 0) mbar_arrive(&tempty[acc]);
     }
     if (lane == 0) bulk_wait_all();
+  } else if (warp == kEmbRawWarp) {
+    // Raw-pixel loader: for each tile and pixel group (frame t of the slot,
+    // patch-row quad yq), TMA bulk copies bring the 4 pixel rows of every run
+    // of the tile's tokens that share a patch row (one contiguous span of a
+    // frame row) into raw stage rs: [4][128 tokens][bytes per token].  Lane l
+    // owns tile rows l, l + 32, l + 64, l + 96 and issues the copies of the
+    // runs that start there.  A tile with a row that is not 16-byte aligned is
+    // marked for direct reads instead.
+    const int bpt = ep.C == 3 ? 48 : 32;
+    int rs = 0;
+    uint32_t rph = 0;
+    int armed = 0;  // groups armed so far (group i uses stage i % kEmbRawStages, phase i / kEmbRawStages)
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      const int m0 = (tile / n_tiles) * kBM;
+      const int rows = min(kBM, M - m0);
+      const uint8_t* src[4][2];
+      size_t pitch[4][2];
+      int run_r[4], run_len[4];
+      bool aligned = true;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        run_len[q] = 0;
+        run_r[q] = lane + 32 * q;
+        int req, sl, ty, tx;
+        if (run_r[q] < rows && embed_token(ep, m0 + run_r[q], req, sl, ty, tx) && (tx == 0 || run_r[q] == 0)) {
+          run_len[q] = min(ep.wp[req] - tx, rows - run_r[q]);
+          const AssembleArgs* a = embed_job(ep, req);
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const int f = sl * ep.T + (t < ep.T ? t : 0);
+            pitch[q][t] = a->pitch[f];
+            src[q][t] = static_cast<const uint8_t*>(a->frames[f]) + static_cast<size_t>(ty) * 16 * pitch[q][t] +
+                        static_cast<size_t>(tx) * bpt;
+            aligned = aligned && ((reinterpret_cast<uintptr_t>(src[q][t]) | pitch[q][t]) & 15u) == 0;
+          }
+        }
+      }
+      const bool bulk = __all_sync(0xffffffffu, aligned);
+      const int groups = num_kb / ep.C;
+      for (int g = 0; g < groups && ok; ++g) {
+        if (!mbar_wait_warp(&raw_empty[rs], rph ^ 1u, err, kDevTimeoutProducer, lane)) {
+          ok = false;
+          break;
+        }
+        const int t = g >> 2, yq = g & 3;
+        if (lane == 0) {
+          raw_bulk[rs] = bulk ? 1 : 0;
+          if (bulk)
+            mbar_arrive_expect_tx(&raw_full[rs], static_cast<uint32_t>(rows * 4 * bpt));
+          else
+            mbar_arrive(&raw_full[rs]);
+        }
+        ++armed;
+        __syncwarp();
+        if (bulk) {
+          uint8_t* dst = sRaw + rs * kEmbRawBytes;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (run_len[q] == 0) continue;
+            const uint8_t* p = t == 0 ? src[q][0] : src[q][1];
+            const size_t pt = t == 0 ? pitch[q][0] : pitch[q][1];
+#pragma unroll
+            for (int y = 0; y < 4; ++y)
+              bulk_load_1d(dst + (y * kBM + run_r[q]) * bpt, p + static_cast<size_t>(4 * yq + y) * pt,
+                           static_cast<uint32_t>(run_len[q] * bpt), &raw_full[rs]);
+          }
+        }
+        if (++rs == kEmbRawStages) {
+          rs = 0;
+          rph ^= 1u;
+        }
+      }
+    }
+    // No copy may still write into shared memory when the CTA exits: wait
+    // (bounded) for the last group armed in each stage.
+    if (lane == 0)
+      for (int k = 0; k < kEmbRawStages && k < armed; ++k) {
+        const int last = armed - 1 - ((armed - 1 - k) % kEmbRawStages);
+        mbar_drain_gemm(&raw_full[k], static_cast<uint32_t>(last / kEmbRawStages) & 1u);
+      }
   } else {
     // Producer thread i fills pieces 4h .. 4h + 3 of A row r (one token).
     const int i = static_cast<int>(threadIdx.x) - 32 * (2 + kEmbEpiWarps);
     const int r = i % kBM, h = i / kBM;
-    int stage = 0;
-    uint32_t phase = 0;
+    const int bpt = ep.C == 3 ? 48 : 32;
+    int stage = 0, rs = 0;
+    uint32_t phase = 0, rph = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       const EmbedRow er = embed_row(ep, (tile / n_tiles) * kBM + r);
       // K steps in pixel groups g = 4 t + yq, the C channel blocks of a group
-      // in a row (the W copies follow the same order), so each pixel is loaded
-      // once for all channels.  Two raw buffers taken in turn: group g + 1's
-      // loads are issued before group g is converted (4 T groups, an even
-      // number).
+      // in a row (the W copies follow the same order), so each pixel is read
+      // once for all channels.  The group's bytes come from the raw stage the
+      // loader filled (or, for an unaligned tile, from the frames); once they
+      // are in registers the stage is handed back.
       const int groups = num_kb / ep.C;
-      EmbedRaw ra, rb;
-      embed_load(er, 0, ep.C, h, ra);
-      for (int g = 0; g < groups && ok; g += 2) {
-        embed_load(er, g + 1, ep.C, h, rb);
+      for (int g = 0; g < groups && ok; ++g) {
+        if (!mbar_wait_warp(&raw_full[rs], rph, err, kDevTimeoutProducer, lane)) {
+          ok = false;
+          break;
+        }
+        EmbedRaw raw;
+        if (*reinterpret_cast<volatile int*>(&raw_bulk[rs]))
+          embed_load_raw(sRaw + rs * kEmbRawBytes, r, h, bpt, er.valid, raw);
+        else
+          embed_load(er, g, ep.C, h, raw);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&raw_empty[rs]);
+        if (++rs == kEmbRawStages) {
+          rs = 0;
+          rph ^= 1u;
+        }
         for (int c = 0; c < ep.C && ok; ++c)
-          ok = embed_step<S>(er, ra, c, r, h, ep.C, sA, full, empty, stage, phase, err, lane);
-        if (g + 2 < groups) embed_load(er, g + 2, ep.C, h, ra);
-        for (int c = 0; c < ep.C && ok; ++c)
-          ok = embed_step<S>(er, rb, c, r, h, ep.C, sA, full, empty, stage, phase, err, lane);
+          ok = embed_step<S>(er, raw, c, r, h, ep.C, sA, full, empty, stage, phase, err, lane);
       }
     }
   }
