@@ -634,23 +634,30 @@ namespace {
 
 // ---- The tubelet embedding as an implicit GEMM (the Conv3d of Section 3.4.1
 // with kernel = stride = (T, 16, 16), bias, plus the (tau, row, column)
-// embedding in the epilogue).  No token matrix is stored: eight producer warps
-// build each 128-row A stage in shared memory from the frames themselves --
-// two threads per tile row, i.e. per token, write its 64 K elements (slot
-// frame t, channel c, patch rows 4 yq .. 4 yq + 3) as bf16 in the
-// 128-byte-swizzled layout, normalised exactly as the assemble kernel does,
-// with the next K block's loads already in flight -- then fence the writes
-// into the async proxy and arrive on the stage's barrier; TMA streams the W tile onto the same barrier; one thread
-// issues tcgen05.mma; four epilogue warps add bias and position embedding and
-// store the float32 rows by TMA.  Each token's position is also written out
-// for the encoder->decoder Linear.  The K blocks of the weights' (t, c, y, x)
-// order are taken channel blocks of a pixel group together (embed_kblock), so
-// each pixel is read once for its three channels; the assemble + GEMM path
-// takes the same order (EpiAux::kperm) and gives the same bits.
+// embedding in the epilogue).  No token matrix is stored.  A loader warp
+// brings the tile's pixels in by TMA bulk copies: for each pixel group (frame t
+// of the slot, patch-row quad yq), one copy per patch row of every run of
+// tokens that share a patch row -- the run's pixels are one contiguous span of
+// a frame row -- into a two-stage raw ring.  Eight producer warps (two threads
+// per tile row, i.e. per token) take the group's bytes into registers, hand
+// the raw stage back, and for each channel write the token's 64 K elements
+// (patch rows 4 yq .. 4 yq + 3) as bf16 into the 128-byte-swizzled A stage,
+// normalised exactly as the assemble kernel does, then fence the writes into
+// the async proxy and arrive on the stage's barrier; TMA streams the W tile
+// onto the same barrier; one thread issues tcgen05.mma; four epilogue warps add
+// bias and position embedding and store the float32 rows by TMA.  Each
+// token's position is also written out for the encoder->decoder Linear.  The K
+// blocks of the weights' (t, c, y, x) order are taken channel blocks of a
+// pixel group together (embed_kblock), so each pixel is copied and converted
+// from one load for its three channels; the assemble + GEMM path takes the
+// same order (EpiAux::kperm) and gives the same bits.  A tile with a frame row
+// that is not 16-byte aligned skips the copies and its producers read the
+// frames directly.
 //
-// Warp roles (448 threads): warp 0 TMA (W), warp 1 TMEM allocator + MMA
+// Warp roles (480 threads): warp 0 TMA (W), warp 1 TMEM allocator + MMA
 // issuer, warps 2..5 epilogue (TMEM lanes 32 (w % 4) .. +31, every column),
-// warps 6..13 operand producers (two threads per tile row).
+// warps 6..13 operand producers (two threads per tile row), warp 14 the
+// raw-pixel loader.
 constexpr int kEmbEpiWarps = 4;
 constexpr int kEmbCvtWarps = 8;  // two per row: 256 threads
 constexpr int kEmbRawWarp = 2 + kEmbEpiWarps + kEmbCvtWarps;  // the raw-pixel loader
