@@ -68,7 +68,7 @@ TILE_CACHE = os.path.join(tempfile.gettempdir(), f"revo_tiles_{os.getpid()}.txt"
 # DRAM bytes (read + write) of one attn_tc_kernel launch of the tick's batched
 # RGB encoder attention, from an ncu capture of the current kernel version
 # (None once the kernel changes).
-ATTN_DRAM_BYTES_PER_LAUNCH = None
+ATTN_DRAM_BYTES_PER_LAUNCH = 330185984 + 89459200
 
 
 def run_pipelined(R, ctx, req_list, n: int, depth: int, start: int = 0):
@@ -992,24 +992,34 @@ def run_profile_kernel(args) -> None:
                           args.steps, "device_error": R.take_device_error()}))
         ctx.close()
         return
-    if args.profile_kernel in ("embed_tick", "embed_tick_separate"):
-        # The tick's RGB tubelet embedding (16 requests, 70200 tokens, K = 1536):
-        # the implicit GEMM, or the assemble kernel + the GEMM over the stored tokens.
+    if args.profile_kernel in ("embed_tick", "embed_tick_separate", "embed_tick_depth",
+                               "embed_tick_depth_separate"):
+        # The tick's RGB (K = 1536, 70200 tokens) or depth (K = 512, 44280 tokens)
+        # tubelet embedding over its 16 requests: the implicit GEMM, or the
+        # assemble kernel + the GEMM over the stored tokens.
+        import synth
+        rgb = not args.profile_kernel.startswith("embed_tick_depth")
+        C = 3 if rgb else 1
+        Kt = 2 * C * 256
         jobs, taus = [], []
         for wl in MIX16:
-            import synth
-            h, w = synth.WORKLOADS[wl]["rgb"]
-            fr = [torch.randint(0, 256, (h, w, 3), dtype=torch.uint8, device="cuda") for _ in range(6)]
-            jobs.append(dict(height=h, width=w, frames=fr, pitch_bytes=w * 3, mu_sigma=None))
+            h, w = synth.WORKLOADS[wl]["rgb" if rgb else "depth"]
+            if rgb:
+                fr = [torch.randint(0, 256, (h, w, 3), dtype=torch.uint8, device="cuda") for _ in range(6)]
+                ms = None
+            else:
+                fr = [torch.randint(300, 5000, (h, w), dtype=torch.int16, device="cuda") for _ in range(6)]
+                ms = torch.tensor([2000.0, 900.0], device="cuda")
+            jobs.append(dict(height=h, width=w, frames=fr, pitch_bytes=w * (3 if rgb else 2), mu_sigma=ms))
             taus.append([5, 3, 1])
-        Mt = sum(tick_segments(True))
-        Wt = (torch.randn((D, 1536), device="cuda") / 40).to(torch.bfloat16)
+        Mt = sum(tick_segments(rgb))
+        Wt = (torch.randn((D, Kt), device="cuda") / 40).to(torch.bfloat16)
         b = torch.zeros(D, device="cuda")
         out = torch.empty((Mt, D), device="cuda")
-        if args.profile_kernel == "embed_tick":
-            launch = lambda: R.op_embed_batch(3, 5, 2, jobs, taus, Wt, b, out, D, stream=stream)  # noqa: E731
+        if not args.profile_kernel.endswith("separate"):
+            launch = lambda: R.op_embed_batch(C, 5, 2, jobs, taus, Wt, b, out, D, stream=stream)  # noqa: E731
         else:
-            tok = torch.empty((Mt, 1536), dtype=torch.bfloat16, device="cuda")
+            tok = torch.empty((Mt, Kt), dtype=torch.bfloat16, device="cuda")
             row, ajobs = 0, []
             for j in jobs:
                 n = 3 * (j["height"] // 16) * (j["width"] // 16)
@@ -1017,9 +1027,9 @@ def run_profile_kernel(args) -> None:
                 row += n
 
             def launch():
-                R.op_assemble_batch(3, 5, 2, ajobs, 1, stream=stream)
-                R.op_linear(R.BF16, 0, tok, Wt, b, out, Mt, D, 1536, 256 | R.TILE_PAIR, stream=stream)
-        flops = 2 * Mt * D * 1536
+                R.op_assemble_batch(C, 5, 2, ajobs, 1, stream=stream)
+                R.op_linear(R.BF16, 0, tok, Wt, b, out, Mt, D, Kt, 256 | R.TILE_PAIR, stream=stream)
+        flops = 2 * Mt * D * Kt
     elif args.profile_kernel in ("attention", "attention_split"):
         qkv = torch.randn((N, 3 * D), device="cuda").to(torch.bfloat16)
         out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
@@ -1118,7 +1128,8 @@ def run_profile_kernel(args) -> None:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-kernel", choices=["embed", "embed_tick", "embed_tick_separate", "attention",
+    ap.add_argument("--profile-kernel", choices=["embed", "embed_tick", "embed_tick_separate", "embed_tick_depth",
+                                                 "embed_tick_depth_separate", "attention",
                                                  "attention_split", "attention_tick", "fc1", "fc1_pair",
                                                  "fc1_fp8", "fc1_fp8_pair", "fc2", "fc2_pair", "fc1_tick", "fc2_tick",
                                                  "assemble", "blend", "pe"],

@@ -638,7 +638,7 @@ namespace {
 // brings the tile's pixels in by TMA bulk copies: for each pixel group (frame t
 // of the slot, patch-row quad yq), one copy per patch row of every run of
 // tokens that share a patch row -- the run's pixels are one contiguous span of
-// a frame row -- into a two-stage raw ring.  Eight producer warps (two threads
+// a frame row -- into a raw ring (two RGB or four depth groups).  Eight producer warps (two threads
 // per tile row, i.e. per token) take the group's bytes into registers, hand
 // the raw stage back, and for each channel write the token's 64 K elements
 // (patch rows 4 yq .. 4 yq + 3) as bf16 into the 128-byte-swizzled A stage,
@@ -662,8 +662,12 @@ constexpr int kEmbEpiWarps = 4;
 constexpr int kEmbCvtWarps = 8;  // two per row: 256 threads
 constexpr int kEmbRawWarp = 2 + kEmbEpiWarps + kEmbCvtWarps;  // the raw-pixel loader
 constexpr int kEmbThreads = 32 * (kEmbRawWarp + 1);
-constexpr int kEmbRawStages = 2;
-constexpr int kEmbRawBytes = kBM * 4 * 48;  // one pixel group of a tile: 4 patch rows x 128 tokens x 48 B (RGB)
+// The raw-pixel ring: 64 KB holding pixel groups of a tile (4 patch rows x 128
+// tokens x 48 B RGB or 32 B depth): 2 RGB groups (3 K blocks each) or 4 depth
+// groups (1 K block each), enough to cover the copies' latency.
+constexpr int kEmbRawRing = 4 * kBM * 4 * 32;
+constexpr int kEmbRawMaxStages = 4;
+REVO_DEVI int embed_raw_stages(int C) { return C == 3 ? 2 : 4; }
 
 template <int BN>
 struct EmbedCfg {
@@ -672,7 +676,7 @@ struct EmbedCfg {
   static constexpr int kBBytes = BN * kBK * 2;
   static constexpr int kTmemCols = tmem_cols_for(BN);
   static constexpr int kSmemBytes = 1024 /*align slack*/ + kStages * (kABytes + kBBytes) +
-                                    kEmbEpiWarps * kOutChunkBytes + kEmbRawStages * kEmbRawBytes + 256 /*barriers*/;
+                                    kEmbEpiWarps * kOutChunkBytes + kEmbRawRing + 256 /*barriers*/;
 };
 static_assert(EmbedCfg<256>::kSmemBytes <= 232448 && EmbedCfg<128>::kSmemBytes <= 232448, "shared memory per CTA");
 
@@ -937,15 +941,17 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
   uint8_t* sA = smem;
   uint8_t* sB = smem + S * Cfg::kABytes;
   uint8_t* sOut = sB + S * Cfg::kBBytes;
-  uint8_t* sRaw = sOut + kEmbEpiWarps * kOutChunkBytes;  // kEmbRawStages pixel groups
-  uint64_t* full = reinterpret_cast<uint64_t*>(sRaw + kEmbRawStages * kEmbRawBytes);
+  uint8_t* sRaw = sOut + kEmbEpiWarps * kOutChunkBytes;  // the raw-pixel ring
+  uint64_t* full = reinterpret_cast<uint64_t*>(sRaw + kEmbRawRing);
   uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
-  uint64_t* raw_full = tempty + 2;                  // [kEmbRawStages] a pixel group landed
-  uint64_t* raw_empty = raw_full + kEmbRawStages;   // [kEmbRawStages] the producers hold it in registers
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(raw_empty + kEmbRawStages);
-  int* raw_bulk = reinterpret_cast<int*>(tmem_slot + 1);  // [kEmbRawStages] 1: copied; 0: read the frames directly
+  uint64_t* raw_full = tempty + 2;                    // [raw stages] a pixel group landed
+  uint64_t* raw_empty = raw_full + kEmbRawMaxStages;  // [raw stages] the producers hold it in registers
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(raw_empty + kEmbRawMaxStages);
+  int* raw_bulk = reinterpret_cast<int*>(tmem_slot + 1);  // [raw stages] 1: copied; 0: read the frames directly
+  const int RS = embed_raw_stages(ep.C);
+  const int raw_bytes = kBM * 4 * (ep.C == 3 ? 48 : 32);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -965,7 +971,7 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], kEmbEpiWarps);
     }
-    for (int a = 0; a < kEmbRawStages; ++a) {
+    for (int a = 0; a < RS; ++a) {
       mbar_init(&raw_full[a], 1);
       mbar_init(&raw_empty[a], kEmbCvtWarps);
     }
@@ -1075,7 +1081,7 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
     const int bpt = ep.C == 3 ? 48 : 32;
     int rs = 0;
     uint32_t rph = 0;
-    int armed = 0;  // groups armed so far (group i uses stage i % kEmbRawStages, phase i / kEmbRawStages)
+    int armed = 0;  // groups armed so far (group i uses stage i % RS, phase i / RS)
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       const int m0 = (tile / n_tiles) * kBM;
@@ -1120,7 +1126,7 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
         ++armed;
         __syncwarp();
         if (bulk) {
-          uint8_t* dst = sRaw + rs * kEmbRawBytes;
+          uint8_t* dst = sRaw + rs * raw_bytes;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             if (run_len[q] == 0) continue;
@@ -1132,7 +1138,7 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
                            static_cast<uint32_t>(run_len[q] * bpt), &raw_full[rs]);
           }
         }
-        if (++rs == kEmbRawStages) {
+        if (++rs == RS) {
           rs = 0;
           rph ^= 1u;
         }
@@ -1141,9 +1147,9 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
     // No copy may still write into shared memory when the CTA exits: wait
     // (bounded) for the last group armed in each stage.
     if (lane == 0)
-      for (int k = 0; k < kEmbRawStages && k < armed; ++k) {
-        const int last = armed - 1 - ((armed - 1 - k) % kEmbRawStages);
-        mbar_drain_gemm(&raw_full[k], static_cast<uint32_t>(last / kEmbRawStages) & 1u);
+      for (int k = 0; k < RS && k < armed; ++k) {
+        const int last = armed - 1 - ((armed - 1 - k) % RS);
+        mbar_drain_gemm(&raw_full[k], static_cast<uint32_t>(last / RS) & 1u);
       }
   } else {
     // Producer thread i fills pieces 4h .. 4h + 3 of A row r (one token).
@@ -1153,8 +1159,13 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
     int stage = 0, rs = 0;
     uint32_t phase = 0, rph = 0;
     bool ok = true;
+    // The next tile's row (request lookup, frame pointers, depth statistics)
+    // is read while this tile is converted.
+    EmbedRow er_next = embed_row(ep, (static_cast<int>(blockIdx.x) / n_tiles) * kBM + r);
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-      const EmbedRow er = embed_row(ep, (tile / n_tiles) * kBM + r);
+      const EmbedRow er = er_next;
+      const int nt = tile + static_cast<int>(gridDim.x);
+      if (nt < num_tiles) er_next = embed_row(ep, (nt / n_tiles) * kBM + r);
       // K steps in pixel groups g = 4 t + yq, the C channel blocks of a group
       // in a row (the W copies follow the same order), so each pixel is read
       // once for all channels.  The group's bytes come from the raw stage the
@@ -1168,12 +1179,12 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
         }
         EmbedRaw raw;
         if (*reinterpret_cast<volatile int*>(&raw_bulk[rs]))
-          embed_load_raw(sRaw + rs * kEmbRawBytes, r, h, bpt, er.valid, raw);
+          embed_load_raw(sRaw + rs * raw_bytes, r, h, bpt, er.valid, raw);
         else
           embed_load(er, g, ep.C, h, raw);
         __syncwarp();
         if (lane == 0) mbar_arrive(&raw_empty[rs]);
-        if (++rs == kEmbRawStages) {
+        if (++rs == RS) {
           rs = 0;
           rph ^= 1u;
         }
