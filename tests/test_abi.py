@@ -89,6 +89,20 @@ def test_null_arguments_are_rejected_before_any_device_work(lib):
     dup = (C.c_int * 2)(0, 0)
     assert lib.revo_fec_decode(2, 1, 8, dup, 1, 8, 1, 8, 1, None) == R.REVO_EINVAL
     assert lib.revo_op_frame_metrics(None, 8, None, 8, 4, 4, 1, 1, 255.0, None, None, None) == R.REVO_EINVAL
+    jobs = (R.AssembleJob * 1)()
+    jobs[0].height, jobs[0].width, jobs[0].pitch_bytes = 32, 32, 96
+    taus = (C.c_int * 8)()
+    emb = lib.revo_op_embed_batch
+    assert emb(3, 5, 2, 1, None, taus, 1, None, 1, 768, None) == R.REVO_EINVAL       # no jobs
+    assert emb(3, 5, 3, 1, C.cast(jobs, C.c_void_p), taus, 1, None, 1, 768, None) == R.REVO_EINVAL  # T = 3
+    assert emb(3, 4, 2, 1, C.cast(jobs, C.c_void_p), taus, 1, None, 1, 768, None) == R.REVO_EINVAL  # k + 1 odd
+    assert emb(3, 5, 2, 1, C.cast(jobs, C.c_void_p), taus, 1, None, 1, 700, None) == R.REVO_EINVAL  # N % 192
+    assert emb(2, 5, 2, 1, C.cast(jobs, C.c_void_p), taus, 1, None, 1, 768, None) == R.REVO_EINVAL  # 2 channels
+    assert emb(3, 5, 2, 1, C.cast(jobs, C.c_void_p), taus, 1, None, 1, 768, None) == R.REVO_EINVAL  # no frames
+    jobs[0].width = 40  # not a multiple of 16
+    for f in range(6):
+        jobs[0].frames[f] = 16
+    assert emb(3, 5, 2, 1, C.cast(jobs, C.c_void_p), taus, 1, None, 1, 768, None) == R.REVO_EINVAL
     lib.revo_recover_destroy(None)
 
 
