@@ -482,10 +482,11 @@ __global__ void blend_kernel_dev(const BlendArgs* __restrict__ a) { blend_body(*
 // are issued before the arithmetic, which is blend_body's.
 constexpr int kBlendThreads = 128;
 
-REVO_DEVI void blend16_body(const BlendArgs& a) {
+// `block`: this block's index within the frame's launch blocks.
+REVO_DEVI void blend16_body(const BlendArgs& a, long long block) {
   const int C = a.C, W = a.W;
   const int runs = W >> 3;
-  const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  const long long idx = block * blockDim.x + threadIdx.x;
   if (idx >= static_cast<long long>(a.H) * runs) return;
   const int r8 = static_cast<int>(idx % runs);
   const int y = static_cast<int>(idx / runs);
@@ -580,12 +581,28 @@ REVO_DEVI void blend16_body(const BlendArgs& a) {
   }
 }
 
-__global__ void __launch_bounds__(kBlendThreads) blend16_kernel(const __grid_constant__ BlendArgs a) { blend16_body(a); }
-__global__ void __launch_bounds__(kBlendThreads) blend16_kernel_dev(const BlendArgs* __restrict__ a) {
-  blend16_body(*a);
+__global__ void __launch_bounds__(kBlendThreads) blend16_kernel(const __grid_constant__ BlendArgs a) {
+  blend16_body(a, blockIdx.x);
 }
-__global__ void __launch_bounds__(kBlendThreads) blend16_kernel_batch(const uint8_t* __restrict__ args, size_t stride) {
-  blend16_body(*reinterpret_cast<const BlendArgs*>(args + blockIdx.y * stride));
+__global__ void __launch_bounds__(kBlendThreads) blend16_kernel_dev(const BlendArgs* __restrict__ a) {
+  blend16_body(*a, blockIdx.x);
+}
+// One launch for a batch with no idle blocks: the frames' blocks are laid end
+// to end (block_start[i] = the first block of frame i, a prefix over the
+// frames' sizes); a block finds its frame by binary search.
+struct BlendBatchPlan {
+  int n;
+  int block_start[kMaxSegments + 1];
+};
+__global__ void __launch_bounds__(kBlendThreads) blend16_kernel_batch(const uint8_t* __restrict__ args, size_t stride,
+                                                                      const __grid_constant__ BlendBatchPlan plan) {
+  const int b = static_cast<int>(blockIdx.x);
+  int lo = 0, hi = plan.n - 1;  // the last frame whose blocks start at or before b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (plan.block_start[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  blend16_body(*reinterpret_cast<const BlendArgs*>(args + lo * stride), b - plan.block_start[lo]);
 }
 
 __global__ void f32_to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {
@@ -639,16 +656,21 @@ cudaError_t launch_assemble_batch(const AssembleArgs* host, int n, const Assembl
 
 cudaError_t launch_blend_batch(const BlendArgs* host, int n, const BlendArgs* dev, size_t stride, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  if (n > 65535 || !dev) return cudaErrorInvalidValue;
-  long long threads = 0;
+  if (n > kMaxSegments || !dev) return cudaErrorInvalidValue;
+  BlendBatchPlan plan{};
+  plan.n = n;
+  long long blocks = 0;
   for (int i = 0; i < n; ++i) {
     const BlendArgs& a = host[i];
     if (a.p != 16 || a.H % 16 || a.W % 16 || (a.C != 1 && a.C != 3)) return cudaErrorInvalidValue;
-    threads = std::max(threads, static_cast<long long>(a.H) * (a.W / 8));
+    plan.block_start[i] = static_cast<int>(blocks);
+    blocks += (static_cast<long long>(a.H) * (a.W / 8) + kBlendThreads - 1) / kBlendThreads;
+    if (blocks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
   }
-  if (threads == 0) return cudaSuccess;
-  const dim3 grid(static_cast<unsigned>((threads + kBlendThreads - 1) / kBlendThreads), static_cast<unsigned>(n));
-  blend16_kernel_batch<<<grid, kBlendThreads, 0, st>>>(reinterpret_cast<const uint8_t*>(dev), stride);
+  plan.block_start[n] = static_cast<int>(blocks);
+  if (blocks == 0) return cudaSuccess;
+  blend16_kernel_batch<<<static_cast<unsigned>(blocks), kBlendThreads, 0, st>>>(reinterpret_cast<const uint8_t*>(dev),
+                                                                                 stride, plan);
   return cudaGetLastError();
 }
 
