@@ -145,6 +145,8 @@ REVO_DEVI void bulk_load_1d(void* smem_dst, const void* gmem_src, uint32_t bytes
 REVO_DEVI void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Waits until no committed bulk group is still reading its shared-memory source.
 REVO_DEVI void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+REVO_DEVI void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 // Waits until every committed bulk group has completed.
 REVO_DEVI void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 

@@ -170,16 +170,26 @@ REVO_DEVI void add_pe_chunk(uint64_t (&v)[16], const EpiAux& aux, int2 d, int co
   }
 }
 
-// `pe_d`: the row's position (kEpiF32Pe only).
+// `pe_d`: the row's position (kEpiF32Pe only).  `release` (a shared::cluster
+// barrier address, or 0): the accumulator buffer is handed back to the MMA
+// warp there as soon as this chunk's TMEM columns are in registers (the last
+// chunk of the warp's tile), before its arithmetic and store.
+REVO_DEVI void release_accumulator(uint32_t release, int lane) {
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive_cluster(release);
+}
+
 template <int EPI, bool F8>
 REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, int n0, int c0, uint8_t* chunk,
                               const CUtensorMap* map, int row0, int lane, float rs, const float* __restrict__ cs,
-                              const EpiAux& aux, int2 pe_d) {
+                              const EpiAux& aux, int2 pe_d, uint32_t release = 0, int bufs = 1) {
   uint4 pieces[8];
   if (EPI == kEpiF32 || EPI == kEpiF32Pe || epi_resid(EPI)) {
     uint32_t r[32];
     tmem_ld32(taddr + c0, r);
     tmem_wait_ld();
+    if (release) release_accumulator(release, lane);
     uint64_t v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = pk2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
@@ -198,6 +208,7 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
     tmem_ld32(taddr + c0, rr[0]);
     tmem_ld32(taddr + c0 + 32, rr[1]);
     tmem_wait_ld();
+    if (release) release_accumulator(release, lane);
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       uint64_t v[16];
@@ -215,8 +226,14 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
                                           pack_bf16_pair(v[4 * k + 2]), pack_bf16_pair(v[4 * k + 3]));
     }
   }
-  // The staging chunk is free once the previous bulk copy has read it.
-  if (lane == 0) bulk_wait_read0();
+  // The staging chunk is free once the bulk copy that last used it has read it
+  // (with two chunks taken in turn: all but the most recent copy).
+  if (lane == 0) {
+    if (bufs == 2)
+      bulk_wait_read1();
+    else
+      bulk_wait_read0();
+  }
   __syncwarp();
   stage_row(chunk, lane, pieces);
   fence_proxy_async_smem();
@@ -419,14 +436,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int my_row = m0 + q * 32 + lane;
       const float rs = (F8 && my_row < M) ? __ldg(row_scale + my_row) : 0.f;
       const int2 pe_d = (EPI == kEpiF32Pe && my_row < M) ? __ldg(ln.pe_pos + my_row) : make_int2(0, 0);
+      const uint32_t rel = smem_u32(&tempty[acc]);
+      bool released = false;
 #pragma unroll 1
       for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += kChunkCols) {
         if (n0 + c0 >= N) break;
-        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale, ln, pe_d);
+        const bool last = c0 + kChunkCols >= (half + 1) * (BN / 2) || n0 + c0 + kChunkCols >= N;
+        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale, ln, pe_d,
+                                last ? rel : 0u);
+        released = released || last;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
+      if (!released) release_accumulator(rel, lane);
       if constexpr (epi_ln(EPI))
         ln_after_tile<EPI == kEpiResidLn8 ? 2 : 1>(ln, m0, M, N, n_tiles, e, lane, ln_flag, ln_in, ln_out, ln_phase,
                                                    err);
@@ -450,6 +470,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 // release the stage in both CTAs and hand each CTA's epilogue its 128
 // accumulator rows (its own TMEM, same column address); the epilogue warps of
 // both CTAs free an accumulator buffer on rank 0's barrier.
+// Staging chunks per epilogue warp (two in turn measured slower: the fifth
+// pipeline stage they cost is worth more, fc2 at the tick's rows 225 -> 235 us).
+constexpr int kPairOutBufs = 1;
+
 template <int BN>
 struct TcGemmPairCfg {
   static constexpr int kABytes = kBM * 128;         // 128 rows x 128 B of K
@@ -457,8 +481,8 @@ struct TcGemmPairCfg {
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStages = (192 * 1024) / kStageBytes;  // BN 256: 6, BN 128: 8
   static constexpr int kTmemCols = tmem_cols_for(BN);
-  static constexpr int kSmemBytes =
-      1024 /*align slack*/ + kStages * kStageBytes + kEpiWarps * kOutChunkBytes + 256 /*barriers*/;
+  static constexpr int kSmemBytes = 1024 /*align slack*/ + kStages * kStageBytes +
+                                    kEpiWarps * kPairOutBufs * kOutChunkBytes + 256 /*barriers*/;
 };
 
 template <int BN, int EPI, bool F8>
@@ -478,7 +502,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   uint8_t* sA = smem;
   uint8_t* sB = smem + S * Cfg::kABytes;
   uint8_t* sOut = sB + S * Cfg::kBBytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sOut + kEpiWarps * kOutChunkBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sOut + kEpiWarps * kPairOutBufs * kOutChunkBytes);
   uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
@@ -590,7 +614,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int e = warp - 2;
     const int q = warp & 3;
     const int half = e >> 2;
-    uint8_t* chunk = sOut + e * kOutChunkBytes;
+    uint8_t* chunks = sOut + e * kPairOutBufs * kOutChunkBytes;
+    int cc = 0;  // chunks this warp has staged
     int t_local = 0;
     uint32_t ln_phase = 0;
     for (int tile = pair; tile < num_tiles; tile += npairs, ++t_local) {
@@ -604,14 +629,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       const int my_row = m0 + q * 32 + lane;
       const float rs = (F8 && my_row < M) ? __ldg(row_scale + my_row) : 0.f;
       const int2 pe_d = (EPI == kEpiF32Pe && my_row < M) ? __ldg(ln.pe_pos + my_row) : make_int2(0, 0);
+      const uint32_t rel = mapa_shared(smem_u32(&tempty[acc]), 0);
+      bool released = false;
 #pragma unroll 1
       for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2) && m0 + q * 32 < M; c0 += kChunkCols) {
         if (n0 + c0 >= N) break;
-        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, rs, col_scale, ln, pe_d);
+        const bool last = c0 + kChunkCols >= (half + 1) * (BN / 2) || n0 + c0 + kChunkCols >= N;
+        epilogue_chunk<EPI, F8>(taddr, bias, n0, c0, chunks + (cc % kPairOutBufs) * kOutChunkBytes, &tmC, m0 + q * 32,
+                                lane, rs, col_scale, ln, pe_d, last ? rel : 0u, kPairOutBufs);
+        ++cc;
+        released = released || last;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[acc]), 0));
+      if (!released) release_accumulator(rel, lane);
       if constexpr (epi_ln(EPI))
         ln_after_tile<EPI == kEpiResidLn8 ? 2 : 1>(ln, m0, M, N, n_tiles, e, lane, ln_flag, ln_in, ln_out, ln_phase,
                                                    err);
@@ -1059,15 +1088,17 @@ __global__ void __launch_bounds__(kEmbThreads, 1)
       if (!mbar_wait(&tfull[acc], acc_phase, err, kDevTimeoutEpilogue)) break;
       tc_fence_after();
       const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BN;
+      const uint32_t rel = smem_u32(&tempty[acc]);
+      bool released = false;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN && m0 + q * 32 < M; c0 += 32) {
         if (n0 + c0 >= N) break;
+        const bool last = c0 + 32 >= BN || n0 + c0 + 32 >= N;
         epilogue_chunk<kEpiF32Pe, false>(taddr, bias, n0, c0, chunk, &tmC, m0 + q * 32, lane, 0.f, nullptr, pe,
-                                         pe_d);
+                                         pe_d, last ? rel : 0u);
+        released = released || last;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
+      if (!released) release_accumulator(rel, lane);
     }
     if (lane == 0) bulk_wait_all();
   } else if (warp == kEmbRawWarp) {
