@@ -1068,14 +1068,16 @@ def run_profile_kernel(args) -> None:
                                         stats, out, Ww * 3, stream=stream)
             nbytes = head.numel() * 4 + 2 * Hh * Ww * 3 + mask.numel() * 4
         flops = None
-    elif args.profile_kernel in ("fc1_fp8", "fc1_fp8_pair"):  # the same fc1 with E4M3 operands
+    elif args.profile_kernel in ("fc1_fp8", "fc1_fp8_pair", "fc1_fp8_tick"):  # the same fc1 with E4M3 operands
+        if args.profile_kernel == "fc1_fp8_tick":
+            N = sum(tick_segments(True))
         a = torch.randint(0, 120, (N, D), dtype=torch.uint8, device="cuda")
         w = torch.randint(0, 120, (4 * D, D), dtype=torch.uint8, device="cuda")
         sa = torch.full((N,), 0.01, device="cuda")
         sw = torch.full((4 * D,), 0.01, device="cuda")
         b = torch.zeros(4 * D, device="cuda")
         out = torch.empty((N, 4 * D), dtype=torch.bfloat16, device="cuda")
-        tile = 256 | (R.TILE_PAIR if args.profile_kernel == "fc1_fp8_pair" else 0)
+        tile = 256 | (R.TILE_PAIR if args.profile_kernel != "fc1_fp8" else 0)
         launch = lambda: R.op_linear_fp8(2, a, sa, w, sw, b, out, N, 4 * D, D, tile, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
     elif args.profile_kernel in ("fc1_tick", "fc2_tick"):  # the tick's RGB rows (M = 70200), CTA-pair 256 tiles
@@ -1131,7 +1133,8 @@ def main():
     ap.add_argument("--profile-kernel", choices=["embed", "embed_tick", "embed_tick_separate", "embed_tick_depth",
                                                  "embed_tick_depth_separate", "attention",
                                                  "attention_split", "attention_tick", "fc1", "fc1_pair",
-                                                 "fc1_fp8", "fc1_fp8_pair", "fc2", "fc2_pair", "fc1_tick", "fc2_tick",
+                                                 "fc1_fp8", "fc1_fp8_pair", "fc1_fp8_tick", "fc2", "fc2_pair",
+                                                 "fc1_tick", "fc2_tick",
                                                  "assemble", "blend", "pe"],
                     default=None, help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
