@@ -16,8 +16,8 @@
 //
 // The FP8 variant takes E4M3 operands (tcgen05 kind::f8f6f4, 128 elements =
 // one 128-byte swizzle atom per stage row, so the pipeline is byte-for-byte the
-// same) and multiplies each accumulator by its row's activation scale and its
-// column's weight scale before the bias.
+// same) and multiplies each accumulator by its row's activation scale times its
+// column's weight scale and adds the bias in one FMA.
 //
 // A second form runs 256-row tiles on a CTA pair (a two-CTA cluster on two
 // SMs issuing one tcgen05.mma.cta_group::2 per K step; see gemm_tc_pair_kernel).
@@ -87,15 +87,19 @@ REVO_DEVI void stage_row(uint8_t* chunk, int row, const uint4 (&pieces)[8]) {
 // multiply, add and FMA issues once per two values; every operation rounds
 // exactly as its scalar form would.
 
-// v[i] *= rs * cs[col + i] (FP8 dequantisation: token scale x channel scale).
-REVO_DEVI void apply_scales(uint64_t (&v)[16], float rs, const float* __restrict__ cs, int col) {
+// v[i] = v[i] * (rs * cs[col + i]) + b[col + i] in one rounding (FP8
+// dequantisation -- token scale x channel scale -- fused with the bias).
+REVO_DEVI void scales_bias(uint64_t (&v)[16], float rs, const float* __restrict__ cs, const float* __restrict__ bias,
+                           int col) {
   const float4* c4 = reinterpret_cast<const float4*>(cs + col);
+  const float4* b4 = reinterpret_cast<const float4*>(bias + col);
   const uint64_t rs2 = pk2(rs, rs);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const float4 c = __ldg(c4 + i);
-    v[2 * i] = mul2(v[2 * i], mul2(rs2, pk2(c.x, c.y)));
-    v[2 * i + 1] = mul2(v[2 * i + 1], mul2(rs2, pk2(c.z, c.w)));
+    const float4 b = bias ? __ldg(b4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    v[2 * i] = fma2(v[2 * i], mul2(rs2, pk2(c.x, c.y)), pk2(b.x, b.y));
+    v[2 * i + 1] = fma2(v[2 * i + 1], mul2(rs2, pk2(c.z, c.w)), pk2(b.z, b.w));
   }
 }
 
@@ -193,8 +197,10 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
     uint64_t v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = pk2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
-    if (F8) apply_scales(v, rs, cs, n0 + c0);
-    add_bias(v, bias, n0 + c0);
+    if (F8)
+      scales_bias(v, rs, cs, bias, n0 + c0);
+    else
+      add_bias(v, bias, n0 + c0);
     if (EPI == kEpiF32Pe) add_pe_chunk(v, aux, pe_d, n0 + c0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -214,8 +220,10 @@ REVO_DEVI void epilogue_chunk(uint32_t taddr, const float* __restrict__ bias, in
       uint64_t v[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[i] = pk2(__uint_as_float(rr[half][2 * i]), __uint_as_float(rr[half][2 * i + 1]));
-      if (F8) apply_scales(v, rs, cs, n0 + c0 + 32 * half);
-      add_bias(v, bias, n0 + c0 + 32 * half);
+      if (F8)
+        scales_bias(v, rs, cs, bias, n0 + c0 + 32 * half);
+      else
+        add_bias(v, bias, n0 + c0 + 32 * half);
       if (EPI == kEpiGeluBf16) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = gelu_tanh2(v[i]);
