@@ -218,7 +218,8 @@ REVO_API revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out)
  * Submits one request and returns a ticket.  REVO_CLEAN requests are queued on
  * the device at once (the frame enters the stream's history).  Other requests
  * join the pending batch; a batch is launched when max_batch requests are
- * pending, when a lane is free and requests are waiting, or on poll/flush.
+ * pending, when a lane is free and requests are waiting, on flush, or on a
+ * poll that waits (timeout_us != 0) for one of them.
  * Host inputs are copied before return.
  * Errors: REVO_EINVAL (bad ids, flags, shapes, pointers), REVO_ENOREF (fewer
  * than k clean frames in the stream's history for a requested modality),
@@ -232,7 +233,8 @@ REVO_API revo_status revo_recover_flush(revo_ctx* ctx);
 /*
  * Waits up to timeout_us microseconds (0 = do not wait, < 0 = forever) for a
  * ticket.  REVO_OK: finished, *out filled, outputs written, the ticket is
- * retired.  REVO_EAGAIN: still running (timeout 0).  REVO_ETIMEDOUT: the wait
+ * retired.  REVO_EAGAIN: still running or still pending (timeout 0; a pending
+ * request is then left to be batched with later arrivals).  REVO_ETIMEDOUT: the wait
  * ran out.  REVO_EINVAL: unknown ticket.  A device-side failure of the batch is
  * reported in out->status.
  */

@@ -242,6 +242,18 @@ bool lane_idle(revo_ctx* c, int l) {
   return !L.used || cudaEventQuery(L.last_end) == cudaSuccess;
 }
 
+// A lane with room runs at most one batch: a new batch queued behind it starts
+// on the device as soon as the running one ends, with no host round trip in
+// between.  Lanes with two batches in flight leave new arrivals pending, to be
+// launched together.
+bool lane_room(revo_ctx* c, int l) {
+  if (lane_idle(c, l)) return true;
+  int in_flight = 0;
+  for (auto& kv : c->batches)
+    if (kv.second.lane == l && !batch_check(c, kv.second, false)) ++in_flight;
+  return in_flight < 2;
+}
+
 // Enqueues the forward of `jobs` (modality m) on lane L.  Without graphs: plain
 // launches.  With graphs: the per-request arguments are uploaded to the lane's
 // device table (one copy from pinned memory), then the graph captured for these
@@ -307,14 +319,16 @@ cudaError_t lane_forward(revo_ctx* c, Lane& L, int m, const std::vector<PlaneJob
 revo_status launch_batch(revo_ctx* c, int count) {
   if (count <= 0 || c->pending.empty()) return REVO_OK;
   if (count > static_cast<int>(c->pending.size())) count = static_cast<int>(c->pending.size());
-  // Prefer an idle lane; otherwise round-robin (stream order queues the work).
+  // Prefer an idle lane, then one with room; otherwise round-robin (stream
+  // order queues the work).
   int lane = -1;
-  for (int i = 0; i < c->n_lanes; ++i) {
+  for (int i = 0; i < c->n_lanes && lane < 0; ++i) {
     const int l = (c->next_lane + i) % c->n_lanes;
-    if (lane_idle(c, l)) {
-      lane = l;
-      break;
-    }
+    if (lane_idle(c, l)) lane = l;
+  }
+  for (int i = 0; i < c->n_lanes && lane < 0; ++i) {
+    const int l = (c->next_lane + i) % c->n_lanes;
+    if (lane_room(c, l)) lane = l;
   }
   if (lane < 0) lane = c->next_lane;
   c->next_lane = (lane + 1) % c->n_lanes;
@@ -401,10 +415,10 @@ revo_status launch_batch(revo_ctx* c, int count) {
 // Launches batches while a lane is idle and frames are waiting.
 void dispatch(revo_ctx* c, bool force) {
   while (!c->pending.empty()) {
-    bool idle = false;
-    for (int l = 0; l < c->n_lanes; ++l) idle = idle || lane_idle(c, l);
+    bool room = false;
+    for (int l = 0; l < c->n_lanes; ++l) room = room || lane_room(c, l);
     const bool full = static_cast<int>(c->pending.size()) >= c->cfg.max_batch;
-    if (!(idle || full || force)) break;
+    if (!(room || full || force)) break;
     launch_batch(c, c->cfg.max_batch);
   }
 }
@@ -435,8 +449,12 @@ revo_status push_clean(revo_ctx* c, const revo_request* r, int m, uint64_t* tick
   Ring& ring = c->rings[m][r->stream_id];
   if (ring.count > 0 && (ring.H != pl.height || ring.W != pl.width))
     return fail(REVO_EINVAL, "clean frame size differs from the stream's history%s");
-  // Work that reads this ring must be launched (and ordered) before the slot is overwritten.
-  dispatch(c, true);
+  // Work that reads this ring must be launched (and ordered) before the slot is
+  // overwritten: pending requests of this stream hold pointers into it.  Other
+  // streams' pending requests stay pending (to be batched with later arrivals).
+  bool reads_ring = false;
+  for (const Pending& p : c->pending) reads_ring = reads_ring || p.req.stream_id == r->stream_id;
+  dispatch(c, reads_ring);
   for (int l = 0; l < c->n_lanes; ++l)
     if (c->lanes[l].used) cudaStreamWaitEvent(c->copy_st, c->lanes[l].last_end, 0);
   ring.H = pl.height;
@@ -909,8 +927,15 @@ revo_status revo_recover_poll(revo_ctx* c, uint64_t ticket, int64_t timeout_us, 
   cudaSetDevice(c->device);
   auto it = c->tickets.find(ticket);
   if (it == c->tickets.end()) return fail(REVO_EINVAL, "unknown ticket%s");
-  if (it->second.batch == 0) dispatch(c, true);
-  dispatch(c, false);
+  if (it->second.batch == 0) {
+    // Still pending.  A caller that will wait launches it now; a non-blocking
+    // poll leaves it to be batched with later arrivals (it starts as soon as a
+    // lane is free or max_batch requests are pending).
+    dispatch(c, timeout_us != 0);
+    if (it->second.batch == 0) return REVO_EAGAIN;
+  } else {
+    dispatch(c, false);
+  }
   Batch& b = c->batches.at(it->second.batch);
   const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
   while (!batch_check(c, b, timeout_us < 0)) {

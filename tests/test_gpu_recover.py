@@ -238,12 +238,16 @@ def test_batch_result_equals_alone():
     with make_ctx(VITB, R.BF16, (480, 640), max_batch=3, max_streams=4) as ctx:
         keep = [push_refs(ctx, sid, rgb, dep) for sid, (rgb, dep) in enumerate(reqs)]
         outs = [Outputs(rgb, dep) for rgb, dep in reqs]
-        # hold the lane busy so all three are admitted into one batch
-        tickets = [ctx.submit(o.request(sid, *reqs[sid])) for sid, o in enumerate(outs)]
-        ctx.flush()
+        # REVO_HOLD on the first two: all three are admitted into one batch
+        tickets = []
+        for sid, o in enumerate(outs):
+            r = o.request(sid, *reqs[sid])
+            if sid < 2:
+                r.flags |= R.HOLD
+            tickets.append(ctx.submit(r))
         sizes = [ctx.poll(t).batch_size for t in tickets]
         del keep
-    assert max(sizes) >= 2
+    assert sizes == [3, 3, 3]
     for a, o in zip(alone, outs):
         for x, y in zip(a, o.numpy()):
             np.testing.assert_array_equal(x, y)
