@@ -733,7 +733,7 @@ cudaError_t net_forward(Net* net, Workspace* ws, const PlaneJob* jobs, int n, cu
     // Done: the implicit GEMM above includes both.
   } else if (f.tc) {
     EpiAux pe = pe_aux(ws, ws->pe_enc, ws->pe_om_enc, s.D);
-    pe.kperm = s.C == 3 ? 1 : 0;  // the implicit GEMM's K-block order: the same bits on both paths
+    pe.kperm = s.C == 3 && s.p == 16 ? 1 : 0;  // the implicit GEMM's K-block order: the same bits on both paths
     if ((e = f.linear(&ws->m_tok, ws->tok, net->patch, kEpiF32Pe, ws->x, s.D, M, &ws->o_x_enc, &pe)) != cudaSuccess)
       return e;
   } else {

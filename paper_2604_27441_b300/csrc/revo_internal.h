@@ -81,11 +81,11 @@ struct EpiAux {
   const float* pe_tab;     // [pe_rows][pe_part]
   const float* pe_omega;   // [pe_part / 2]
   int pe_rows, pe_part;    // N == 3 * pe_part, pe_part % 64 == 0
-  // Order of the K blocks (64 wide) for the RGB tubelet embedding (K = T * 3 *
-  // 256 in (t, c, y, x) order): 0 natural; 1 the three channel blocks of each
-  // (frame t, patch-row quad) consecutive -- step i takes block
-  // embed_kblock(i), so the implicit GEMM reads each pixel quad once for all
-  // three channels.
+  // Order of the K blocks (64 wide) for the RGB tubelet embedding with 16 x 16
+  // patches (K = T * 3 * 256 in (t, c, y, x) order): 0 natural; 1 the three
+  // channel blocks of each (frame t, patch-row quad) consecutive -- step i
+  // takes block embed_kblock(i), so the implicit GEMM reads each pixel quad
+  // once for all three channels.
   int kperm;
 };
 cudaError_t launch_gemm_tc(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, int bn, int epi,
