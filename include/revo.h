@@ -62,8 +62,8 @@ typedef enum { REVO_FP32 = 0, REVO_BF16 = 1, REVO_FP8 = 2 } revo_precision;
 #define REVO_HOLD 8u    /* admit the request to the pending batch without
                            launching: the batch starts on the submit that fills
                            max_batch, on a submit without this flag, or on
-                           flush / poll (no counterpart in the paper: a serving
-                           control)                                             */
+                           flush / a waiting poll (no counterpart in the paper:
+                           a serving control)                                   */
 
 /*
  * Network shape and runtime limits.  revo_config_default() fills the ViT-B
