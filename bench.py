@@ -754,11 +754,16 @@ def measure_batch1(R, torch, precision, stream, steps, warmup, in_flight=2, grap
     reqs = [s.reqs[0] for s in streams]
     run_pipelined(R, ctx, reqs, warmup, in_flight)
     torch.cuda.synchronize()
+    mark = os.environ.get("REVO_PROFILE_RANGE") == "1"  # the timed frames only, for a profiler (see measure_tick)
+    if mark:
+        torch.cuda.profiler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     lat, launches = run_pipelined(R, ctx, reqs, steps, in_flight)
     e1.record(stream)
     torch.cuda.synchronize()
+    if mark:
+        torch.cuda.profiler.stop()
     sec = e0.elapsed_time(e1) / 1e3
     lat_s = sorted(lat)
     out = {"frames_per_s": steps / sec, "ms_per_step": sec * 1e3 / steps, "steps": steps, "batch": 1,
