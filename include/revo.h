@@ -218,7 +218,8 @@ REVO_API revo_status revo_recover_create(const revo_config* cfg, revo_ctx** out)
  * Submits one request and returns a ticket.  REVO_CLEAN requests are queued on
  * the device at once (the frame enters the stream's history).  Other requests
  * join the pending batch; a batch is launched when max_batch requests are
- * pending, when a lane is free and requests are waiting, on flush, or on a
+ * pending, when a lane has room (at most one batch running on it: the new one
+ * queues behind it on the device) and requests are waiting, on flush, or on a
  * poll that waits (timeout_us != 0) for one of them.
  * Host inputs are copied before return.
  * Errors: REVO_EINVAL (bad ids, flags, shapes, pointers), REVO_ENOREF (fewer

@@ -8,9 +8,10 @@
 //
 // Scheduling (continuous batching): submitted frames wait in a pending queue;
 // a batch of up to max_batch pending frames is launched on a lane whenever a
-// lane is idle, when max_batch frames are waiting, or on poll/flush.  Frames
-// that arrive while batches run are admitted into the next batch as lanes and
-// staging slots free up.  All device work is ordered with events: a batch waits
+// lane has room (at most one batch running on it), when max_batch frames are
+// waiting, on flush, or on a waiting poll.  Frames that arrive while both
+// batches of every lane run are admitted together into the next batch as lanes
+// and staging slots free up.  All device work is ordered with events: a batch waits
 // for the copy stream (input uploads, reference pushes); a reference push
 // waits for every lane's last batch.
 #include <stdio.h>
@@ -412,7 +413,8 @@ revo_status launch_batch(revo_ctx* c, int count) {
   return st;
 }
 
-// Launches batches while a lane is idle and frames are waiting.
+// Launches batches while a lane has room (see lane_room) and frames are
+// waiting, or while max_batch are pending, or all of them when forced.
 void dispatch(revo_ctx* c, bool force) {
   while (!c->pending.empty()) {
     bool room = false;
