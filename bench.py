@@ -425,6 +425,39 @@ def attention_roofline(R, torch, stream) -> dict:
                                  "frac": tf(f1, sec1s) / peak if peak else None}}
 
 
+def tensor_roofline(R, torch, stream) -> dict:
+    """The contractions besides attention at the 16-stream tick's sizes, each
+    timed alone on the stream with CUDA events (3 warm-up + 10 launches):
+    fc1 (GELU) and fc2 (residual) over the 70200 RGB rows on CTA pairs, fc1
+    with E4M3 operands, and the tubelet embedding (the Conv3d as an implicit
+    GEMM) over the tick's RGB and depth frames.  Achieved = 2 M N K / launch
+    time; peak = the measured bf16 burst (E4M3: twice it, the nominal ratio)."""
+    peak = peaks().get("bf16_tflops")
+    out = {}
+    for name, fp8 in (("fc1_tick", False), ("fc2_tick", False), ("fc1_fp8_tick", True), ("embed_tick", False),
+                      ("embed_tick_depth", False)):
+        launch, flops, _ = profile_launch(R, torch, name, stream)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                launch()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(10):
+                launch()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / 10
+        pk = (2 * peak if fp8 else peak) if peak else None
+        out[name] = {"us_per_launch": sec * 1e6, "flops_per_launch": flops, "achieved_tflops": flops / sec / 1e12,
+                     "peak_tflops": pk, "frac": flops / sec / 1e12 / pk if pk else None}
+        del launch
+        torch.cuda.empty_cache()
+    assert R.take_device_error() == 0
+    out["peak_source"] = ("MEASURED_PEAKS.json bf16_tflops (burst; kernels timed alone); E4M3: 2x"
+                          if peak else None)
+    return out
+
+
 class StreamIO:
     """One conference stream's buffers: k clean references pushed once, then a
     few corrupted frames (seeded, same size) to recover in turn."""
@@ -882,6 +915,8 @@ def run_ours(args) -> None:
                                           f"{args.seconds:.0f} s, {args.precision}")
         extra["roofline"] = roof
         extra["elementwise"] = elementwise_roofline(R, torch, stream)
+        if precision != R.FP32:
+            extra["tensor"] = tensor_roofline(R, torch, stream)
         if not args.no_cpu_baseline:
             inputs = oracle_sample_inputs()
             secs = [oracle_frame_seconds(inputs) for _ in range(args.oracle_frames)]
@@ -981,38 +1016,20 @@ def run_kt(args) -> None:
                       "config": {"workload": "k/T sweep, 640x480 RGB-D, batch 1"}, "rows": rows}), flush=True)
 
 
-def run_profile_kernel(args) -> None:
-    """Launches one kernel of the step at the bench's shape (for ncu captures):
-    W warm-up + K timed launches on one stream, CUDA-event timed."""
-    import torch
-
-    import paper_2604_27441_b300 as R
+def profile_launch(R, torch, name, stream):
+    """One launch of a kernel of the step at the bench's shape, by name (the
+    --profile-kernel choices except "embed"): returns (launch, flops, bytes);
+    flops is None for the HBM-bound stages."""
     fl = flops_per_model(3, H, W)
     N, D = fl["N"], 768
-    stream = torch.cuda.Stream()
-    if args.profile_kernel == "embed":  # the implicit-GEMM tubelet embedding inside one 640x480 RGB-D request
-        import synth
-        cfg = R.config(**VITB, precision=R.BF16, max_height=480, max_width=640, max_streams=1, max_batch=1,
-                       use_graphs=1, autotune=0)
-        ctx = R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
-                        synth.flatten(synth.weights(synth.DEPTH, seed=1)), stream=stream)
-        sio = StreamIO(R, torch, ctx, 0, "640x480", 4100, 0.2, 1, True)
-        for _ in range(args.warmup):
-            ctx.poll(ctx.submit(sio.reqs[0]))
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            ctx.poll(ctx.submit(sio.reqs[0]))
-        print(json.dumps({"kernel": "embed (whole requests)", "us_per_request": (time.perf_counter() - t0) * 1e6 /
-                          args.steps, "device_error": R.take_device_error()}))
-        ctx.close()
-        return
-    if args.profile_kernel in ("embed_tick", "embed_tick_separate", "embed_tick_depth",
+    nbytes = None
+    if name in ("embed_tick", "embed_tick_separate", "embed_tick_depth",
                                "embed_tick_depth_separate"):
         # The tick's RGB (K = 1536, 70200 tokens) or depth (K = 512, 44280 tokens)
         # tubelet embedding over its 16 requests: the implicit GEMM, or the
         # assemble kernel + the GEMM over the stored tokens.
         import synth
-        rgb = not args.profile_kernel.startswith("embed_tick_depth")
+        rgb = not name.startswith("embed_tick_depth")
         C = 3 if rgb else 1
         Kt = 2 * C * 256
         jobs, taus = [], []
@@ -1030,7 +1047,7 @@ def run_profile_kernel(args) -> None:
         Wt = (torch.randn((D, Kt), device="cuda") / 40).to(torch.bfloat16)
         b = torch.zeros(D, device="cuda")
         out = torch.empty((Mt, D), device="cuda")
-        if not args.profile_kernel.endswith("separate"):
+        if not name.endswith("separate"):
             launch = lambda: R.op_embed_batch(C, 5, 2, jobs, taus, Wt, b, out, D, stream=stream)  # noqa: E731
         else:
             tok = torch.empty((Mt, Kt), dtype=torch.bfloat16, device="cuda")
@@ -1044,14 +1061,14 @@ def run_profile_kernel(args) -> None:
                 R.op_assemble_batch(C, 5, 2, ajobs, 1, stream=stream)
                 R.op_linear(R.BF16, 0, tok, Wt, b, out, Mt, D, Kt, 256 | R.TILE_PAIR, stream=stream)
         flops = 2 * Mt * D * Kt
-    elif args.profile_kernel in ("attention", "attention_split"):
+    elif name in ("attention", "attention_split"):
         qkv = torch.randn((N, 3 * D), device="cuda").to(torch.bfloat16)
         out = torch.empty((N, D), dtype=torch.bfloat16, device="cuda")
-        split = args.profile_kernel == "attention_split"
+        split = name == "attention_split"
         launch = lambda: R.op_attention(R.BF16, qkv, out, N, D, 12, [0, N], stream=stream,  # noqa: E731
                                         split_tail=split)
         flops = fl["attn_enc_per_block"]
-    elif args.profile_kernel == "attention_tick":  # the tick's batched RGB encoder attention
+    elif name == "attention_tick":  # the tick's batched RGB encoder attention
         lens = tick_segments(True)
         seg = np.concatenate([[0], np.cumsum(lens)]).astype(int).tolist()
         M = seg[-1]
@@ -1059,17 +1076,17 @@ def run_profile_kernel(args) -> None:
         out = torch.empty((M, D), dtype=torch.bfloat16, device="cuda")
         launch = lambda: R.op_attention(R.BF16, qkv, out, M, D, 12, seg, stream=stream)  # noqa: E731
         flops = sum(4 * n * n * D for n in lens)
-    elif args.profile_kernel == "pe":  # the position embedding of one 1280x720 request at the encoder width
+    elif name == "pe":  # the position embedding of one 1280x720 request at the encoder width
         S, hp, wp = 3, 45, 80
         x = torch.zeros((S * hp * wp, D), device="cuda")
         launch = lambda: R.op_add_position(x, S, hp, wp, D, [5, 3, 1], stream=stream)  # noqa: E731
         flops, nbytes = None, 2 * x.numel() * 4
-    elif args.profile_kernel in ("assemble", "blend"):  # the HBM-bound stages at 1280x720 RGB, k = 5, T = 2
+    elif name in ("assemble", "blend"):  # the HBM-bound stages at 1280x720 RGB, k = 5, T = 2
         Hh, Ww, k, T, p = 720, 1280, 5, 2, 16
         frames = [torch.randint(0, 256, (Hh, Ww, 3), dtype=torch.uint8, device="cuda") for _ in range(k + 1)]
         P = (Hh // p) * (Ww // p)
         stats = torch.zeros(2, device="cuda")
-        if args.profile_kernel == "assemble":
+        if name == "assemble":
             tokens = torch.empty(((k + 1) // T * P, T * 3 * p * p), dtype=torch.bfloat16, device="cuda")
             launch = lambda: R.op_assemble(3, k, T, p, Hh, Ww, frames[:k], frames[k], Ww * 3, stats,  # noqa: E731
                                            tokens, 1, stream=stream)
@@ -1082,8 +1099,8 @@ def run_profile_kernel(args) -> None:
                                         stats, out, Ww * 3, stream=stream)
             nbytes = head.numel() * 4 + 2 * Hh * Ww * 3 + mask.numel() * 4
         flops = None
-    elif args.profile_kernel in ("fc1_fp8", "fc1_fp8_pair", "fc1_fp8_tick"):  # the same fc1 with E4M3 operands
-        if args.profile_kernel == "fc1_fp8_tick":
+    elif name in ("fc1_fp8", "fc1_fp8_pair", "fc1_fp8_tick"):  # the same fc1 with E4M3 operands
+        if name == "fc1_fp8_tick":
             N = sum(tick_segments(True))
         a = torch.randint(0, 120, (N, D), dtype=torch.uint8, device="cuda")
         w = torch.randint(0, 120, (4 * D, D), dtype=torch.uint8, device="cuda")
@@ -1091,12 +1108,12 @@ def run_profile_kernel(args) -> None:
         sw = torch.full((4 * D,), 0.01, device="cuda")
         b = torch.zeros(4 * D, device="cuda")
         out = torch.empty((N, 4 * D), dtype=torch.bfloat16, device="cuda")
-        tile = 256 | (R.TILE_PAIR if args.profile_kernel != "fc1_fp8" else 0)
+        tile = 256 | (R.TILE_PAIR if name != "fc1_fp8" else 0)
         launch = lambda: R.op_linear_fp8(2, a, sa, w, sw, b, out, N, 4 * D, D, tile, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
-    elif args.profile_kernel in ("fc1_tick", "fc2_tick"):  # the tick's RGB rows (M = 70200), CTA-pair 256 tiles
+    elif name in ("fc1_tick", "fc2_tick"):  # the tick's RGB rows (M = 70200), CTA-pair 256 tiles
         Mt = sum(tick_segments(True))
-        if args.profile_kernel == "fc1_tick":
+        if name == "fc1_tick":
             a = torch.randn((Mt, D), device="cuda").to(torch.bfloat16)
             w = (torch.randn((4 * D, D), device="cuda") / 28).to(torch.bfloat16)
             b = torch.zeros(4 * D, device="cuda")
@@ -1111,12 +1128,12 @@ def run_profile_kernel(args) -> None:
             launch = lambda: R.op_linear(R.BF16, 3, a, w, b, out, Mt, D, 4 * D, 256 | R.TILE_PAIR,  # noqa: E731
                                          stream=stream)
         flops = 2 * Mt * D * 4 * D
-    elif args.profile_kernel in ("fc2", "fc2_pair"):  # fc2 of an encoder block: residual f32 += [N, 3072] x [768, 3072]^T
+    elif name in ("fc2", "fc2_pair"):  # fc2 of an encoder block: residual f32 += [N, 3072] x [768, 3072]^T
         a = torch.randn((N, 4 * D), device="cuda").to(torch.bfloat16)
         w = (torch.randn((D, 4 * D), device="cuda") / 56).to(torch.bfloat16)
         b = torch.zeros(D, device="cuda")
         out = torch.zeros((N, D), device="cuda")
-        tile = 256 | (R.TILE_PAIR if args.profile_kernel == "fc2_pair" else 0)
+        tile = 256 | (R.TILE_PAIR if name == "fc2_pair" else 0)
         launch = lambda: R.op_linear(R.BF16, 3, a, w, b, out, N, D, 4 * D, tile, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
     else:  # fc1 of an encoder block: [N, 768] x [3072, 768]^T + GELU (fc1_pair: 256-row tiles on CTA pairs)
@@ -1124,9 +1141,36 @@ def run_profile_kernel(args) -> None:
         w = (torch.randn((4 * D, D), device="cuda") / 28).to(torch.bfloat16)
         b = torch.zeros(4 * D, device="cuda")
         out = torch.empty((N, 4 * D), dtype=torch.bfloat16, device="cuda")
-        tile = 256 | (R.TILE_PAIR if args.profile_kernel == "fc1_pair" else 0)
+        tile = 256 | (R.TILE_PAIR if name == "fc1_pair" else 0)
         launch = lambda: R.op_linear(R.BF16, 2, a, w, b, out, N, 4 * D, D, tile, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
+    return launch, flops, nbytes
+
+
+def run_profile_kernel(args) -> None:
+    """Launches one kernel of the step at the bench's shape (for ncu captures):
+    W warm-up + K timed launches on one stream, CUDA-event timed."""
+    import torch
+
+    import paper_2604_27441_b300 as R
+    stream = torch.cuda.Stream()
+    if args.profile_kernel == "embed":  # the implicit-GEMM tubelet embedding inside one 640x480 RGB-D request
+        import synth
+        cfg = R.config(**VITB, precision=R.BF16, max_height=480, max_width=640, max_streams=1, max_batch=1,
+                       use_graphs=1, autotune=0)
+        ctx = R.Context(cfg, synth.flatten(synth.weights(synth.RGB, seed=0)),
+                        synth.flatten(synth.weights(synth.DEPTH, seed=1)), stream=stream)
+        sio = StreamIO(R, torch, ctx, 0, "640x480", 4100, 0.2, 1, True)
+        for _ in range(args.warmup):
+            ctx.poll(ctx.submit(sio.reqs[0]))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.poll(ctx.submit(sio.reqs[0]))
+        print(json.dumps({"kernel": "embed (whole requests)", "us_per_request": (time.perf_counter() - t0) * 1e6 /
+                          args.steps, "device_error": R.take_device_error()}))
+        ctx.close()
+        return
+    launch, flops, nbytes = profile_launch(R, torch, args.profile_kernel, stream)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         launch()
