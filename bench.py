@@ -292,9 +292,10 @@ def run_reference(args) -> None:
 def elementwise_roofline(R, torch, stream) -> dict:
     """The HBM-bound stages alone at the largest frame of the workloads (1280x720
     RGB): the fused unpack + normalise + tubelet gather (assemble) and the
-    de-normalise + masked blend.  L2 is flushed (a 256 MB write, then a read of
-    it) before every timed launch; achieved = algorithmic bytes / CUDA-event
-    time."""
+    de-normalise + masked blend; the same two over the tick's 16 RGB planes in
+    one launch each, and the LayerNorm over the tick's RGB rows.  L2 is flushed
+    (a 256 MB write, then a read of it) before every timed launch; achieved =
+    algorithmic bytes / CUDA-event time."""
     Hh, Ww, k, T, p = 720, 1280, 5, 2, 16
     frame = Hh * Ww * 3
     refs = [torch.randint(0, 256, (Hh, Ww, 3), dtype=torch.uint8, device="cuda") for _ in range(k)]
@@ -360,9 +361,16 @@ def elementwise_roofline(R, torch, stream) -> dict:
     out["assemble_rgb_tick_batch16"] = mk(timed(lambda: R.op_assemble_batch(3, k, T, ajobs, 1, stream=stream)),
                                           bytes_ta)
     out["blend_rgb_tick_batch16"] = mk(timed(lambda: R.op_blend_batch(3, bjobs, stream=stream)), bytes_tb)
+    del keep, ajobs, bjobs
+    # The LayerNorm over the tick's RGB rows (x float32 in, h bf16 out), the
+    # standalone launch the forward runs before qkv and fc1.
+    ln, _, bytes_ln = profile_launch(R, torch, "layernorm_tick", stream)
+    out["layernorm_rgb_tick_70200x768"] = mk(timed(ln), bytes_ln)
+    del ln
     out["peak_source"] = "MEASURED_PEAKS.json hbm_gbs" if hbm else None
     out["note"] = ("single frame: one launch for one 1280x720 plane (launch ramp dominates 16.7 MB); "
-                   "tick_batch16: one launch over the 16 requests' RGB planes, as the forward runs them")
+                   "tick_batch16: one launch over the 16 requests' RGB planes, as the forward runs them; "
+                   "layernorm: one launch over the tick's 70200 RGB rows at D = 768")
     return out
 
 
@@ -428,15 +436,20 @@ def attention_roofline(R, torch, stream) -> dict:
 def tensor_roofline(R, torch, stream) -> dict:
     """The contractions besides attention at the 16-stream tick's sizes, each
     timed alone on the stream with CUDA events (3 warm-up + 10 launches):
-    fc1 (GELU) and fc2 (residual) over the 70200 RGB rows on CTA pairs, fc1
-    with E4M3 operands, and the tubelet embedding (the Conv3d as an implicit
-    GEMM) over the tick's RGB and depth frames.  Achieved = 2 M N K / launch
-    time; peak = the measured bf16 burst (E4M3: twice it, the nominal ratio)."""
+    fc1 (GELU), fc2 and proj (residual) over the 70200 RGB rows on CTA pairs,
+    fc1 with E4M3 operands, and the tubelet embedding (the Conv3d as an
+    implicit GEMM) over the tick's RGB and depth frames.  Achieved = 2 M N K /
+    launch time; peak = the measured bf16 burst (E4M3: twice it, the nominal
+    ratio).  For fc1, fc2 and proj also the HBM rate of their algorithmic bytes
+    (operands read once, the output written once; the residual's float32 x
+    read and written) against the measured copy rate: proj (K = 768 into a
+    float32 residual) has more bytes per FLOP than the tensor/HBM balance."""
     peak = peaks().get("bf16_tflops")
+    hbm = peaks().get("hbm_gbs")
     out = {}
-    for name, fp8 in (("fc1_tick", False), ("fc2_tick", False), ("fc1_fp8_tick", True), ("embed_tick", False),
-                      ("embed_tick_depth", False)):
-        launch, flops, _ = profile_launch(R, torch, name, stream)
+    for name, fp8 in (("fc1_tick", False), ("fc2_tick", False), ("proj_tick", False), ("fc1_fp8_tick", True),
+                      ("embed_tick", False), ("embed_tick_depth", False)):
+        launch, flops, nbytes = profile_launch(R, torch, name, stream)
         with torch.cuda.stream(stream):
             for _ in range(3):
                 launch()
@@ -450,11 +463,14 @@ def tensor_roofline(R, torch, stream) -> dict:
         pk = (2 * peak if fp8 else peak) if peak else None
         out[name] = {"us_per_launch": sec * 1e6, "flops_per_launch": flops, "achieved_tflops": flops / sec / 1e12,
                      "peak_tflops": pk, "frac": flops / sec / 1e12 / pk if pk else None}
+        if nbytes:
+            out[name].update(bytes_per_launch=nbytes, achieved_gbs=nbytes / sec / 1e9,
+                             frac_of_measured_hbm=nbytes / sec / 1e9 / hbm if hbm else None)
         del launch
         torch.cuda.empty_cache()
     assert R.take_device_error() == 0
-    out["peak_source"] = ("MEASURED_PEAKS.json bf16_tflops (burst; kernels timed alone); E4M3: 2x"
-                          if peak else None)
+    out["peak_source"] = ("MEASURED_PEAKS.json bf16_tflops (burst; kernels timed alone); E4M3: 2x; "
+                          "hbm_gbs for the byte rates" if peak else None)
     return out
 
 
@@ -1111,7 +1127,9 @@ def profile_launch(R, torch, name, stream):
         tile = 256 | (R.TILE_PAIR if name != "fc1_fp8" else 0)
         launch = lambda: R.op_linear_fp8(2, a, sa, w, sw, b, out, N, 4 * D, D, tile, stream=stream)  # noqa: E731
         flops = 2 * N * D * 4 * D
-    elif name in ("fc1_tick", "fc2_tick"):  # the tick's RGB rows (M = 70200), CTA-pair 256 tiles
+    elif name in ("fc1_tick", "fc2_tick", "proj_tick"):  # the tick's RGB rows (M = 70200), CTA-pair 256 tiles
+        # nbytes: the operands read once and the output written once (the
+        # residual epilogue's float32 x read and written).
         Mt = sum(tick_segments(True))
         if name == "fc1_tick":
             a = torch.randn((Mt, D), device="cuda").to(torch.bfloat16)
@@ -1120,14 +1138,26 @@ def profile_launch(R, torch, name, stream):
             out = torch.empty((Mt, 4 * D), dtype=torch.bfloat16, device="cuda")
             launch = lambda: R.op_linear(R.BF16, 2, a, w, b, out, Mt, 4 * D, D, 256 | R.TILE_PAIR,  # noqa: E731
                                          stream=stream)
+            Kt, Nt, ob = D, 4 * D, 2
         else:
-            a = torch.randn((Mt, 4 * D), device="cuda").to(torch.bfloat16)
-            w = (torch.randn((D, 4 * D), device="cuda") / 56).to(torch.bfloat16)
+            Kt = 4 * D if name == "fc2_tick" else D
+            a = torch.randn((Mt, Kt), device="cuda").to(torch.bfloat16)
+            w = (torch.randn((D, Kt), device="cuda") / (56 if name == "fc2_tick" else 28)).to(torch.bfloat16)
             b = torch.zeros(D, device="cuda")
             out = torch.zeros((Mt, D), device="cuda")
-            launch = lambda: R.op_linear(R.BF16, 3, a, w, b, out, Mt, D, 4 * D, 256 | R.TILE_PAIR,  # noqa: E731
+            launch = lambda: R.op_linear(R.BF16, 3, a, w, b, out, Mt, D, Kt, 256 | R.TILE_PAIR,  # noqa: E731
                                          stream=stream)
-        flops = 2 * Mt * D * 4 * D
+            Nt, ob = D, 8
+        flops = 2 * Mt * Nt * Kt
+        nbytes = Mt * Kt * 2 + Nt * Kt * 2 + Mt * Nt * ob
+    elif name == "layernorm_tick":  # LayerNorm over the tick's RGB rows: x float32 -> h bf16 (the GEMMs' A)
+        Mt = sum(tick_segments(True))
+        x = torch.randn((Mt, D), device="cuda")
+        g = 1 + 0.1 * torch.rand(D, device="cuda")
+        b = 0.02 * torch.rand(D, device="cuda")
+        h = torch.empty((Mt, D), dtype=torch.bfloat16, device="cuda")
+        launch = lambda: R.op_layernorm(x, g, b, h, Mt, D, 1, stream=stream)  # noqa: E731
+        flops, nbytes = None, Mt * D * (4 + 2) + 2 * D * 4
     elif name in ("fc2", "fc2_pair"):  # fc2 of an encoder block: residual f32 += [N, 3072] x [768, 3072]^T
         a = torch.randn((N, 4 * D), device="cuda").to(torch.bfloat16)
         w = (torch.randn((D, 4 * D), device="cuda") / 56).to(torch.bfloat16)
@@ -1192,7 +1222,7 @@ def main():
                                                  "embed_tick_depth_separate", "attention",
                                                  "attention_split", "attention_tick", "fc1", "fc1_pair",
                                                  "fc1_fp8", "fc1_fp8_pair", "fc1_fp8_tick", "fc2", "fc2_pair",
-                                                 "fc1_tick", "fc2_tick",
+                                                 "fc1_tick", "fc2_tick", "proj_tick", "layernorm_tick",
                                                  "assemble", "blend", "pe"],
                     default=None, help="only launch one kernel of the step (for profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
