@@ -31,12 +31,14 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -220,6 +222,54 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class SmClockProbe:
+    """The SM clock read through NVML (the driver's libnvidia-ml, by ctypes)
+    about every millisecond while a short timed region runs (a few ms: too
+    short for nvidia-smi's 200 ms samples).  Reads only; gives no samples
+    where the library cannot be loaded."""
+
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, gpu_index: int):
+        self.gpu, self.samples = gpu_index, []
+        self._stop, self._thread, self._lib = threading.Event(), None, None
+
+    def __enter__(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return self
+            self._lib = lib
+            handle = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(handle)) != 0:
+                return self
+            clk = ctypes.c_uint()
+
+            def poll():
+                while not self._stop.is_set():
+                    if lib.nvmlDeviceGetClockInfo(handle, self.NVML_CLOCK_SM, ctypes.byref(clk)) == 0:
+                        self.samples.append(clk.value)
+                    time.sleep(0.001)
+
+            self._thread = threading.Thread(target=poll, daemon=True)
+            self._thread.start()
+        except OSError:
+            self._thread = None
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._thread is not None:
+            self._thread.join(timeout=1.0)
+        if self._lib is not None:
+            self._lib.nvmlShutdown()
+
+    def summary(self) -> dict:
+        return {"sm_mhz_median": statistics.median(self.samples) if self.samples else None,
+                "samples": len(self.samples), "source": "NVML, ~1 ms"}
+
+
 # ------------------------------------------------------------ oracle arm --
 # One oracle measurement serves both CPU figures (the main arm's cpu_baseline
 # and the --impl reference arm): seconds per 320x240 RGB-D frame of the FP64
@@ -390,7 +440,9 @@ def attention_roofline(R, torch, stream) -> dict:
     requests' token segments (N = 900 x 6, 3600 x 6, 10800 x 4; 12 heads x 64),
     in the form the forward runs (one CTA per unit).  Achieved = 4 N^2 D summed
     over the segments / launch time.  Beside it the same kernel on one 640x480
-    request (N = 3600) and its tail-cut form (REVO_ATTN_SPLIT_TAIL)."""
+    request (N = 3600) and its tail-cut form (REVO_ATTN_SPLIT_TAIL).  `clock`:
+    the SM clock during the timed launches (NVML), so that runs on different
+    boxes can be compared."""
     D, heads = 768, 12
     lens = tick_segments(True)
     seg = np.concatenate([[0], np.cumsum(lens)]).astype(int).tolist()
@@ -398,20 +450,23 @@ def attention_roofline(R, torch, stream) -> dict:
     qkv = torch.randn((M, 3 * D), device="cuda").to(torch.bfloat16)
     out = torch.empty((M, D), dtype=torch.bfloat16, device="cuda")
 
-    def timed(fn, reps):
+    def timed(fn, reps, probe=None):
         with torch.cuda.stream(stream):
             for _ in range(3):
                 fn()
+            torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                fn()
-            e1.record(stream)
-        torch.cuda.synchronize()
+            with probe if probe is not None else contextlib.nullcontext():
+                e0.record(stream)
+                for _ in range(reps):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3 / reps
 
     flops = sum(4 * n * n * D for n in lens)
-    sec = timed(lambda: R.op_attention(R.BF16, qkv, out, M, D, heads, seg, stream=stream), 10)
+    probe = SmClockProbe(torch.cuda.current_device())
+    sec = timed(lambda: R.op_attention(R.BF16, qkv, out, M, D, heads, seg, stream=stream), 10, probe)
     N1 = 3600
     f1 = 4 * N1 * N1 * D
     q1, o1 = qkv[:N1].contiguous(), out[:N1]
@@ -426,7 +481,7 @@ def attention_roofline(R, torch, stream) -> dict:
             "frac": tf(flops, sec) / peak if peak else None, "traffic": ATTN_DRAM_BYTES_PER_LAUNCH,
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)" if peak else None,
-            "flops_per_launch": flops, "us_per_launch": sec * 1e6,
+            "flops_per_launch": flops, "us_per_launch": sec * 1e6, "clock": probe.summary(),
             "n3600_alone": {"us_per_launch": sec1 * 1e6, "achieved": tf(f1, sec1),
                             "frac": tf(f1, sec1) / peak if peak else None},
             "n3600_split_tail": {"us_per_launch": sec1s * 1e6, "achieved": tf(f1, sec1s),
