@@ -895,10 +895,11 @@ def oracle_640_values(plane_pair):
 
 
 def quality(values, ref, plane_pair) -> dict:
-    """Error of one precision's float outputs against the FP64 oracle: PSNR of
-    RGB in [0, 1] units and of depth / 65535, over the whole frame (the gate)
-    and over the lost pixels alone (stricter: the received ones are the
-    decoded values on both sides), max |error| in [0, 1] units and mm."""
+    """Error of one precision's float outputs (the de-normalised network output
+    at every pixel, before the blend) against the FP64 oracle's: PSNR of RGB in
+    [0, 1] units and of depth / 65535 over the whole frame (the gate) and over
+    the lost pixels alone (the ones the blend takes from the network), max
+    |error| in [0, 1] units and mm."""
     er = values[0] - ref[0]
     ed = values[1] - ref[1]
     lost_rgb, lost_dep = plane_pair[0].lost, plane_pair[1].lost
