@@ -3,7 +3,7 @@
  *
  * The library recovers the lost pixels of decoded RGB (uint8) and depth
  * (uint16 mm) video frames, the post-decode recovery step of ReVo's receiver
- * (Section 3.4, "Neural Loss Recovery Module"): a ViViT encoder-decoder reads
+ * (Section 3.4, the neural loss-recovery module): a ViViT encoder-decoder reads
  * the k closest clean frames and the corrupted current frame and outputs a
  * reconstructed frame (Section 3.4.1); RGB and depth use separate models of the
  * same architecture (Section 3.4.2) and run on independent CUDA streams
