@@ -183,6 +183,30 @@ def test_small_network_parity(precision):
     check(precision, got, oracle(SMALL, rgb, dep, "small"), rgb, dep)
 
 
+@pytest.mark.parametrize("pattern", ["none_lost", "all_lost"])
+def test_small_network_degenerate_masks(pattern):
+    """The mask's two degenerate cases through the whole path: nothing lost
+    (every output code is the decoded frame's, bit for bit) and every pixel
+    lost (the decoded frame is all zeros and every code is the network's)."""
+    H, W = 64, 96
+    rows = [] if pattern == "none_lost" else list(range(H))
+    rgb = synth.make_tiny_plane(31, "rgb", H, W, 5, lost_rows=rows)
+    dep = synth.make_tiny_plane(32, "depth", H, W, 5, lost_rows=rows)
+    assert rgb.lost.all() == (pattern == "all_lost") and rgb.lost.any() == (pattern == "all_lost")
+    with make_ctx(SMALL, 1, (H, W)) as ctx:
+        got = run(ctx, 0, rgb, dep)
+    ref = oracle(SMALL, rgb, dep, "small-" + pattern)
+    check(1, got, ref, rgb, dep)
+    if pattern == "none_lost":
+        np.testing.assert_array_equal(got[0], rgb.decoded)
+        np.testing.assert_array_equal(got[1], dep.decoded)
+    else:
+        assert not rgb.decoded.any() and not dep.decoded.any()
+        # The oracle's codes for a fully lost frame are its quantised values.
+        np.testing.assert_array_equal(ref[0][0], O.quantise_rgb(ref[0][1]))
+        np.testing.assert_array_equal(ref[1][0], O.quantise_depth(ref[1][1]))
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_vitb_320x240_parity(precision):
     rgb, dep = synth.make_request(1001, "320x240")
